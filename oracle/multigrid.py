@@ -1,0 +1,215 @@
+"""Block basis, restrictor, prolongator and coarse operator (oracle; test
+infrastructure only).
+
+* Test vectors.  The paper builds its basis from exact low modes of Q
+  (Sec. 3) and states that inexact modes work the same way (Sec. 3, opening
+  paragraphs; Sec. conclusion).  The reading used here: N_v random starts, each
+  relaxed by ``n_smooth`` minimal-residual steps on D v = 0
+  (r = -D v; alpha = <D r, r> / <D r, D r>; v += alpha r; r -= alpha D r).
+* Chirality-split block fields (Eq. mg_basis): u_{alpha c}^{B_y} =
+  P_alpha theta_{B_y} v_c, orthonormalised inside each block and chirality by
+  Gram-Schmidt (modified Gram-Schmidt, two passes, then normalisation; a
+  vector whose remaining norm is <= 1e-12 of its starting norm is rank
+  deficient and raises).
+* R0 (Eq. res_mg): (R psi)_{alpha c}(y) = sum_{x in B_y} phi_{alpha c}^{B_y}(x)^dag psi(x).
+* T0 (Eq. pro_mg): (T psi1)(x) = sum_{alpha c} psi1_{alpha c}(y(x)) phi_{alpha c}^{B_y}(x).
+* Coarse operator D1 = R0 D T0 (Sec. 2 with Q replaced by D, equivalent by
+  App. chirality since [P, gamma5] = 0), stored as the nine-slot stencil of
+  Fig. A: Dhat[d, y] maps X(nbr_d(y)) into Y(y).  Slot d < 8 collects the
+  hopping terms of D that cross the face of B_y in hop direction d (the
+  neighbour block may be y itself when L_mu / b_mu = 1, and the +mu and -mu
+  neighbours coincide when L_mu / b_mu = 2; slots stay separate and are summed
+  on application); slot 8 collects the clover term and every hop that stays
+  inside B_y.
+
+Arrays: the basis is phi[y, alpha, c, k, spin, colour] over the |B| sites k of
+block y (site-in-block order) with the spins of the other chirality zero;
+coarse fields are (V1, 2 N_v) with dof index alpha*N_v + c; a coarse batch
+puts the RHS axis first.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import dirac as _d
+from . import lattice as _lat
+
+
+class RankError(ValueError):
+    """Raised when a block basis vector is linearly dependent on earlier ones."""
+
+
+def inner(a: np.ndarray, b: np.ndarray) -> complex:
+    return complex(np.vdot(a.reshape(-1), b.reshape(-1)))
+
+
+def mr_smooth(U, v, kappa, csw, n_smooth, bc_t=-1.0, A=None) -> np.ndarray:
+    """n_smooth minimal-residual steps on D v = 0 for one field."""
+    if A is None:
+        A = _d.clover_matrix(U, kappa, csw)
+    v = v.copy()
+    r = -_d.dirac(U, v, kappa, csw, bc_t, A)
+    for _ in range(n_smooth):
+        w = _d.dirac(U, r, kappa, csw, bc_t, A)
+        alpha = inner(w, r) / inner(w, w).real
+        v += alpha * r
+        r -= alpha * w
+    return v
+
+
+def block_gram_schmidt(u: np.ndarray) -> np.ndarray:
+    """Orthonormalise the rows u[c] (vectors) in order c = 0, 1, ...:
+    two passes of modified Gram-Schmidt against the finished phi_j, j < c,
+    then normalisation."""
+    n = u.shape[0]
+    phi = np.zeros_like(u)
+    for c in range(n):
+        w = u[c].copy()
+        start = np.linalg.norm(w)
+        for _ in range(2):
+            for j in range(c):
+                w -= np.vdot(phi[j], w) * phi[j]
+        nrm = np.linalg.norm(w)
+        if not nrm > 1e-12 * start:
+            raise RankError(f"basis vector {c} is rank deficient ({nrm:.3e} of {start:.3e})")
+        phi[c] = w / nrm
+    return phi
+
+
+def build_basis(vecs: np.ndarray, L, b) -> np.ndarray:
+    """phi[y, alpha, c, k, s, a] from test vectors vecs (Nv, L..., 4, 3):
+    P_alpha theta_{B_y} v_c, then Gram-Schmidt per (block, chirality)."""
+    nv = vecs.shape[0]
+    sites = _lat.block_sites(L, b)  # (V1, nB)
+    V1, nB = sites.shape
+    flat = vecs.reshape(nv, -1, 4, 3)
+    phi = np.zeros((V1, 2, nv, nB, 4, 3), dtype=np.complex128)
+    for alpha in range(2):
+        P = _d.chiral_projector(alpha)
+        proj = np.einsum("st,nvtc->nvsc", P, flat)
+        for y in range(V1):
+            u = proj[:, sites[y]]  # (nv, nB, 4, 3)
+            phi[y, alpha] = block_gram_schmidt(u.reshape(nv, -1)).reshape(nv, nB, 4, 3)
+    return phi
+
+
+def subspace(U, starts, kappa, csw, b, n_smooth, bc_t=-1.0) -> np.ndarray:
+    """Test vectors from random starts (smoothing) then the block basis."""
+    A = _d.clover_matrix(U, kappa, csw)
+    vecs = np.stack([mr_smooth(U, s, kappa, csw, n_smooth, bc_t, A) for s in starts])
+    return build_basis(vecs, U.shape[:4], b)
+
+
+def restrict(phi: np.ndarray, psi: np.ndarray, L, b) -> np.ndarray:
+    """R0 psi (Eq. res_mg) for one field -> (V1, 2 Nv), or a batch."""
+    if psi.ndim == 7:
+        return np.stack([restrict(phi, p, L, b) for p in psi])
+    sites = _lat.block_sites(L, b)
+    V1, _, nv = phi.shape[:3]
+    loc = psi.reshape(-1, 4, 3)[sites]  # (V1, nB, 4, 3)
+    out = np.einsum("yacksi,yksi->yac", np.conj(phi), loc)
+    return out.reshape(V1, 2 * nv)
+
+
+def prolong(phi: np.ndarray, psi1: np.ndarray, L, b) -> np.ndarray:
+    """T0 psi1 (Eq. pro_mg) for one coarse field (V1, 2 Nv) -> fine field."""
+    if psi1.ndim == 3:
+        return np.stack([prolong(phi, p, L, b) for p in psi1])
+    L = tuple(int(v) for v in L)
+    sites = _lat.block_sites(L, b)
+    V1, _, nv = phi.shape[:3]
+    c1 = psi1.reshape(V1, 2, nv)
+    loc = np.einsum("yac,yacksi->yksi", c1, phi)
+    out = np.zeros((_lat.volume(L), 4, 3), dtype=np.complex128)
+    out[sites] = loc
+    return out.reshape(L + (4, 3))
+
+
+def _crossing_mask(L, b, d: int) -> np.ndarray:
+    """True at the sites whose hop in slot d leaves their block."""
+    x = _lat.coords(L)
+    mu = d % 4
+    r = x[:, mu] % int(b[mu])
+    if d < 4:
+        m = r == int(b[mu]) - 1
+    else:
+        m = r == 0
+    return m.reshape(tuple(int(v) for v in L))
+
+
+def coarse_operator(U, phi, kappa, csw, b, bc_t=-1.0) -> np.ndarray:
+    """Dhat[d, y, i, j], d = 0..8, as described in the module docstring:
+    column j = (beta, c') is the restriction of D applied to T e_j split by
+    hop slot."""
+    L = tuple(int(v) for v in U.shape[:4])
+    V1, _, nv = phi.shape[:3]
+    n = 2 * nv
+    A = _d.clover_matrix(U, kappa, csw)
+    masks = [_crossing_mask(L, b, d)[..., None, None] for d in range(8)]
+    Dhat = np.zeros((9, V1, n, n), dtype=np.complex128)
+    for j in range(n):
+        e = np.zeros((V1, n), dtype=np.complex128)
+        e[:, j] = 1.0
+        Phi = prolong(phi, e, L, b)  # phi_j on every block
+        inside = _d.apply_clover(A, Phi)
+        for d in range(8):
+            h = _d.hop(U, Phi, d, bc_t)
+            Dhat[d, :, :, j] = restrict(phi, np.where(masks[d], h, 0), L, b)
+            inside += np.where(masks[d], 0, h)
+        Dhat[8, :, :, j] = restrict(phi, inside, L, b)
+    return Dhat
+
+
+def coarse_apply(Dhat: np.ndarray, X: np.ndarray, Lb) -> np.ndarray:
+    """Y(y) = sum_{d=0}^{8} Dhat[d, y] X(nbr_d(y)) for (V1, n) or a batch."""
+    if X.ndim == 3:
+        return np.stack([coarse_apply(Dhat, x, Lb) for x in X])
+    nbr = _lat.coarse_neighbour_table(Lb)
+    Y = np.zeros_like(X)
+    for d in range(9):
+        Y += np.einsum("yij,yj->yi", Dhat[d], X[nbr[:, d]])
+    return Y
+
+
+def coarse_apply_dagger(Dhat: np.ndarray, X: np.ndarray, Lb) -> np.ndarray:
+    """The adjoint of ``coarse_apply``: Y(y') = sum_{d, y : nbr_d(y) = y'}
+    Dhat[d, y]^dag X(y)."""
+    if X.ndim == 3:
+        return np.stack([coarse_apply_dagger(Dhat, x, Lb) for x in X])
+    nbr = _lat.coarse_neighbour_table(Lb)
+    Y = np.zeros_like(X)
+    for d in range(9):
+        contrib = np.einsum("yji,yj->yi", np.conj(Dhat[d]), X)
+        np.add.at(Y, nbr[:, d], contrib)
+    return Y
+
+
+def coarse_gamma5(nv: int) -> np.ndarray:
+    """gamma5 on a coarse site: +1 on alpha = 0 dofs, -1 on alpha = 1."""
+    return np.concatenate([np.ones(nv), -np.ones(nv)])
+
+
+def dense_coarse(Dhat: np.ndarray, Lb) -> np.ndarray:
+    """The dense (V1 n x V1 n) matrix of the stencil (slots that land on the
+    same block pair are summed)."""
+    nbr = _lat.coarse_neighbour_table(Lb)
+    V1, n = Dhat.shape[1], Dhat.shape[2]
+    M = np.zeros((V1 * n, V1 * n), dtype=np.complex128)
+    for d in range(9):
+        for y in range(V1):
+            z = nbr[y, d]
+            M[y * n:(y + 1) * n, z * n:(z + 1) * n] += Dhat[d, y]
+    return M
+
+
+def dense_prolongator(phi: np.ndarray, L, b) -> np.ndarray:
+    """The (12V x V1 n) matrix of T0, column j = T e_j."""
+    L = tuple(int(v) for v in L)
+    V1, _, nv = phi.shape[:3]
+    n = 2 * nv
+    cols = []
+    for j in range(V1 * n):
+        e = np.zeros(V1 * n, dtype=np.complex128)
+        e[j] = 1
+        cols.append(prolong(phi, e.reshape(V1, n), L, b).reshape(-1))
+    return np.stack(cols, axis=1)

@@ -1,0 +1,82 @@
+"""Krylov solves and propagator pieces (oracle; test infrastructure only).
+
+* The propagator S = D^-1 is unique, so ``cgne`` -- the conjugate-gradient
+  method (Hestenes-Stiefel) on the normal equations D^dag D x = D^dag b, the
+  plain method -- is only a way to reach it; it stops when the recursively
+  updated residual of D x = b satisfies ||r|| / ||b|| <= tol.
+* Sec. 2: S = S0 + S1 with S1 = T Q1^-1 R gamma5, Q1 = R Q T, Q = gamma5 D;
+  App. chirality: with [P, gamma5] = 0 this equals T D1^-1 R with
+  D1 = R D T.  ``pieces`` returns psi = S eta, psi1 = T D1^-1 R eta and
+  psi0 = psi - psi1.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import dirac as _d
+from . import multigrid as _mg
+
+
+def _vdot(a, b):
+    return complex(np.vdot(a.reshape(-1), b.reshape(-1)))
+
+
+def _norm2(a):
+    return float(np.vdot(a.reshape(-1), a.reshape(-1)).real)
+
+
+def cgne(apply, apply_dag, b, tol=1e-11, maxiter=100000, x0=None):
+    """CG on D^dag D x = D^dag b.  Returns (x, iterations, final ||r||/||b||)."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - apply(x) if x0 is not None else b.copy()
+    bn = np.sqrt(_norm2(b))
+    if bn == 0:
+        return x, 0, 0.0
+    z = apply_dag(r)
+    p = z.copy()
+    zz = _norm2(z)
+    it = 0
+    while np.sqrt(_norm2(r)) / bn > tol and it < maxiter:
+        w = apply(p)
+        a = zz / _norm2(w)
+        x += a * p
+        r -= a * w
+        z = apply_dag(r)
+        zz_new = _norm2(z)
+        p = z + (zz_new / zz) * p
+        zz = zz_new
+        it += 1
+    return x, it, np.sqrt(_norm2(r)) / bn
+
+
+def solve_fine(U, b, kappa, csw, bc_t=-1.0, tol=1e-11, maxiter=100000, A=None):
+    """x = D^-1 b for one field by ``cgne``."""
+    if A is None:
+        A = _d.clover_matrix(U, kappa, csw)
+    f = lambda v: _d.dirac(U, v, kappa, csw, bc_t, A)  # noqa: E731
+    g = lambda v: _d.dirac_dagger(U, v, kappa, csw, bc_t, A)  # noqa: E731
+    return cgne(f, g, b, tol, maxiter)
+
+
+def solve_coarse(Dhat, b1, Lb, tol=1e-12, maxiter=100000):
+    """X = D1^-1 b1 for one coarse field by ``cgne``."""
+    f = lambda v: _mg.coarse_apply(Dhat, v, Lb)  # noqa: E731
+    g = lambda v: _mg.coarse_apply_dagger(Dhat, v, Lb)  # noqa: E731
+    return cgne(f, g, b1, tol, maxiter)
+
+
+def true_residual(U, x, b, kappa, csw, bc_t=-1.0, A=None) -> float:
+    """||b - D x|| / ||b|| in FP64."""
+    r = b - _d.dirac(U, x, kappa, csw, bc_t, A)
+    return float(np.sqrt(_norm2(r) / _norm2(b)))
+
+
+def pieces(U, phi, Dhat, eta, kappa, csw, b, bc_t=-1.0, tol=1e-11):
+    """(psi, psi1, psi0) for one source eta: psi = D^-1 eta,
+    psi1 = T D1^-1 R eta, psi0 = psi - psi1."""
+    L = U.shape[:4]
+    Lb = tuple(int(L[m]) // int(b[m]) for m in range(4))
+    psi, _, _ = solve_fine(U, eta, kappa, csw, bc_t, tol)
+    X, _, _ = solve_coarse(Dhat, _mg.restrict(phi, eta, L, b), Lb, tol * 0.1)
+    psi1 = _mg.prolong(phi, X, L, b)
+    return psi, psi1, psi - psi1
