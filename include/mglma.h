@@ -1,0 +1,129 @@
+/* mglma -- GB300 (sm_103a) hot path of multigrid low-mode averaging.
+ *
+ * C ABI of libmglma.so.  The operations follow arXiv:2412.06347 (Gruber,
+ * Harris, Krstic Marinkovic, "Multigrid low-mode averaging"); each entry
+ * point names the passage that defines what it computes.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice: x = (x0, x1, x2, x3), x0 is time, extents L[0..3]; the canonical
+ *   site index is ((x0*L1 + x1)*L2 + x2)*L3 + x3; V = L0 L1 L2 L3.
+ * Canonical spinor batch: complex128, interleaved (re, im), index order
+ *   [rhs][site][spin 4][colour 3]; 24 doubles per site per RHS.
+ * Canonical links: complex128 [site][mu 4][row 3][col 3]; U_mu(x) sits on the
+ *   link x -> x + mu.  Links are periodic.
+ * Gamma matrices: chiral basis, gamma5 = diag(1, 1, -1, -1); chirality
+ *   alpha = 0 is spins {0, 1}, alpha = 1 is spins {2, 3}.
+ * Dirac operator (the paper uses O(a)-improved Wilson fermions, Tab.
+ *   ensembles, without printing D):
+ *     D psi(x) = A(x) psi(x) - 1/2 sum_mu [(1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                                         + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)]
+ *     A(x) = 4 + m0 + c_sw (i/4) sum_{mu nu} sigma_{mu nu} Fhat_{mu nu}(x),
+ *     m0 = 1/(2 kappa) - 4, Fhat from the four clover leaves; a fermion hop
+ *     across the time boundary is multiplied by t_bc.  This is D itself, not
+ *     2 kappa D.
+ * Blocks (Sec. 3, Eqs. block_decomp, block_def): sides b[mu] dividing L[mu];
+ *   block y_mu = x_mu / b_mu, block index and site-in-block index
+ *   lexicographic like the site index.
+ * Coarse fields: complex128 [rhs][coarse site][2 Nv], dof alpha*Nv + c.
+ * Coarse operator export: complex128 [9 slots][V1][2Nv][2Nv]; slot d < 4 is
+ *   the +mu neighbour, 4..7 the -mu neighbour, 8 the block itself.
+ *
+ * Pointers: every double* argument may be host memory (pageable or pinned)
+ *   or device memory of the context's device; the library detects which.
+ *   Host inputs are copied in and host outputs copied out before the call
+ *   returns.  Device buffers are read/written in stream order on the given
+ *   stream (NULL = the context's own stream) and must stay valid until that
+ *   stream reaches the call's work.  The caller owns all buffers it passes;
+ *   the library owns every handle until the matching *_free.
+ * Errors: every call returns an mglma_status; nothing throws across the ABI.
+ *   mglma_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef MGLMA_H
+#define MGLMA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mglma_ctx_s* mglma_ctx;
+typedef struct mglma_gauge_s* mglma_gauge;
+typedef struct mglma_subspace_s* mglma_subspace;
+typedef struct mglma_coarse_s* mglma_coarse;
+
+typedef enum {
+  MGLMA_OK = 0,
+  MGLMA_ERR_INVALID = 1,       /* bad argument (sizes, NULL, blocking)          */
+  MGLMA_ERR_OOM = 2,           /* device allocation failed                      */
+  MGLMA_ERR_CUDA = 3,          /* a CUDA runtime call failed                    */
+  MGLMA_ERR_RANK = 4,          /* a block basis vector is linearly dependent    */
+  MGLMA_ERR_NOT_CONVERGED = 5, /* iteration cap reached; best iterate returned  */
+  MGLMA_ERR_NUMERIC = 6,       /* non-finite value met                          */
+  MGLMA_ERR_TIMEOUT = 7,       /* a bounded device wait gave up                 */
+  MGLMA_ERR_REJECTED = 8       /* admission refused (serving)                   */
+} mglma_status;
+
+typedef enum { MGLMA_FP64 = 0, MGLMA_FP32 = 1, MGLMA_BF16 = 2, MGLMA_FP16 = 3 } mglma_prec;
+
+typedef enum {
+  MGLMA_OP_D = 0,     /* D                 */
+  MGLMA_OP_DDAG = 1,  /* D^dag = g5 D g5   */
+  MGLMA_OP_Q = 2,     /* Q = gamma5 D (Sec. 2) */
+  MGLMA_OP_DDAGD = 3  /* D^dag D           */
+} mglma_op;
+
+typedef struct {
+  int L[4];
+  int t_bc; /* -1 antiperiodic (default), +1 periodic */
+} mglma_lattice;
+
+/* ---------------------------------------------------------------- context */
+/* Creates a context on CUDA device `device` (own stream and memory pool). */
+mglma_status mglma_create(int device, mglma_ctx* out);
+void mglma_destroy(mglma_ctx ctx);
+const char* mglma_last_error(void);
+/* Library version string. */
+const char* mglma_version(void);
+
+/* Per-kernel timing with CUDA events on the launching stream (off by
+ * default).  enable = 1 starts collecting, 0 stops; reset clears. */
+mglma_status mglma_profile(mglma_ctx ctx, int enable, int reset);
+/* Fetches the accumulated launches and milliseconds of kernel class `name`
+ * ("dslash64", "dslash32", "blas", "reduce", "restrict", "prolong",
+ * "coarse", "pack", "setup").  Synchronises the context stream. */
+mglma_status mglma_profile_get(mglma_ctx ctx, const char* name, long long* launches, double* ms);
+
+/* ---------------------------------------------------------------- gauge field */
+/* Loads links and builds everything the operator needs: reconstruct-12 FP32
+ * and full FP64 copies of U, the clover term A(x) with the mass folded in,
+ * both chirality blocks (O(a)-improved Wilson-clover action, Tab. ensembles).
+ * links: canonical complex128 links of time slices t_begin .. t_begin +
+ *   t_count - 1 (host or device).  Pass *inout = NULL on the first slab; the
+ *   handle is created and returned.  The clover term is built when the last
+ *   missing time slice arrives; only then can the handle be used.
+ * Links must be SU(3) to 1e-10 (rows orthonormal, det 1): reconstruct-12
+ *   relies on it; larger deviations give MGLMA_ERR_INVALID. */
+mglma_status mglma_gauge_load(mglma_ctx ctx, const mglma_lattice* lat, const double* links, int64_t t_begin,
+                              int64_t t_count, double kappa, double csw, mglma_gauge* inout);
+void mglma_gauge_free(mglma_gauge g);
+/* Lattice extents and V of a gauge handle. */
+mglma_status mglma_gauge_info(mglma_gauge g, int L[4], int64_t* volume);
+
+/* Applies op to nrhs canonical spinors: out = op(in).  compute selects the
+ * arithmetic: MGLMA_FP64 (FP64 links and clover) or MGLMA_FP32 (FP32
+ * reconstruct-12 links, FP32 clover, inputs rounded to FP32).  The definition
+ * of D is the one stated at the top of this header (Sec. 2: Q = gamma5 D). */
+mglma_status mglma_dirac_apply(mglma_ctx ctx, mglma_gauge g, mglma_op op, int nrhs, const double* in, double* out,
+                               mglma_prec compute, void* cuda_stream);
+
+/* Debug export of the integer tables the kernels compute on the fly:
+ * nbr[V][8] (hop slots +0..+3, -0..-3) and block_of_site[V] for the given
+ * block sides (block may be NULL to skip it).  Host pointers. */
+mglma_status mglma_debug_tables(mglma_gauge g, const int block[4], int32_t* nbr, int32_t* block_of_site);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGLMA_H */

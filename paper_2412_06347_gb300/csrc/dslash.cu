@@ -1,0 +1,743 @@
+// Wilson-clover operator on GB300: layout conversion, gauge packing with an
+// SU(3) check, clover construction, and the multi-RHS stencil.
+//
+// The operator (O(a)-improved Wilson fermions of Tab. ensembles; Q = gamma5 D
+// of Sec. 2):
+//   D psi(x) = A(x) psi(x) - 1/2 sum_mu [(1 - gamma_mu) U_mu(x) psi(x+mu)
+//                                      + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)]
+// in the chiral basis gamma_mu = [[0, e_mu], [e_mu^dag, 0]] with e_0 = -1,
+// e_k = -i sigma_k.  (1 + s gamma_mu) psi for s = +-1 has upper half
+// h = u + s e_mu l and lower half s e_mu^dag h (u, l: spins {0,1}, {2,3}), so
+// each hop moves one two-spin half spinor through the link (spin projection).
+//
+// Stencil kernel design: one thread per site and NR right-hand sides held in
+// registers, so each link and clover entry is read once for NR spinors; the
+// spinor layout [rhs][chunk][site] makes every 16-byte load of a warp
+// coalesced; neighbours are found arithmetically (no halo, no tables); links
+// are stored reconstruct-12 in FP32 with the third row rebuilt in registers.
+#include "internal.h"
+#include "cplx.cuh"
+#include "lattice.cuh"
+
+namespace mglma {
+
+// ------------------------------------------------------------ spinor IO
+template <typename R>
+struct IO;
+
+template <>
+struct IO<float> {
+  __device__ __forceinline__ static void load(const void* base, int64_t V, int rhs, int64_t site, Cx<float> s[12]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + (size_t)rhs * 6 * V + site;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      float4 v = __ldg(p + j * V);
+      s[2 * j] = cx(v.x, v.y);
+      s[2 * j + 1] = cx(v.z, v.w);
+    }
+  }
+  __device__ __forceinline__ static void store(void* base, int64_t V, int rhs, int64_t site, const Cx<float> s[12]) {
+    float4* p = reinterpret_cast<float4*>(base) + (size_t)rhs * 6 * V + site;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) p[j * V] = make_float4(s[2 * j].re, s[2 * j].im, s[2 * j + 1].re, s[2 * j + 1].im);
+  }
+};
+
+template <>
+struct IO<double> {
+  __device__ __forceinline__ static void load(const void* base, int64_t V, int rhs, int64_t site, Cx<double> s[12]) {
+    const double2* p = reinterpret_cast<const double2*>(base) + (size_t)rhs * 12 * V + site;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      double2 v = __ldg(p + j * V);
+      s[j] = cx(v.x, v.y);
+    }
+  }
+  __device__ __forceinline__ static void store(void* base, int64_t V, int rhs, int64_t site, const Cx<double> s[12]) {
+    double2* p = reinterpret_cast<double2*>(base) + (size_t)rhs * 12 * V + site;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) p[j * V] = make_double2(s[j].re, s[j].im);
+  }
+};
+
+// ------------------------------------------------------------ links
+template <typename R>
+struct Link;
+
+template <>
+struct Link<float> {  // reconstruct-12
+  __device__ __forceinline__ static void load(const void* U, int64_t V, int mu, int64_t site, M3<float>& m) {
+    const float4* p = reinterpret_cast<const float4*>(U) + (size_t)mu * 3 * V + site;
+    float4 a = __ldg(p), b = __ldg(p + V), c = __ldg(p + 2 * V);
+    m.e[0][0] = cx(a.x, a.y);
+    m.e[0][1] = cx(a.z, a.w);
+    m.e[0][2] = cx(b.x, b.y);
+    m.e[1][0] = cx(b.z, b.w);
+    m.e[1][1] = cx(c.x, c.y);
+    m.e[1][2] = cx(c.z, c.w);
+    // row2 = conj(row0 x row1)
+    m.e[2][0] = conj(m.e[0][1] * m.e[1][2] - m.e[0][2] * m.e[1][1]);
+    m.e[2][1] = conj(m.e[0][2] * m.e[1][0] - m.e[0][0] * m.e[1][2]);
+    m.e[2][2] = conj(m.e[0][0] * m.e[1][1] - m.e[0][1] * m.e[1][0]);
+  }
+};
+
+template <>
+struct Link<double> {  // full 18 reals
+  __device__ __forceinline__ static void load(const void* U, int64_t V, int mu, int64_t site, M3<double>& m) {
+    const double2* p = reinterpret_cast<const double2*>(U) + (size_t)mu * 9 * V + site;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double2 v = __ldg(p + k * V);
+      m.e[k / 3][k % 3] = cx(v.x, v.y);
+    }
+  }
+};
+
+// ------------------------------------------------------------ clover blocks
+// packed Hermitian 6x6: 6 real diagonals, then 15 (re, im) upper entries
+__device__ __forceinline__ int offdiag_slot(int i, int j) {  // i < j
+  // row-major position of (i, j) among the 15 upper entries
+  return i * 5 - (i * (i - 1)) / 2 + (j - i - 1);
+}
+
+template <typename R>
+struct Clover;
+
+template <>
+struct Clover<float> {
+  __device__ __forceinline__ static void load(const void* C, int64_t V, int chi, int64_t site, float c[36]) {
+    const float4* p = reinterpret_cast<const float4*>(C) + (size_t)chi * 9 * V + site;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      float4 v = __ldg(p + j * V);
+      c[4 * j] = v.x;
+      c[4 * j + 1] = v.y;
+      c[4 * j + 2] = v.z;
+      c[4 * j + 3] = v.w;
+    }
+  }
+};
+template <>
+struct Clover<double> {
+  __device__ __forceinline__ static void load(const void* C, int64_t V, int chi, int64_t site, double c[36]) {
+    const double2* p = reinterpret_cast<const double2*>(C) + (size_t)chi * 18 * V + site;
+#pragma unroll
+    for (int j = 0; j < 18; ++j) {
+      double2 v = __ldg(p + j * V);
+      c[2 * j] = v.x;
+      c[2 * j + 1] = v.y;
+    }
+  }
+};
+
+// out[i] (+)= sum_j A_ij in[j] for one packed Hermitian 6x6 block
+template <typename R>
+__device__ __forceinline__ void clover_apply6(const R c[36], const Cx<R>* in, Cx<R>* out) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    Cx<R> s = c[i] * in[i];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (j == i) continue;
+      if (i < j) {
+        int k = 6 + 2 * offdiag_slot(i, j);
+        cfma(s, cx(c[k], c[k + 1]), in[j]);
+      } else {
+        int k = 6 + 2 * offdiag_slot(j, i);
+        cfma_conj(s, cx(c[k], c[k + 1]), in[j]);
+      }
+    }
+    out[i] = s;
+  }
+}
+
+// ------------------------------------------------------------ spin projection
+// i sigma_k applied to a two-spin half spinor (a, b), per colour
+template <typename R>
+__device__ __forceinline__ void isigma(int k, const Cx<R> a[3], const Cx<R> b[3], Cx<R> o0[3], Cx<R> o1[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (k == 1) {
+      o0[c] = mul_i(b[c]);
+      o1[c] = mul_i(a[c]);
+    } else if (k == 2) {
+      o0[c] = b[c];
+      o1[c] = -a[c];
+    } else {
+      o0[c] = mul_i(a[c]);
+      o1[c] = -mul_i(b[c]);
+    }
+  }
+}
+
+// h = upper half of (1 + s gamma_mu) psi;  psi[spin*3 + colour]
+template <typename R>
+__device__ __forceinline__ void project(int mu, R s, const Cx<R> psi[12], Cx<R> h0[3], Cx<R> h1[3]) {
+  if (mu == 0) {  // e_0 = -1: h = u - s l
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      h0[c] = psi[c] - s * psi[6 + c];
+      h1[c] = psi[3 + c] - s * psi[9 + c];
+    }
+  } else {  // e_k = -i sigma_k: h = u - s (i sigma_k) l
+    Cx<R> t0[3], t1[3];
+    isigma<R>(mu, psi + 6, psi + 9, t0, t1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      h0[c] = psi[c] - s * t0[c];
+      h1[c] = psi[3 + c] - s * t1[c];
+    }
+  }
+}
+
+// acc += (h, s e_mu^dag h)
+template <typename R>
+__device__ __forceinline__ void reconstruct_add(int mu, R s, const Cx<R> h0[3], const Cx<R> h1[3], Cx<R> acc[12]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c] = acc[c] + h0[c];
+    acc[3 + c] = acc[3 + c] + h1[c];
+  }
+  if (mu == 0) {  // e_0^dag = -1
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[6 + c] = acc[6 + c] - s * h0[c];
+      acc[9 + c] = acc[9 + c] - s * h1[c];
+    }
+  } else {  // e_k^dag = i sigma_k
+    Cx<R> t0[3], t1[3];
+    isigma<R>(mu, h0, h1, t0, t1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[6 + c] = acc[6 + c] + s * t0[c];
+      acc[9 + c] = acc[9 + c] + s * t1[c];
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void mat_vec(const M3<R>& U, const Cx<R> h[3], Cx<R> o[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Cx<R> s = cx<R>(0, 0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) cfma(s, U.e[a][b], h[b]);
+    o[a] = s;
+  }
+}
+template <typename R>
+__device__ __forceinline__ void mat_dag_vec(const M3<R>& U, const Cx<R> h[3], Cx<R> o[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Cx<R> s = cx<R>(0, 0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) cfma_conj(s, U.e[b][a], h[b]);
+    o[a] = s;
+  }
+}
+
+// one hop term: acc += f * (1 + s gamma_mu) W psi, W = U (fwd) or U^dag (bwd)
+template <typename R, bool FWD>
+__device__ __forceinline__ void hop_add(int mu, R s, R f, const M3<R>& U, const Cx<R> psi[12], Cx<R> acc[12]) {
+  Cx<R> h0[3], h1[3], g0[3], g1[3];
+  project<R>(mu, s, psi, h0, h1);
+  if (FWD) {
+    mat_vec<R>(U, h0, g0);
+    mat_vec<R>(U, h1, g1);
+  } else {
+    mat_dag_vec<R>(U, h0, g0);
+    mat_dag_vec<R>(U, h1, g1);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    g0[c] = f * g0[c];
+    g1[c] = f * g1[c];
+  }
+  reconstruct_add<R>(mu, s, g0, g1, acc);
+}
+
+struct DslashArgs {
+  LatIdx q;
+  double bc;
+  int nrhs;
+  int g5out;
+};
+
+// out = op(in) for NR right-hand sides per thread.  DAG selects D^dag
+// (projectors 1 +- gamma swap); g5out multiplies the result by gamma5.
+template <typename R, int NR, bool DAG>
+__global__ void __launch_bounds__(128) dslash_kernel(const void* __restrict__ in, void* __restrict__ out,
+                                                     const void* __restrict__ U, const void* __restrict__ C,
+                                                     DslashArgs a) {
+  const int64_t V = a.q.V;
+  const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (site >= V) return;
+  const int r0 = blockIdx.y * NR;
+  int x[4];
+  site_coords(a.q, site, x);
+  const R sF = DAG ? R(1) : R(-1);  // forward hop carries (1 + sF gamma)
+  const R sB = -sF;
+
+  Cx<R> acc[NR][12];
+  // clover term
+  {
+    Cx<R> psi[12];
+    R c[36];
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+      Clover<R>::load(C, V, chi, site, c);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r0 + r < a.nrhs) {
+          IO<R>::load(in, V, r0 + r, site, psi);
+          clover_apply6<R>(c, psi + 6 * chi, acc[r] + 6 * chi);
+        }
+      }
+    }
+  }
+  // hopping terms
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    M3<R> Um;
+    Cx<R> psi[12];
+    {
+      const int64_t nf = nbr_fwd(a.q, site, x, mu);
+      const R f = R(-0.5) * ((mu == 0 && x[0] == a.q.L[0] - 1) ? R(a.bc) : R(1));
+      Link<R>::load(U, V, mu, site, Um);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r0 + r < a.nrhs) {
+          IO<R>::load(in, V, r0 + r, nf, psi);
+          hop_add<R, true>(mu, sF, f, Um, psi, acc[r]);
+        }
+    }
+    {
+      const int64_t nb = nbr_bwd(a.q, site, x, mu);
+      const R f = R(-0.5) * ((mu == 0 && x[0] == 0) ? R(a.bc) : R(1));
+      Link<R>::load(U, V, mu, nb, Um);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r0 + r < a.nrhs) {
+          IO<R>::load(in, V, r0 + r, nb, psi);
+          hop_add<R, false>(mu, sB, f, Um, psi, acc[r]);
+        }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+    if (r0 + r < a.nrhs) {
+      if (a.g5out) {
+#pragma unroll
+        for (int k = 6; k < 12; ++k) acc[r][k] = -acc[r][k];
+      }
+      IO<R>::store(out, V, r0 + r, site, acc[r]);
+    }
+}
+
+// ------------------------------------------------------------ hop-slot pieces (FP64, setup)
+struct SlotArgs {
+  LatIdx q;
+  double bc;
+  int b[4];
+  int slot;
+};
+
+__device__ __forceinline__ bool crosses(const int x[4], const int b[4], int d) {
+  const int mu = d & 3;
+  const int r = x[mu] % b[mu];
+  return d < 4 ? (r == b[mu] - 1) : (r == 0);
+}
+
+__global__ void __launch_bounds__(128) dslash_slot_kernel(const double2* __restrict__ in, double2* __restrict__ out,
+                                                          const double2* __restrict__ U, const double2* __restrict__ C,
+                                                          SlotArgs a) {
+  const int64_t V = a.q.V;
+  const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (site >= V) return;
+  int x[4];
+  site_coords(a.q, site, x);
+  Cx<double> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = cx(0.0, 0.0);
+  Cx<double> psi[12];
+  if (a.slot == 8) {
+    double c[36];
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+      Clover<double>::load(C, V, chi, site, c);
+      IO<double>::load(in, V, 0, site, psi);
+      clover_apply6<double>(c, psi + 6 * chi, acc + 6 * chi);
+    }
+  }
+  for (int d = 0; d < 8; ++d) {
+    const bool cr = crosses(x, a.b, d);
+    if (a.slot == 8 ? cr : (d != a.slot || !cr)) continue;
+    const int mu = d & 3;
+    M3<double> Um;
+    if (d < 4) {
+      const int64_t nf = nbr_fwd(a.q, site, x, mu);
+      const double f = -0.5 * ((mu == 0 && x[0] == a.q.L[0] - 1) ? a.bc : 1.0);
+      Link<double>::load(U, V, mu, site, Um);
+      IO<double>::load(in, V, 0, nf, psi);
+      hop_add<double, true>(mu, -1.0, f, Um, psi, acc);
+    } else {
+      const int64_t nb = nbr_bwd(a.q, site, x, mu);
+      const double f = -0.5 * ((mu == 0 && x[0] == 0) ? a.bc : 1.0);
+      Link<double>::load(U, V, mu, nb, Um);
+      IO<double>::load(in, V, 0, nb, psi);
+      hop_add<double, false>(mu, 1.0, f, Um, psi, acc);
+    }
+  }
+  IO<double>::store(out, V, 0, site, acc);
+}
+
+// ------------------------------------------------------------ layout conversion
+template <typename R>
+__global__ void pack_kernel(const double* __restrict__ canon, void* __restrict__ dst, int64_t V, int nrhs) {
+  const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (site >= V || r >= nrhs) return;
+  const double2* p = reinterpret_cast<const double2*>(canon) + ((size_t)r * V + site) * 12;
+  Cx<R> s[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    double2 v = p[k];
+    s[k] = cx((R)v.x, (R)v.y);
+  }
+  IO<R>::store(dst, V, r, site, s);
+}
+
+template <typename R>
+__global__ void unpack_kernel(const void* __restrict__ src, double* __restrict__ canon, int64_t V, int nrhs) {
+  const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (site >= V || r >= nrhs) return;
+  Cx<R> s[12];
+  IO<R>::load(src, V, r, site, s);
+  double2* p = reinterpret_cast<double2*>(canon) + ((size_t)r * V + site) * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) p[k] = make_double2((double)s[k].re, (double)s[k].im);
+}
+
+template <typename RI, typename RO>
+__global__ void convert_kernel(const void* __restrict__ src, void* __restrict__ dst, int64_t V, int nrhs) {
+  const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (site >= V || r >= nrhs) return;
+  Cx<RI> s[12];
+  IO<RI>::load(src, V, r, site, s);
+  Cx<RO> t[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) t[k] = cx((RO)s[k].re, (RO)s[k].im);
+  IO<RO>::store(dst, V, r, site, t);
+}
+
+// ------------------------------------------------------------ gauge packing
+__device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void gauge_pack_kernel(const double* __restrict__ links, int64_t site0, int64_t nsites, int64_t V,
+                                  double2* __restrict__ U64, float4* __restrict__ U32, double* dev_max) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsites * 4) return;
+  const int64_t site = site0 + i / 4;
+  const int mu = (int)(i % 4);
+  const double2* p = reinterpret_cast<const double2*>(links) + i * 9;
+  M3<double> m;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    double2 v = p[k];
+    m.e[k / 3][k % 3] = cx(v.x, v.y);
+    U64[((size_t)mu * 9 + k) * V + site] = v;
+  }
+  float4* q = U32 + (size_t)mu * 3 * V + site;
+  q[0] = make_float4((float)m.e[0][0].re, (float)m.e[0][0].im, (float)m.e[0][1].re, (float)m.e[0][1].im);
+  q[V] = make_float4((float)m.e[0][2].re, (float)m.e[0][2].im, (float)m.e[1][0].re, (float)m.e[1][0].im);
+  q[2 * V] = make_float4((float)m.e[1][1].re, (float)m.e[1][1].im, (float)m.e[1][2].re, (float)m.e[1][2].im);
+  // SU(3) check: |U U^dag - 1| and |row2 - conj(row0 x row1)|
+  M3<double> uu = mul(m, dagger(m));
+  double dev = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      double re = uu.e[a][b].re - (a == b ? 1.0 : 0.0);
+      dev = fmax(dev, fabs(re));
+      dev = fmax(dev, fabs(uu.e[a][b].im));
+    }
+  Cx<double> r2[3];
+  r2[0] = conj(m.e[0][1] * m.e[1][2] - m.e[0][2] * m.e[1][1]);
+  r2[1] = conj(m.e[0][2] * m.e[1][0] - m.e[0][0] * m.e[1][2]);
+  r2[2] = conj(m.e[0][0] * m.e[1][1] - m.e[0][1] * m.e[1][0]);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    dev = fmax(dev, fabs(r2[b].re - m.e[2][b].re));
+    dev = fmax(dev, fabs(r2[b].im - m.e[2][b].im));
+  }
+  if (!(dev == dev)) dev = 1e300;  // NaN
+  atomic_max_pos(dev_max, dev);
+}
+
+// ------------------------------------------------------------ clover construction
+__device__ __forceinline__ M3<double> link64(const double2* U, int64_t V, int mu, int64_t site) {
+  M3<double> m;
+  Link<double>::load(U, V, mu, site, m);
+  return m;
+}
+
+// Fhat_{mu nu}(x) = (Q - Q^dag) / 8, Q the four mu-nu leaves at x
+__device__ M3<double> field_strength(const double2* U, const LatIdx& q, const int x[4], int64_t site, int mu,
+                                     int nu) {
+  const int64_t V = q.V;
+  M3<double> Um = link64(U, V, mu, site), Un = link64(U, V, nu, site);
+  // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+  M3<double> Q = mul(mul(Um, link64(U, V, nu, shifted(q, x, mu, 1, nu, 0))),
+                     mul(dagger(link64(U, V, mu, shifted(q, x, mu, 0, nu, 1))), dagger(Un)));
+  // leaf 2: U_nu(x) U_mu(x+nu-mu)^dag U_nu(x-mu)^dag U_mu(x-mu)
+  const int64_t xm = shifted(q, x, mu, -1, nu, 0);
+  M3<double> l2 = mul(mul(Un, dagger(link64(U, V, mu, shifted(q, x, mu, -1, nu, 1)))),
+                      mul(dagger(link64(U, V, nu, xm)), link64(U, V, mu, xm)));
+  Q = add(Q, l2);
+  // leaf 3: U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu)
+  const int64_t xmn = shifted(q, x, mu, -1, nu, -1);
+  const int64_t xn = shifted(q, x, mu, 0, nu, -1);
+  M3<double> l3 = mul(mul(dagger(link64(U, V, mu, xm)), dagger(link64(U, V, nu, xmn))),
+                      mul(link64(U, V, mu, xmn), link64(U, V, nu, xn)));
+  Q = add(Q, l3);
+  // leaf 4: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^dag
+  M3<double> l4 = mul(mul(dagger(link64(U, V, nu, xn)), link64(U, V, mu, xn)),
+                      mul(link64(U, V, nu, shifted(q, x, mu, 1, nu, -1)), dagger(Um)));
+  Q = add(Q, l4);
+  M3<double> F;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) F.e[a][b] = 0.125 * (Q.e[a][b] - conj(Q.e[b][a]));
+  return F;
+}
+
+// Chirality blocks of A(x) = (4 + m0) + c_sw (i/4) sum sigma_{mu nu} Fhat_{mu nu}.
+// With sigma_{0k} = diag(sigma_k, -sigma_k) and sigma_{jk} = -eps_{jkl}
+// diag(sigma_l, sigma_l) the upper block is sum_l sigma_l (x) G_l with
+// G_l = (i c_sw/2)(F_{0l} - B_l) and the lower one uses G'_l = -(i c_sw/2)(F_{0l} + B_l),
+// where B_1 = F_23, B_2 = F_31, B_3 = F_12.
+__global__ void clover_kernel(const double2* __restrict__ U, LatIdx q, double diag, double csw,
+                              double2* __restrict__ C64, float4* __restrict__ C32) {
+  const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (site >= q.V) return;
+  int x[4];
+  site_coords(q, site, x);
+  M3<double> F01 = field_strength(U, q, x, site, 0, 1);
+  M3<double> F02 = field_strength(U, q, x, site, 0, 2);
+  M3<double> F03 = field_strength(U, q, x, site, 0, 3);
+  M3<double> F12 = field_strength(U, q, x, site, 1, 2);
+  M3<double> F13 = field_strength(U, q, x, site, 1, 3);
+  M3<double> F23 = field_strength(U, q, x, site, 2, 3);
+  const Cx<double> ih = cx(0.0, 0.5 * csw);  // i c_sw / 2
+  for (int chi = 0; chi < 2; ++chi) {
+    const double sg = chi == 0 ? 1.0 : -1.0;
+    M3<double> G[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        // upper: F_0l - B_l ; lower: -(F_0l + B_l)
+        Cx<double> g1 = chi == 0 ? F01.e[a][b] - F23.e[a][b] : -(F01.e[a][b] + F23.e[a][b]);
+        Cx<double> g2 = chi == 0 ? F02.e[a][b] + F13.e[a][b] : -(F02.e[a][b] - F13.e[a][b]);
+        Cx<double> g3 = chi == 0 ? F03.e[a][b] - F12.e[a][b] : -(F03.e[a][b] + F12.e[a][b]);
+        G[0].e[a][b] = ih * g1;
+        G[1].e[a][b] = ih * g2;
+        G[2].e[a][b] = ih * g3;
+      }
+    (void)sg;
+    // 6x6 block on (s, a): [[G3, G1 - i G2], [G1 + i G2, -G3]] + diag
+    Cx<double> Bk[6][6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        Bk[a][b] = G[2].e[a][b];
+        Bk[a][3 + b] = G[0].e[a][b] - mul_i(G[1].e[a][b]);
+        Bk[3 + a][b] = G[0].e[a][b] + mul_i(G[1].e[a][b]);
+        Bk[3 + a][3 + b] = -G[2].e[a][b];
+      }
+    double pk[36];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) pk[i] = Bk[i][i].re + diag;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) {
+        const int k = 6 + 2 * offdiag_slot(i, j);
+        pk[k] = Bk[i][j].re;
+        pk[k + 1] = Bk[i][j].im;
+      }
+#pragma unroll
+    for (int j = 0; j < 18; ++j) C64[((size_t)chi * 18 + j) * q.V + site] = make_double2(pk[2 * j], pk[2 * j + 1]);
+#pragma unroll
+    for (int j = 0; j < 9; ++j)
+      C32[((size_t)chi * 9 + j) * q.V + site] =
+          make_float4((float)pk[4 * j], (float)pk[4 * j + 1], (float)pk[4 * j + 2], (float)pk[4 * j + 3]);
+  }
+}
+
+__global__ void tables_kernel(LatIdx q, int b0, int b1, int b2, int b3, int32_t* nbr, int32_t* blk) {
+  const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (site >= q.V) return;
+  int x[4];
+  site_coords(q, site, x);
+  for (int mu = 0; mu < 4; ++mu) {
+    nbr[site * 8 + mu] = (int32_t)nbr_fwd(q, site, x, mu);
+    nbr[site * 8 + 4 + mu] = (int32_t)nbr_bwd(q, site, x, mu);
+  }
+  if (blk) {
+    const int b[4] = {b0, b1, b2, b3};
+    int Lb[4];
+    for (int m = 0; m < 4; ++m) Lb[m] = q.L[m] / b[m];
+    const int y0 = x[0] / b[0], y1 = x[1] / b[1], y2 = x[2] / b[2], y3 = x[3] / b[3];
+    blk[site] = ((y0 * Lb[1] + y1) * Lb[2] + y2) * Lb[3] + y3;
+  }
+}
+
+// ============================================================ host side
+static inline dim3 site_grid(int64_t V, int threads, int ny = 1) {
+  return dim3((unsigned)((V + threads - 1) / threads), (unsigned)ny, 1);
+}
+
+mglma_status pack_spinor(mglma_ctx ctx, const double* canon, Spinor& dst, cudaStream_t s) {
+  ProfScope ps(ctx, K_PACK, s);
+  if (dst.prec == MGLMA_FP64)
+    pack_kernel<double><<<site_grid(dst.V, 256, dst.nrhs), 256, 0, s>>>(canon, dst.p, dst.V, dst.nrhs);
+  else
+    pack_kernel<float><<<site_grid(dst.V, 256, dst.nrhs), 256, 0, s>>>(canon, dst.p, dst.V, dst.nrhs);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status unpack_spinor(mglma_ctx ctx, const Spinor& src, double* canon, cudaStream_t s) {
+  ProfScope ps(ctx, K_PACK, s);
+  if (src.prec == MGLMA_FP64)
+    unpack_kernel<double><<<site_grid(src.V, 256, src.nrhs), 256, 0, s>>>(src.p, canon, src.V, src.nrhs);
+  else
+    unpack_kernel<float><<<site_grid(src.V, 256, src.nrhs), 256, 0, s>>>(src.p, canon, src.V, src.nrhs);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status convert_spinor(mglma_ctx ctx, const Spinor& src, Spinor& dst, cudaStream_t s) {
+  if (src.V != dst.V || src.nrhs != dst.nrhs) return fail(MGLMA_ERR_INVALID, "convert_spinor: shape mismatch");
+  ProfScope ps(ctx, K_PACK, s);
+  dim3 g = site_grid(src.V, 256, src.nrhs);
+  if (src.prec == MGLMA_FP64 && dst.prec == MGLMA_FP32)
+    convert_kernel<double, float><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs);
+  else if (src.prec == MGLMA_FP32 && dst.prec == MGLMA_FP64)
+    convert_kernel<float, double><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs);
+  else if (src.prec == MGLMA_FP64)
+    convert_kernel<double, double><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs);
+  else
+    convert_kernel<float, float><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+template <typename R, int NR, bool DAG>
+static void launch_dslash(const Spinor& in, Spinor& out, const void* U, const void* C, const DslashArgs& a,
+                          cudaStream_t s) {
+  dim3 grid((unsigned)((in.V + 127) / 128), (unsigned)((in.nrhs + NR - 1) / NR), 1);
+  dslash_kernel<R, NR, DAG><<<grid, 128, 0, s>>>(in.p, out.p, U, C, a);
+}
+
+// RHS per thread: chosen by nrhs (tuned values; see the autotuner in solver.cu)
+static int g_nr32 = 2;
+static int g_nr64 = 1;
+void set_dslash_nr(int nr32, int nr64) {
+  if (nr32 == 1 || nr32 == 2 || nr32 == 4) g_nr32 = nr32;
+  if (nr64 == 1 || nr64 == 2) g_nr64 = nr64;
+}
+
+mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, bool dagger,
+                    bool gamma5_out, cudaStream_t s) {
+  if (in.prec != out.prec || in.V != G->g.V || out.V != G->g.V || in.nrhs != out.nrhs)
+    return fail(MGLMA_ERR_INVALID, "dslash: field shape/precision mismatch");
+  if (in.p == out.p) return fail(MGLMA_ERR_INVALID, "dslash: in and out must differ");
+  DslashArgs a;
+  a.q = make_latidx(G->g.L);
+  a.bc = (double)G->g.t_bc;
+  a.nrhs = in.nrhs;
+  a.g5out = gamma5_out ? 1 : 0;
+  if (in.prec == MGLMA_FP64) {
+    ProfScope ps(ctx, K_DSLASH64, s);
+    const int nr = in.nrhs >= 2 ? g_nr64 : 1;
+    if (nr == 2)
+      dagger ? launch_dslash<double, 2, true>(in, out, G->U64, G->C64, a, s)
+             : launch_dslash<double, 2, false>(in, out, G->U64, G->C64, a, s);
+    else
+      dagger ? launch_dslash<double, 1, true>(in, out, G->U64, G->C64, a, s)
+             : launch_dslash<double, 1, false>(in, out, G->U64, G->C64, a, s);
+  } else {
+    ProfScope ps(ctx, K_DSLASH32, s);
+    int nr = g_nr32;
+    if (in.nrhs < nr) nr = in.nrhs >= 2 ? 2 : 1;
+    if (nr == 4)
+      dagger ? launch_dslash<float, 4, true>(in, out, G->U32, G->C32, a, s)
+             : launch_dslash<float, 4, false>(in, out, G->U32, G->C32, a, s);
+    else if (nr == 2)
+      dagger ? launch_dslash<float, 2, true>(in, out, G->U32, G->C32, a, s)
+             : launch_dslash<float, 2, false>(in, out, G->U32, G->C32, a, s);
+    else
+      dagger ? launch_dslash<float, 1, true>(in, out, G->U32, G->C32, a, s)
+             : launch_dslash<float, 1, false>(in, out, G->U32, G->C32, a, s);
+  }
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status dslash_slot64(mglma_ctx ctx, const mglma_gauge_s* G, const int block[4], const Spinor& in,
+                           Spinor& out, int slot, cudaStream_t s) {
+  if (in.prec != MGLMA_FP64 || out.prec != MGLMA_FP64 || in.nrhs != 1 || out.nrhs != 1)
+    return fail(MGLMA_ERR_INVALID, "dslash_slot64: needs single FP64 fields");
+  SlotArgs a;
+  a.q = make_latidx(G->g.L);
+  a.bc = (double)G->g.t_bc;
+  for (int m = 0; m < 4; ++m) a.b[m] = block[m];
+  a.slot = slot;
+  ProfScope ps(ctx, K_SETUP, s);
+  dslash_slot_kernel<<<site_grid(G->g.V, 128), 128, 0, s>>>((const double2*)in.p, (double2*)out.p, G->U64, G->C64,
+                                                             a);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status gauge_pack_slab(mglma_ctx ctx, mglma_gauge_s* G, const double* links_dev, int64_t site0,
+                             int64_t nsites, double* dev_max, cudaStream_t s) {
+  ProfScope ps(ctx, K_SETUP, s);
+  const int64_t n = nsites * 4;
+  gauge_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(links_dev, site0, nsites, G->g.V, G->U64, G->U32,
+                                                                 dev_max);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status clover_build(mglma_ctx ctx, mglma_gauge_s* G, cudaStream_t s) {
+  ProfScope ps(ctx, K_SETUP, s);
+  LatIdx q = make_latidx(G->g.L);
+  clover_kernel<<<site_grid(G->g.V, 64), 64, 0, s>>>(G->U64, q, 4.0 + G->m0, G->csw, G->C64, G->C32);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status debug_tables(mglma_ctx ctx, const mglma_gauge_s* G, const int* block, int32_t* nbr_dev,
+                          int32_t* blk_dev, cudaStream_t s) {
+  LatIdx q = make_latidx(G->g.L);
+  int b[4] = {1, 1, 1, 1};
+  if (block)
+    for (int m = 0; m < 4; ++m) b[m] = block[m];
+  tables_kernel<<<site_grid(G->g.V, 256), 256, 0, s>>>(q, b[0], b[1], b[2], b[3], nbr_dev, blk_dev);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+}  // namespace mglma

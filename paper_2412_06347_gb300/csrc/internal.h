@@ -1,0 +1,213 @@
+// Internal definitions shared by the CUDA translation units of libmglma.
+//
+// Device layouts (all fields live in HBM; sites in the canonical lexicographic
+// order ((x0*L1 + x1)*L2 + x2)*L3 + x3):
+//   fine spinor batch, FP32 : [rhs][6 chunks][V] float4   (24 reals per site)
+//   fine spinor batch, FP64 : [rhs][12 chunks][V] double2
+//     chunk j of a site holds reals 4j..4j+3 (FP32) / 2j..2j+1 (FP64) of the
+//     site vector, real index k = 2*(spin*3 + colour) + re/im.
+//   gauge, FP64             : [mu][9][V] double2, full 3x3 (row-major)
+//   gauge, FP32             : [mu][3][V] float4, rows 0 and 1 only
+//                             (reconstruct-12: row2 = conj(row0 x row1))
+//   clover, FP64            : [2 chiralities][18][V] double2
+//   clover, FP32            : [2 chiralities][9][V] float4
+//     each chirality block is a Hermitian 6x6 matrix on (spin mod 2)*3 +
+//     colour, packed as 6 real diagonal entries then the 15 upper off-diagonal
+//     entries (i<j, row-major) as (re, im) pairs: 36 reals.
+//   coarse field            : [rhs][V1][2 Nv] complex (float2 / double2),
+//                             dof index alpha*Nv + c
+//   block basis             : [V1][2 Nv][3 chunks of 2 complex][|B|]
+//                             (FP64 double2x? see subspace.cu)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mglma.h"
+
+namespace mglma {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+mglma_status fail(mglma_status st, const std::string& msg);
+
+#define MG_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return ::mglma::fail(MGLMA_ERR_CUDA, std::string(#call) + ": " +             \
+                                               cudaGetErrorString(e_));            \
+  } while (0)
+
+#define MG_CHECK(expr)                                                             \
+  do {                                                                             \
+    mglma_status s_ = (expr);                                                      \
+    if (s_ != MGLMA_OK) return s_;                                                 \
+  } while (0)
+
+#define MG_LAUNCH_CHECK() MG_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+  int L[4];
+  int64_t V;
+  int t_bc;  // -1 antiperiodic, +1 periodic fermion hops across x0 = L0-1 <-> 0
+};
+
+inline Geom make_geom(const int L[4], int t_bc) {
+  Geom g;
+  for (int m = 0; m < 4; ++m) g.L[m] = L[m];
+  g.V = (int64_t)L[0] * L[1] * L[2] * L[3];
+  g.t_bc = t_bc;
+  return g;
+}
+
+// ---------------------------------------------------------------- device memory
+// Stream-ordered allocations from one pool per context; freed memory is
+// cached by the pool so repeated solves do not return memory to the driver.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------- handles
+struct KernelStat {
+  std::string name;
+  long long launches = 0;
+  double ms = 0.0;
+};
+
+}  // namespace mglma
+
+struct mglma_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;  // default stream of the context
+  cudaMemPool_t pool = nullptr;
+  int sm_count = 0;
+  // optional per-kernel timing (CUDA events around launches)
+  bool profile = false;
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_cache;
+  mglma::KernelStat stats[16];
+};
+
+struct mglma_gauge_s {
+  mglma_ctx ctx = nullptr;
+  mglma::Geom g;
+  double kappa = 0, csw = 0, m0 = 0;
+  double2* U64 = nullptr;  // [4][9][V]
+  float4* U32 = nullptr;   // [4][3][V]
+  double2* C64 = nullptr;  // [2][18][V]
+  float4* C32 = nullptr;   // [2][9][V]
+  double* links_host_check = nullptr;
+  int slabs_loaded = 0;   // time slices received
+  std::vector<char> slab_seen;
+  bool ready = false;
+  double unitarity_dev = 0;  // max |U U^dag - 1| seen at load
+};
+
+namespace mglma {
+
+// kernel-statistics kinds (timing is optional, see mglma_profile)
+enum KernelKind {
+  K_DSLASH64 = 0,
+  K_DSLASH32 = 1,
+  K_BLAS = 2,
+  K_REDUCE = 3,
+  K_RESTRICT = 4,
+  K_PROLONG = 5,
+  K_COARSE = 6,
+  K_PACK = 7,
+  K_SETUP = 8,
+  K_NKINDS = 9
+};
+const char* kernel_kind_name(int k);
+
+// Event bracket around one launch when profiling is on.
+struct ProfScope {
+  mglma_ctx ctx;
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(mglma_ctx c, int k, cudaStream_t st);
+  ~ProfScope();
+};
+
+// ---------------------------------------------------------------- memory
+mglma_status dalloc(mglma_ctx ctx, void** p, size_t bytes, cudaStream_t s);
+void dfree(mglma_ctx ctx, void* p, cudaStream_t s);
+bool is_device_pointer(const void* p);
+
+// ---------------------------------------------------------------- fine fields
+// Internal spinor batch (see layout at top).
+struct Spinor {
+  void* p = nullptr;
+  int prec = MGLMA_FP32;  // MGLMA_FP64 or MGLMA_FP32
+  int nrhs = 0;
+  int64_t V = 0;
+  size_t rhs_reals() const { return (size_t)24 * V; }
+  size_t bytes() const { return rhs_reals() * nrhs * (prec == MGLMA_FP64 ? 8 : 4); }
+};
+
+// conversions canonical complex128 (device) <-> internal
+mglma_status pack_spinor(mglma_ctx, const double* canon, Spinor& dst, cudaStream_t s);
+mglma_status unpack_spinor(mglma_ctx, const Spinor& src, double* canon, cudaStream_t s);
+mglma_status convert_spinor(mglma_ctx, const Spinor& src, Spinor& dst, cudaStream_t s);
+
+// fine operator application: out = op(in), op in {D, D^dag, gamma5 D, gamma5 D^dag}
+mglma_status dslash(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, bool dagger,
+                    bool gamma5_out, cudaStream_t s);
+// single hop-slot pieces of D in FP64, used to assemble the coarse operator:
+// slot d < 8: the hop term of slot d at sites whose hop leaves their block
+// (zero elsewhere); slot 8: clover term plus every hop that stays in the block.
+mglma_status dslash_slot64(mglma_ctx, const mglma_gauge_s* G, const int block[4], const Spinor& in,
+                           Spinor& out, int slot, cudaStream_t s);
+
+// gauge setup
+mglma_status gauge_pack_and_clover(mglma_ctx, mglma_gauge_s* G, const double* links_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------- BLAS-1 (multi-RHS)
+// Every scalar is per RHS and lives in device memory.  All vectors are rhs-major
+// blocks of n reals (n = 24 V for fine fields, 4 Nv V1 for coarse fields).
+struct Vec {
+  void* p = nullptr;
+  int prec = MGLMA_FP32;
+  int nrhs = 0;
+  size_t n = 0;  // reals per RHS (even)
+};
+inline Vec as_vec(const Spinor& s) {
+  Vec v;
+  v.p = s.p;
+  v.prec = s.prec;
+  v.nrhs = s.nrhs;
+  v.n = s.rhs_reals();
+  return v;
+}
+
+// y = a*x + y with complex a per RHS (a: double2[nrhs] on device)
+mglma_status caxpy(mglma_ctx, const double2* a, const Vec& x, Vec& y, cudaStream_t s, double sign = 1.0);
+// y = x + a*y
+mglma_status cxpay(mglma_ctx, const Vec& x, const double2* a, Vec& y, cudaStream_t s);
+// y = x (precision conversion allowed)
+mglma_status copy_vec(mglma_ctx, const Vec& x, Vec& y, cudaStream_t s);
+mglma_status zero_vec(mglma_ctx, Vec& y, cudaStream_t s);
+// y -= sum_j a[j] x_j for j < k (x_j = base + j*stride_rhs_block)
+// dots: out[r] = <x_r, y_r> (complex, FP64 accumulate); norms: out[r] = |x_r|^2
+mglma_status cdot(mglma_ctx, const Vec& x, const Vec& y, double2* out, cudaStream_t s);
+mglma_status norm2(mglma_ctx, const Vec& x, double* out, cudaStream_t s);
+
+// scalar kernels over per-RHS arrays (tiny launches)
+// out[r] = num[r] / den[r] (real), gated by active mask
+mglma_status scalar_div(mglma_ctx, const double* num, const double* den, double2* out, const int* active,
+                        int nrhs, cudaStream_t s);
+
+}  // namespace mglma
