@@ -118,6 +118,102 @@ mglma_status mglma_gauge_info(mglma_gauge g, int L[4], int64_t* volume);
 mglma_status mglma_dirac_apply(mglma_ctx ctx, mglma_gauge g, mglma_op op, int nrhs, const double* in, double* out,
                                mglma_prec compute, void* cuda_stream);
 
+/* ---------------------------------------------------------------- block basis (Sec. 3, Sec. 4) */
+/* Builds the chirality-split block basis of Eq. mg_basis:
+ *   1. nv Gaussian start vectors drawn on the device from the counter-based
+ *      generator (SplitMix64 keyed by (seed, tag 3), Box-Muller pairs);
+ *   2. n_smooth minimal-residual steps on D v = 0 in FP64 (the paper uses
+ *      exact low modes of Q and notes inexact ones work the same way);
+ *   3. P_alpha theta_{B_y} v_c for every block y (sides block[4], each
+ *      dividing L) and chirality alpha, orthonormalised per (block, alpha) --
+ *      the unique factor with positive real R that Gram-Schmidt gives -- in
+ *      FP64.
+ * store: MGLMA_FP64 (keeps the FP64 basis: FP64 R0/T0 and export work),
+ *   MGLMA_FP32, or MGLMA_FP16 (one FP32 scale per (block, alpha, c)); the
+ *   FP64 basis is kept until mglma_coarse_build in every case.
+ * Returns MGLMA_ERR_RANK when a vector's remaining norm falls below 1e-6 of
+ * its starting norm inside a block (the paper assumes full rank, App.
+ * chirality). */
+mglma_status mglma_subspace_build(mglma_ctx ctx, mglma_gauge g, const int block[4], int nv, int n_smooth,
+                                  uint64_t seed, mglma_prec store, mglma_subspace* out);
+/* Same from caller-provided test vectors (e.g. exact low modes, Sec. 3):
+ * vecs = nv canonical spinors (host or device). */
+mglma_status mglma_subspace_load(mglma_ctx ctx, mglma_gauge g, const int block[4], int nv, const double* vecs,
+                                 mglma_prec store, mglma_subspace* out);
+void mglma_subspace_free(mglma_subspace s);
+mglma_status mglma_subspace_info(mglma_subspace s, int* nv, int Lb[4], int64_t* coarse_volume);
+/* Exports the FP64 basis as complex128 [V1][2][nv][|B|][4][3] (spins of the
+ * other chirality are zero); sites of a block in site-in-block order. */
+mglma_status mglma_subspace_export(mglma_subspace s, double* phi);
+/* R0 (Eq. res_mg): out[rhs][y][alpha nv + c] = sum_{x in B_y} phi^dag psi(x).
+ * in: nrhs canonical spinors; out: nrhs canonical coarse fields. */
+mglma_status mglma_restrict(mglma_ctx ctx, mglma_subspace s, int nrhs, const double* in, double* out,
+                            mglma_prec compute, void* cuda_stream);
+/* T0 (Eq. pro_mg): out(x) = sum_{alpha c} in[y(x)][alpha nv + c] phi(x). */
+mglma_status mglma_prolong(mglma_ctx ctx, mglma_subspace s, int nrhs, const double* in, double* out,
+                           mglma_prec compute, void* cuda_stream);
+
+/* ---------------------------------------------------------------- coarse operator (Sec. 2, Fig. A) */
+/* Builds D1 = R0 D T0 in FP64 as the nine-slot stencil of dense
+ * (2nv x 2nv) blocks; store selects the copy used by the solvers' coarse
+ * applications: MGLMA_BF16 (FP32 accumulation), MGLMA_FP32 or MGLMA_FP64.
+ * The FP64 operator is always kept (export, FP64 coarse residuals). */
+mglma_status mglma_coarse_build(mglma_ctx ctx, mglma_gauge g, mglma_subspace s, mglma_prec store,
+                                mglma_coarse* out);
+void mglma_coarse_free(mglma_coarse c);
+mglma_status mglma_coarse_info(mglma_coarse c, int* nv, int Lb[4], int64_t* coarse_volume);
+/* Exports the FP64 stencil as complex128 [9][V1][2nv][2nv]. */
+mglma_status mglma_coarse_export(mglma_coarse c, double* dhat);
+/* out = D1 in for nrhs canonical coarse fields; compute MGLMA_FP64 uses the
+ * FP64 operator, MGLMA_FP32 the stored low-precision copy. */
+mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse c, int nrhs, const double* in, double* out,
+                                mglma_prec compute, void* cuda_stream);
+
+/* ---------------------------------------------------------------- solves (Sec. 2, Sec. 5) */
+typedef enum {
+  MGLMA_SOLVER_CGNE = 0, /* FP64 CG on D^dag D x = D^dag b: the plain method */
+  MGLMA_SOLVER_MG = 1    /* FP64 defect correction around FP32 flexible GCR
+                            preconditioned by the coarse-grid correction
+                            T0 D1^-1 R0 plus MR smoothing */
+} mglma_solver;
+
+typedef struct {
+  int method;           /* mglma_solver */
+  double tol;           /* target FP64 ||b - D x|| / ||b|| (e.g. 1e-10) */
+  int max_iter;         /* cap on iterations (CGNE) / inner FGCR iterations (MG) */
+  int gcr_m;            /* FGCR restart length (MG) */
+  int nu;               /* MR smoothing steps after the coarse correction (MG) */
+  double inner_tol;     /* relative reduction asked of each FP32 cycle (MG) */
+  double coarse_tol;    /* relative tolerance of the preconditioner's coarse solve */
+  int coarse_max_iter;  /* cap on coarse iterations per preconditioner call */
+  int check_every;      /* host polls residual norms every this many iterations */
+} mglma_solve_params;
+
+typedef struct {
+  int iterations;              /* CGNE iterations / FGCR iterations summed over cycles */
+  int outer;                   /* FP64 defect-correction cycles (MG) */
+  long long coarse_iterations; /* coarse-solver iterations (MG) */
+  double residual;             /* final FP64 ||b - D x|| / ||b|| */
+  int converged;               /* 1 if residual <= tol */
+} mglma_solve_stats;
+
+/* Fills *p with the library defaults for `method`. */
+void mglma_solve_params_default(mglma_solve_params* p, int method);
+
+/* Solves D x = b (x = S b, the propagator of Sec. 2 applied to b) for
+ * ngroups groups of right-hand sides; group g holds group_nrhs[g] canonical
+ * spinors, the groups stored back to back in b and x.  Each group runs as one
+ * batch; every RHS follows its own recurrence, so its result does not depend
+ * on the batch it is in.  coarse may be NULL for MGLMA_SOLVER_CGNE.
+ * x_coarse (nullable): also returns the coarse-space piece
+ *   psi1 = T0 D1^-1 R0 b (S1 b of Sec. 2 via App. chirality), with D1^-1
+ *   solved to tol by FP64 defect correction; S0 b = x - psi1.
+ * stats (nullable): one entry per RHS.
+ * Returns MGLMA_ERR_NOT_CONVERGED (best iterate in x) if any RHS misses tol. */
+mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge g, mglma_coarse coarse, const mglma_solve_params* params,
+                               int ngroups, const int* group_nrhs, const double* b, double* x, double* x_coarse,
+                               mglma_solve_stats* stats, void* cuda_stream);
+
 /* Debug export of the integer tables the kernels compute on the fly:
  * nbr[V][8] (hop slots +0..+3, -0..-3) and block_of_site[V] for the given
  * block sides (block may be NULL to skip it).  Host pointers. */

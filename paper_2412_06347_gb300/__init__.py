@@ -11,14 +11,7 @@ context's device; the library detects which.  There is no CPU fallback: if
 from __future__ import annotations
 
 from . import _capi
-from ._capi import (  # noqa: F401
-    MglmaError, Context, lib,
-    MGLMA_FP64, MGLMA_FP32, MGLMA_BF16, MGLMA_FP16,
-    MGLMA_OP_D, MGLMA_OP_DDAG, MGLMA_OP_Q, MGLMA_OP_DDAGD,
-    mglma_create, mglma_destroy, mglma_version, mglma_last_error,
-    mglma_profile, mglma_profile_get,
-    mglma_gauge_load, mglma_gauge_free, mglma_gauge_info,
-    mglma_dirac_apply, mglma_debug_tables,
-)
+from ._capi import *  # noqa: F401,F403
+from ._capi import MglmaError, Context, lib  # noqa: F401
 
 __all__ = [n for n in dir(_capi) if n.startswith("mglma_") or n.startswith("MGLMA_")] + ["Context", "MglmaError"]

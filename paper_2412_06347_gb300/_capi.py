@@ -10,6 +10,7 @@ from . import build as _build
 
 MGLMA_FP64, MGLMA_FP32, MGLMA_BF16, MGLMA_FP16 = 0, 1, 2, 3
 MGLMA_OP_D, MGLMA_OP_DDAG, MGLMA_OP_Q, MGLMA_OP_DDAGD = 0, 1, 2, 3
+MGLMA_SOLVER_CGNE, MGLMA_SOLVER_MG = 0, 1
 _STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "NOT_CONVERGED", 6: "NUMERIC",
            7: "TIMEOUT", 8: "REJECTED"}
 
@@ -59,6 +60,35 @@ _sig("mglma_gauge_free", None, _vp)
 _sig("mglma_gauge_info", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(_i64))
 _sig("mglma_dirac_apply", C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp)
 _sig("mglma_debug_tables", C.c_int, _vp, C.POINTER(C.c_int), _vp, _vp)
+_sig("mglma_subspace_build", C.c_int, _vp, _vp, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_uint64, C.c_int,
+     C.POINTER(_vp))
+_sig("mglma_subspace_load", C.c_int, _vp, _vp, C.POINTER(C.c_int), C.c_int, _vp, C.c_int, C.POINTER(_vp))
+_sig("mglma_subspace_free", None, _vp)
+_sig("mglma_subspace_info", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_i64))
+_sig("mglma_subspace_export", C.c_int, _vp, _vp)
+_sig("mglma_restrict", C.c_int, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp)
+_sig("mglma_prolong", C.c_int, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp)
+_sig("mglma_coarse_build", C.c_int, _vp, _vp, _vp, C.c_int, C.POINTER(_vp))
+_sig("mglma_coarse_free", None, _vp)
+_sig("mglma_coarse_info", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_i64))
+_sig("mglma_coarse_export", C.c_int, _vp, _vp)
+_sig("mglma_coarse_apply", C.c_int, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp)
+
+
+class mglma_solve_params(C.Structure):
+    _fields_ = [("method", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("gcr_m", C.c_int),
+                ("nu", C.c_int), ("inner_tol", C.c_double), ("coarse_tol", C.c_double),
+                ("coarse_max_iter", C.c_int), ("check_every", C.c_int)]
+
+
+class mglma_solve_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("outer", C.c_int), ("coarse_iterations", C.c_longlong),
+                ("residual", C.c_double), ("converged", C.c_int)]
+
+
+_sig("mglma_solve_params_default", None, C.POINTER(mglma_solve_params), C.c_int)
+_sig("mglma_solve_batch", C.c_int, _vp, _vp, _vp, C.POINTER(mglma_solve_params), C.c_int, C.POINTER(C.c_int), _vp,
+     _vp, _vp, C.POINTER(mglma_solve_stats), _vp)
 
 
 def _check(st: int):
@@ -168,3 +198,92 @@ def mglma_dirac_apply(ctx, g, op, nrhs, inp, out, compute=MGLMA_FP64, stream=Non
 def mglma_debug_tables(g, block, nbr, block_of_site=None):
     b = (C.c_int * 4)(*block) if block is not None else None
     _check(lib.mglma_debug_tables(g, b, ptr(nbr), ptr(block_of_site)))
+
+
+def _block(b):
+    return (C.c_int * 4)(*[int(v) for v in b])
+
+
+def mglma_subspace_build(ctx, g, block, nv, n_smooth, seed, store=MGLMA_FP32):
+    h = _vp()
+    _check(lib.mglma_subspace_build(_h(ctx), g, _block(block), int(nv), int(n_smooth), int(seed), int(store),
+                                    C.byref(h)))
+    return h.value
+
+
+def mglma_subspace_load(ctx, g, block, nv, vecs, store=MGLMA_FP32):
+    h = _vp()
+    _check(lib.mglma_subspace_load(_h(ctx), g, _block(block), int(nv), ptr(vecs), int(store), C.byref(h)))
+    return h.value
+
+
+def mglma_subspace_free(sub):
+    lib.mglma_subspace_free(sub)
+
+
+def mglma_subspace_info(sub):
+    nv = C.c_int()
+    Lb = (C.c_int * 4)()
+    V1 = _i64()
+    _check(lib.mglma_subspace_info(sub, C.byref(nv), Lb, C.byref(V1)))
+    return nv.value, tuple(Lb), V1.value
+
+
+def mglma_subspace_export(sub, phi):
+    _check(lib.mglma_subspace_export(sub, ptr(phi)))
+
+
+def mglma_restrict(ctx, sub, nrhs, inp, out, compute=MGLMA_FP64, stream=None):
+    _check(lib.mglma_restrict(_h(ctx), sub, int(nrhs), ptr(inp), ptr(out), int(compute), _stream_ptr(stream)))
+
+
+def mglma_prolong(ctx, sub, nrhs, inp, out, compute=MGLMA_FP64, stream=None):
+    _check(lib.mglma_prolong(_h(ctx), sub, int(nrhs), ptr(inp), ptr(out), int(compute), _stream_ptr(stream)))
+
+
+def mglma_coarse_build(ctx, g, sub, store=MGLMA_BF16):
+    h = _vp()
+    _check(lib.mglma_coarse_build(_h(ctx), g, sub, int(store), C.byref(h)))
+    return h.value
+
+
+def mglma_coarse_free(c):
+    lib.mglma_coarse_free(c)
+
+
+def mglma_coarse_info(c):
+    nv = C.c_int()
+    Lb = (C.c_int * 4)()
+    V1 = _i64()
+    _check(lib.mglma_coarse_info(c, C.byref(nv), Lb, C.byref(V1)))
+    return nv.value, tuple(Lb), V1.value
+
+
+def mglma_coarse_export(c, dhat):
+    _check(lib.mglma_coarse_export(c, ptr(dhat)))
+
+
+def mglma_coarse_apply(ctx, c, nrhs, inp, out, compute=MGLMA_FP64, stream=None):
+    _check(lib.mglma_coarse_apply(_h(ctx), c, int(nrhs), ptr(inp), ptr(out), int(compute), _stream_ptr(stream)))
+
+
+def mglma_solve_params_default(method=MGLMA_SOLVER_MG, **overrides):
+    p = mglma_solve_params()
+    lib.mglma_solve_params_default(C.byref(p), int(method))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def mglma_solve_batch(ctx, g, coarse, params, group_nrhs, b, x, x_coarse=None, stream=None, raise_on_error=True):
+    """Returns (status, stats list of dicts)."""
+    groups = [int(v) for v in group_nrhs]
+    arr = (C.c_int * len(groups))(*groups)
+    st = (mglma_solve_stats * max(1, sum(groups)))()
+    status = lib.mglma_solve_batch(_h(ctx), g, coarse, C.byref(params), len(groups), arr, ptr(b), ptr(x),
+                                   ptr(x_coarse), st, _stream_ptr(stream))
+    if status != 0 and raise_on_error:
+        _check(status)
+    out = [dict(iterations=s.iterations, outer=s.outer, coarse_iterations=s.coarse_iterations,
+                residual=s.residual, converged=bool(s.converged)) for s in st[:sum(groups)]]
+    return status, out

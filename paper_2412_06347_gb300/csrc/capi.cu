@@ -110,17 +110,6 @@ mglma_status clover_build(mglma_ctx ctx, mglma_gauge_s* G, cudaStream_t s);
 mglma_status debug_tables(mglma_ctx ctx, const mglma_gauge_s* G, const int* block, int32_t* nbr_dev,
                           int32_t* blk_dev, cudaStream_t s);
 
-// Host-or-device staging of one canonical buffer.
-struct Staged {
-  mglma_ctx ctx = nullptr;
-  cudaStream_t s = nullptr;
-  double* dev = nullptr;
-  bool owned = false;
-  ~Staged() {
-    if (owned) dfree(ctx, dev, s);
-  }
-};
-
 mglma_status stage_in(mglma_ctx ctx, const double* p, size_t bytes, cudaStream_t s, Staged& st) {
   st.ctx = ctx;
   st.s = s;

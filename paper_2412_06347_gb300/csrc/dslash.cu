@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(128) dslash_slot_kernel(const double2* __restr
                                                           SlotArgs a) {
   const int64_t V = a.q.V;
   const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y;
   if (site >= V) return;
   int x[4];
   site_coords(a.q, site, x);
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(128) dslash_slot_kernel(const double2* __restr
 #pragma unroll
     for (int chi = 0; chi < 2; ++chi) {
       Clover<double>::load(C, V, chi, site, c);
-      IO<double>::load(in, V, 0, site, psi);
+      IO<double>::load(in, V, rhs, site, psi);
       clover_apply6<double>(c, psi + 6 * chi, acc + 6 * chi);
     }
   }
@@ -379,17 +380,17 @@ __global__ void __launch_bounds__(128) dslash_slot_kernel(const double2* __restr
       const int64_t nf = nbr_fwd(a.q, site, x, mu);
       const double f = -0.5 * ((mu == 0 && x[0] == a.q.L[0] - 1) ? a.bc : 1.0);
       Link<double>::load(U, V, mu, site, Um);
-      IO<double>::load(in, V, 0, nf, psi);
+      IO<double>::load(in, V, rhs, nf, psi);
       hop_add<double, true>(mu, -1.0, f, Um, psi, acc);
     } else {
       const int64_t nb = nbr_bwd(a.q, site, x, mu);
       const double f = -0.5 * ((mu == 0 && x[0] == 0) ? a.bc : 1.0);
       Link<double>::load(U, V, mu, nb, Um);
-      IO<double>::load(in, V, 0, nb, psi);
+      IO<double>::load(in, V, rhs, nb, psi);
       hop_add<double, false>(mu, 1.0, f, Um, psi, acc);
     }
   }
-  IO<double>::store(out, V, 0, site, acc);
+  IO<double>::store(out, V, rhs, site, acc);
 }
 
 // ------------------------------------------------------------ layout conversion
@@ -420,16 +421,23 @@ __global__ void unpack_kernel(const void* __restrict__ src, double* __restrict__
   for (int k = 0; k < 12; ++k) p[k] = make_double2((double)s[k].re, (double)s[k].im);
 }
 
+// dst = scale_r * src (+ dst if accumulate); scale NULL means 1
 template <typename RI, typename RO>
-__global__ void convert_kernel(const void* __restrict__ src, void* __restrict__ dst, int64_t V, int nrhs) {
+__global__ void convert_kernel(const void* __restrict__ src, void* __restrict__ dst, int64_t V, int nrhs,
+                               const double* __restrict__ scale, int accumulate) {
   const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (site >= V || r >= nrhs) return;
   Cx<RI> s[12];
   IO<RI>::load(src, V, r, site, s);
+  const double f = scale ? scale[r] : 1.0;
   Cx<RO> t[12];
+  if (accumulate) IO<RO>::load(dst, V, r, site, t);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) t[k] = cx((RO)s[k].re, (RO)s[k].im);
+  for (int k = 0; k < 12; ++k) {
+    const RO re = (RO)(f * (double)s[k].re), im = (RO)(f * (double)s[k].im);
+    t[k] = accumulate ? cx(t[k].re + re, t[k].im + im) : cx(re, im);
+  }
   IO<RO>::store(dst, V, r, site, t);
 }
 
@@ -627,18 +635,20 @@ mglma_status unpack_spinor(mglma_ctx ctx, const Spinor& src, double* canon, cuda
   return MGLMA_OK;
 }
 
-mglma_status convert_spinor(mglma_ctx ctx, const Spinor& src, Spinor& dst, cudaStream_t s) {
+mglma_status convert_spinor(mglma_ctx ctx, const Spinor& src, Spinor& dst, cudaStream_t s, const double* scale,
+                            bool accumulate) {
   if (src.V != dst.V || src.nrhs != dst.nrhs) return fail(MGLMA_ERR_INVALID, "convert_spinor: shape mismatch");
   ProfScope ps(ctx, K_PACK, s);
   dim3 g = site_grid(src.V, 256, src.nrhs);
+  const int acc = accumulate ? 1 : 0;
   if (src.prec == MGLMA_FP64 && dst.prec == MGLMA_FP32)
-    convert_kernel<double, float><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs);
+    convert_kernel<double, float><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs, scale, acc);
   else if (src.prec == MGLMA_FP32 && dst.prec == MGLMA_FP64)
-    convert_kernel<float, double><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs);
+    convert_kernel<float, double><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs, scale, acc);
   else if (src.prec == MGLMA_FP64)
-    convert_kernel<double, double><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs);
+    convert_kernel<double, double><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs, scale, acc);
   else
-    convert_kernel<float, float><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs);
+    convert_kernel<float, float><<<g, 256, 0, s>>>(src.p, dst.p, src.V, src.nrhs, scale, acc);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }
@@ -695,18 +705,18 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
   return MGLMA_OK;
 }
 
-mglma_status dslash_slot64(mglma_ctx ctx, const mglma_gauge_s* G, const int block[4], const Spinor& in,
-                           Spinor& out, int slot, cudaStream_t s) {
-  if (in.prec != MGLMA_FP64 || out.prec != MGLMA_FP64 || in.nrhs != 1 || out.nrhs != 1)
-    return fail(MGLMA_ERR_INVALID, "dslash_slot64: needs single FP64 fields");
+mglma_status dslash_slot64_batch(mglma_ctx ctx, const mglma_gauge_s* G, const int block[4], const Spinor& in,
+                                 Spinor& out, int slot, cudaStream_t s) {
+  if (in.prec != MGLMA_FP64 || out.prec != MGLMA_FP64 || in.nrhs != out.nrhs)
+    return fail(MGLMA_ERR_INVALID, "dslash_slot64: needs FP64 fields of equal size");
   SlotArgs a;
   a.q = make_latidx(G->g.L);
   a.bc = (double)G->g.t_bc;
   for (int m = 0; m < 4; ++m) a.b[m] = block[m];
   a.slot = slot;
   ProfScope ps(ctx, K_SETUP, s);
-  dslash_slot_kernel<<<site_grid(G->g.V, 128), 128, 0, s>>>((const double2*)in.p, (double2*)out.p, G->U64, G->C64,
-                                                             a);
+  dslash_slot_kernel<<<site_grid(G->g.V, 128, in.nrhs), 128, 0, s>>>((const double2*)in.p, (double2*)out.p, G->U64,
+                                                                      G->C64, a);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }

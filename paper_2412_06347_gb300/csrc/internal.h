@@ -16,8 +16,7 @@
 //     entries (i<j, row-major) as (re, im) pairs: 36 reals.
 //   coarse field            : [rhs][V1][2 Nv] complex (float2 / double2),
 //                             dof index alpha*Nv + c
-//   block basis             : [V1][2 Nv][3 chunks of 2 complex][|B|]
-//                             (FP64 double2x? see subspace.cu)
+//   block basis, coarse operator: see subspace.h / subspace.cu / coarse.cu
 #pragma once
 
 #include <cuda_runtime.h>
@@ -67,14 +66,6 @@ inline Geom make_geom(const int L[4], int t_bc) {
   return g;
 }
 
-// ---------------------------------------------------------------- device memory
-// Stream-ordered allocations from one pool per context; freed memory is
-// cached by the pool so repeated solves do not return memory to the driver.
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
 // ---------------------------------------------------------------- handles
 struct KernelStat {
   std::string name;
@@ -108,7 +99,6 @@ struct mglma_gauge_s {
   float4* U32 = nullptr;   // [4][3][V]
   double2* C64 = nullptr;  // [2][18][V]
   float4* C32 = nullptr;   // [2][9][V]
-  double* links_host_check = nullptr;
   int slabs_loaded = 0;   // time slices received
   std::vector<char> slab_seen;
   bool ready = false;
@@ -147,6 +137,21 @@ mglma_status dalloc(mglma_ctx ctx, void** p, size_t bytes, cudaStream_t s);
 void dfree(mglma_ctx ctx, void* p, cudaStream_t s);
 bool is_device_pointer(const void* p);
 
+// host-or-device staging of one canonical buffer (capi.cu)
+struct Staged {
+  mglma_ctx ctx = nullptr;
+  cudaStream_t s = nullptr;
+  double* dev = nullptr;
+  bool owned = false;
+  ~Staged() {
+    if (owned) dfree(ctx, dev, s);
+  }
+};
+mglma_status stage_in(mglma_ctx ctx, const double* p, size_t bytes, cudaStream_t s, Staged& st);
+mglma_status stage_out_alloc(mglma_ctx ctx, double* p, size_t bytes, cudaStream_t s, Staged& st);
+mglma_status stage_out_finish(double* p, size_t bytes, cudaStream_t s, Staged& st);
+cudaStream_t pick_stream(mglma_ctx ctx, void* s);
+
 // ---------------------------------------------------------------- fine fields
 // Internal spinor batch (see layout at top).
 struct Spinor {
@@ -161,7 +166,10 @@ struct Spinor {
 // conversions canonical complex128 (device) <-> internal
 mglma_status pack_spinor(mglma_ctx, const double* canon, Spinor& dst, cudaStream_t s);
 mglma_status unpack_spinor(mglma_ctx, const Spinor& src, double* canon, cudaStream_t s);
-mglma_status convert_spinor(mglma_ctx, const Spinor& src, Spinor& dst, cudaStream_t s);
+// dst = scale_r * src (+ dst when accumulate); precisions may differ; scale
+// (device, per RHS) NULL means 1
+mglma_status convert_spinor(mglma_ctx, const Spinor& src, Spinor& dst, cudaStream_t s, const double* scale = nullptr,
+                            bool accumulate = false);
 
 // fine operator application: out = op(in), op in {D, D^dag, gamma5 D, gamma5 D^dag}
 mglma_status dslash(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, bool dagger,
@@ -169,11 +177,9 @@ mglma_status dslash(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor&
 // single hop-slot pieces of D in FP64, used to assemble the coarse operator:
 // slot d < 8: the hop term of slot d at sites whose hop leaves their block
 // (zero elsewhere); slot 8: clover term plus every hop that stays in the block.
-mglma_status dslash_slot64(mglma_ctx, const mglma_gauge_s* G, const int block[4], const Spinor& in,
-                           Spinor& out, int slot, cudaStream_t s);
+mglma_status dslash_slot64_batch(mglma_ctx, const mglma_gauge_s* G, const int block[4], const Spinor& in,
+                                 Spinor& out, int slot, cudaStream_t s);
 
-// gauge setup
-mglma_status gauge_pack_and_clover(mglma_ctx, mglma_gauge_s* G, const double* links_dev, cudaStream_t s);
 
 // ---------------------------------------------------------------- BLAS-1 (multi-RHS)
 // Every scalar is per RHS and lives in device memory.  All vectors are rhs-major
@@ -182,7 +188,8 @@ struct Vec {
   void* p = nullptr;
   int prec = MGLMA_FP32;
   int nrhs = 0;
-  size_t n = 0;  // reals per RHS (even)
+  size_t n = 0;  // reals per RHS (multiple of 4)
+  size_t bytes() const { return n * (size_t)nrhs * (prec == MGLMA_FP64 ? 8 : 4); }
 };
 inline Vec as_vec(const Spinor& s) {
   Vec v;
@@ -193,21 +200,24 @@ inline Vec as_vec(const Spinor& s) {
   return v;
 }
 
-// y = a*x + y with complex a per RHS (a: double2[nrhs] on device)
+// y = a x + b y (complex a, b per RHS from device arrays; a NULL uses a_def
+// for every RHS, b NULL uses b_def); sign scales a
+mglma_status axpby(mglma_ctx, const double2* a, double2 a_def, const Vec& x, const double2* b, double2 b_def,
+                   Vec& y, cudaStream_t s, double sign = 1.0);
 mglma_status caxpy(mglma_ctx, const double2* a, const Vec& x, Vec& y, cudaStream_t s, double sign = 1.0);
-// y = x + a*y
-mglma_status cxpay(mglma_ctx, const Vec& x, const double2* a, Vec& y, cudaStream_t s);
-// y = x (precision conversion allowed)
+// x += a p ; r -= a w
+mglma_status axpy2(mglma_ctx, const double2* a, const Vec& p, Vec& x, const Vec& w, Vec& r, cudaStream_t s);
+// y -= sum_{j<k} c[j*nrhs + r] x_j  where x_j starts jstride reals after x_{j-1}
+mglma_status multi_axpy(mglma_ctx, const Vec& x0, size_t jstride_reals, int k, Vec& y, const double2* c,
+                        cudaStream_t s);
 mglma_status copy_vec(mglma_ctx, const Vec& x, Vec& y, cudaStream_t s);
 mglma_status zero_vec(mglma_ctx, Vec& y, cudaStream_t s);
-// y -= sum_j a[j] x_j for j < k (x_j = base + j*stride_rhs_block)
-// dots: out[r] = <x_r, y_r> (complex, FP64 accumulate); norms: out[r] = |x_r|^2
+// out[r] = <x_r, y_r> = sum conj(x) y (FP64 accumulation, deterministic)
 mglma_status cdot(mglma_ctx, const Vec& x, const Vec& y, double2* out, cudaStream_t s);
+// out[j*nrhs + r] = <x_j,r, y_r> for j < k
+mglma_status multi_cdot(mglma_ctx, const Vec& x0, size_t jstride_reals, int k, const Vec& y, double2* out,
+                        cudaStream_t s);
+// out[r] = |x_r|^2
 mglma_status norm2(mglma_ctx, const Vec& x, double* out, cudaStream_t s);
-
-// scalar kernels over per-RHS arrays (tiny launches)
-// out[r] = num[r] / den[r] (real), gated by active mask
-mglma_status scalar_div(mglma_ctx, const double* num, const double* den, double2* out, const int* active,
-                        int nrhs, cudaStream_t s);
 
 }  // namespace mglma

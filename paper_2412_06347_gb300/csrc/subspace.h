@@ -1,0 +1,61 @@
+// Block basis handle and coarse-operator handle (shared by subspace.cu,
+// coarse.cu, multigrid solver and C ABI).
+#pragma once
+#include "internal.h"
+
+namespace mglma {
+
+struct BlockGeo {
+  int L[4], b[4], Lb[4];
+  int64_t V, V1;
+  int nB;
+};
+BlockGeo make_blockgeo(const int L[4], const int b[4]);
+
+}  // namespace mglma
+
+struct mglma_subspace_s {
+  mglma_ctx ctx = nullptr;
+  mglma_gauge gauge = nullptr;
+  int nv = 0;
+  int store = MGLMA_FP32;
+  mglma::BlockGeo geo;
+  double2* phi64 = nullptr;  // [V1][2Nv][6][nB]
+  float4* phi32 = nullptr;   // [V1][2Nv][3][nB]
+  uint2* phi16 = nullptr;    // [V1][2Nv][3][nB], halves
+  float* scale16 = nullptr;  // [V1][2Nv]
+};
+
+struct mglma_coarse_s {
+  mglma_ctx ctx = nullptr;
+  mglma_subspace sub = nullptr;
+  int nv = 0, n2 = 0;
+  int store = MGLMA_BF16;
+  mglma::BlockGeo geo;
+  double2* A64 = nullptr;        // [V1][9][n2 (j)][n2 (i)] column-major blocks, FP64 master (optional)
+  float2* A32 = nullptr;         // same layout, FP32
+  __nv_bfloat162* A16 = nullptr; // same layout, BF16 (re, im)
+};
+
+namespace mglma {
+
+mglma_status restrict_fine(mglma_ctx ctx, const mglma_subspace_s* S, const Spinor& in, void* out_coarse,
+                           cudaStream_t s);
+mglma_status prolong_coarse(mglma_ctx ctx, const mglma_subspace_s* S, const void* in_coarse, Spinor& out,
+                            bool accumulate, cudaStream_t s);
+mglma_status mr_smooth64(mglma_ctx ctx, const mglma_gauge_s* G, Spinor& v, int n_smooth, cudaStream_t s);
+
+// coarse fields: internal [rhs][V1][n2] float2 (FP32) or double2 (FP64)
+mglma_status coarse_to_canonical(mglma_ctx ctx, const void* c, int prec, size_t ncplx, double* canon,
+                                 cudaStream_t s);
+mglma_status coarse_from_canonical(mglma_ctx ctx, const double* canon, size_t ncplx, void* c, int prec,
+                                   cudaStream_t s);
+// dst = scale_r src (+ dst when accumulate) on coarse fields of `per` complex per RHS
+mglma_status coarse_scale_convert(mglma_ctx ctx, const void* src, int sprec, void* dst, int dprec,
+                                  const double* scale, size_t per, int nrhs, bool accumulate, cudaStream_t s);
+// Y = Dhat X for nrhs coarse fields; prec of X/Y: FP64 (FP64 operator) or FP32
+// (FP32 or BF16 operator as stored)
+mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X, void* Y, int nrhs, int prec,
+                          bool dagger, cudaStream_t s);
+
+}  // namespace mglma

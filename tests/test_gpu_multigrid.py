@@ -1,0 +1,138 @@
+"""GPU parity of the block basis, R0/T0, the coarse operator and its
+application against the FP64 oracle.  The oracle builds its own basis from the
+same seeded start vectors (the counter-based generator both sides implement);
+the factor is unique, so the two agree to rounding.  Bars: FP64 to 1e-11
+(basis, Gram-Schmidt conditioning) / 1e-12 (operators); FP32 to 2e-6; FP16
+basis to 2e-3; BF16 operator to 2e-2."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import dirac as D
+from oracle import lattice as lat
+from oracle import multigrid as MG
+from tests.gpu_util import rel_per_rhs
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # name: L, block, nv, eps, seed, kappa, csw, n_smooth
+    "c1": ((8, 8, 8, 8), (2, 2, 2, 2), 8, 0.3, 1001, 0.12, 1.0, 5),
+    "ragged": ((6, 4, 6, 2), (3, 2, 2, 1), 5, 0.3, 7, 0.125, 1.7, 3),
+    "lma": ((4, 2, 2, 4), (4, 2, 2, 4), 4, 0.3, 9, 0.125, 1.9, 2),
+}
+
+
+@pytest.fixture(scope="module")
+def m():
+    import paper_2412_06347_gb300 as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(m):
+    c = m.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def setup(request, m, ctx):
+    L, b, nv, eps, seed, kappa, csw, ns = CASES[request.param]
+    U = synthetic.gauge_links(L, eps, seed)
+    g = m.mglma_gauge_load(ctx, L, U, kappa, csw)
+    sub = m.mglma_subspace_build(ctx, g, b, nv, ns, seed + 1000, m.MGLMA_FP64)
+    starts = synthetic.gaussian_start_vectors(L, nv, seed + 1000)
+    phi = MG.subspace(U, starts, kappa, csw, b, ns)
+    yield dict(L=L, b=b, nv=nv, U=U, g=g, sub=sub, phi=phi, kappa=kappa, csw=csw, seed=seed)
+    m.mglma_subspace_free(sub)
+    m.mglma_gauge_free(g)
+
+
+def test_basis_matches_oracle(m, setup):
+    s = setup
+    phi = np.zeros_like(s["phi"])
+    m.mglma_subspace_export(s["sub"], phi)
+    assert np.linalg.norm(phi - s["phi"]) / np.linalg.norm(s["phi"]) < 1e-11
+    nv, Lb, V1 = m.mglma_subspace_info(s["sub"])
+    assert nv == s["nv"] and V1 == lat.volume(lat.block_grid(s["L"], s["b"]))
+
+
+def test_restrict_prolong_fp64(m, ctx, setup):
+    s = setup
+    L, b, phi = s["L"], s["b"], s["phi"]
+    psi = synthetic.random_spinors(L, 3, 21)
+    V1 = phi.shape[0]
+    out = np.zeros((3, V1, 2 * s["nv"]), dtype=np.complex128)
+    m.mglma_restrict(ctx, s["sub"], 3, psi, out, m.MGLMA_FP64)
+    assert rel_per_rhs(out, MG.restrict(phi, psi, L, b)).max() < 1e-11
+    c = synthetic.random_coarse(V1, 2 * s["nv"], 2, 22)
+    f = np.zeros((2,) + tuple(L) + (4, 3), dtype=np.complex128)
+    m.mglma_prolong(ctx, s["sub"], 2, c, f, m.MGLMA_FP64)
+    assert rel_per_rhs(f, MG.prolong(phi, c, L, b)).max() < 1e-11
+
+
+def test_coarse_operator_and_apply(m, ctx, setup):
+    s = setup
+    L, b = s["L"], s["b"]
+    Lb = lat.block_grid(L, b)
+    V1, n2 = lat.volume(Lb), 2 * s["nv"]
+    Dhat_ref = MG.coarse_operator(s["U"], s["phi"], s["kappa"], s["csw"], b)
+    for store, tol in ((m.MGLMA_FP64, 2e-6), (m.MGLMA_FP32, 2e-6), (m.MGLMA_BF16, 2e-2)):
+        C = m.mglma_coarse_build(ctx, s["g"], s["sub"], store)
+        Dh = np.zeros((9, V1, n2, n2), dtype=np.complex128)
+        m.mglma_coarse_export(C, Dh)
+        assert np.linalg.norm(Dh - Dhat_ref) / np.linalg.norm(Dhat_ref) < 1e-11
+        X = synthetic.random_coarse(V1, n2, 9, 23)
+        ref = MG.coarse_apply(Dhat_ref, X, Lb)
+        Y = np.zeros_like(X)
+        m.mglma_coarse_apply(ctx, C, 9, X, Y, m.MGLMA_FP64)
+        assert rel_per_rhs(Y, ref).max() < 1e-12
+        m.mglma_coarse_apply(ctx, C, 9, X, Y, m.MGLMA_FP32)
+        assert rel_per_rhs(Y, ref).max() < tol
+        m.mglma_coarse_free(C)
+
+
+def test_low_precision_transfers(m, ctx):
+    L, b, nv = (8, 4, 4, 8), (4, 4, 4, 4), 6
+    U = synthetic.gauge_links(L, 0.2, 31)
+    g = m.mglma_gauge_load(ctx, L, U, 0.125, 1.7)
+    phi = MG.subspace(U, synthetic.gaussian_start_vectors(L, nv, 32), 0.125, 1.7, b, 2)
+    psi = synthetic.random_spinors(L, 5, 33)
+    ref = MG.restrict(phi, psi, L, b)
+    c = synthetic.random_coarse(phi.shape[0], 2 * nv, 5, 34)
+    pref = MG.prolong(phi, c, L, b)
+    for store, tol in ((m.MGLMA_FP32, 2e-6), (m.MGLMA_FP16, 2e-3)):
+        sub = m.mglma_subspace_build(ctx, g, b, nv, 2, 32, store)
+        out = np.zeros_like(ref)
+        m.mglma_restrict(ctx, sub, 5, psi, out, m.MGLMA_FP32)
+        assert rel_per_rhs(out, ref).max() < tol
+        f = np.zeros_like(psi)
+        m.mglma_prolong(ctx, sub, 5, c, f, m.MGLMA_FP32)
+        assert rel_per_rhs(f, pref).max() < tol
+        m.mglma_subspace_free(sub)
+    m.mglma_gauge_free(g)
+
+
+def test_subspace_load_exact_modes_and_rank_error(m, ctx):
+    """Basis from caller-given vectors (exact low modes of Q, Sec. 3) and the
+    rank check on linearly dependent vectors."""
+    L, b, nv = (4, 2, 2, 2), (2, 2, 2, 2), 3
+    U = synthetic.gauge_links(L, 0.4, 61)
+    kappa, csw = 0.125, 1.5
+    g = m.mglma_gauge_load(ctx, L, U, kappa, csw)
+    M = D.dense_dirac(U, kappa, csw)
+    G5 = np.kron(np.eye(lat.volume(L)), np.kron(D.gamma5(), np.eye(3)))
+    w, v = np.linalg.eigh(G5 @ M)
+    order = np.argsort(np.abs(w))[:nv]
+    modes = np.ascontiguousarray(v[:, order].T.reshape((nv,) + L + (4, 3)))
+    sub = m.mglma_subspace_load(ctx, g, b, nv, modes, m.MGLMA_FP64)
+    phi = np.zeros_like(MG.build_basis(modes, L, b))
+    m.mglma_subspace_export(sub, phi)
+    assert np.linalg.norm(phi - MG.build_basis(modes, L, b)) < 1e-11 * np.linalg.norm(phi)
+    m.mglma_subspace_free(sub)
+    bad = np.ascontiguousarray(np.stack([modes[0], modes[1], modes[0] * (2 - 1j)]))
+    with pytest.raises(m.MglmaError) as e:
+        m.mglma_subspace_load(ctx, g, b, nv, bad, m.MGLMA_FP64)
+    assert e.value.status == 4
+    m.mglma_gauge_free(g)
