@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the multigrid low-mode-averaging hot path on GB300.
+
+A step solves one group of right-hand sides D x = b to a FP64 relative
+residual of 1e-10 with the mixed-precision multigrid solver (FP64 defect
+correction around FP32 flexible GCR preconditioned by T0 D1^-1 R0 with a BF16
+coarse stencil, plus MR smoothing).  The default workload is the 2 fm box
+shape 64x32^3 with its 96 point + Z2 noise sources; consecutive steps take
+consecutive groups of those sources.  The JSON line reports:
+
+* value       -- solves/s with sources resident in HBM (device timing);
+* e2e         -- solves/s through the C ABI with pinned host buffers, the
+                 host->device copy of b and device->host copy of x inside;
+* fp64_plain  -- the plain FP64 CGNE solve on the GPU (bounded sample);
+* roofline    -- the dominant kernel's algorithmic bytes / time against the
+                 measured HBM peak, from CUDA events on its launch stream;
+* cpu_baseline-- the FP64 oracle timed on the host cores (bounded sample);
+* clocks      -- nvidia-smi samples taken during the timed region.
+
+`--impl reference` runs the oracle alone as the reference arm.
+Multi-GPU (--gpus N under torchrun): independent replicas, each solving its
+own sources (weak scaling); no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s @res 1e-10 mixed vs FP64; dslash GB/s vs HBM peak; p50/p99 latency"
+
+WORKLOADS = {
+    # 64x32^3, eps 0.15, kappa 0.1266, csw 1.9, 4^4 blocks, Nv 24 (FP16 basis),
+    # 96 sources: 48 point (4 sites x 12 spin-colour) + 48 Z2
+    "c4": dict(L=(64, 32, 32, 32), eps=0.15, kappa=0.1266, csw=1.9, block=(4, 4, 4, 4), nv=24, sub_store="fp16",
+               coarse_store="bf16", n_smooth=5, n_cg=60, n_sources=96, n_point=48, group=16, cfg=4),
+    # 32x16^3, eps 0.2, kappa 0.125, csw 1.7, 4^4 blocks, Nv 16: single-RHS solves
+    "c2": dict(L=(32, 16, 16, 16), eps=0.2, kappa=0.125, csw=1.7, block=(4, 4, 4, 4), nv=16, sub_store="fp32",
+               coarse_store="bf16", n_smooth=5, n_cg=60, n_sources=64, n_point=0, group=1, cfg=2),
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), float(p["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def sources(w, first, count):
+    """Sources first .. first+count-1 of the workload: point sources first
+    (sites drawn from the seed, 12 spin-colour columns each), then Z2 noise."""
+    import synthetic
+    L = w["L"]
+    seed = 3000 + w["cfg"]
+    out = np.empty((count,) + tuple(L) + (4, 3), dtype=np.complex128)
+    for i in range(count):
+        k = (first + i) % w["n_sources"]
+        if k < w["n_point"]:
+            site = int(synthetic.point_source_sites(L, w["n_point"] // 12, seed)[k // 12])
+            out[i] = 0
+            out[i].reshape(-1, 12)[site, k % 12] = 1.0
+        else:
+            out[i] = synthetic.z2_noise(L, 1, seed, first_rhs=k - w["n_point"])[0]
+    return out
+
+
+class Clocks:
+    """nvidia-smi sampling in the background during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+                power.append(float(p[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s, pw in zip(sm, power) if pw > 200] or sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+KINDS = ("dslash64", "dslash32", "blas", "reduce", "restrict", "prolong", "coarse", "pack", "setup", "scalar")
+
+
+def profile_snapshot(m, ctx):
+    out = {}
+    for k in KINDS:
+        try:
+            out[k] = m.mglma_profile_get(ctx, k)
+        except Exception:
+            pass
+    return out
+
+
+def cpu_baseline(w, gpu_cgne_iters, budget_slices=4):
+    """The FP64 oracle on the host cores: plain CG on the normal equations
+    (the oracle's solver), timed for two iterations on a budget_slices x
+    L1 x L2 x L3 slab of the same operator and extrapolated to one full
+    solve: per-iteration time x (V / V_slab) x the iteration count the GPU's
+    FP64 CGNE needed on this workload.  The clover build is set-up, untimed
+    (as the GPU's gauge load is)."""
+    import synthetic
+    from oracle import dirac as D
+    from oracle import solvers as S
+    L = (budget_slices,) + tuple(w["L"][1:])
+    U = synthetic.gauge_links(L, w["eps"], 1000 + w["cfg"])
+    A = D.clover_matrix(U, w["kappa"], w["csw"])
+    b = synthetic.z2_noise(L, 1, 3000 + w["cfg"])[0]
+    t0 = time.perf_counter()
+    S.solve_fine(U, b, w["kappa"], w["csw"], tol=1e-300, maxiter=2, A=A)
+    t_iter = (time.perf_counter() - t0) / 2
+    scale = np.prod(w["L"]) / np.prod(L)
+    t_solve = t_iter * scale * gpu_cgne_iters
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"2 FP64 CGNE iterations of the numpy oracle on a {'x'.join(map(str, L))} slab "
+                       f"({t_iter:.2f} s/iteration), scaled by volume x{scale:.0f} and by the "
+                       f"{gpu_cgne_iters} iterations the GPU FP64 CGNE took")}
+
+
+def run_reference(args, w):
+    """The reference arm: the oracle itself, each step a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    iters = 720 if args.workload == "c4" else 460  # FP64 CGNE counts measured on the GPU for these workloads
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, iters, budget_slices=2)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = float(np.mean(vals))
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "lattice": "x".join(map(str, w["L"]))},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}, "vs_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mglma", choices=["mglma", "reference"])
+    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS))
+    ap.add_argument("--group", type=int, default=0, help="sources per step (default: the workload's)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-solver sample")
+    args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload])
+    if args.group:
+        w["group"] = args.group
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import paper_2412_06347_gb300 as m
+    import synthetic
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hbm, _, _, peak_kind = peaks()
+
+    prec = {"fp16": m.MGLMA_FP16, "fp32": m.MGLMA_FP32, "fp64": m.MGLMA_FP64, "bf16": m.MGLMA_BF16}
+    L = w["L"]
+    V = int(np.prod(L))
+    G = w["group"]
+    ctx = m.Context(local)
+    U = synthetic.gauge_links(L, w["eps"], 1000 + w["cfg"])
+    g = m.mglma_gauge_load(ctx, L, U, w["kappa"], w["csw"])
+    del U
+    sub = m.mglma_subspace_create(ctx, g, w["block"], w["nv"], w["n_smooth"], 2000 + w["cfg"], prec[w["sub_store"]],
+                                  n_cg=w["n_cg"], cg_prec=m.MGLMA_FP32)
+    C = m.mglma_coarse_build(ctx, g, sub, prec[w["coarse_store"]])
+    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG)
+    stream = torch.cuda.Stream(device=dev)
+
+    nsteps = args.warmup + args.steps
+    # every rank solves its own sources (replicas): rank r starts at source r*G*steps
+    base = rank * G * nsteps
+    host_b = [sources(w, base + i * G, G) for i in range(nsteps)]
+    dev_b = [torch.from_numpy(b).to(dev) for b in host_b]
+    dev_x = torch.zeros_like(dev_b[0])
+
+    def step(i, b, x):
+        st, stats = m.mglma_solve_batch(ctx, g, C, prm, [G], b, x, stream=stream, raise_on_error=False)
+        if st not in (0, 5):
+            raise m.MglmaError(st, m.mglma_last_error())
+        return stats
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(i, dev_b[i], dev_x)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    # ---- timed region: sources resident in HBM
+    clocks = Clocks(local)
+    clocks.start()
+    m.mglma_profile(ctx, True, True)
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    all_stats = []
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for i in range(args.warmup, nsteps):
+        all_stats += step(i, dev_b[i], dev_x)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    ms = t_start.elapsed_time(t_end)
+    clk = clocks.stop()
+    prof = profile_snapshot(m, ctx)
+    m.mglma_profile(ctx, False, True)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    solves = G * args.steps * world
+    value = solves / (ms / 1e3)
+    resid = max(s["residual"] for s in all_stats)
+    iters = [s["iterations"] for s in all_stats]
+
+    # ---- end to end: pinned host buffers, copies inside the timed region
+    pin_b = [torch.from_numpy(b).pin_memory() for b in host_b[args.warmup:]]
+    pin_x = torch.zeros_like(pin_b[0]).pin_memory()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for b in pin_b:
+        step(0, b, pin_x)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": solves / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": G * V * 24 * 8,
+           "d2h_bytes_per_step": G * V * 24 * 8}
+
+    # ---- roofline of the dominant kernel class in the timed region
+    top = max(((k, v) for k, v in prof.items() if k != "setup"), key=lambda kv: kv[1][1])
+    kname, (kl, kms, kbytes, kflops) = top
+    achieved = kbytes / (kms / 1e3) / 1e9
+    share = {k: round(v[1] / ms, 4) for k, v in prof.items() if v[0]}
+    dsl = prof.get("dslash32", (0, 0, 0, 0))
+    roofline = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs", "launches": kl, "avg_launch_ms": kms / max(kl, 1),
+                "time_share": share,
+                "dslash32": {"achieved": round(dsl[2] / (dsl[1] / 1e3) / 1e9, 1) if dsl[1] else None,
+                             "frac": round(dsl[2] / (dsl[1] / 1e3) / 1e9 / hbm, 4) if dsl[1] else None,
+                             "launches": dsl[0]}}
+    launches = sum(v[0] for v in prof.values()) + prof.get("reduce", (0,))[0]  # reductions are two kernels
+
+    # ---- plain FP64 solver on the GPU (bounded sample: one source)
+    fp64 = None
+    cg_iters = 720 if args.workload == "c4" else 460
+    if not args.no_fp64 and rank == 0:
+        pc = m.mglma_solve_params_default(m.MGLMA_SOLVER_CGNE)
+        b1 = dev_b[0][:1].contiguous()
+        x1 = torch.zeros_like(b1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, s1 = m.mglma_solve_batch(ctx, g, None, pc, [1], b1, x1, stream=stream, raise_on_error=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t1 = e0.elapsed_time(e1) / 1e3
+        cg_iters = s1[0]["iterations"]
+        fp64 = {"value": 1.0 / t1, "unit": "solves/s", "iterations": cg_iters, "residual": s1[0]["residual"],
+                "sample": "first source of the workload, FP64 CG on the normal equations"}
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        cpu = cpu_baseline(w, cg_iters)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer / bf16 coarse",
+            "data": "synthetic (seeded SU(3) links, point + Z2 sources)",
+            "config": {"workload": args.workload, "lattice": "x".join(map(str, L)), "eps": w["eps"],
+                       "kappa": w["kappa"], "csw": w["csw"], "block": "x".join(map(str, w["block"])),
+                       "Nv": w["nv"], "basis": w["sub_store"], "coarse_operator": w["coarse_store"],
+                       "setup": f"{w['n_smooth']} MR + {w['n_cg']} CG relaxation steps",
+                       "rhs_per_step": G, "global_batch": G * world, "tol": 1e-10,
+                       "l2": "inputs larger than L2 (each source 0.4 GB)", "parallelism": f"replicas x{world}"},
+            "residual_max": resid, "fgcr_iterations": [min(iters), max(iters)],
+            "e2e": e2e, "roofline": roofline, "gpu_launches": launches, "clocks": clk,
+            "fp64_plain": fp64,
+            "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    m.mglma_coarse_free(C)
+    m.mglma_subspace_free(sub)
+    m.mglma_gauge_free(g)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -90,10 +90,14 @@ const char* mglma_version(void);
 /* Per-kernel timing with CUDA events on the launching stream (off by
  * default).  enable = 1 starts collecting, 0 stops; reset clears. */
 mglma_status mglma_profile(mglma_ctx ctx, int enable, int reset);
-/* Fetches the accumulated launches and milliseconds of kernel class `name`
- * ("dslash64", "dslash32", "blas", "reduce", "restrict", "prolong",
- * "coarse", "pack", "setup").  Synchronises the context stream. */
-mglma_status mglma_profile_get(mglma_ctx ctx, const char* name, long long* launches, double* ms);
+/* Fetches the accumulated launches, milliseconds, algorithmic bytes and
+ * algorithmic flops of kernel class `name` ("dslash64", "dslash32", "blas",
+ * "reduce", "restrict", "prolong", "coarse", "pack", "setup").  Algorithmic
+ * bytes count every operand read once and every result written once (for
+ * the stencil: links, clover, input and output spinors).  Waits for the
+ * recorded events.  Any output pointer may be NULL. */
+mglma_status mglma_profile_get(mglma_ctx ctx, const char* name, long long* launches, double* ms, double* bytes,
+                               double* flops);
 
 /* ---------------------------------------------------------------- gauge field */
 /* Loads links and builds everything the operator needs: reconstruct-12 FP32
@@ -128,14 +132,31 @@ mglma_status mglma_dirac_apply(mglma_ctx ctx, mglma_gauge g, mglma_op op, int nr
  *      dividing L) and chirality alpha, orthonormalised per (block, alpha) --
  *      the unique factor with positive real R that Gram-Schmidt gives -- in
  *      FP64.
- * store: MGLMA_FP64 (keeps the FP64 basis: FP64 R0/T0 and export work),
- *   MGLMA_FP32, or MGLMA_FP16 (one FP32 scale per (block, alpha, c)); the
- *   FP64 basis is kept until mglma_coarse_build in every case.
+ * store: the copy the FP32 solvers read: MGLMA_FP64 or MGLMA_FP32 (FP32
+ *   basis), or MGLMA_FP16 (one FP32 scale per (block, alpha, c)).  The FP64
+ *   basis is always kept (FP64 R0/T0, coarse build, export).
  * Returns MGLMA_ERR_RANK when a vector's remaining norm falls below 1e-6 of
  * its starting norm inside a block (the paper assumes full rank, App.
  * chirality). */
 mglma_status mglma_subspace_build(mglma_ctx ctx, mglma_gauge g, const int block[4], int nv, int n_smooth,
                                   uint64_t seed, mglma_prec store, mglma_subspace* out);
+/* The same with the full set-up recipe: after the n_smooth MR steps each
+ * vector takes n_cg conjugate-gradient steps on the normal equations of
+ * D x = 0 (in cg_prec arithmetic, FP64 or FP32), which filters it towards the
+ * low right singular vectors of D -- the low modes of Q (App. chirality) that
+ * the paper's basis is built from.  mglma_subspace_build is this call with
+ * n_cg = 0. */
+typedef struct {
+  int block[4];
+  int nv;
+  int n_smooth;
+  int n_cg;
+  int cg_prec;
+  uint64_t seed;
+  int store;
+} mglma_subspace_params;
+mglma_status mglma_subspace_create(mglma_ctx ctx, mglma_gauge g, const mglma_subspace_params* params,
+                                   mglma_subspace* out);
 /* Same from caller-provided test vectors (e.g. exact low modes, Sec. 3):
  * vecs = nv canonical spinors (host or device). */
 mglma_status mglma_subspace_load(mglma_ctx ctx, mglma_gauge g, const int block[4], int nv, const double* vecs,

@@ -5,7 +5,9 @@ infrastructure only).
   (Sec. 3) and states that inexact modes work the same way (Sec. 3, opening
   paragraphs; Sec. conclusion).  The reading used here: N_v random starts, each
   relaxed by ``n_smooth`` minimal-residual steps on D v = 0
-  (r = -D v; alpha = <D r, r> / <D r, D r>; v += alpha r; r -= alpha D r).
+  (r = -D v; alpha = <D r, r> / <D r, D r>; v += alpha r; r -= alpha D r),
+  optionally followed by ``n_cg`` CG steps on the normal equations of
+  D x = 0 (``cg_relax``), which filter towards the low modes of Q.
 * Chirality-split block fields (Eq. mg_basis): u_{alpha c}^{B_y} =
   P_alpha theta_{B_y} v_c, orthonormalised inside each block and chirality by
   Gram-Schmidt (modified Gram-Schmidt, two passes, then normalisation; a
@@ -57,6 +59,31 @@ def mr_smooth(U, v, kappa, csw, n_smooth, bc_t=-1.0, A=None) -> np.ndarray:
     return v
 
 
+def cg_relax(U, v, kappa, csw, n_cg, bc_t=-1.0, A=None) -> np.ndarray:
+    """n_cg conjugate-gradient steps on the normal equations of D x = 0 from
+    x0 = v (one field): the iterate minimises ||D x|| over x0 + Krylov space,
+    so it keeps mostly the low right singular vectors of D, which App.
+    chirality identifies with the low modes of Q.  Fixed step count, no
+    stopping test."""
+    if A is None:
+        A = _d.clover_matrix(U, kappa, csw)
+    x = v.copy()
+    r = -_d.dirac(U, x, kappa, csw, bc_t, A)
+    z = _d.dirac_dagger(U, r, kappa, csw, bc_t, A)
+    p = z.copy()
+    zz = inner(z, z).real
+    for _ in range(n_cg):
+        w = _d.dirac(U, p, kappa, csw, bc_t, A)
+        a = zz / inner(w, w).real
+        x += a * p
+        r -= a * w
+        z = _d.dirac_dagger(U, r, kappa, csw, bc_t, A)
+        zz_new = inner(z, z).real
+        p = z + (zz_new / zz) * p
+        zz = zz_new
+    return x
+
+
 def block_gram_schmidt(u: np.ndarray) -> np.ndarray:
     """Orthonormalise the rows u[c] (vectors) in order c = 0, 1, ...:
     two passes of modified Gram-Schmidt against the finished phi_j, j < c,
@@ -93,10 +120,22 @@ def build_basis(vecs: np.ndarray, L, b) -> np.ndarray:
     return phi
 
 
-def subspace(U, starts, kappa, csw, b, n_smooth, bc_t=-1.0) -> np.ndarray:
-    """Test vectors from random starts (smoothing) then the block basis."""
+def make_test_vectors(U, starts, kappa, csw, n_smooth, n_cg=0, bc_t=-1.0) -> np.ndarray:
+    """Random starts -> n_smooth MR steps -> n_cg CG steps on D x = 0."""
     A = _d.clover_matrix(U, kappa, csw)
-    vecs = np.stack([mr_smooth(U, s, kappa, csw, n_smooth, bc_t, A) for s in starts])
+    out = []
+    for s in starts:
+        v = mr_smooth(U, s, kappa, csw, n_smooth, bc_t, A)
+        if n_cg:
+            v = cg_relax(U, v, kappa, csw, n_cg, bc_t, A)
+        out.append(v)
+    return np.stack(out)
+
+
+def subspace(U, starts, kappa, csw, b, n_smooth, bc_t=-1.0, n_cg=0) -> np.ndarray:
+    """Test vectors from random starts (smoothing, relaxation), then the block
+    basis."""
+    vecs = make_test_vectors(U, starts, kappa, csw, n_smooth, n_cg, bc_t)
     return build_basis(vecs, U.shape[:4], b)
 
 

@@ -53,7 +53,8 @@ _sig("mglma_destroy", None, _vp)
 _sig("mglma_last_error", C.c_char_p)
 _sig("mglma_version", C.c_char_p)
 _sig("mglma_profile", C.c_int, _vp, C.c_int, C.c_int)
-_sig("mglma_profile_get", C.c_int, _vp, C.c_char_p, C.POINTER(C.c_longlong), C.POINTER(C.c_double))
+_sig("mglma_profile_get", C.c_int, _vp, C.c_char_p, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+     C.POINTER(C.c_double), C.POINTER(C.c_double))
 _sig("mglma_gauge_load", C.c_int, _vp, C.POINTER(mglma_lattice), _vp, _i64, _i64, C.c_double, C.c_double,
      C.POINTER(_vp))
 _sig("mglma_gauge_free", None, _vp)
@@ -62,6 +63,12 @@ _sig("mglma_dirac_apply", C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int
 _sig("mglma_debug_tables", C.c_int, _vp, C.POINTER(C.c_int), _vp, _vp)
 _sig("mglma_subspace_build", C.c_int, _vp, _vp, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_uint64, C.c_int,
      C.POINTER(_vp))
+class mglma_subspace_params(C.Structure):
+    _fields_ = [("block", C.c_int * 4), ("nv", C.c_int), ("n_smooth", C.c_int), ("n_cg", C.c_int),
+                ("cg_prec", C.c_int), ("seed", C.c_uint64), ("store", C.c_int)]
+
+
+_sig("mglma_subspace_create", C.c_int, _vp, _vp, C.POINTER(mglma_subspace_params), C.POINTER(_vp))
 _sig("mglma_subspace_load", C.c_int, _vp, _vp, C.POINTER(C.c_int), C.c_int, _vp, C.c_int, C.POINTER(_vp))
 _sig("mglma_subspace_free", None, _vp)
 _sig("mglma_subspace_info", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_i64))
@@ -163,10 +170,11 @@ def mglma_profile(ctx, enable: bool, reset: bool = False):
 
 
 def mglma_profile_get(ctx, name: str):
+    """(launches, milliseconds, algorithmic bytes, algorithmic flops) of a kernel class."""
     n = C.c_longlong()
-    ms = C.c_double()
-    _check(lib.mglma_profile_get(_h(ctx), name.encode(), C.byref(n), C.byref(ms)))
-    return n.value, ms.value
+    ms, by, fl = C.c_double(), C.c_double(), C.c_double()
+    _check(lib.mglma_profile_get(_h(ctx), name.encode(), C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)))
+    return n.value, ms.value, by.value, fl.value
 
 
 def mglma_gauge_load(ctx, L, links, kappa, csw, t_bc=-1, t_begin=0, t_count=None, gauge=None):
@@ -208,6 +216,13 @@ def mglma_subspace_build(ctx, g, block, nv, n_smooth, seed, store=MGLMA_FP32):
     h = _vp()
     _check(lib.mglma_subspace_build(_h(ctx), g, _block(block), int(nv), int(n_smooth), int(seed), int(store),
                                     C.byref(h)))
+    return h.value
+
+
+def mglma_subspace_create(ctx, g, block, nv, n_smooth, seed, store=MGLMA_FP32, n_cg=0, cg_prec=MGLMA_FP64):
+    p = mglma_subspace_params(_block(block), int(nv), int(n_smooth), int(n_cg), int(cg_prec), int(seed), int(store))
+    h = _vp()
+    _check(lib.mglma_subspace_create(_h(ctx), g, C.byref(p), C.byref(h)))
     return h.value
 
 

@@ -188,7 +188,7 @@ mglma_status axpby(mglma_ctx ctx, const double2* a, double2 a_def, const Vec& x,
                    Vec& y, cudaStream_t s, double sign) {
   if (x.prec != y.prec || x.n != y.n || x.nrhs != y.nrhs) return fail(MGLMA_ERR_INVALID, "axpby: mismatch");
   if (y.nrhs == 0) return MGLMA_OK;
-  ProfScope ps(ctx, K_BLAS, s);
+  ProfScope ps(ctx, K_BLAS, s, 3.0 * y.bytes());
   const size_t m = pairs(y);
   dim3 g = ew_grid(ctx, m, y.nrhs);
   if (y.prec == MGLMA_FP64)
@@ -206,7 +206,7 @@ mglma_status caxpy(mglma_ctx ctx, const double2* a, const Vec& x, Vec& y, cudaSt
 mglma_status axpy2(mglma_ctx ctx, const double2* a, const Vec& p, Vec& x, const Vec& w, Vec& r, cudaStream_t s) {
   if (p.prec != x.prec || w.prec != r.prec || p.prec != w.prec || p.n != w.n)
     return fail(MGLMA_ERR_INVALID, "axpy2: mismatch");
-  ProfScope ps(ctx, K_BLAS, s);
+  ProfScope ps(ctx, K_BLAS, s, 6.0 * p.bytes());
   const size_t m = pairs(p);
   dim3 g = ew_grid(ctx, m, p.nrhs);
   if (p.prec == MGLMA_FP64)
@@ -222,7 +222,7 @@ mglma_status axpy2(mglma_ctx ctx, const double2* a, const Vec& p, Vec& x, const 
 mglma_status multi_axpy(mglma_ctx ctx, const Vec& x0, size_t jstride_reals, int k, Vec& y, const double2* c,
                         cudaStream_t s) {
   if (k == 0) return MGLMA_OK;
-  ProfScope ps(ctx, K_BLAS, s);
+  ProfScope ps(ctx, K_BLAS, s, (k + 2.0) * y.bytes());
   const size_t m = pairs(y);
   dim3 g = ew_grid(ctx, m, y.nrhs);
   if (y.prec == MGLMA_FP64)
@@ -260,7 +260,7 @@ template <bool NORM>
 static mglma_status reduce_impl(mglma_ctx ctx, const Vec& x0, size_t jstride_reals, int k, const Vec* y,
                                 double2* out2, double* out1, cudaStream_t s) {
   if (k == 0 || x0.nrhs == 0) return MGLMA_OK;
-  ProfScope ps(ctx, K_REDUCE, s);
+  ProfScope ps(ctx, K_REDUCE, s, (NORM ? 1.0 : k + 1.0) * x0.bytes());
   const size_t m = pairs(x0);
   const int nb = reduce_blocks(ctx, m, x0.nrhs);
   double2* part = nullptr;

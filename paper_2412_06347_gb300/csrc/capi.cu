@@ -20,8 +20,10 @@ mglma_status fail(mglma_status st, const std::string& msg) {
 }
 
 static const char* kKindNames[K_NKINDS] = {"dslash64", "dslash32", "blas",  "reduce", "restrict",
-                                           "prolong",  "coarse",   "pack",  "setup"};
+                                           "prolong",  "coarse",   "pack",  "setup", "scalar"};
 const char* kernel_kind_name(int k) { return (k >= 0 && k < K_NKINDS) ? kKindNames[k] : "?"; }
+
+void resolve_profile(mglma_ctx ctx);
 
 static cudaEvent_t take_event(mglma_ctx ctx) {
   if (!ctx->event_cache.empty()) {
@@ -34,7 +36,8 @@ static cudaEvent_t take_event(mglma_ctx ctx) {
   return e;
 }
 
-ProfScope::ProfScope(mglma_ctx c, int k, cudaStream_t st) : ctx(c), kind(k), s(st) {
+ProfScope::ProfScope(mglma_ctx c, int k, cudaStream_t st, double bytes_, double flops_)
+    : ctx(c), kind(k), s(st), bytes(bytes_), flops(flops_) {
   if (ctx && ctx->profile) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cs);
@@ -48,29 +51,20 @@ ProfScope::ProfScope(mglma_ctx c, int k, cudaStream_t st) : ctx(c), kind(k), s(s
 ProfScope::~ProfScope() {
   if (a) {
     cudaEventRecord(b, s);
-    ctx->pending.push_back({kind, a, b});
-    if (ctx->pending.size() > 4096) {  // resolve in batches to bound the list
-      for (auto& p : ctx->pending) {
-        cudaEventSynchronize(p.b);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, p.a, p.b);
-        ctx->stats[p.kind].launches += 1;
-        ctx->stats[p.kind].ms += ms;
-        ctx->event_cache.push_back(p.a);
-        ctx->event_cache.push_back(p.b);
-      }
-      ctx->pending.clear();
-    }
+    ctx->pending.push_back({kind, a, b, bytes, flops});
+    if (ctx->pending.size() > 4096) resolve_profile(ctx);  // bound the list
   }
 }
 
-static void resolve_profile(mglma_ctx ctx) {
+void resolve_profile(mglma_ctx ctx) {
   for (auto& p : ctx->pending) {
     cudaEventSynchronize(p.b);
     float ms = 0;
     cudaEventElapsedTime(&ms, p.a, p.b);
     ctx->stats[p.kind].launches += 1;
     ctx->stats[p.kind].ms += ms;
+    ctx->stats[p.kind].bytes += p.bytes;
+    ctx->stats[p.kind].flops += p.flops;
     ctx->event_cache.push_back(p.a);
     ctx->event_cache.push_back(p.b);
   }
@@ -206,18 +200,23 @@ mglma_status mglma_profile(mglma_ctx ctx, int enable, int reset) {
     for (int k = 0; k < K_NKINDS; ++k) {
       ctx->stats[k].launches = 0;
       ctx->stats[k].ms = 0;
+      ctx->stats[k].bytes = 0;
+      ctx->stats[k].flops = 0;
     }
   ctx->profile = enable != 0;
   return MGLMA_OK;
 }
 
-mglma_status mglma_profile_get(mglma_ctx ctx, const char* name, long long* launches, double* ms) {
+mglma_status mglma_profile_get(mglma_ctx ctx, const char* name, long long* launches, double* ms, double* bytes,
+                               double* flops) {
   if (!ctx || !name) return fail(MGLMA_ERR_INVALID, "mglma_profile_get: NULL argument");
   resolve_profile(ctx);
   for (int k = 0; k < K_NKINDS; ++k)
     if (ctx->stats[k].name == name) {
       if (launches) *launches = ctx->stats[k].launches;
       if (ms) *ms = ctx->stats[k].ms;
+      if (bytes) *bytes = ctx->stats[k].bytes;
+      if (flops) *flops = ctx->stats[k].flops;
       return MGLMA_OK;
     }
   return fail(MGLMA_ERR_INVALID, std::string("mglma_profile_get: unknown kernel class ") + name);

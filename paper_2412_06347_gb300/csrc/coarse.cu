@@ -218,7 +218,12 @@ static mglma_status launch_capply(const AT* A, const void* X, void* Y, const mgl
 mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X, void* Y, int nrhs, int prec,
                           bool dagger, cudaStream_t s) {
   if (nrhs == 0) return MGLMA_OK;
-  ProfScope ps(ctx, K_COARSE, s);
+  // algorithmic traffic: the operator once (9 (2Nv)^2 complex per coarse
+  // site) plus each RHS's input and output once; 8 flops per complex MAC
+  const double V1 = (double)Cc->geo.V1, n2 = Cc->n2, N = nrhs;
+  const double ca = prec == MGLMA_FP64 ? 16.0 : (Cc->A16 ? 4.0 : (Cc->A32 ? 8.0 : 16.0));
+  const double cf = prec == MGLMA_FP64 ? 16.0 : 8.0;
+  ProfScope ps(ctx, K_COARSE, s, V1 * (9.0 * n2 * n2 * ca + 2.0 * N * n2 * cf), V1 * 9.0 * n2 * n2 * 8.0 * N);
   if (prec == MGLMA_FP64) {
     if (!Cc->A64) return fail(MGLMA_ERR_INVALID, "coarse apply: FP64 operator not kept");
     return launch_capply<double, double2, 4>(Cc->A64, X, Y, Cc, nrhs, dagger, s);

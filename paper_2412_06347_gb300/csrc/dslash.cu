@@ -678,8 +678,13 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
   a.bc = (double)G->g.t_bc;
   a.nrhs = in.nrhs;
   a.g5out = gamma5_out ? 1 : 0;
+  // algorithmic traffic per site: links + clover once, spinor in and out once
+  // per RHS (FP32: 4 x 48 B reconstruct-12 links + 288 B clover; FP64: 4 x
+  // 144 B links + 576 B clover); 1896 flops per site per RHS
+  const double V = (double)in.V, N = (double)in.nrhs;
+  const double flops = 1896.0 * V * N;
   if (in.prec == MGLMA_FP64) {
-    ProfScope ps(ctx, K_DSLASH64, s);
+    ProfScope ps(ctx, K_DSLASH64, s, V * (1152.0 + 384.0 * N), flops);
     const int nr = in.nrhs >= 2 ? g_nr64 : 1;
     if (nr == 2)
       dagger ? launch_dslash<double, 2, true>(in, out, G->U64, G->C64, a, s)
@@ -688,7 +693,7 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
       dagger ? launch_dslash<double, 1, true>(in, out, G->U64, G->C64, a, s)
              : launch_dslash<double, 1, false>(in, out, G->U64, G->C64, a, s);
   } else {
-    ProfScope ps(ctx, K_DSLASH32, s);
+    ProfScope ps(ctx, K_DSLASH32, s, V * (480.0 + 192.0 * N), flops);
     int nr = g_nr32;
     if (in.nrhs < nr) nr = in.nrhs >= 2 ? 2 : 1;
     if (nr == 4)

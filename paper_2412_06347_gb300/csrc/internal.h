@@ -71,6 +71,8 @@ struct KernelStat {
   std::string name;
   long long launches = 0;
   double ms = 0.0;
+  double bytes = 0.0;  // algorithmic bytes of the timed launches
+  double flops = 0.0;  // algorithmic flops of the timed launches
 };
 
 }  // namespace mglma
@@ -85,6 +87,7 @@ struct mglma_ctx_s {
   struct Pending {
     int kind;
     cudaEvent_t a, b;
+    double bytes, flops;
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_cache;
@@ -118,7 +121,8 @@ enum KernelKind {
   K_COARSE = 6,
   K_PACK = 7,
   K_SETUP = 8,
-  K_NKINDS = 9
+  K_SCALAR = 9,
+  K_NKINDS = 10
 };
 const char* kernel_kind_name(int k);
 
@@ -127,8 +131,9 @@ struct ProfScope {
   mglma_ctx ctx;
   int kind;
   cudaStream_t s;
+  double bytes, flops;
   cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(mglma_ctx c, int k, cudaStream_t st);
+  ProfScope(mglma_ctx c, int k, cudaStream_t st, double bytes_ = 0, double flops_ = 0);
   ~ProfScope();
 };
 

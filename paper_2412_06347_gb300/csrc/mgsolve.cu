@@ -113,16 +113,25 @@ static mglma_status gcr(mglma_ctx ctx, cudaStream_t s, const OpFn& A, const OpFn
     MG_CHECK(A(Zk, Wk));
     if (k > 0) {
       MG_CHECK(multi_cdot(ctx, W, stride, k, Wk, dots, s));
-      gcr_coef_kernel<<<(k * n + 63) / 64, 64, 0, s>>>(dots, nw, coef, k, n);
+      {
+        ProfScope ps(ctx, K_SCALAR, s);
+        gcr_coef_kernel<<<(k * n + 63) / 64, 64, 0, s>>>(dots, nw, coef, k, n);
+      }
       MG_CHECK(multi_axpy(ctx, W, stride, k, Wk, coef, s));
       MG_CHECK(multi_axpy(ctx, Z, stride, k, Zk, coef, s));
     }
     MG_CHECK(norm2(ctx, Wk, nw + (size_t)k * n, s));
     MG_CHECK(cdot(ctx, Wk, r, num, s));
-    gcr_alpha_kernel<<<nb, tb, 0, s>>>(num, nw + (size_t)k * n, sc.active, a, n);
+    {
+      ProfScope ps(ctx, K_SCALAR, s);
+      gcr_alpha_kernel<<<nb, tb, 0, s>>>(num, nw + (size_t)k * n, sc.active, a, n);
+    }
     MG_CHECK(axpy2(ctx, a, Zk, x, Wk, r, s));
     MG_CHECK(norm2(ctx, r, rr, s));
-    gcr_mask_kernel<<<nb, tb, 0, s>>>(rr, bb, tol2, sc.active, n);
+    {
+      ProfScope ps(ctx, K_SCALAR, s);
+      gcr_mask_kernel<<<nb, tb, 0, s>>>(rr, bb, tol2, sc.active, n);
+    }
     MG_LAUNCH_CHECK();
     ++it;
     if (poll_every > 0 && (it % poll_every == 0 || it == max_iter)) {

@@ -43,8 +43,24 @@ __global__ void mr_alpha_kernel(const double2* num, const double* den, double2* 
   a[r] = d > 0 ? make_double2(v.x / d, v.y / d) : make_double2(0, 0);
 }
 
-mglma_status mr_alpha(mglma_ctx, const double2* num, const double* den, double2* a, int n, cudaStream_t s) {
+mglma_status mr_alpha(mglma_ctx ctx, const double2* num, const double* den, double2* a, int n, cudaStream_t s) {
+  ProfScope ps(ctx, K_SCALAR, s);
   mr_alpha_kernel<<<(n + 63) / 64, 64, 0, s>>>(num, den, a, n);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status cg_scalars(mglma_ctx ctx, const double* zz, const double* ww, double2* alpha, const int* active, int n,
+                        cudaStream_t s) {
+  ProfScope ps(ctx, K_SCALAR, s);
+  cg_alpha_kernel<<<(n + 63) / 64, 64, 0, s>>>(zz, ww, alpha, active, n);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+mglma_status cg_beta(mglma_ctx ctx, const double* zz_new, double* zz, double2* beta, const int* active, int n,
+                     cudaStream_t s) {
+  ProfScope ps(ctx, K_SCALAR, s);
+  cg_beta_kernel<<<(n + 63) / 64, 64, 0, s>>>(zz_new, zz, beta, active, n);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }
@@ -144,16 +160,15 @@ mglma_status cgne64(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& b, Spin
   };
   MG_CHECK(true_residual());
   MG_CHECK(start());
-  const int tpb = 64, nb = (n + tpb - 1) / tpb;
   int iter = 0, restarts = 0;
   while (true) {
     MG_CHECK(dslash(ctx, G, p, w, false, false, s));
     MG_CHECK(norm2(ctx, vw, ww, s));
-    cg_alpha_kernel<<<nb, tpb, 0, s>>>(zz, ww, alpha, sc.active, n);
+    MG_CHECK(cg_scalars(ctx, zz, ww, alpha, sc.active, n, s));
     MG_CHECK(axpy2(ctx, alpha, vp, vx, vw, vr, s));
     MG_CHECK(dslash(ctx, G, r, z, true, false, s));
     MG_CHECK(norm2(ctx, vz, zzn, s));
-    cg_beta_kernel<<<nb, tpb, 0, s>>>(zzn, zz, beta, sc.active, n);
+    MG_CHECK(cg_beta(ctx, zzn, zz, beta, sc.active, n, s));
     MG_CHECK(axpby(ctx, nullptr, C1, vz, beta, C0, vp, s));  // p = z + beta p
     MG_LAUNCH_CHECK();
     ++iter;

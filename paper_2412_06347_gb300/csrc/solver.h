@@ -56,6 +56,11 @@ constexpr double2 C1 = {1.0, 0.0};
 constexpr double2 CM1 = {-1.0, 0.0};
 constexpr double2 C0 = {0.0, 0.0};
 
+// CG step lengths: alpha = active ? zz / ww : 0 ; beta = active ? zz_new / zz : 0, zz <- zz_new
+mglma_status cg_scalars(mglma_ctx, const double* zz, const double* ww, double2* alpha, const int* active, int n,
+                        cudaStream_t s);
+mglma_status cg_beta(mglma_ctx, const double* zz_new, double* zz, double2* beta, const int* active, int n,
+                     cudaStream_t s);
 // a[r] = <w, r>_r / |w|_r^2 (complex, in place allowed: a may alias num)
 mglma_status mr_alpha(mglma_ctx ctx, const double2* num, const double* den, double2* a, int n, cudaStream_t s);
 

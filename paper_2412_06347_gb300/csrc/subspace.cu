@@ -532,9 +532,18 @@ static mglma_status launch_prolong(const mglma_subspace_s* S, const void* coarse
   return MGLMA_OK;
 }
 
+// algorithmic traffic of R0 / T0: the basis once (2Nv x 6 complex per site
+// in its storage precision) plus the fine and coarse fields once per RHS
+static double transfer_bytes(const mglma_subspace_s* S, int prec, int nrhs) {
+  const double V = (double)S->geo.V, V1 = (double)S->geo.V1, n2 = 2.0 * S->nv, N = nrhs;
+  const double cb = prec == MGLMA_FP64 ? 16.0 : (S->phi16 ? 4.0 : 8.0);
+  const double cf = prec == MGLMA_FP64 ? 16.0 : 8.0;
+  return V * n2 * 6.0 * cb + N * (V * 12.0 * cf + V1 * n2 * cf) + (S->phi16 && prec != MGLMA_FP64 ? V1 * n2 * 4.0 : 0.0);
+}
+
 mglma_status restrict_fine(mglma_ctx ctx, const mglma_subspace_s* S, const Spinor& in, void* out_coarse,
                            cudaStream_t s) {
-  ProfScope ps(ctx, K_RESTRICT, s);
+  ProfScope ps(ctx, K_RESTRICT, s, transfer_bytes(S, in.prec, in.nrhs), 8.0 * S->geo.V * 12.0 * S->nv * in.nrhs);
   if (in.prec == MGLMA_FP64) {
     if (!S->phi64) return fail(MGLMA_ERR_INVALID, "restrict: FP64 needs a subspace stored in FP64");
     return launch_restrict<double, double, 2>(S, in.p, in.nrhs, S->phi64, out_coarse, s);
@@ -545,7 +554,7 @@ mglma_status restrict_fine(mglma_ctx ctx, const mglma_subspace_s* S, const Spino
 
 mglma_status prolong_coarse(mglma_ctx ctx, const mglma_subspace_s* S, const void* in_coarse, Spinor& out,
                             bool accumulate, cudaStream_t s) {
-  ProfScope ps(ctx, K_PROLONG, s);
+  ProfScope ps(ctx, K_PROLONG, s, transfer_bytes(S, out.prec, out.nrhs), 8.0 * S->geo.V * 12.0 * S->nv * out.nrhs);
   if (out.prec == MGLMA_FP64) {
     if (!S->phi64) return fail(MGLMA_ERR_INVALID, "prolong: FP64 needs a subspace stored in FP64");
     return launch_prolong<double, double, 2>(S, in_coarse, out.nrhs, S->phi64, out.p, accumulate, s);
@@ -622,6 +631,40 @@ mglma_status mr_smooth64(mglma_ctx ctx, const mglma_gauge_s* G, Spinor& v, int n
   return MGLMA_OK;
 }
 
+// n_cg CG steps on the normal equations of D x = 0 from x0 = v, all RHS of v
+// at once, fixed step count (no host synchronisation).
+mglma_status cg_relax(mglma_ctx ctx, const mglma_gauge_s* G, Spinor& v, int n_cg, cudaStream_t s) {
+  if (n_cg <= 0) return MGLMA_OK;
+  const int n = v.nrhs;
+  FreeList fr(ctx, s);
+  Spinor r, z, p, w;
+  for (Spinor* f : {&r, &z, &p, &w}) {
+    MG_CHECK(alloc_spinor(ctx, *f, v.prec, n, v.V, s));
+    fr.add(f->p);
+  }
+  Scalars sc;
+  MG_CHECK(sc.alloc(ctx, n, 3, 2, s));
+  double *zz = sc.d, *zzn = sc.d + n, *ww = sc.d + 2 * n;
+  double2 *alpha = sc.z, *beta = sc.z + n;
+  Vec vv = as_vec(v), vr = as_vec(r), vz = as_vec(z), vp = as_vec(p), vw = as_vec(w);
+  MG_CHECK(dslash(ctx, G, v, r, false, false, s));
+  MG_CHECK(axpby(ctx, nullptr, C0, vr, nullptr, CM1, vr, s));  // r = -D v
+  MG_CHECK(dslash(ctx, G, r, z, true, false, s));
+  MG_CHECK(copy_vec(ctx, vz, vp, s));
+  MG_CHECK(norm2(ctx, vz, zz, s));
+  for (int it = 0; it < n_cg; ++it) {
+    MG_CHECK(dslash(ctx, G, p, w, false, false, s));
+    MG_CHECK(norm2(ctx, vw, ww, s));
+    MG_CHECK(cg_scalars(ctx, zz, ww, alpha, sc.active, n, s));
+    MG_CHECK(axpy2(ctx, alpha, vp, vv, vw, vr, s));
+    MG_CHECK(dslash(ctx, G, r, z, true, false, s));
+    MG_CHECK(norm2(ctx, vz, zzn, s));
+    MG_CHECK(cg_beta(ctx, zzn, zz, beta, sc.active, n, s));
+    MG_CHECK(axpby(ctx, nullptr, C1, vz, beta, C0, vp, s));
+  }
+  return MGLMA_OK;
+}
+
 }  // namespace mglma
 
 using namespace mglma;
@@ -653,11 +696,30 @@ static mglma_status subspace_common(mglma_ctx ctx, mglma_gauge G, const int bloc
 
 mglma_status mglma_subspace_build(mglma_ctx ctx, mglma_gauge G, const int block[4], int nv, int n_smooth,
                                   uint64_t seed, mglma_prec store, mglma_subspace* out) {
+  if (!block) return fail(MGLMA_ERR_INVALID, "subspace: NULL block");
+  mglma_subspace_params p;
+  for (int m = 0; m < 4; ++m) p.block[m] = block[m];
+  p.nv = nv;
+  p.n_smooth = n_smooth;
+  p.n_cg = 0;
+  p.cg_prec = MGLMA_FP64;
+  p.seed = seed;
+  p.store = store;
+  return mglma_subspace_create(ctx, G, &p, out);
+}
+
+mglma_status mglma_subspace_create(mglma_ctx ctx, mglma_gauge G, const mglma_subspace_params* prm,
+                                   mglma_subspace* out) {
+  if (!prm) return fail(MGLMA_ERR_INVALID, "subspace: NULL parameters");
+  const int* block = prm->block;
+  const int nv = prm->nv, n_smooth = prm->n_smooth;
+  const uint64_t seed = prm->seed;
+  const mglma_prec store = (mglma_prec)prm->store;
   mglma_subspace_s* S = nullptr;
   MG_CHECK(subspace_common(ctx, G, block, nv, store, &S));
-  if (n_smooth < 0) {
+  if (n_smooth < 0 || prm->n_cg < 0 || (prm->cg_prec != MGLMA_FP64 && prm->cg_prec != MGLMA_FP32)) {
     delete S;
-    return fail(MGLMA_ERR_INVALID, "subspace: n_smooth < 0");
+    return fail(MGLMA_ERR_INVALID, "subspace: bad smoothing parameters");
   }
   MG_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = ctx->stream;
@@ -679,6 +741,18 @@ mglma_status mglma_subspace_build(mglma_ctx ctx, mglma_gauge G, const int block[
     if (cudaGetLastError() != cudaSuccess) st = fail(MGLMA_ERR_CUDA, "random starts launch failed");
   }
   if (st == MGLMA_OK) st = mr_smooth64(ctx, G, v, n_smooth, s);
+  if (st == MGLMA_OK && prm->n_cg > 0) {
+    if (prm->cg_prec == MGLMA_FP64) {
+      st = cg_relax(ctx, G, v, prm->n_cg, s);
+    } else {
+      Spinor v32;
+      st = alloc_spinor(ctx, v32, MGLMA_FP32, nv, G->g.V, s);
+      if (st == MGLMA_OK) st = convert_spinor(ctx, v, v32, s);
+      if (st == MGLMA_OK) st = cg_relax(ctx, G, v32, prm->n_cg, s);
+      if (st == MGLMA_OK) st = convert_spinor(ctx, v32, v, s);
+      dfree(ctx, v32.p, s);
+    }
+  }
   if (st == MGLMA_OK) st = finish_basis(ctx, S, v, s);
   dfree(ctx, v.p, s);
   if (st != MGLMA_OK) {

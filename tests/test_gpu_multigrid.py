@@ -136,3 +136,18 @@ def test_subspace_load_exact_modes_and_rank_error(m, ctx):
         m.mglma_subspace_load(ctx, g, b, nv, bad, m.MGLMA_FP64)
     assert e.value.status == 4
     m.mglma_gauge_free(g)
+
+
+def test_basis_with_cg_relaxation(m, ctx):
+    """Set-up with MR then CG relaxation on D x = 0 (FP64) against the
+    oracle's recipe from the same seeded starts."""
+    L, b, nv, kappa, csw = (8, 4, 4, 8), (2, 2, 2, 4), 4, 0.125, 1.7
+    U = synthetic.gauge_links(L, 0.2, 41)
+    g = m.mglma_gauge_load(ctx, L, U, kappa, csw)
+    sub = m.mglma_subspace_create(ctx, g, b, nv, 3, 42, m.MGLMA_FP64, n_cg=12, cg_prec=m.MGLMA_FP64)
+    ref = MG.subspace(U, synthetic.gaussian_start_vectors(L, nv, 42), kappa, csw, b, 3, n_cg=12)
+    phi = np.zeros_like(ref)
+    m.mglma_subspace_export(sub, phi)
+    assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-10
+    m.mglma_subspace_free(sub)
+    m.mglma_gauge_free(g)

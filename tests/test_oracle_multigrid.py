@@ -192,3 +192,27 @@ def test_eigenvalue_alignment_with_exact_modes():
     wc = np.linalg.eigvalsh(g5[:, None] * MG.dense_coarse(Dhat, Lb))
     for lam in w[order]:
         assert np.min(np.abs(wc - lam)) < 1e-11
+
+
+def test_cg_relaxation_filters_towards_low_modes():
+    """CG on D^dag D x = 0 from a random start: ||D x|| / ||x|| falls with
+    the step count and the iterate's weight moves onto the low modes of Q
+    (App. chirality: the low right singular vectors of D are the low modes of Q)."""
+    L = (4, 2, 2, 2)
+    U = synthetic.gauge_links(L, 0.3, 81)
+    kappa, csw = 0.125, 1.0
+    M = D.dense_dirac(U, kappa, csw)
+    V = lat.volume(L)
+    G5 = np.kron(np.eye(V), np.kron(D.gamma5(), np.eye(3)))
+    w, v = np.linalg.eigh(G5 @ M)
+    low = v[:, np.argsort(np.abs(w))[:12]]
+    x0 = synthetic.gaussian_start_vectors(L, 1, 82)[0]
+    frac, ratio = [], []
+    for n in (0, 5, 20):
+        x = MG.cg_relax(U, x0, kappa, csw, n).reshape(-1)
+        frac.append(np.linalg.norm(low.conj().T @ x) / np.linalg.norm(x))
+        ratio.append(np.linalg.norm(M @ x) / np.linalg.norm(x))
+    assert ratio[0] > ratio[1] > ratio[2]
+    assert frac[0] < frac[1] < frac[2] and frac[2] > 0.8
+    # zero steps is the identity; the step is the CG minimiser along the first direction
+    assert np.array_equal(MG.cg_relax(U, x0, kappa, csw, 0), x0)
