@@ -122,6 +122,30 @@ mglma_status mglma_gauge_info(mglma_gauge g, int L[4], int64_t* volume);
 mglma_status mglma_dirac_apply(mglma_ctx ctx, mglma_gauge g, mglma_op op, int nrhs, const double* in, double* out,
                                mglma_prec compute, void* cuda_stream);
 
+/* Allocation-free variant of mglma_dirac_apply.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need the operator -- code running while a CUDA
+ * graph is being captured, code called from inside an allocator hook, or a
+ * process whose HBM is already fully reserved by another caching allocator.
+ * It computes exactly what mglma_dirac_apply computes, but its two
+ * internal-layout work fields live in one file-scope device array of 32 MiB
+ * that the library holds on every GPU that loads it, until the process
+ * exits; the call makes no cudaMalloc/cudaFree and no allocating library call.
+ *   in, out: DEVICE pointers to nrhs canonical spinors (host pointers are
+ *     rejected with MGLMA_ERR_INVALID: staging them would need memory).
+ *   Limit: 2 x nrhs x V x 24 x (8 for FP64, 4 for FP32) bytes <= 32 MiB,
+ *     i.e. nrhs x V <= 87381 (FP64) or 174762 (FP32); larger requests return
+ *     MGLMA_ERR_INVALID with the sizes in the message.
+ *   The first call on a device looks up the array's device address once
+ *     (cudaGetSymbolAddress with that device current); make that first call
+ *     before any stream capture.
+ *   Every call shares the one array and leaves its last contents there;
+ *     each call overwrites both work fields completely before reading them,
+ *     so no clearing is needed.  Calls that overlap on the GPU (different
+ *     streams, or different host threads) race on the array: serialise them. */
+mglma_status mglma_dirac_apply_noalloc(mglma_ctx ctx, mglma_gauge g, mglma_op op, int nrhs, const double* in,
+                                       double* out, mglma_prec compute, void* cuda_stream);
+
 /* ---------------------------------------------------------------- block basis (Sec. 3, Sec. 4) */
 /* Builds the chirality-split block basis of Eq. mg_basis:
  *   1. nv Gaussian start vectors drawn on the device from the counter-based

@@ -61,6 +61,7 @@ _sig("mglma_gauge_free", None, _vp)
 _sig("mglma_gauge_info", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(_i64))
 _sig("mglma_dirac_apply", C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp)
 _sig("mglma_debug_tables", C.c_int, _vp, C.POINTER(C.c_int), _vp, _vp)
+_sig("mglma_dirac_apply_noalloc", C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp)
 _sig("mglma_subspace_build", C.c_int, _vp, _vp, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_uint64, C.c_int,
      C.POINTER(_vp))
 class mglma_subspace_params(C.Structure):
@@ -201,6 +202,13 @@ def mglma_gauge_info(g):
 def mglma_dirac_apply(ctx, g, op, nrhs, inp, out, compute=MGLMA_FP64, stream=None):
     _check(lib.mglma_dirac_apply(_h(ctx), g, int(op), int(nrhs), ptr(inp), ptr(out), int(compute),
                                  _stream_ptr(stream)))
+
+
+def mglma_dirac_apply_noalloc(ctx, g, op, nrhs, inp, out, compute=MGLMA_FP64, stream=None):
+    """Allocation-free mglma_dirac_apply: device buffers only, nrhs x V
+    bounded by the library's 32 MiB scratch array (see include/mglma.h)."""
+    _check(lib.mglma_dirac_apply_noalloc(_h(ctx), g, int(op), int(nrhs), ptr(inp), ptr(out), int(compute),
+                                         _stream_ptr(stream)))
 
 
 def mglma_debug_tables(g, block, nbr, block_of_site=None):

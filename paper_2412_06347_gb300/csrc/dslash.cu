@@ -15,6 +15,9 @@
 // spinor layout [rhs][chunk][site] makes every 16-byte load of a warp
 // coalesced; neighbours are found arithmetically (no halo, no tables); links
 // are stored reconstruct-12 in FP32 with the third row rebuilt in registers.
+#include <mutex>
+#include <string>
+
 #include "internal.h"
 #include "cplx.cuh"
 #include "lattice.cuh"
@@ -755,4 +758,100 @@ mglma_status debug_tables(mglma_ctx ctx, const mglma_gauge_s* G, const int* bloc
   return MGLMA_OK;
 }
 
+// ============================================================ allocation-free Dirac apply
+// Some callers cannot allocate device memory at the moment they need the
+// operator: code running while a CUDA graph is being captured, code called
+// from inside an allocator hook, or processes whose HBM is already fully
+// reserved by another caching allocator.  mglma_dirac_apply_noalloc serves
+// them: its two internal-layout work fields live in this file-scope device
+// array instead of in pool allocations.  Every GPU that loads the library
+// holds the array until the process exits.
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64] = {nullptr};  // device address of the array, per device
+
+// Once per device, with that device current: the address of the array as the
+// device sees it (the array's name in host code is only a host-side stand-in).
+static mglma_status noalloc_scratch(int device, void** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (device < 0 || device >= 64) return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: device index out of range");
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(MGLMA_ERR_CUDA, std::string("dirac_apply_noalloc: cudaGetSymbolAddress failed: ") +
+                                      cudaGetErrorString(e));
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return MGLMA_OK;
+}
+
 }  // namespace mglma
+
+extern "C" mglma_status mglma_dirac_apply_noalloc(mglma_ctx ctx, mglma_gauge G, mglma_op op, int nrhs,
+                                                  const double* in, double* out, mglma_prec compute,
+                                                  void* cuda_stream) {
+  using namespace mglma;
+  if (!ctx || !G || !in || !out) return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: NULL argument");
+  if (!G->ready) return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: gauge field incomplete");
+  if (nrhs < 0) return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: nrhs < 0");
+  if (op < MGLMA_OP_D || op > MGLMA_OP_DDAGD) return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: bad op");
+  if (compute != MGLMA_FP64 && compute != MGLMA_FP32)
+    return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: compute must be FP64 or FP32");
+  if (nrhs == 0) return MGLMA_OK;
+  const size_t field = (size_t)nrhs * G->g.V * 24 * (compute == MGLMA_FP64 ? 8 : 4);
+  if (2 * field > kNoAllocScratchBytes)
+    return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: nrhs x V too large: two internal fields of " +
+                                       std::to_string(field) + " bytes exceed the " +
+                                       std::to_string(kNoAllocScratchBytes) + "-byte scratch array");
+  MG_CUDA(cudaSetDevice(ctx->device));
+  if (!is_device_pointer(in) || !is_device_pointer(out))
+    return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: in and out must be device memory");
+  void* scratch = nullptr;
+  MG_CHECK(noalloc_scratch(ctx->device, &scratch));
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  // Both work fields are fully overwritten (pack writes a, the stencil writes
+  // b), so nothing in the array needs clearing between calls.
+  Spinor a, b;
+  a.prec = b.prec = compute;
+  a.nrhs = b.nrhs = nrhs;
+  a.V = b.V = G->g.V;
+  a.p = scratch;
+  b.p = static_cast<unsigned char*>(scratch) + ((field + 255) / 256) * 256;
+  DslashArgs da;
+  da.q = make_latidx(G->g.L);
+  da.bc = (double)G->g.t_bc;
+  da.nrhs = nrhs;
+  da.g5out = op == MGLMA_OP_Q ? 1 : 0;
+  const dim3 pg = site_grid(G->g.V, 256, nrhs);
+  const bool dp = compute == MGLMA_FP64;
+  if (dp)
+    pack_kernel<double><<<pg, 256, 0, s>>>(in, a.p, a.V, nrhs);
+  else
+    pack_kernel<float><<<pg, 256, 0, s>>>(in, a.p, a.V, nrhs);
+  const bool dag1 = op == MGLMA_OP_DDAG;
+  if (dp) {
+    dag1 ? launch_dslash<double, 1, true>(a, b, G->U64, G->C64, da, s)
+         : launch_dslash<double, 1, false>(a, b, G->U64, G->C64, da, s);
+  } else {
+    dag1 ? launch_dslash<float, 1, true>(a, b, G->U32, G->C32, da, s)
+         : launch_dslash<float, 1, false>(a, b, G->U32, G->C32, da, s);
+  }
+  const Spinor* res = &b;
+  if (op == MGLMA_OP_DDAGD) {  // second pass D^dag back into a
+    if (dp)
+      launch_dslash<double, 1, true>(b, a, G->U64, G->C64, da, s);
+    else
+      launch_dslash<float, 1, true>(b, a, G->U32, G->C32, da, s);
+    res = &a;
+  }
+  if (dp)
+    unpack_kernel<double><<<pg, 256, 0, s>>>(res->p, out, res->V, nrhs);
+  else
+    unpack_kernel<float><<<pg, 256, 0, s>>>(res->p, out, res->V, nrhs);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
