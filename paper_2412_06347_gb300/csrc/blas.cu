@@ -133,45 +133,129 @@ __device__ __forceinline__ double2 block_sum2(double2 v) {
 
 constexpr int RT = 256;  // reduction threads per block
 
-// stage 1: part[j][r][blk] for j < k of <x_j, y> (DOT) or |x|^2 (NORM, k = 1)
-template <typename R, bool NORM>
-__global__ void __launch_bounds__(RT) reduce1_kernel(const typename Pair<R>::T* __restrict__ x0, size_t jstride, int k,
-                                                     const typename Pair<R>::T* __restrict__ y, size_t m,
-                                                     double2* __restrict__ part, int nrhs) {
+// One launch per reduction: every block writes its partial, the last block
+// of each RHS (atomic ticket) adds the partials in block order and writes the
+// result, then resets the ticket.  Results do not depend on timing.
+// MODE 0: |x|^2 -> out1[r]; 1: <x_j, y> for j < k -> out2[j*n + r];
+// 2: |x|^2 -> out1[r] and <x, y> -> out2[r].
+template <int MODE>
+__device__ __forceinline__ void finish(double2* part, unsigned* count, int k, int nb, int nrhs, double2* out2,
+                                       double* out1) {
+  __shared__ bool last;
   const int r = blockIdx.y;
-  const size_t off = (size_t)r * m;
-  for (int j = 0; j < k; ++j) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(count + r, 1u) == (unsigned)(nb - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int nslot = MODE == 2 ? 2 : k;
+  for (int j = 0; j < nslot; ++j) {
     double2 acc = make_double2(0, 0);
-    const auto* xj = x0 + j * jstride + off;
-    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < m; i += (size_t)gridDim.x * RT) {
-      if (NORM) {
-        acc.x += nrm_pair(xj[i]);
-      } else {
-        double2 d = dot_pair(xj[i], y[off + i]);
+    const double2* pj = part + ((size_t)j * nrhs + r) * nb;
+    for (int i = threadIdx.x; i < nb; i += RT) {
+      const double2 v = __ldcg(pj + i);
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    acc = block_sum2<RT>(acc);
+    if (threadIdx.x == 0) {
+      if (MODE == 0) out1[r] = acc.x;
+      if (MODE == 1) out2[(size_t)j * nrhs + r] = acc;
+      if (MODE == 2) {
+        if (j == 0) out1[r] = acc.x;
+        else out2[r] = acc;
+      }
+    }
+  }
+  if (threadIdx.x == 0) count[r] = 0;
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(RT) reduce_kernel(const typename Pair<R>::T* __restrict__ x0, size_t jstride, int k,
+                                                    const typename Pair<R>::T* __restrict__ y, size_t m,
+                                                    double2* __restrict__ part, unsigned* __restrict__ count,
+                                                    double2* out2, double* out1) {
+  const int r = blockIdx.y, nrhs = gridDim.y, nb = gridDim.x;
+  const size_t off = (size_t)r * m;
+  const size_t step = (size_t)nb * RT;
+  if (MODE == 1) {
+    for (int j = 0; j < k; ++j) {
+      double2 acc = make_double2(0, 0);
+      const auto* xj = x0 + j * jstride + off;
+      size_t i = (size_t)blockIdx.x * RT + threadIdx.x;
+      for (; i + 3 * step < m; i += 4 * step) {
+        const auto a0 = xj[i], a1 = xj[i + step], a2 = xj[i + 2 * step], a3 = xj[i + 3 * step];
+        const auto b0 = y[off + i], b1 = y[off + i + step], b2 = y[off + i + 2 * step], b3 = y[off + i + 3 * step];
+        const double2 d0 = dot_pair(a0, b0), d1 = dot_pair(a1, b1), d2 = dot_pair(a2, b2), d3 = dot_pair(a3, b3);
+        acc.x += (d0.x + d1.x) + (d2.x + d3.x);
+        acc.y += (d0.y + d1.y) + (d2.y + d3.y);
+      }
+      for (; i < m; i += step) {
+        const double2 d = dot_pair(xj[i], y[off + i]);
         acc.x += d.x;
         acc.y += d.y;
       }
+      acc = block_sum2<RT>(acc);
+      if (threadIdx.x == 0) part[((size_t)j * nrhs + r) * nb + blockIdx.x] = acc;
     }
-    acc = block_sum2<RT>(acc);
-    if (threadIdx.x == 0) part[((size_t)j * nrhs + r) * gridDim.x + blockIdx.x] = acc;
+  } else {
+    double nn = 0;
+    double2 dd = make_double2(0, 0);
+    const auto* x = x0 + off;
+    size_t i = (size_t)blockIdx.x * RT + threadIdx.x;
+    for (; i + 3 * step < m; i += 4 * step) {
+      const auto a0 = x[i], a1 = x[i + step], a2 = x[i + 2 * step], a3 = x[i + 3 * step];
+      nn += (nrm_pair(a0) + nrm_pair(a1)) + (nrm_pair(a2) + nrm_pair(a3));
+      if (MODE == 2) {
+        const auto b0 = y[off + i], b1 = y[off + i + step], b2 = y[off + i + 2 * step], b3 = y[off + i + 3 * step];
+        const double2 d0 = dot_pair(a0, b0), d1 = dot_pair(a1, b1), d2 = dot_pair(a2, b2), d3 = dot_pair(a3, b3);
+        dd.x += (d0.x + d1.x) + (d2.x + d3.x);
+        dd.y += (d0.y + d1.y) + (d2.y + d3.y);
+      }
+    }
+    for (; i < m; i += step) {
+      const auto a = x[i];
+      nn += nrm_pair(a);
+      if (MODE == 2) {
+        const double2 d = dot_pair(a, y[off + i]);
+        dd.x += d.x;
+        dd.y += d.y;
+      }
+    }
+    double2 v = block_sum2<RT>(make_double2(nn, 0));
+    if (threadIdx.x == 0) part[(size_t)r * nb + blockIdx.x] = v;
+    if (MODE == 2) {
+      v = block_sum2<RT>(dd);
+      if (threadIdx.x == 0) part[((size_t)nrhs + r) * nb + blockIdx.x] = v;
+    }
   }
+  finish<MODE>(part, count, k, nb, nrhs, out2, out1);
 }
 
-// stage 2: out[j][r] = sum over blocks, fixed order
-__global__ void __launch_bounds__(RT) reduce2_kernel(const double2* __restrict__ part, int nb, double2* out2,
-                                                     double* out1) {
-  const int jr = blockIdx.x;
-  double2 acc = make_double2(0, 0);
-  for (int i = threadIdx.x; i < nb; i += RT) {
-    double2 v = part[(size_t)jr * nb + i];
-    acc.x += v.x;
-    acc.y += v.y;
+// x += a p ; r -= a w ; out1 = |r|^2 (fused GCR / CG update with the new norm)
+template <typename R>
+__global__ void __launch_bounds__(RT) axpy2_norm_kernel(const typename Pair<R>::T* p, typename Pair<R>::T* x,
+                                                        const typename Pair<R>::T* w, typename Pair<R>::T* res,
+                                                        const double2* __restrict__ a, size_t m,
+                                                        double2* __restrict__ part, unsigned* __restrict__ count,
+                                                        double* out1) {
+  const int r = blockIdx.y, nrhs = gridDim.y, nb = gridDim.x;
+  const double2 ar = a[r];
+  const double2 na = make_double2(-ar.x, -ar.y);
+  const double2 one = make_double2(1, 0);
+  const size_t off = (size_t)r * m;
+  double nn = 0;
+  for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < m; i += (size_t)nb * RT) {
+    const auto pv = p[off + i], xv = x[off + i], wv = w[off + i], rv = res[off + i];
+    x[off + i] = lc(pv, xv, ar, one);
+    const auto nr = lc(wv, rv, na, one);
+    res[off + i] = nr;
+    nn += nrm_pair(nr);
   }
-  acc = block_sum2<RT>(acc);
-  if (threadIdx.x == 0) {
-    if (out2) out2[jr] = acc;
-    if (out1) out1[jr] = acc.x;
-  }
+  const double2 v = block_sum2<RT>(make_double2(nn, 0));
+  if (threadIdx.x == 0) part[(size_t)r * nb + blockIdx.x] = v;
+  finish<0>(part, count, 1, nb, nrhs, nullptr, out1);
 }
 
 // --------------------------------------------------------------- host side
@@ -250,46 +334,97 @@ mglma_status zero_vec(mglma_ctx, Vec& y, cudaStream_t s) {
 
 // Blocks per RHS depend on the vector length only, so a RHS's reduction order
 // (and result bits) do not change with the number of RHS in its batch.
-static int reduce_blocks(mglma_ctx, size_t m, int) {
-  size_t want = (m + RT * 4 - 1) / (RT * 4);
-  if (want > 512) want = 512;
+static int reduce_blocks(size_t m) {
+  size_t want = (m + RT * 8 - 1) / (RT * 8);
+  if (want > 592) want = 592;
   return (int)(want < 1 ? 1 : want);
 }
 
-template <bool NORM>
+// Per-stream partial sums and tickets, kept for the life of the context
+// (tickets return to zero after every reduction).
+static mglma_status red_scratch(mglma_ctx ctx, cudaStream_t s, size_t nparts, int ncount, double2** part,
+                                unsigned** count) {
+  auto& R = ctx->red[s];
+  if (R.part_cap < nparts) {
+    if (R.part) cudaFreeAsync(R.part, s);
+    R.part = nullptr;
+    R.part_cap = 0;
+    MG_CHECK(dalloc(ctx, (void**)&R.part, nparts * sizeof(double2), s));
+    R.part_cap = nparts;
+  }
+  if (R.count_cap < ncount) {
+    if (R.count) cudaFreeAsync(R.count, s);
+    R.count = nullptr;
+    R.count_cap = 0;
+    MG_CHECK(dalloc(ctx, (void**)&R.count, ncount * sizeof(unsigned), s));
+    MG_CUDA(cudaMemsetAsync(R.count, 0, ncount * sizeof(unsigned), s));
+    R.count_cap = ncount;
+  }
+  *part = R.part;
+  *count = R.count;
+  return MGLMA_OK;
+}
+
+template <int MODE>
 static mglma_status reduce_impl(mglma_ctx ctx, const Vec& x0, size_t jstride_reals, int k, const Vec* y,
                                 double2* out2, double* out1, cudaStream_t s) {
   if (k == 0 || x0.nrhs == 0) return MGLMA_OK;
-  ProfScope ps(ctx, K_REDUCE, s, (NORM ? 1.0 : k + 1.0) * x0.bytes());
+  ProfScope ps(ctx, K_REDUCE, s, (MODE == 0 ? 1.0 : (MODE == 2 ? 2.0 : k + 1.0)) * x0.bytes());
   const size_t m = pairs(x0);
-  const int nb = reduce_blocks(ctx, m, x0.nrhs);
+  const int nb = reduce_blocks(m);
+  const int nslot = MODE == 2 ? 2 : k;
   double2* part = nullptr;
-  MG_CHECK(dalloc(ctx, (void**)&part, sizeof(double2) * (size_t)nb * x0.nrhs * k, s));
+  unsigned* count = nullptr;
+  MG_CHECK(red_scratch(ctx, s, (size_t)nb * x0.nrhs * nslot, x0.nrhs, &part, &count));
   dim3 g(nb, x0.nrhs, 1);
   if (x0.prec == MGLMA_FP64)
-    reduce1_kernel<double, NORM><<<g, RT, 0, s>>>((const double2*)x0.p, jstride_reals / 2, k,
-                                                  y ? (const double2*)y->p : nullptr, m, part, x0.nrhs);
+    reduce_kernel<double, MODE><<<g, RT, 0, s>>>((const double2*)x0.p, jstride_reals / 2, k,
+                                                 y ? (const double2*)y->p : nullptr, m, part, count, out2, out1);
   else
-    reduce1_kernel<float, NORM><<<g, RT, 0, s>>>((const float4*)x0.p, jstride_reals / 4, k,
-                                                 y ? (const float4*)y->p : nullptr, m, part, x0.nrhs);
-  reduce2_kernel<<<x0.nrhs * k, RT, 0, s>>>(part, nb, out2, out1);
-  dfree(ctx, part, s);
+    reduce_kernel<float, MODE><<<g, RT, 0, s>>>((const float4*)x0.p, jstride_reals / 4, k,
+                                                y ? (const float4*)y->p : nullptr, m, part, count, out2, out1);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }
 
 mglma_status cdot(mglma_ctx ctx, const Vec& x, const Vec& y, double2* out, cudaStream_t s) {
   if (x.prec != y.prec || x.n != y.n || x.nrhs != y.nrhs) return fail(MGLMA_ERR_INVALID, "cdot: mismatch");
-  return reduce_impl<false>(ctx, x, 0, 1, &y, out, nullptr, s);
+  return reduce_impl<1>(ctx, x, 0, 1, &y, out, nullptr, s);
 }
 
 mglma_status multi_cdot(mglma_ctx ctx, const Vec& x0, size_t jstride_reals, int k, const Vec& y, double2* out,
                         cudaStream_t s) {
-  return reduce_impl<false>(ctx, x0, jstride_reals, k, &y, out, nullptr, s);
+  return reduce_impl<1>(ctx, x0, jstride_reals, k, &y, out, nullptr, s);
 }
 
 mglma_status norm2(mglma_ctx ctx, const Vec& x, double* out, cudaStream_t s) {
-  return reduce_impl<true>(ctx, x, 0, 1, nullptr, nullptr, out, s);
+  return reduce_impl<0>(ctx, x, 0, 1, nullptr, nullptr, out, s);
+}
+
+mglma_status norm2_cdot(mglma_ctx ctx, const Vec& x, const Vec& y, double* nrm, double2* dot, cudaStream_t s) {
+  if (x.prec != y.prec || x.n != y.n || x.nrhs != y.nrhs) return fail(MGLMA_ERR_INVALID, "norm2_cdot: mismatch");
+  return reduce_impl<2>(ctx, x, 0, 1, &y, dot, nrm, s);
+}
+
+mglma_status axpy2_norm(mglma_ctx ctx, const double2* a, const Vec& p, Vec& x, const Vec& w, Vec& r, double* rr,
+                        cudaStream_t s) {
+  if (p.prec != x.prec || w.prec != r.prec || p.prec != w.prec || p.n != w.n)
+    return fail(MGLMA_ERR_INVALID, "axpy2_norm: mismatch");
+  ProfScope ps(ctx, K_BLAS, s, 6.0 * p.bytes());
+  const size_t m = pairs(p);
+  const int nb = reduce_blocks(m);
+  double2* part = nullptr;
+  unsigned* count = nullptr;
+  MG_CHECK(red_scratch(ctx, s, (size_t)nb * p.nrhs, p.nrhs, &part, &count));
+  dim3 g(nb, p.nrhs, 1);
+  if (p.prec == MGLMA_FP64)
+    axpy2_norm_kernel<double><<<g, RT, 0, s>>>((const double2*)p.p, (double2*)x.p, (const double2*)w.p,
+                                               (double2*)r.p, a, m, part, count, rr);
+  else
+    axpy2_norm_kernel<float><<<g, RT, 0, s>>>((const float4*)p.p, (float4*)x.p, (const float4*)w.p, (float4*)r.p, a,
+                                              m, part, count, rr);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
 }
 
 }  // namespace mglma

@@ -187,6 +187,11 @@ void mglma_destroy(mglma_ctx ctx) {
   cudaStreamSynchronize(ctx->stream);
   resolve_profile(ctx);
   for (auto e : ctx->event_cache) cudaEventDestroy(e);
+  for (auto& kv : ctx->red) {
+    cudaFreeAsync(kv.second.part, ctx->stream);
+    cudaFreeAsync(kv.second.count, ctx->stream);
+  }
+  cudaStreamSynchronize(ctx->stream);
   cudaStreamDestroy(ctx->stream);
   cudaDeviceSynchronize();
   cudaMemPoolDestroy(ctx->pool);

@@ -221,13 +221,14 @@ mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X
   // algorithmic traffic: the operator once (9 (2Nv)^2 complex per coarse
   // site) plus each RHS's input and output once; 8 flops per complex MAC
   const double V1 = (double)Cc->geo.V1, n2 = Cc->n2, N = nrhs;
-  const double ca = prec == MGLMA_FP64 ? 16.0 : (Cc->A16 ? 4.0 : (Cc->A32 ? 8.0 : 16.0));
+  const double ca = prec == MGLMA_FP64 ? 16.0 : ((Cc->A16 || Cc->Aimg) ? 4.0 : (Cc->A32 ? 8.0 : 16.0));
   const double cf = prec == MGLMA_FP64 ? 16.0 : 8.0;
   ProfScope ps(ctx, K_COARSE, s, V1 * (9.0 * n2 * n2 * ca + 2.0 * N * n2 * cf), V1 * 9.0 * n2 * n2 * 8.0 * N);
   if (prec == MGLMA_FP64) {
     if (!Cc->A64) return fail(MGLMA_ERR_INVALID, "coarse apply: FP64 operator not kept");
     return launch_capply<double, double2, 4>(Cc->A64, X, Y, Cc, nrhs, dagger, s);
   }
+  if (Cc->Aimg) return coarse_apply_tc(ctx, Cc, (const float2*)X, (float2*)Y, nrhs, dagger, s);
   if (Cc->A16) return launch_capply<float, __nv_bfloat162, 8>(Cc->A16, X, Y, Cc, nrhs, dagger, s);
   if (Cc->A32) return launch_capply<float, float2, 8>(Cc->A32, X, Y, Cc, nrhs, dagger, s);
   return launch_capply<float, double2, 8>(Cc->A64, X, Y, Cc, nrhs, dagger, s);
@@ -308,6 +309,8 @@ mglma_status mglma_coarse_build(mglma_ctx ctx, mglma_gauge G, mglma_subspace S, 
     if (store == MGLMA_FP32) {
       e = cudaMalloc(&Cc->A32, na * sizeof(float2));
       if (e == cudaSuccess) a_to32_kernel<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(Cc->A64, Cc->A32, na);
+    } else if (store == MGLMA_BF16 && coarse_tc_supported(n2)) {
+      st = coarse_tc_image(ctx, Cc, s);  // tensor-core operand image
     } else if (store == MGLMA_BF16) {
       e = cudaMalloc(&Cc->A16, na * sizeof(__nv_bfloat162));
       if (e == cudaSuccess) a_to16_kernel<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(Cc->A64, Cc->A16, na);
@@ -330,6 +333,8 @@ void mglma_coarse_free(mglma_coarse Cc) {
   cudaFree(Cc->A64);
   cudaFree(Cc->A32);
   cudaFree(Cc->A16);
+  cudaFree(Cc->Aimg);
+  cudaFree(Cc->tc_err);
   delete Cc;
 }
 
@@ -370,6 +375,7 @@ mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse Cc, int nrhs, const 
   fl.add(Y);
   MG_CHECK(coarse_from_canonical(ctx, si.dev, n, X, compute, s));
   MG_CHECK(coarse_apply(ctx, Cc, X, Y, nrhs, compute, false, s));
+  MG_CHECK(coarse_tc_check(Cc, s));
   MG_CHECK(coarse_to_canonical(ctx, Y, compute, n, so.dev, s));
   MG_CHECK(stage_out_finish(out, n * sizeof(double2), s, so));
   return MGLMA_OK;

@@ -664,7 +664,7 @@ static void launch_dslash(const Spinor& in, Spinor& out, const void* U, const vo
 }
 
 // RHS per thread: chosen by nrhs (tuned values; see the autotuner in solver.cu)
-static int g_nr32 = 2;
+static int g_nr32 = 1;
 static int g_nr64 = 1;
 void set_dslash_nr(int nr32, int nr64) {
   if (nr32 == 1 || nr32 == 2 || nr32 == 4) g_nr32 = nr32;

@@ -77,8 +77,18 @@ struct KernelStat {
 
 }  // namespace mglma
 
+#include <map>
+
 struct mglma_ctx_s {
   int device = 0;
+  // per-stream scratch of the reductions: partial sums and tickets
+  struct RedScratch {
+    double2* part = nullptr;
+    unsigned* count = nullptr;
+    size_t part_cap = 0;
+    int count_cap = 0;
+  };
+  std::map<cudaStream_t, RedScratch> red;
   cudaStream_t stream = nullptr;  // default stream of the context
   cudaMemPool_t pool = nullptr;
   int sm_count = 0;
@@ -224,5 +234,10 @@ mglma_status multi_cdot(mglma_ctx, const Vec& x0, size_t jstride_reals, int k, c
                         cudaStream_t s);
 // out[r] = |x_r|^2
 mglma_status norm2(mglma_ctx, const Vec& x, double* out, cudaStream_t s);
+// nrm[r] = |x_r|^2 and dot[r] = <x_r, y_r> in one pass
+mglma_status norm2_cdot(mglma_ctx, const Vec& x, const Vec& y, double* nrm, double2* dot, cudaStream_t s);
+// x += a p ; r -= a w ; rr[r] = |r_r|^2 in one pass
+mglma_status axpy2_norm(mglma_ctx, const double2* a, const Vec& p, Vec& x, const Vec& w, Vec& r, double* rr,
+                        cudaStream_t s);
 
 }  // namespace mglma

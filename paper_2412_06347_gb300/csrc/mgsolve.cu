@@ -120,14 +120,12 @@ static mglma_status gcr(mglma_ctx ctx, cudaStream_t s, const OpFn& A, const OpFn
       MG_CHECK(multi_axpy(ctx, W, stride, k, Wk, coef, s));
       MG_CHECK(multi_axpy(ctx, Z, stride, k, Zk, coef, s));
     }
-    MG_CHECK(norm2(ctx, Wk, nw + (size_t)k * n, s));
-    MG_CHECK(cdot(ctx, Wk, r, num, s));
+    MG_CHECK(norm2_cdot(ctx, Wk, r, nw + (size_t)k * n, num, s));
     {
       ProfScope ps(ctx, K_SCALAR, s);
       gcr_alpha_kernel<<<nb, tb, 0, s>>>(num, nw + (size_t)k * n, sc.active, a, n);
     }
-    MG_CHECK(axpy2(ctx, a, Zk, x, Wk, r, s));
-    MG_CHECK(norm2(ctx, r, rr, s));
+    MG_CHECK(axpy2_norm(ctx, a, Zk, x, Wk, r, rr, s));
     {
       ProfScope ps(ctx, K_SCALAR, s);
       gcr_mask_kernel<<<nb, tb, 0, s>>>(rr, bb, tol2, sc.active, n);
@@ -300,7 +298,7 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
     MG_CHECK(axpby(ctx, nullptr, CM1, vw, nullptr, C1, vr, s));
   }
   for (int i = 0; i < n; ++i) out[i].coarse_iterations = K.coarse_iters;
-  return MGLMA_OK;
+  return coarse_tc_check(const_cast<mglma_coarse_s*>(C), s);
 }
 
 // X (FP64 coarse, [n][V1][n2]) = D1^-1 b1 to tol by FP64 defect correction

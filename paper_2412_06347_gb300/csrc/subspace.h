@@ -35,6 +35,8 @@ struct mglma_coarse_s {
   double2* A64 = nullptr;        // [V1][9][n2 (j)][n2 (i)] column-major blocks, FP64 master (optional)
   float2* A32 = nullptr;         // same layout, FP32
   __nv_bfloat162* A16 = nullptr; // same layout, BF16 (re, im)
+  uint16_t* Aimg = nullptr;      // BF16 tensor-core image, see coarse_tc.cu
+  int* tc_err = nullptr;         // device error flag of the tensor-core kernel
 };
 
 namespace mglma {
@@ -53,6 +55,12 @@ mglma_status coarse_from_canonical(mglma_ctx ctx, const double* canon, size_t nc
 // dst = scale_r src (+ dst when accumulate) on coarse fields of `per` complex per RHS
 mglma_status coarse_scale_convert(mglma_ctx ctx, const void* src, int sprec, void* dst, int dprec,
                                   const double* scale, size_t per, int nrhs, bool accumulate, cudaStream_t s);
+// tensor-core path (coarse_tc.cu)
+bool coarse_tc_supported(int n2);
+mglma_status coarse_tc_image(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s);
+mglma_status coarse_apply_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float2* X, float2* Y, int nrhs,
+                             bool dagger, cudaStream_t s);
+mglma_status coarse_tc_check(mglma_coarse_s* C, cudaStream_t s);
 // Y = Dhat X for nrhs coarse fields; prec of X/Y: FP64 (FP64 operator) or FP32
 // (FP32 or BF16 operator as stored)
 mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X, void* Y, int nrhs, int prec,

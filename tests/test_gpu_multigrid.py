@@ -151,3 +151,54 @@ def test_basis_with_cg_relaxation(m, ctx):
     assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-10
     m.mglma_subspace_free(sub)
     m.mglma_gauge_free(g)
+
+
+@pytest.mark.parametrize("nrhs", [1, 5, 8, 16, 21, 40])
+def test_coarse_tensor_core_apply(m, ctx, nrhs):
+    """BF16 operator on tcgen05 (FP32 accumulation) for ragged RHS tiles,
+    against the oracle's FP64 stencil application: relative error at the
+    BF16 operand level (<= 2e-2 per RHS)."""
+    L, b, nv, kappa, csw = (8, 8, 4, 8), (2, 2, 2, 2), 8, 0.125, 1.7
+    U = synthetic.gauge_links(L, 0.2, 51)
+    g = m.mglma_gauge_load(ctx, L, U, kappa, csw)
+    sub = m.mglma_subspace_build(ctx, g, b, nv, 2, 52, m.MGLMA_FP64)
+    C = m.mglma_coarse_build(ctx, g, sub, m.MGLMA_BF16)
+    phi = MG.subspace(U, synthetic.gaussian_start_vectors(L, nv, 52), kappa, csw, b, 2)
+    Lb = lat.block_grid(L, b)
+    Dh = MG.coarse_operator(U, phi, kappa, csw, b)
+    X = synthetic.random_coarse(lat.volume(Lb), 2 * nv, nrhs, 53)
+    Y = np.zeros_like(X)
+    m.mglma_coarse_apply(ctx, C, nrhs, X, Y, m.MGLMA_FP32)
+    err = rel_per_rhs(Y, MG.coarse_apply(Dh, X, Lb))
+    assert err.max() < 2e-2 and err.min() > 0
+    m.mglma_coarse_free(C)
+    m.mglma_subspace_free(sub)
+    m.mglma_gauge_free(g)
+
+
+def test_coarse_tensor_core_full_size_properties(m, ctx):
+    """64x32^3 with 4^4 blocks and Nv 24 (8192 coarse sites, 48 dofs): the
+    tensor-core application agrees with the FP64 application of the same
+    operator to BF16 accuracy, and <X, g5 D1 Y> = <g5 D1 X, Y> holds."""
+    L, b, nv = (64, 32, 32, 32), (4, 4, 4, 4), 24
+    U = synthetic.gauge_links(L, 0.15, 1004)
+    g = m.mglma_gauge_load(ctx, L, U, 0.1266, 1.9)
+    del U
+    sub = m.mglma_subspace_build(ctx, g, b, nv, 2, 2004, m.MGLMA_FP16)
+    C = m.mglma_coarse_build(ctx, g, sub, m.MGLMA_BF16)
+    nv_, Lb, V1 = m.mglma_coarse_info(C)
+    X = synthetic.random_coarse(V1, 2 * nv, 3, 61)
+    Y32, Y64 = np.zeros_like(X), np.zeros_like(X)
+    m.mglma_coarse_apply(ctx, C, 3, X, Y32, m.MGLMA_FP32)
+    m.mglma_coarse_apply(ctx, C, 3, X, Y64, m.MGLMA_FP64)
+    assert rel_per_rhs(Y32, Y64).max() < 2e-2
+    g5 = MG.coarse_gamma5(nv)
+    lhs = np.vdot(X[0], g5 * Y64[1])
+    rhs = np.vdot(g5 * Y64[0], X[1])
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    lhs32 = np.vdot(X[0], g5 * Y32[1])
+    rhs32 = np.vdot(g5 * Y32[0], X[1])
+    assert abs(lhs32 - rhs32) <= 2e-2 * abs(lhs32)
+    m.mglma_coarse_free(C)
+    m.mglma_subspace_free(sub)
+    m.mglma_gauge_free(g)
