@@ -193,6 +193,80 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def micro_dslash(m, torch, ctx, g, V, nrhs, prec, reps, stream):
+    """FP32/FP64 stencil on nrhs fields, launch-level timing from the
+    library's CUDA events on the launching stream."""
+    kind = "dslash32" if prec == m.MGLMA_FP32 else "dslash64"
+    x = torch.randn(nrhs, V, 24, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        m.mglma_dirac_apply(ctx, g, 0, nrhs, x, y, prec, stream=stream)
+    torch.cuda.synchronize()
+    m.mglma_profile(ctx, True, True)
+    for _ in range(reps):
+        m.mglma_dirac_apply(ctx, g, 0, nrhs, x, y, prec, stream=stream)
+    n, ms, by, fl = m.mglma_profile_get(ctx, kind)
+    m.mglma_profile(ctx, False, True)
+    return {"kernel": kind, "nrhs": nrhs, "launches": n, "avg_launch_ms": ms / n,
+            "achieved": round(by / (ms / 1e3) / 1e9, 1), "unit": "GB/s",
+            "bytes_per_launch": by / n, "tflops": round(fl / (ms / 1e3) / 1e12, 2)}
+
+
+def run_micro(args, w):
+    """One kernel class alone on the workload lattice (inputs larger than L2)."""
+    import torch
+    import paper_2412_06347_gb300 as m
+    import synthetic
+    hbm, _, _, peak_kind = peaks()
+    L = w["L"]
+    V = int(np.prod(L))
+    ctx = m.Context(0)
+    U = synthetic.gauge_links(L, w["eps"], 1000 + w["cfg"])
+    g = m.mglma_gauge_load(ctx, L, U, w["kappa"], w["csw"])
+    del U
+    stream = torch.cuda.current_stream()
+    reps = max(args.steps, 1)
+    if args.micro in ("dslash32", "dslash64"):
+        prec = m.MGLMA_FP32 if args.micro == "dslash32" else m.MGLMA_FP64
+        r = micro_dslash(m, torch, ctx, g, V, args.nrhs, prec, reps, stream)
+    else:
+        prec = {"fp16": m.MGLMA_FP16, "fp32": m.MGLMA_FP32, "bf16": m.MGLMA_BF16}
+        sub = m.mglma_subspace_build(ctx, g, w["block"], w["nv"], 1, 2000 + w["cfg"], prec[w["sub_store"]])
+        C = m.mglma_coarse_build(ctx, g, sub, prec[w["coarse_store"]])
+        nv, Lb, V1 = m.mglma_coarse_info(C)
+        n = args.nrhs
+        m.mglma_profile(ctx, True, True)
+        if args.micro == "coarse":
+            X = torch.randn(n, V1, 2 * nv, dtype=torch.complex128, device="cuda")
+            Y = torch.empty_like(X)
+            for _ in range(reps):
+                m.mglma_coarse_apply(ctx, C, n, X, Y, m.MGLMA_FP32, stream=stream)
+            kinds = ["coarse"]
+        else:
+            f = torch.randn(n, V, 12, dtype=torch.complex128, device="cuda")
+            c = torch.empty(n, V1, 2 * nv, dtype=torch.complex128, device="cuda")
+            for _ in range(reps):
+                m.mglma_restrict(ctx, sub, n, f, c, m.MGLMA_FP32, stream=stream)
+                m.mglma_prolong(ctx, sub, n, c, f, m.MGLMA_FP32, stream=stream)
+            kinds = ["restrict", "prolong"]
+        r = {}
+        for k in kinds:
+            nl, ms, by, fl = m.mglma_profile_get(ctx, k)
+            r[k] = {"launches": nl, "avg_launch_ms": ms / nl, "achieved": round(by / (ms / 1e3) / 1e9, 1),
+                    "unit": "GB/s", "frac": round(by / (ms / 1e3) / 1e9 / hbm, 4),
+                    "tflops": round(fl / (ms / 1e3) / 1e12, 2)}
+        r = {"kernels": r, "nrhs": n}
+        m.mglma_coarse_free(C)
+        m.mglma_subspace_free(sub)
+    if "achieved" in r:
+        r["frac"] = round(r["achieved"] / hbm, 4)
+    r.update({"micro": args.micro, "workload": args.workload, "lattice": "x".join(map(str, L)), "peak": hbm,
+              "peak_source": f"{peak_kind} hbm_gbs"})
+    print(json.dumps(r), flush=True)
+    m.mglma_gauge_free(g)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -203,12 +277,18 @@ def main():
     ap.add_argument("--group", type=int, default=0, help="sources per step (default: the workload's)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-solver sample")
+    ap.add_argument("--micro", default="", choices=["", "dslash32", "dslash64", "coarse", "transfer"],
+                    help="time one kernel class on the workload lattice instead of the solve")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch in --micro mode")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.group:
         w["group"] = args.group
     if args.impl == "reference":
         run_reference(args, w)
+        return
+    if args.micro:
+        run_micro(args, w)
         return
 
     import torch
@@ -317,6 +397,14 @@ def main():
                              "launches": dsl[0]}}
     launches = sum(v[0] for v in prof.values()) + prof.get("reduce", (0,))[0]  # reductions are two kernels
 
+    # ---- the stencil alone at N = 1 and N = G (the "dslash GB/s vs HBM peak" part of the metric)
+    dslash = {}
+    if rank == 0:
+        for n in (1, G):
+            r = micro_dslash(m, torch, ctx, g, V, n, m.MGLMA_FP32, 20, stream)
+            r["frac"] = round(r["achieved"] / hbm, 4)
+            dslash[f"nrhs{n}"] = r
+
     # ---- plain FP64 solver on the GPU (bounded sample: one source)
     fp64 = None
     cg_iters = 720 if args.workload == "c4" else 460
@@ -351,7 +439,7 @@ def main():
                        "rhs_per_step": G, "global_batch": G * world, "tol": 1e-10,
                        "l2": "inputs larger than L2 (each source 0.4 GB)", "parallelism": f"replicas x{world}"},
             "residual_max": resid, "fgcr_iterations": [min(iters), max(iters)],
-            "e2e": e2e, "roofline": roofline, "gpu_launches": launches, "clocks": clk,
+            "e2e": e2e, "roofline": roofline, "dslash_fp32": dslash, "gpu_launches": launches, "clocks": clk,
             "fp64_plain": fp64,
             "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu,

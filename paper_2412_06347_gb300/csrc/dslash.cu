@@ -274,9 +274,12 @@ __global__ void __launch_bounds__(128) dslash_kernel(const void* __restrict__ in
                                                      const void* __restrict__ U, const void* __restrict__ C,
                                                      DslashArgs a) {
   const int64_t V = a.q.V;
-  const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // RHS tiles run fastest in launch order, so the CTAs that share a block of
+  // sites are resident together and its links and clover come from L2
+  const int ntile = (a.nrhs + NR - 1) / NR;
+  const int64_t site = (int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x;
   if (site >= V) return;
-  const int r0 = blockIdx.y * NR;
+  const int r0 = (blockIdx.x % ntile) * NR;
   int x[4];
   site_coords(a.q, site, x);
   const R sF = DAG ? R(1) : R(-1);  // forward hop carries (1 + sF gamma)
@@ -659,8 +662,8 @@ mglma_status convert_spinor(mglma_ctx ctx, const Spinor& src, Spinor& dst, cudaS
 template <typename R, int NR, bool DAG>
 static void launch_dslash(const Spinor& in, Spinor& out, const void* U, const void* C, const DslashArgs& a,
                           cudaStream_t s) {
-  dim3 grid((unsigned)((in.V + 127) / 128), (unsigned)((in.nrhs + NR - 1) / NR), 1);
-  dslash_kernel<R, NR, DAG><<<grid, 128, 0, s>>>(in.p, out.p, U, C, a);
+  const size_t tiles = (size_t)((in.V + 127) / 128) * ((in.nrhs + NR - 1) / NR);
+  dslash_kernel<R, NR, DAG><<<(unsigned)tiles, 128, 0, s>>>(in.p, out.p, U, C, a);
 }
 
 // RHS per thread: chosen by nrhs (tuned values; see the autotuner in solver.cu)

@@ -224,10 +224,10 @@ void mglma_solve_params_default(mglma_solve_params* p, int method) {
   p->tol = 1e-10;
   p->max_iter = method == MGLMA_SOLVER_CGNE ? 100000 : 4000;
   p->gcr_m = 8;
-  p->nu = 4;
+  p->nu = 2;
   p->inner_tol = 1e-5;
-  p->coarse_tol = 0.05;
-  p->coarse_max_iter = 50;
+  p->coarse_tol = 0.02;
+  p->coarse_max_iter = 100;
   p->check_every = method == MGLMA_SOLVER_CGNE ? 20 : 1;
 }
 

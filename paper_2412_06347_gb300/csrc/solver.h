@@ -68,10 +68,10 @@ struct MgParams {
   double tol = 1e-10;
   int max_iter = 2000;
   int gcr_m = 8;
-  int nu = 4;
+  int nu = 2;
   double inner_tol = 1e-5;
-  double coarse_tol = 0.05;
-  int coarse_max_iter = 50;
+  double coarse_tol = 0.02;
+  int coarse_max_iter = 100;
 };
 
 mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_s* C, const Spinor& b, Spinor& x,

@@ -171,8 +171,10 @@ __global__ void __launch_bounds__(RP_THREADS) restrict_kernel(const void* __rest
                                                               Cx<R>* __restrict__ out) {
   extern __shared__ unsigned char smraw[];
   Cx<R>* sm = reinterpret_cast<Cx<R>*>(smraw);  // [NRT][12][RP_CHUNK]
-  const int64_t y = blockIdx.x;
-  const int r0 = blockIdx.y * NRT;
+  // RHS tiles fastest: the CTAs of one block run together and share its basis in L2
+  const int ntile = (nrhs + NRT - 1) / NRT;
+  const int64_t y = blockIdx.x / ntile;
+  const int r0 = (int)(blockIdx.x % ntile) * NRT;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   constexpr int NW = RP_THREADS / 32;
   constexpr int MAXJ = JW;  // dofs per warp
@@ -233,8 +235,9 @@ __global__ void __launch_bounds__(RP_THREADS) prolong_kernel(const Cx<R>* __rest
                                                              void* __restrict__ fine, int accumulate) {
   extern __shared__ unsigned char smraw[];
   Cx<R>* cs = reinterpret_cast<Cx<R>*>(smraw);  // [NRT][n2]
-  const int64_t y = blockIdx.x;
-  const int r0 = blockIdx.y * NRT;
+  const int ntile = (nrhs + NRT - 1) / NRT;
+  const int64_t y = blockIdx.x / ntile;
+  const int r0 = (int)(blockIdx.x % ntile) * NRT;
   for (int idx = threadIdx.x; idx < NRT * n2; idx += RP_THREADS) {
     const int j = idx % n2, r = idx / n2;
     cs[idx] = (r0 + r < nrhs) ? coarse[((size_t)(r0 + r) * g.V1 + y) * n2 + j] : cx<R>(0, 0);
@@ -498,7 +501,7 @@ static mglma_status launch_restrict_jw(const mglma_subspace_s* S, const void* fi
     cudaFuncSetAttribute(restrict_kernel<R, B, NRT, JW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr_set = true;
   }
-  dim3 grid((unsigned)g.V1, (unsigned)((nrhs + NRT - 1) / NRT), 1);
+  const unsigned grid = (unsigned)(g.V1 * ((nrhs + NRT - 1) / NRT));
   restrict_kernel<R, B, NRT, JW><<<grid, RP_THREADS, smem, s>>>(fine, nrhs, basis, S->scale16, g, 2 * S->nv,
                                                                 reinterpret_cast<Cx<R>*>(out));
   MG_LAUNCH_CHECK();
@@ -525,7 +528,7 @@ static mglma_status launch_prolong(const mglma_subspace_s* S, const void* coarse
                                    void* fine, bool acc, cudaStream_t s) {
   const BlockGeo g = S->geo;
   const int smem = NRT * 2 * S->nv * 2 * (int)sizeof(R);
-  dim3 grid((unsigned)g.V1, (unsigned)((nrhs + NRT - 1) / NRT), 1);
+  const unsigned grid = (unsigned)(g.V1 * ((nrhs + NRT - 1) / NRT));
   prolong_kernel<R, B, NRT><<<grid, RP_THREADS, smem, s>>>(reinterpret_cast<const Cx<R>*>(coarse), nrhs, basis,
                                                            S->scale16, g, 2 * S->nv, fine, acc ? 1 : 0);
   MG_LAUNCH_CHECK();
