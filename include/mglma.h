@@ -214,6 +214,23 @@ mglma_status mglma_coarse_export(mglma_coarse c, double* dhat);
 mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse c, int nrhs, const double* in, double* out,
                                 mglma_prec compute, void* cuda_stream);
 
+/* ---------------------------------------------------------------- sources (Sec. 5) */
+typedef enum { MGLMA_SOURCE_Z2 = 0, MGLMA_SOURCE_Z4 = 1, MGLMA_SOURCE_POINT = 2 } mglma_source_kind;
+/* Writes nrhs canonical sources to out (host or device):
+ *   Z2: every real component +-1 (imaginary 0); Z4: (+-1 +- i)/sqrt(2), the
+ *     noise the paper's stochastic estimator uses.  Component (spin s,
+ *     colour c) of RHS r at site x takes draw n = ((first + r) V + x) 12 +
+ *     3 s + c of the counter-based stream key = mix64(mix64(seed) ^ 2)
+ *     (mix64 = SplitMix64 output function): bit 63 of mix64(key + n) is the
+ *     real sign, bit 62 the imaginary sign.
+ *   POINT: a unit vector at site point_sites[r], spin-colour point_sc[r]
+ *     (host arrays of nrhs entries).
+ * t_slice >= 0 keeps only the time slice x0 = t_slice (time dilution,
+ * Sec. 5); -1 keeps the whole lattice. */
+mglma_status mglma_sources(mglma_ctx ctx, const mglma_lattice* lat, int kind, int nrhs, uint64_t seed,
+                           int64_t first, const int64_t* point_sites, const int* point_sc, int t_slice, double* out,
+                           void* cuda_stream);
+
 /* ---------------------------------------------------------------- solves (Sec. 2, Sec. 5) */
 typedef enum {
   MGLMA_SOLVER_CGNE = 0, /* FP64 CG on D^dag D x = D^dag b: the plain method */

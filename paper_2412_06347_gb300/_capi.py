@@ -11,6 +11,7 @@ from . import build as _build
 MGLMA_FP64, MGLMA_FP32, MGLMA_BF16, MGLMA_FP16 = 0, 1, 2, 3
 MGLMA_OP_D, MGLMA_OP_DDAG, MGLMA_OP_Q, MGLMA_OP_DDAGD = 0, 1, 2, 3
 MGLMA_SOLVER_CGNE, MGLMA_SOLVER_MG = 0, 1
+MGLMA_SOURCE_Z2, MGLMA_SOURCE_Z4, MGLMA_SOURCE_POINT = 0, 1, 2
 _STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "NOT_CONVERGED", 6: "NUMERIC",
            7: "TIMEOUT", 8: "REJECTED"}
 
@@ -94,6 +95,8 @@ class mglma_solve_stats(C.Structure):
                 ("residual", C.c_double), ("converged", C.c_int)]
 
 
+_sig("mglma_sources", C.c_int, _vp, C.POINTER(mglma_lattice), C.c_int, C.c_int, C.c_uint64, _i64,
+     C.POINTER(_i64), C.POINTER(C.c_int), C.c_int, _vp, _vp)
 _sig("mglma_solve_params_default", None, C.POINTER(mglma_solve_params), C.c_int)
 _sig("mglma_solve_batch", C.c_int, _vp, _vp, _vp, C.POINTER(mglma_solve_params), C.c_int, C.POINTER(C.c_int), _vp,
      _vp, _vp, C.POINTER(mglma_solve_stats), _vp)
@@ -310,3 +313,11 @@ def mglma_solve_batch(ctx, g, coarse, params, group_nrhs, b, x, x_coarse=None, s
     out = [dict(iterations=s.iterations, outer=s.outer, coarse_iterations=s.coarse_iterations,
                 residual=s.residual, converged=bool(s.converged)) for s in st[:sum(groups)]]
     return status, out
+
+
+def mglma_sources(ctx, L, kind, nrhs, seed, out, first=0, point_sites=None, point_sc=None, t_slice=-1, stream=None):
+    lat = mglma_lattice((C.c_int * 4)(*[int(v) for v in L]), -1)
+    ps = (_i64 * nrhs)(*[int(v) for v in point_sites]) if point_sites is not None else None
+    pc = (C.c_int * nrhs)(*[int(v) for v in point_sc]) if point_sc is not None else None
+    _check(lib.mglma_sources(_h(ctx), C.byref(lat), int(kind), int(nrhs), int(seed), int(first), ps, pc,
+                             int(t_slice), ptr(out), _stream_ptr(stream)))

@@ -171,6 +171,67 @@ __device__ __forceinline__ void finish(double2* part, unsigned* count, int k, in
   if (threadIdx.x == 0) count[r] = 0;
 }
 
+// FP32 data: products of one 16-byte load are summed in FP32, sixteen loads
+// are gathered in an FP32 partial, and only that partial enters the FP64
+// accumulator (keeps the FP64 pipe, which is narrow on GB300, off the
+// critical path).  FP64 data accumulate in FP64 throughout.
+template <typename R>
+struct RAcc;
+template <>
+struct RAcc<float> {
+  float n = 0.f, dr = 0.f, di = 0.f;
+  int c = 0;
+  double N = 0, DR = 0, DI = 0;
+  __device__ __forceinline__ void add_n(float4 a) {
+    n += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+    tick();
+  }
+  __device__ __forceinline__ void add_d(float4 a, float4 b) {
+    dr += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+    di += a.x * b.y - a.y * b.x + a.z * b.w - a.w * b.z;
+    tick();
+  }
+  __device__ __forceinline__ void add_nd(float4 a, float4 b) {
+    n += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+    dr += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+    di += a.x * b.y - a.y * b.x + a.z * b.w - a.w * b.z;
+    tick();
+  }
+  __device__ __forceinline__ void tick() {
+    if (++c == 16) flush();
+  }
+  __device__ __forceinline__ void flush() {
+    N += n;
+    DR += dr;
+    DI += di;
+    n = dr = di = 0.f;
+    c = 0;
+  }
+  __device__ __forceinline__ double norm() {
+    flush();
+    return N;
+  }
+  __device__ __forceinline__ double2 dot() {
+    flush();
+    return make_double2(DR, DI);
+  }
+};
+template <>
+struct RAcc<double> {
+  double N = 0, DR = 0, DI = 0;
+  __device__ __forceinline__ void add_n(double2 a) { N += a.x * a.x + a.y * a.y; }
+  __device__ __forceinline__ void add_d(double2 a, double2 b) {
+    DR += a.x * b.x + a.y * b.y;
+    DI += a.x * b.y - a.y * b.x;
+  }
+  __device__ __forceinline__ void add_nd(double2 a, double2 b) {
+    add_n(a);
+    add_d(a, b);
+  }
+  __device__ __forceinline__ double norm() { return N; }
+  __device__ __forceinline__ double2 dot() { return make_double2(DR, DI); }
+};
+
 template <typename R, int MODE>
 __global__ void __launch_bounds__(RT) reduce_kernel(const typename Pair<R>::T* __restrict__ x0, size_t jstride, int k,
                                                     const typename Pair<R>::T* __restrict__ y, size_t m,
@@ -181,48 +242,48 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const typename Pair<R>::T* _
   const size_t step = (size_t)nb * RT;
   if (MODE == 1) {
     for (int j = 0; j < k; ++j) {
-      double2 acc = make_double2(0, 0);
+      RAcc<R> acc;
       const auto* xj = x0 + j * jstride + off;
       size_t i = (size_t)blockIdx.x * RT + threadIdx.x;
       for (; i + 3 * step < m; i += 4 * step) {
         const auto a0 = xj[i], a1 = xj[i + step], a2 = xj[i + 2 * step], a3 = xj[i + 3 * step];
         const auto b0 = y[off + i], b1 = y[off + i + step], b2 = y[off + i + 2 * step], b3 = y[off + i + 3 * step];
-        const double2 d0 = dot_pair(a0, b0), d1 = dot_pair(a1, b1), d2 = dot_pair(a2, b2), d3 = dot_pair(a3, b3);
-        acc.x += (d0.x + d1.x) + (d2.x + d3.x);
-        acc.y += (d0.y + d1.y) + (d2.y + d3.y);
+        acc.add_d(a0, b0);
+        acc.add_d(a1, b1);
+        acc.add_d(a2, b2);
+        acc.add_d(a3, b3);
       }
-      for (; i < m; i += step) {
-        const double2 d = dot_pair(xj[i], y[off + i]);
-        acc.x += d.x;
-        acc.y += d.y;
-      }
-      acc = block_sum2<RT>(acc);
-      if (threadIdx.x == 0) part[((size_t)j * nrhs + r) * nb + blockIdx.x] = acc;
+      for (; i < m; i += step) acc.add_d(xj[i], y[off + i]);
+      const double2 v = block_sum2<RT>(acc.dot());
+      if (threadIdx.x == 0) part[((size_t)j * nrhs + r) * nb + blockIdx.x] = v;
     }
   } else {
-    double nn = 0;
-    double2 dd = make_double2(0, 0);
+    RAcc<R> acc;
     const auto* x = x0 + off;
     size_t i = (size_t)blockIdx.x * RT + threadIdx.x;
     for (; i + 3 * step < m; i += 4 * step) {
       const auto a0 = x[i], a1 = x[i + step], a2 = x[i + 2 * step], a3 = x[i + 3 * step];
-      nn += (nrm_pair(a0) + nrm_pair(a1)) + (nrm_pair(a2) + nrm_pair(a3));
       if (MODE == 2) {
         const auto b0 = y[off + i], b1 = y[off + i + step], b2 = y[off + i + 2 * step], b3 = y[off + i + 3 * step];
-        const double2 d0 = dot_pair(a0, b0), d1 = dot_pair(a1, b1), d2 = dot_pair(a2, b2), d3 = dot_pair(a3, b3);
-        dd.x += (d0.x + d1.x) + (d2.x + d3.x);
-        dd.y += (d0.y + d1.y) + (d2.y + d3.y);
+        acc.add_nd(a0, b0);
+        acc.add_nd(a1, b1);
+        acc.add_nd(a2, b2);
+        acc.add_nd(a3, b3);
+      } else {
+        acc.add_n(a0);
+        acc.add_n(a1);
+        acc.add_n(a2);
+        acc.add_n(a3);
       }
     }
     for (; i < m; i += step) {
-      const auto a = x[i];
-      nn += nrm_pair(a);
-      if (MODE == 2) {
-        const double2 d = dot_pair(a, y[off + i]);
-        dd.x += d.x;
-        dd.y += d.y;
-      }
+      if (MODE == 2)
+        acc.add_nd(x[i], y[off + i]);
+      else
+        acc.add_n(x[i]);
     }
+    const double nn = acc.norm();
+    const double2 dd = MODE == 2 ? acc.dot() : make_double2(0, 0);
     double2 v = block_sum2<RT>(make_double2(nn, 0));
     if (threadIdx.x == 0) part[(size_t)r * nb + blockIdx.x] = v;
     if (MODE == 2) {
@@ -245,15 +306,15 @@ __global__ void __launch_bounds__(RT) axpy2_norm_kernel(const typename Pair<R>::
   const double2 na = make_double2(-ar.x, -ar.y);
   const double2 one = make_double2(1, 0);
   const size_t off = (size_t)r * m;
-  double nn = 0;
+  RAcc<R> acc;
   for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < m; i += (size_t)nb * RT) {
     const auto pv = p[off + i], xv = x[off + i], wv = w[off + i], rv = res[off + i];
     x[off + i] = lc(pv, xv, ar, one);
     const auto nr = lc(wv, rv, na, one);
     res[off + i] = nr;
-    nn += nrm_pair(nr);
+    acc.add_n(nr);
   }
-  const double2 v = block_sum2<RT>(make_double2(nn, 0));
+  const double2 v = block_sum2<RT>(make_double2(acc.norm(), 0));
   if (threadIdx.x == 0) part[(size_t)r * nb + blockIdx.x] = v;
   finish<0>(part, count, 1, nb, nrhs, nullptr, out1);
 }

@@ -147,3 +147,26 @@ def test_full_size_sampled_sites(m, ctx):
     lhs, rhs = np.vdot(chi, b), np.vdot(a, eta)
     assert abs(lhs - rhs) / abs(lhs) < 1e-12
     m.mglma_gauge_free(g)
+
+
+def test_sources_bit_exact(m, ctx):
+    """Device sources equal the host generator bit for bit (same counter
+    definition); point sources and time dilution."""
+    L = (6, 4, 2, 4)
+    z2 = np.zeros((3,) + L + (4, 3), dtype=np.complex128)
+    m.mglma_sources(ctx, L, m.MGLMA_SOURCE_Z2, 3, 77, z2, first=2)
+    assert np.array_equal(z2, synthetic.z2_noise(L, 3, 77, first_rhs=2))
+    z4 = np.zeros_like(z2)
+    m.mglma_sources(ctx, L, m.MGLMA_SOURCE_Z4, 3, 78, z4)
+    assert np.array_equal(z4, synthetic.z4_noise(L, 3, 78))
+    td = np.zeros_like(z2)
+    m.mglma_sources(ctx, L, m.MGLMA_SOURCE_Z4, 3, 78, td, t_slice=4)
+    ref = synthetic.z4_noise(L, 3, 78)
+    ref[:, :4] = 0
+    ref[:, 5:] = 0
+    assert np.array_equal(td, ref)
+    pt = np.zeros_like(z2)
+    sites = [0, 17, lat.volume(L) - 1]
+    m.mglma_sources(ctx, L, m.MGLMA_SOURCE_POINT, 3, 0, pt, point_sites=sites, point_sc=[0, 5, 11])
+    ref = np.concatenate([synthetic.point_sources(L, [s], sc) for s, sc in zip(sites, [0, 5, 11])])
+    assert np.array_equal(pt, ref)
