@@ -249,6 +249,7 @@ typedef struct {
   double coarse_tol;    /* relative tolerance of the preconditioner's coarse solve */
   int coarse_max_iter;  /* cap on coarse iterations per preconditioner call */
   int check_every;      /* host polls residual norms every this many iterations */
+  int max_batch;        /* RHS solved together (0: as many as free HBM allows, <= 64) */
 } mglma_solve_params;
 
 typedef struct {
@@ -264,9 +265,11 @@ void mglma_solve_params_default(mglma_solve_params* p, int method);
 
 /* Solves D x = b (x = S b, the propagator of Sec. 2 applied to b) for
  * ngroups groups of right-hand sides; group g holds group_nrhs[g] canonical
- * spinors, the groups stored back to back in b and x.  Each group runs as one
- * batch; every RHS follows its own recurrence, so its result does not depend
- * on the batch it is in.  coarse may be NULL for MGLMA_SOLVER_CGNE.
+ * spinors, the groups stored back to back in b and x.  Uneven groups are
+ * merged: all RHS run as lockstep batches of up to max_batch RHS (one launch
+ * of every kernel covers the whole batch).  Every RHS follows its own
+ * recurrence with its own scalars and convergence mask, so its result does
+ * not depend on the batch it is in.  coarse may be NULL for MGLMA_SOLVER_CGNE.
  * x_coarse (nullable): also returns the coarse-space piece
  *   psi1 = T0 D1^-1 R0 b (S1 b of Sec. 2 via App. chirality), with D1^-1
  *   solved to tol by FP64 defect correction; S0 b = x - psi1.
@@ -275,6 +278,21 @@ void mglma_solve_params_default(mglma_solve_params* p, int method);
 mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge g, mglma_coarse coarse, const mglma_solve_params* params,
                                int ngroups, const int* group_nrhs, const double* b, double* x, double* x_coarse,
                                mglma_solve_stats* stats, void* cuda_stream);
+
+/* ---------------------------------------------------------------- autotuning */
+/* Times the candidate RHS tile widths for nrhs right-hand sides with CUDA
+ * events and keeps the fastest in the context (used by every later call
+ * with an RHS count in the same power-of-two bucket):
+ *   kernel 0: RHS per thread of the FP32 stencil (1, 2, 4), needs g;
+ *   kernel 1: RHS per tile of the tensor-core coarse stencil (8, 16), needs c.
+ * g or c may be NULL to skip that kernel. */
+mglma_status mglma_autotune(mglma_ctx ctx, mglma_gauge g, mglma_coarse c, int nrhs);
+/* The tuned choice (0 if none) and its time in ms for kernel / nrhs. */
+mglma_status mglma_autotune_get(mglma_ctx ctx, int kernel, int nrhs, int* choice, double* ms);
+/* Text cache of the tuned table, one line per entry, keyed by GPU name;
+ * entries of other GPUs are ignored on load. */
+mglma_status mglma_autotune_save(mglma_ctx ctx, const char* path);
+mglma_status mglma_autotune_load(mglma_ctx ctx, const char* path);
 
 /* Debug export of the integer tables the kernels compute on the fly:
  * nbr[V][8] (hop slots +0..+3, -0..-3) and block_of_site[V] for the given

@@ -87,7 +87,7 @@ _sig("mglma_coarse_apply", C.c_int, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp)
 class mglma_solve_params(C.Structure):
     _fields_ = [("method", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("gcr_m", C.c_int),
                 ("nu", C.c_int), ("inner_tol", C.c_double), ("coarse_tol", C.c_double),
-                ("coarse_max_iter", C.c_int), ("check_every", C.c_int)]
+                ("coarse_max_iter", C.c_int), ("check_every", C.c_int), ("max_batch", C.c_int)]
 
 
 class mglma_solve_stats(C.Structure):
@@ -97,6 +97,10 @@ class mglma_solve_stats(C.Structure):
 
 _sig("mglma_sources", C.c_int, _vp, C.POINTER(mglma_lattice), C.c_int, C.c_int, C.c_uint64, _i64,
      C.POINTER(_i64), C.POINTER(C.c_int), C.c_int, _vp, _vp)
+_sig("mglma_autotune", C.c_int, _vp, _vp, _vp, C.c_int)
+_sig("mglma_autotune_get", C.c_int, _vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double))
+_sig("mglma_autotune_save", C.c_int, _vp, C.c_char_p)
+_sig("mglma_autotune_load", C.c_int, _vp, C.c_char_p)
 _sig("mglma_solve_params_default", None, C.POINTER(mglma_solve_params), C.c_int)
 _sig("mglma_solve_batch", C.c_int, _vp, _vp, _vp, C.POINTER(mglma_solve_params), C.c_int, C.POINTER(C.c_int), _vp,
      _vp, _vp, C.POINTER(mglma_solve_stats), _vp)
@@ -321,3 +325,22 @@ def mglma_sources(ctx, L, kind, nrhs, seed, out, first=0, point_sites=None, poin
     pc = (C.c_int * nrhs)(*[int(v) for v in point_sc]) if point_sc is not None else None
     _check(lib.mglma_sources(_h(ctx), C.byref(lat), int(kind), int(nrhs), int(seed), int(first), ps, pc,
                              int(t_slice), ptr(out), _stream_ptr(stream)))
+
+
+def mglma_autotune(ctx, g=None, coarse=None, nrhs=1):
+    _check(lib.mglma_autotune(_h(ctx), g, coarse, int(nrhs)))
+
+
+def mglma_autotune_get(ctx, kernel, nrhs):
+    c = C.c_int()
+    ms = C.c_double()
+    _check(lib.mglma_autotune_get(_h(ctx), int(kernel), int(nrhs), C.byref(c), C.byref(ms)))
+    return c.value, ms.value
+
+
+def mglma_autotune_save(ctx, path):
+    _check(lib.mglma_autotune_save(_h(ctx), str(path).encode()))
+
+
+def mglma_autotune_load(ctx, path):
+    _check(lib.mglma_autotune_load(_h(ctx), str(path).encode()))

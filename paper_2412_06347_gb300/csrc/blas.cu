@@ -401,29 +401,37 @@ static int reduce_blocks(size_t m) {
   return (int)(want < 1 ? 1 : want);
 }
 
-// Per-stream partial sums and tickets, kept for the life of the context
-// (tickets return to zero after every reduction).
+// Per-stream partial sums and tickets, allocated once with a fixed capacity
+// (blocks per RHS <= 592, RHS <= 64, directions <= 64) and never moved, so
+// CUDA graphs that captured reductions stay valid; tickets return to zero
+// after every reduction.
+constexpr size_t kRedParts = (size_t)592 * 64 * 64;
+constexpr int kRedCounts = 64;
 static mglma_status red_scratch(mglma_ctx ctx, cudaStream_t s, size_t nparts, int ncount, double2** part,
                                 unsigned** count) {
+  if (nparts > kRedParts || ncount > kRedCounts)
+    return fail(MGLMA_ERR_INVALID, "reduction: more than 64 RHS or 64 directions in one launch");
   auto& R = ctx->red[s];
-  if (R.part_cap < nparts) {
-    if (R.part) cudaFreeAsync(R.part, s);
-    R.part = nullptr;
-    R.part_cap = 0;
-    MG_CHECK(dalloc(ctx, (void**)&R.part, nparts * sizeof(double2), s));
-    R.part_cap = nparts;
-  }
-  if (R.count_cap < ncount) {
-    if (R.count) cudaFreeAsync(R.count, s);
-    R.count = nullptr;
-    R.count_cap = 0;
-    MG_CHECK(dalloc(ctx, (void**)&R.count, ncount * sizeof(unsigned), s));
-    MG_CUDA(cudaMemsetAsync(R.count, 0, ncount * sizeof(unsigned), s));
-    R.count_cap = ncount;
+  if (!R.part) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(MGLMA_ERR_INVALID, "reduction: first use of a stream inside a graph capture");
+    MG_CHECK(dalloc(ctx, (void**)&R.part, kRedParts * sizeof(double2), s));
+    MG_CHECK(dalloc(ctx, (void**)&R.count, kRedCounts * sizeof(unsigned), s));
+    MG_CUDA(cudaMemsetAsync(R.count, 0, kRedCounts * sizeof(unsigned), s));
+    R.part_cap = kRedParts;
+    R.count_cap = kRedCounts;
   }
   *part = R.part;
   *count = R.count;
   return MGLMA_OK;
+}
+
+mglma_status red_scratch_ready(mglma_ctx ctx, cudaStream_t s) {
+  double2* p;
+  unsigned* c;
+  return red_scratch(ctx, s, 1, 1, &p, &c);
 }
 
 template <int MODE>

@@ -41,7 +41,14 @@ ProfScope::ProfScope(mglma_ctx c, int k, cudaStream_t st, double bytes_, double 
   if (ctx && ctx->profile) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cs);
-    if (cs != cudaStreamCaptureStatusNone) return;  // no timing inside graph capture
+    if (cs != cudaStreamCaptureStatusNone) {
+      if (!ctx->capture_events) return;
+      cudaEventCreate(&a);  // owned by the graph's list
+      cudaEventCreate(&b);
+      cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+      captured = true;
+      return;
+    }
     a = take_event(ctx);
     b = take_event(ctx);
     cudaEventRecord(a, s);
@@ -49,10 +56,29 @@ ProfScope::ProfScope(mglma_ctx c, int k, cudaStream_t st, double bytes_, double 
 }
 
 ProfScope::~ProfScope() {
+  if (a && captured) {
+    cudaEventRecordWithFlags(b, s, cudaEventRecordExternal);
+    ctx->capture_events->push_back({kind, a, b, bytes, flops});
+    return;
+  }
   if (a) {
     cudaEventRecord(b, s);
     ctx->pending.push_back({kind, a, b, bytes, flops});
     if (ctx->pending.size() > 4096) resolve_profile(ctx);  // bound the list
+  }
+}
+
+void resolve_graph_events(mglma_ctx ctx, const std::vector<mglma_ctx_s::Pending>& ev) {
+  for (auto& p : ev) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    ctx->stats[p.kind].launches += 1;
+    ctx->stats[p.kind].ms += ms;
+    ctx->stats[p.kind].bytes += p.bytes;
+    ctx->stats[p.kind].flops += p.flops;
   }
 }
 

@@ -341,8 +341,9 @@ mglma_status coarse_apply_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float
                              bool dagger, cudaStream_t s) {
   if (!C->Aimg || !coarse_tc_supported(C->n2)) return fail(MGLMA_ERR_INVALID, "coarse_apply_tc: no tensor image");
   int* err = C->tc_err;
-  if (nrhs <= 8 && tc_smem(C->n2, 8) <= 227 * 1024) return launch_tc<8>(ctx, C, X, Y, nrhs, dagger, err, s);
-  if (tc_smem(C->n2, 16) <= 227 * 1024) return launch_tc<16>(ctx, C, X, Y, nrhs, dagger, err, s);
+  const bool fit16 = tc_smem(C->n2, 16) <= 227 * 1024;
+  const int nt = tuned(ctx, TUNE_COARSE_NT, nrhs, (nrhs <= 8 || !fit16) ? 8 : 16);
+  if (nt == 16 && fit16) return launch_tc<16>(ctx, C, X, Y, nrhs, dagger, err, s);
   return launch_tc<8>(ctx, C, X, Y, nrhs, dagger, err, s);
 }
 

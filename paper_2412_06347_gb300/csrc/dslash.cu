@@ -666,13 +666,8 @@ static void launch_dslash(const Spinor& in, Spinor& out, const void* U, const vo
   dslash_kernel<R, NR, DAG><<<(unsigned)tiles, 128, 0, s>>>(in.p, out.p, U, C, a);
 }
 
-// RHS per thread: chosen by nrhs (tuned values; see the autotuner in solver.cu)
-static int g_nr32 = 1;
-static int g_nr64 = 1;
-void set_dslash_nr(int nr32, int nr64) {
-  if (nr32 == 1 || nr32 == 2 || nr32 == 4) g_nr32 = nr32;
-  if (nr64 == 1 || nr64 == 2) g_nr64 = nr64;
-}
+// RHS per thread: 1 unless the autotuner (tune.cu) measured a better width
+// for this RHS count on this context
 
 mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, bool dagger,
                     bool gamma5_out, cudaStream_t s) {
@@ -691,7 +686,7 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
   const double flops = 1896.0 * V * N;
   if (in.prec == MGLMA_FP64) {
     ProfScope ps(ctx, K_DSLASH64, s, V * (1152.0 + 384.0 * N), flops);
-    const int nr = in.nrhs >= 2 ? g_nr64 : 1;
+    const int nr = 1;
     if (nr == 2)
       dagger ? launch_dslash<double, 2, true>(in, out, G->U64, G->C64, a, s)
              : launch_dslash<double, 2, false>(in, out, G->U64, G->C64, a, s);
@@ -700,7 +695,7 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
              : launch_dslash<double, 1, false>(in, out, G->U64, G->C64, a, s);
   } else {
     ProfScope ps(ctx, K_DSLASH32, s, V * (480.0 + 192.0 * N), flops);
-    int nr = g_nr32;
+    int nr = tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, 1);
     if (in.nrhs < nr) nr = in.nrhs >= 2 ? 2 : 1;
     if (nr == 4)
       dagger ? launch_dslash<float, 4, true>(in, out, G->U32, G->C32, a, s)

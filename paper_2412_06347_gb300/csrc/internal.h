@@ -89,6 +89,8 @@ struct mglma_ctx_s {
     int count_cap = 0;
   };
   std::map<cudaStream_t, RedScratch> red;
+  // autotuned tile choices: key = kernel * 1024 + RHS bucket -> (choice, ms)
+  std::map<int, std::pair<int, double>> tune;
   cudaStream_t stream = nullptr;  // default stream of the context
   cudaMemPool_t pool = nullptr;
   int sm_count = 0;
@@ -100,6 +102,9 @@ struct mglma_ctx_s {
     double bytes, flops;
   };
   std::vector<Pending> pending;
+  // while a CUDA graph is captured with profiling on, launch brackets become
+  // external event-record nodes listed here (resolved after each replay)
+  std::vector<Pending>* capture_events = nullptr;
   std::vector<cudaEvent_t> event_cache;
   mglma::KernelStat stats[16];
 };
@@ -119,6 +124,18 @@ struct mglma_gauge_s {
 };
 
 namespace mglma {
+
+// tile-choice keys of the autotuner
+enum TuneKernel { TUNE_DSLASH32_NR = 0, TUNE_COARSE_NT = 1 };
+inline int rhs_bucket(int n) {
+  int b = 1;
+  while (b < n && b < 64) b *= 2;
+  return b;
+}
+inline int tuned(const mglma_ctx_s* ctx, int kernel, int nrhs, int dflt) {
+  auto it = ctx->tune.find(kernel * 1024 + rhs_bucket(nrhs));
+  return it == ctx->tune.end() ? dflt : it->second.first;
+}
 
 // kernel-statistics kinds (timing is optional, see mglma_profile)
 enum KernelKind {
@@ -143,6 +160,7 @@ struct ProfScope {
   cudaStream_t s;
   double bytes, flops;
   cudaEvent_t a = nullptr, b = nullptr;
+  bool captured = false;
   ProfScope(mglma_ctx c, int k, cudaStream_t st, double bytes_ = 0, double flops_ = 0);
   ~ProfScope();
 };
@@ -234,6 +252,10 @@ mglma_status multi_cdot(mglma_ctx, const Vec& x0, size_t jstride_reals, int k, c
                         cudaStream_t s);
 // out[r] = |x_r|^2
 mglma_status norm2(mglma_ctx, const Vec& x, double* out, cudaStream_t s);
+// allocates the stream's reduction scratch (must happen before a graph capture)
+mglma_status red_scratch_ready(mglma_ctx, cudaStream_t s);
+// accumulates the launch times of a replayed graph's event brackets
+void resolve_graph_events(mglma_ctx ctx, const std::vector<mglma_ctx_s::Pending>& ev);
 // nrm[r] = |x_r|^2 and dot[r] = <x_r, y_r> in one pass
 mglma_status norm2_cdot(mglma_ctx, const Vec& x, const Vec& y, double* nrm, double2* dot, cudaStream_t s);
 // x += a p ; r -= a w ; rr[r] = |r_r|^2 in one pass

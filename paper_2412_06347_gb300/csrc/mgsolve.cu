@@ -52,16 +52,117 @@ __global__ void sqrt_kernel(const double* in, double* out, int n, int inverse) {
 
 using OpFn = std::function<mglma_status(const Vec& in, Vec& out)>;
 
-static Vec dir(const Vec& base, int j) {
-  Vec v = base;
-  v.p = (char*)base.p + (size_t)j * base.bytes();
-  return v;
-}
-
 struct GcrResult {
   int iterations = 0;
   std::vector<int> per_rhs;  // iterations while active (when polled every step)
 };
+
+// Persistent workspace of batched GCR(m) for up to `cap` RHS: m search
+// directions Z and their images W (direction j of RHS r at j*cap + r), the
+// residual, and the per-RHS scalars.  Reused across solves so CUDA graphs
+// that captured its kernels stay valid.
+struct GcrWork {
+  mglma_ctx ctx = nullptr;
+  cudaStream_t s = nullptr;
+  int cap = 0, m = 0;
+  Vec proto;  // precision and reals per RHS
+  void *Zp = nullptr, *Wp = nullptr, *rp = nullptr;
+  Scalars sc;
+  ~GcrWork() {
+    if (ctx) {
+      dfree(ctx, Zp, s);
+      dfree(ctx, Wp, s);
+      dfree(ctx, rp, s);
+    }
+  }
+  mglma_status setup(mglma_ctx c, cudaStream_t st, const Vec& like, int capacity, int mm) {
+    ctx = c;
+    s = st;
+    cap = capacity;
+    m = mm;
+    proto = like;
+    proto.nrhs = cap;
+    MG_CHECK(dalloc(ctx, &Zp, proto.bytes() * m, s));
+    MG_CHECK(dalloc(ctx, &Wp, proto.bytes() * m, s));
+    MG_CHECK(dalloc(ctx, &rp, proto.bytes(), s));
+    MG_CHECK(sc.alloc(ctx, cap, m + 2, 2 * m + 2, s));
+    return red_scratch_ready(ctx, s);
+  }
+  size_t stride() const { return (size_t)cap * proto.n; }  // reals between directions
+  Vec view(void* base, int j, int n) const {
+    Vec v = proto;
+    v.nrhs = n;
+    v.p = (char*)base + (size_t)j * proto.bytes();
+    return v;
+  }
+};
+
+// x = 0, r = b, bb = |b|^2, active = (bb > 0)
+static mglma_status gcr_init(GcrWork& w, const Vec& b, Vec& x) {
+  const int n = b.nrhs;
+  Vec r = w.view(w.rp, 0, n);
+  double* bb = w.sc.d + (size_t)(w.m + 1) * w.cap;
+  MG_CHECK(zero_vec(w.ctx, x, w.s));
+  MG_CHECK(copy_vec(w.ctx, b, r, w.s));
+  MG_CHECK(norm2(w.ctx, b, bb, w.s));
+  ProfScope ps(w.ctx, K_SCALAR, w.s);
+  MG_CHECK(fill_int(w.sc.active, 1, n, w.s));
+  gcr_mask_kernel<<<(n + 63) / 64, 64, 0, w.s>>>(bb, bb, 0.0, w.sc.active, n);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+// iteration with direction slot k (no host interaction)
+static mglma_status gcr_iter(GcrWork& w, const OpFn& A, const OpFn* M, Vec& x, int n, int k, double tol2) {
+  mglma_ctx ctx = w.ctx;
+  cudaStream_t s = w.s;
+  const int cap = w.cap;
+  double* nw = w.sc.d;  // [m][cap]
+  double* rr = w.sc.d + (size_t)w.m * cap;
+  double* bb = w.sc.d + (size_t)(w.m + 1) * cap;
+  double2* dots = w.sc.z;
+  double2* coef = w.sc.z + (size_t)w.m * cap;
+  double2* num = w.sc.z + (size_t)2 * w.m * cap;
+  double2* a = w.sc.z + (size_t)(2 * w.m + 1) * cap;
+  Vec r = w.view(w.rp, 0, n), Z0 = w.view(w.Zp, 0, n), W0 = w.view(w.Wp, 0, n);
+  Vec Zk = w.view(w.Zp, k, n), Wk = w.view(w.Wp, k, n);
+  const int tb = 64, nb = (n + tb - 1) / tb;
+  if (M) {
+    MG_CHECK((*M)(r, Zk));
+  } else {
+    MG_CHECK(copy_vec(ctx, r, Zk, s));
+  }
+  MG_CHECK(A(Zk, Wk));
+  if (k > 0) {
+    // dots and coefficients are stored [j][n] (dense in n) for j < k
+    MG_CHECK(multi_cdot(ctx, W0, w.stride(), k, Wk, dots, s));
+    {
+      ProfScope ps(ctx, K_SCALAR, s);
+      gcr_coef_kernel<<<(k * n + 63) / 64, 64, 0, s>>>(dots, nw, coef, k, n);
+    }
+    MG_CHECK(multi_axpy(ctx, W0, w.stride(), k, Wk, coef, s));
+    MG_CHECK(multi_axpy(ctx, Z0, w.stride(), k, Zk, coef, s));
+  }
+  MG_CHECK(norm2_cdot(ctx, Wk, r, nw + (size_t)k * n, num, s));
+  {
+    ProfScope ps(ctx, K_SCALAR, s);
+    gcr_alpha_kernel<<<nb, tb, 0, s>>>(num, nw + (size_t)k * n, w.sc.active, a, n);
+  }
+  MG_CHECK(axpy2_norm(ctx, a, Zk, x, Wk, r, rr, s));
+  {
+    ProfScope ps(ctx, K_SCALAR, s);
+    gcr_mask_kernel<<<nb, tb, 0, s>>>(rr, bb, tol2, w.sc.active, n);
+  }
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+static mglma_status read_active(GcrWork& w, int n, std::vector<int>& h) {
+  h.resize(n);
+  MG_CUDA(cudaMemcpyAsync(h.data(), w.sc.active, sizeof(int) * n, cudaMemcpyDeviceToHost, w.s));
+  MG_CUDA(cudaStreamSynchronize(w.s));
+  return MGLMA_OK;
+}
 
 // Batched flexible GCR(m): x = A^-1 b per RHS to |r| <= tol |b| (or max_iter).
 // M (nullable) is the right preconditioner.  poll_every > 0 reads the active
@@ -72,69 +173,17 @@ static mglma_status gcr(mglma_ctx ctx, cudaStream_t s, const OpFn& A, const OpFn
   res = GcrResult();
   res.per_rhs.assign(n, 0);
   if (n == 0) return MGLMA_OK;
-  FreeList fl(ctx, s);
-  Vec Z = b, W = b, r = b;
-  MG_CHECK(dalloc(ctx, &Z.p, b.bytes() * m, s));
-  fl.add(Z.p);
-  MG_CHECK(dalloc(ctx, &W.p, b.bytes() * m, s));
-  fl.add(W.p);
-  MG_CHECK(dalloc(ctx, &r.p, b.bytes(), s));
-  fl.add(r.p);
-  Scalars sc;
-  MG_CHECK(sc.alloc(ctx, n, m + 2, 2 * m + 2, s));
-  double* nw = sc.d;             // [m][n]
-  double* rr = sc.d + m * n;     // [n]
-  double* bb = sc.d + (m + 1) * n;
-  double2* dots = sc.z;          // [m][n]
-  double2* coef = sc.z + m * n;  // [m][n]
-  double2* num = sc.z + 2 * m * n;
-  double2* a = sc.z + (2 * m + 1) * n;
-  const size_t stride = (size_t)n * b.n;  // reals between directions
-  MG_CHECK(zero_vec(ctx, x, s));
-  MG_CHECK(copy_vec(ctx, b, r, s));
-  MG_CHECK(norm2(ctx, b, bb, s));
-  const double tol2 = tol * tol;
-  const int tb = 64, nb = (n + tb - 1) / tb;
-  gcr_mask_kernel<<<nb, tb, 0, s>>>(bb, bb, 0.0, sc.active, n);  // zero sources never become active
-  std::vector<int> hact(n, 1), prev(n, 1);
-  if (poll_every == 1) {
-    MG_CUDA(cudaMemcpyAsync(prev.data(), sc.active, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
-    MG_CUDA(cudaStreamSynchronize(s));
-  }
+  GcrWork w;
+  MG_CHECK(w.setup(ctx, s, b, n, m));
+  MG_CHECK(gcr_init(w, b, x));
+  std::vector<int> hact, prev;
+  if (poll_every == 1) MG_CHECK(read_active(w, n, prev));
   int it = 0;
   while (it < max_iter) {
-    const int k = it % m;
-    Vec Zk = dir(Z, k), Wk = dir(W, k);
-    if (M) {
-      MG_CHECK((*M)(r, Zk));
-    } else {
-      MG_CHECK(copy_vec(ctx, r, Zk, s));
-    }
-    MG_CHECK(A(Zk, Wk));
-    if (k > 0) {
-      MG_CHECK(multi_cdot(ctx, W, stride, k, Wk, dots, s));
-      {
-        ProfScope ps(ctx, K_SCALAR, s);
-        gcr_coef_kernel<<<(k * n + 63) / 64, 64, 0, s>>>(dots, nw, coef, k, n);
-      }
-      MG_CHECK(multi_axpy(ctx, W, stride, k, Wk, coef, s));
-      MG_CHECK(multi_axpy(ctx, Z, stride, k, Zk, coef, s));
-    }
-    MG_CHECK(norm2_cdot(ctx, Wk, r, nw + (size_t)k * n, num, s));
-    {
-      ProfScope ps(ctx, K_SCALAR, s);
-      gcr_alpha_kernel<<<nb, tb, 0, s>>>(num, nw + (size_t)k * n, sc.active, a, n);
-    }
-    MG_CHECK(axpy2_norm(ctx, a, Zk, x, Wk, r, rr, s));
-    {
-      ProfScope ps(ctx, K_SCALAR, s);
-      gcr_mask_kernel<<<nb, tb, 0, s>>>(rr, bb, tol2, sc.active, n);
-    }
-    MG_LAUNCH_CHECK();
+    MG_CHECK(gcr_iter(w, A, M, x, n, it % m, tol * tol));
     ++it;
     if (poll_every > 0 && (it % poll_every == 0 || it == max_iter)) {
-      MG_CUDA(cudaMemcpyAsync(hact.data(), sc.active, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
-      MG_CUDA(cudaStreamSynchronize(s));
+      MG_CHECK(read_active(w, n, hact));
       bool any = false;
       for (int i = 0; i < n; ++i) {
         if (poll_every == 1 && prev[i]) res.per_rhs[i]++;  // active going into this iteration
@@ -149,6 +198,132 @@ static mglma_status gcr(mglma_ctx ctx, cudaStream_t s, const OpFn& A, const OpFn
     for (int i = 0; i < n; ++i) res.per_rhs[i] = it;
   return MGLMA_OK;
 }
+
+// Coarse solve of the preconditioner: GCR(m) on the coarse stencil with a
+// persistent workspace; one restart cycle of m iterations is captured as a
+// CUDA graph and replayed, with one host poll per cycle.  With profiling on,
+// a separately captured copy records event brackets around every launch.
+struct CoarseSolver {
+  mglma_ctx ctx = nullptr;
+  cudaStream_t s = nullptr;
+  const mglma_coarse_s* C = nullptr;
+  int m = 16;
+  GcrWork w;
+  struct Graphs {
+    cudaGraphExec_t init = nullptr, cycle = nullptr;
+    int n = -1;
+    std::vector<mglma_ctx_s::Pending> ev_init, ev_cycle;
+  } g[2];  // [0] plain, [1] with profiling events
+  const void* gb = nullptr;
+  void* gx = nullptr;
+  double gtol = -1;
+  bool warmed = false;
+  ~CoarseSolver() { reset(); }
+  void reset() {
+    for (auto& G : g) {
+      if (G.init) cudaGraphExecDestroy(G.init);
+      if (G.cycle) cudaGraphExecDestroy(G.cycle);
+      G.init = G.cycle = nullptr;
+      G.n = -1;
+      for (auto* L : {&G.ev_init, &G.ev_cycle})
+        for (auto& p : *L) {
+          cudaEventDestroy(p.a);
+          cudaEventDestroy(p.b);
+        }
+      G.ev_init.clear();
+      G.ev_cycle.clear();
+    }
+  }
+  OpFn op() {
+    return [this](const Vec& in, Vec& out) { return coarse_apply(ctx, C, in.p, out.p, in.nrhs, MGLMA_FP32, false, s); };
+  }
+  mglma_status capture(Graphs& G, const Vec& b, Vec& x, double tol, bool prof) {
+    const int n = b.nrhs;
+    OpFn A = op();
+    for (int part = 0; part < 2; ++part) {
+      cudaGraph_t graph = nullptr;
+      ctx->capture_events = prof ? (part == 0 ? &G.ev_init : &G.ev_cycle) : nullptr;
+      MG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      mglma_status st = MGLMA_OK;
+      if (part == 0) {
+        st = gcr_init(w, b, x);
+      } else {
+        for (int k = 0; k < m && st == MGLMA_OK; ++k) st = gcr_iter(w, A, nullptr, x, n, k, tol * tol);
+      }
+      cudaError_t e = cudaStreamEndCapture(s, &graph);
+      ctx->capture_events = nullptr;
+      if (st != MGLMA_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (e != cudaSuccess) return fail(MGLMA_ERR_CUDA, std::string("coarse graph capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(part == 0 ? &G.init : &G.cycle, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return fail(MGLMA_ERR_CUDA, std::string("coarse graph instantiate: ") + cudaGetErrorString(e));
+    }
+    G.n = n;
+    return MGLMA_OK;
+  }
+  // e1 = D1^-1 b1 to tol (or max_iter, rounded up to whole cycles)
+  mglma_status solve(const Vec& b, Vec& x, double tol, int max_iter, long long* iters) {
+    const int n = b.nrhs;
+    if (!w.cap) MG_CHECK(w.setup(ctx, s, b, n, m));
+    if (n > w.cap) return fail(MGLMA_ERR_INVALID, "coarse solve: more RHS than the workspace holds");
+    const int cycles = (max_iter + m - 1) / m;
+    std::vector<int> hact;
+    const bool prof = ctx->profile;
+    if (!warmed) {
+      // first use runs uncaptured (kernel attributes and scratch get set up)
+      OpFn A = op();
+      MG_CHECK(gcr_init(w, b, x));
+      int c = 0;
+      for (; c < cycles; ++c) {
+        for (int k = 0; k < m; ++k) MG_CHECK(gcr_iter(w, A, nullptr, x, n, k, tol * tol));
+        MG_CHECK(read_active(w, n, hact));
+        bool any = false;
+        for (int v : hact) any = any || v;
+        if (!any) {
+          ++c;
+          break;
+        }
+      }
+      *iters += (long long)c * m;
+      warmed = true;
+      return MGLMA_OK;
+    }
+    if (b.p != gb || x.p != gx || tol != gtol) {
+      reset();
+      gb = b.p;
+      gx = x.p;
+      gtol = tol;
+    }
+    Graphs& G = g[prof ? 1 : 0];
+    if (G.n != n) {
+      if (G.init) {
+        cudaGraphExecDestroy(G.init);
+        cudaGraphExecDestroy(G.cycle);
+        G.init = G.cycle = nullptr;
+      }
+      MG_CHECK(capture(G, b, x, tol, prof));
+    }
+    MG_CUDA(cudaGraphLaunch(G.init, s));
+    int c = 0;
+    for (; c < cycles; ++c) {
+      MG_CUDA(cudaGraphLaunch(G.cycle, s));
+      MG_CHECK(read_active(w, n, hact));
+      if (prof) resolve_graph_events(ctx, c == 0 ? G.ev_init : std::vector<mglma_ctx_s::Pending>());
+      if (prof) resolve_graph_events(ctx, G.ev_cycle);
+      bool any = false;
+      for (int v : hact) any = any || v;
+      if (!any) {
+        ++c;
+        break;
+      }
+    }
+    *iters += (long long)c * m;
+    return MGLMA_OK;
+  }
+};
 
 static Spinor as_spinor(const Vec& v, int64_t V) {
   Spinor f;
@@ -170,6 +345,7 @@ struct TwoLevel {
   long long coarse_iters = 0;
   Vec b1, e1, sv, tv;
   Scalars sc;
+  CoarseSolver cs;
   bool ready = false;
   ~TwoLevel() {
     dfree(ctx, b1.p, s);
@@ -190,6 +366,9 @@ struct TwoLevel {
     MG_CHECK(dalloc(ctx, &sv.p, r.bytes(), s));
     MG_CHECK(dalloc(ctx, &tv.p, r.bytes(), s));
     MG_CHECK(sc.alloc(ctx, n, 1, 1, s));
+    cs.ctx = ctx;
+    cs.s = s;
+    cs.C = C;
     ready = true;
     return MGLMA_OK;
   }
@@ -200,10 +379,7 @@ struct TwoLevel {
     const int64_t V = S->geo.V;
     Spinor rs = as_spinor(r, V), zs = as_spinor(z, V);
     MG_CHECK(restrict_fine(ctx, S, rs, b1.p, s));
-    OpFn Ac = [&](const Vec& in, Vec& out) { return coarse_apply(ctx, C, in.p, out.p, in.nrhs, MGLMA_FP32, false, s); };
-    GcrResult cr;
-    MG_CHECK(gcr(ctx, s, Ac, nullptr, b1, e1, 16, p->coarse_max_iter, p->coarse_tol, 10, cr));
-    coarse_iters += cr.iterations;
+    MG_CHECK(cs.solve(b1, e1, p->coarse_tol, p->coarse_max_iter, &coarse_iters));
     MG_CHECK(prolong_coarse(ctx, S, e1.p, zs, false, s));
     if (p->nu > 0) {
       // s = r - D z ; nu MR steps on D e = s, accumulated into z

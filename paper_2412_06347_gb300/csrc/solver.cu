@@ -10,6 +10,7 @@
 // propagator S = D^-1 of Sec. 2 applied to b); converged RHS are frozen by a
 // zero step length; when all recursive residuals pass the target the true
 // FP64 residual b - D x is formed and any RHS above it restarts from there.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -69,6 +70,12 @@ mglma_status cg_beta(mglma_ctx ctx, const double* zz_new, double* zz, double2* b
 __global__ void fill_int_kernel(int* p, int v, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
+}
+
+mglma_status fill_int(int* p, int v, int n, cudaStream_t s) {
+  fill_int_kernel<<<(n + 63) / 64, 64, 0, s>>>(p, v, n);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
 }
 
 mglma_status Scalars::alloc(mglma_ctx c, int n, int count_d, int count_z, cudaStream_t st) {
@@ -229,6 +236,7 @@ void mglma_solve_params_default(mglma_solve_params* p, int method) {
   p->coarse_tol = 0.02;
   p->coarse_max_iter = 100;
   p->check_every = method == MGLMA_SOLVER_CGNE ? 20 : 1;
+  p->max_batch = 0;
 }
 
 mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, const mglma_solve_params* prm,
@@ -261,11 +269,18 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
   MG_CHECK(stage_in(ctx, b, per * total, s, sb));
   MG_CHECK(stage_out_alloc(ctx, x, per * total, s, sx));
   if (x_coarse) MG_CHECK(stage_out_alloc(ctx, x_coarse, per * total, s, sxc));
+  // ragged groups are merged into lockstep batches sized by free HBM
+  int cap = prm->max_batch > 0 ? prm->max_batch : 64;
+  if (prm->max_batch <= 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    const size_t per_site = prm->method == MGLMA_SOLVER_CGNE ? 6 * 192 : 4 * 192 + (size_t)(6 + 2 * prm->gcr_m) * 96;
+    const size_t per_rhs = per_site * (size_t)V;
+    cap = (int)std::max<size_t>(1, std::min<size_t>(64, (size_t)(0.7 * (double)fr) / per_rhs));
+  }
   bool all_conv = true;
-  int off = 0;
-  for (int g = 0; g < ngroups; ++g) {
-    const int n = group_nrhs[g];
-    if (n == 0) continue;
+  for (int off = 0; off < total;) {
+    const int n = std::min(cap, total - off);
     FreeList fl(ctx, s);
     Spinor B, X;
     MG_CHECK(alloc_spinor(ctx, B, MGLMA_FP64, n, V, s));
@@ -321,6 +336,7 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
     }
     off += n;
   }
+  (void)ngroups;
   MG_CHECK(stage_out_finish(x, per * total, s, sx));
   if (x_coarse) MG_CHECK(stage_out_finish(x_coarse, per * total, s, sxc));
   MG_CUDA(cudaStreamSynchronize(s));

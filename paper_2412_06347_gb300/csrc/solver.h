@@ -49,6 +49,7 @@ struct FreeList {
   }
 };
 
+mglma_status fill_int(int* p, int v, int n, cudaStream_t s);
 mglma_status read_doubles(const double* dev, std::vector<double>& host, int n, cudaStream_t s);
 mglma_status alloc_spinor(mglma_ctx ctx, Spinor& f, int prec, int nrhs, int64_t V, cudaStream_t s);
 
