@@ -197,6 +197,34 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(m, torch, ctx, g, C, w, args, dev, stream):
+    """Continuous-batching server on the resident lattice: Poisson arrivals
+    (seed 4242, 20 requests/s), RHS per request uniform in 1..max, sources
+    generated on the device, latency from arrival to completion."""
+    import synthetic
+    n = args.serve_requests
+    arrivals = synthetic.poisson_arrivals(n, 20.0, 4242)
+    sizes = synthetic.uniform_ints(n, 1, args.serve_max_rhs, 4242, synthetic.TAG_GROUPS)
+    V = int(np.prod(w["L"]))
+    reqs, first = [], 5000
+    for i in range(n):
+        b = torch.empty((int(sizes[i]), V, 12), dtype=torch.complex128, device=dev)
+        make_sources(m, ctx, w, first, int(sizes[i]), b)
+        first += int(sizes[i])
+        reqs.append(dict(lattice=0, b=b, x=torch.zeros_like(b), arrival=float(arrivals[i])))
+    torch.cuda.synchronize()
+    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG)
+    stats, res = m.mglma_serve(ctx, [(g, C)], reqs, prm, max_slots=32, hbm_fraction=0.6)
+    ok = all(r["status"] == 0 for r in res)
+    resid = max(s["residual"] for r in res for s in r["stats"])
+    return {"requests": stats["requests"], "rhs": stats["rhs"], "p50_s": round(stats["p50_s"], 3),
+            "p99_s": round(stats["p99_s"], 3), "mean_s": round(stats["mean_s"], 3),
+            "solves_per_s": round(stats["solves_per_s"], 4), "wall_s": round(stats["wall_s"], 2),
+            "offered": "Poisson 20 requests/s (seed 4242), RHS per request uniform in 1.." + str(args.serve_max_rhs),
+            "slots": stats["slots"][0], "slot_gb": round(stats["slot_bytes"][0] / 1e9, 2), "all_ok": ok,
+            "residual_max": resid}
+
+
 def micro_dslash(m, torch, ctx, g, V, nrhs, prec, reps, stream):
     """FP32/FP64 stencil on nrhs fields, launch-level timing from the
     library's CUDA events on the launching stream."""
@@ -284,6 +312,9 @@ def main():
     ap.add_argument("--micro", default="", choices=["", "dslash32", "dslash64", "coarse", "transfer"],
                     help="time one kernel class on the workload lattice instead of the solve")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch in --micro mode")
+    ap.add_argument("--serve-requests", type=int, default=6,
+                    help="requests of the seeded Poisson stream served after the timed solves (0: skip)")
+    ap.add_argument("--serve-max-rhs", type=int, default=4, help="RHS per request drawn uniformly in 1..this")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.group:
@@ -417,6 +448,11 @@ def main():
             r["frac"] = round(r["achieved"] / hbm, 4)
             dslash[f"nrhs{n}"] = r
 
+    # ---- serving: a bounded prefix of the seeded Poisson request stream
+    serving = None
+    if args.serve_requests > 0 and rank == 0:
+        serving = run_serving(m, torch, ctx, g, C, w, args, dev, stream)
+
     # ---- plain FP64 solver on the GPU (bounded sample: one source)
     fp64 = None
     cg_iters = 720 if args.workload == "c4" else 460
@@ -452,6 +488,7 @@ def main():
                        "l2": "inputs larger than L2 (each source 0.4 GB)", "parallelism": f"replicas x{world}"},
             "residual_max": resid, "fgcr_iterations": [min(iters), max(iters)],
             "e2e": e2e, "roofline": roofline, "dslash_fp32": dslash, "gpu_launches": launches, "clocks": clk,
+            "serving": serving,
             "fp64_plain": fp64,
             "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu,

@@ -279,6 +279,67 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge g, mglma_coarse coarse
                                int ngroups, const int* group_nrhs, const double* b, double* x, double* x_coarse,
                                mglma_solve_stats* stats, void* cuda_stream);
 
+/* ---------------------------------------------------------------- serving */
+/* A resident lattice the server solves on: gauge field and its coarse
+ * operator (the coarse operator's basis must belong to the same gauge). */
+typedef struct {
+  mglma_gauge gauge;
+  mglma_coarse coarse;
+} mglma_serve_lattice;
+
+/* One solve request: nrhs canonical sources b for lattice `lattice`,
+ * solutions written to x (each host or device).  arrival is the time on the
+ * serving clock (seconds since mglma_serve started) at which the request was
+ * made; latency is measured from it. */
+typedef struct {
+  int lattice;
+  int nrhs;
+  const double* b;
+  double* x;
+  double arrival;
+  int64_t id;
+} mglma_request;
+
+/* Called by the server to pull requests: fill *out and return 1 when a
+ * request with arrival <= now exists, return 0 when none has arrived yet, -1
+ * when the stream has ended. */
+typedef int (*mglma_request_fn)(void* user, double now, mglma_request* out);
+/* Called once per request when all its RHS are done (or it was rejected):
+ * status, latency (completion - arrival, seconds) and one stats entry per
+ * RHS.  x holds the solutions when status is MGLMA_OK. */
+typedef void (*mglma_done_fn)(void* user, const mglma_request* req, mglma_status status, double latency,
+                              const mglma_solve_stats* per_rhs);
+
+typedef struct {
+  int nlattices;                        /* 1..8 */
+  const mglma_serve_lattice* lattices;
+  int max_slots;                        /* RHS in flight per lattice, upper bound */
+  double hbm_fraction;                  /* share of the HBM free at start the slots may take */
+  mglma_solve_params params;            /* MGLMA_SOLVER_MG parameters (tol, gcr_m, nu, ...) */
+} mglma_serve_config;
+
+typedef struct {
+  long long requests, rhs, rejected;
+  double wall_s, solves_per_s;          /* RHS completed per second of serving */
+  double p50_s, p99_s, mean_s, max_s;   /* request latency, arrival to completion */
+  int slots[8];                         /* slots granted per lattice */
+  double slot_bytes[8];                 /* device bytes per slot */
+} mglma_serve_stats;
+
+/* Serves a stream of solve requests with continuous batching.  Per lattice
+ * the server sizes a set of RHS slots from free HBM (admission by memory),
+ * keeps gauge, basis and coarse operator resident, and runs the mixed
+ * multigrid solve of mglma_solve_batch on all occupied slots together.
+ * Requests are admitted RHS by RHS as slots free up (a request larger than
+ * the slot count is spread over time); a RHS joins and leaves at restart
+ * boundaries of the inner FGCR, so requests that arrive while others run
+ * share the same kernel launches, and every RHS follows the recurrence it
+ * would follow alone.  Host sources and solutions pass one RHS at a time
+ * through a staging spinor per lattice.  Lattices are served in turn, one
+ * restart cycle each.  Malformed requests come back with MGLMA_ERR_INVALID. */
+mglma_status mglma_serve(mglma_ctx ctx, const mglma_serve_config* cfg, mglma_request_fn next, mglma_done_fn done,
+                         void* user, mglma_serve_stats* out);
+
 /* ---------------------------------------------------------------- autotuning */
 /* Times the candidate RHS tile widths for nrhs right-hand sides with CUDA
  * events and keeps the fastest in the context (used by every later call

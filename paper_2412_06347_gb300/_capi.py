@@ -344,3 +344,72 @@ def mglma_autotune_save(ctx, path):
 
 def mglma_autotune_load(ctx, path):
     _check(lib.mglma_autotune_load(_h(ctx), str(path).encode()))
+
+
+class mglma_serve_lattice(C.Structure):
+    _fields_ = [("gauge", _vp), ("coarse", _vp)]
+
+
+class mglma_request(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("nrhs", C.c_int), ("b", _vp), ("x", _vp), ("arrival", C.c_double),
+                ("id", C.c_int64)]
+
+
+class mglma_serve_config(C.Structure):
+    _fields_ = [("nlattices", C.c_int), ("lattices", C.POINTER(mglma_serve_lattice)), ("max_slots", C.c_int),
+                ("hbm_fraction", C.c_double), ("params", mglma_solve_params)]
+
+
+class mglma_serve_stats(C.Structure):
+    _fields_ = [("requests", C.c_longlong), ("rhs", C.c_longlong), ("rejected", C.c_longlong),
+                ("wall_s", C.c_double), ("solves_per_s", C.c_double), ("p50_s", C.c_double),
+                ("p99_s", C.c_double), ("mean_s", C.c_double), ("max_s", C.c_double), ("slots", C.c_int * 8),
+                ("slot_bytes", C.c_double * 8)]
+
+
+_REQ_FN = C.CFUNCTYPE(C.c_int, _vp, C.c_double, C.POINTER(mglma_request))
+_DONE_FN = C.CFUNCTYPE(None, _vp, C.POINTER(mglma_request), C.c_int, C.c_double, C.POINTER(mglma_solve_stats))
+_sig("mglma_serve", C.c_int, _vp, C.POINTER(mglma_serve_config), _REQ_FN, _DONE_FN, _vp,
+     C.POINTER(mglma_serve_stats))
+
+
+def mglma_serve(ctx, lattices, requests, params=None, max_slots=16, hbm_fraction=0.8):
+    """Serves `requests` (dicts with lattice, b, x, arrival in seconds, sorted
+    by arrival; b and x numpy arrays or device tensors).  The request
+    callback hands each request to the server once the serving clock passes
+    its arrival.  Returns (stats dict, per-request list of dicts with status,
+    latency and per-RHS stats)."""
+    lat = (mglma_serve_lattice * len(lattices))(*[mglma_serve_lattice(g, c) for g, c in lattices])
+    cfg = mglma_serve_config(len(lattices), lat, int(max_slots), float(hbm_fraction),
+                             params if params is not None else mglma_solve_params_default(MGLMA_SOLVER_MG))
+    order = sorted(range(len(requests)), key=lambda i: requests[i]["arrival"])
+    state = {"next": 0}
+    results = [None] * len(requests)
+
+    def next_fn(user, now, out):
+        k = state["next"]
+        if k >= len(order):
+            return -1
+        i = order[k]
+        rq = requests[i]
+        if rq["arrival"] > now:
+            return 0
+        nrhs = rq["b"].shape[0]
+        out[0] = mglma_request(int(rq["lattice"]), int(nrhs), ptr(rq["b"]), ptr(rq["x"]), float(rq["arrival"]), i)
+        state["next"] = k + 1
+        return 1
+
+    def done_fn(user, req, status, latency, per_rhs):
+        r = req[0]
+        results[r.id] = dict(status=status, latency=latency,
+                             stats=[dict(iterations=per_rhs[j].iterations, outer=per_rhs[j].outer,
+                                         residual=per_rhs[j].residual, converged=bool(per_rhs[j].converged))
+                                    for j in range(r.nrhs)])
+
+    cb_next, cb_done = _REQ_FN(next_fn), _DONE_FN(done_fn)
+    st = mglma_serve_stats()
+    _check(lib.mglma_serve(_h(ctx), C.byref(cfg), cb_next, cb_done, None, C.byref(st)))
+    stats = dict(requests=st.requests, rhs=st.rhs, rejected=st.rejected, wall_s=st.wall_s,
+                 solves_per_s=st.solves_per_s, p50_s=st.p50_s, p99_s=st.p99_s, mean_s=st.mean_s, max_s=st.max_s,
+                 slots=list(st.slots[:len(lattices)]), slot_bytes=list(st.slot_bytes[:len(lattices)]))
+    return stats, results

@@ -14,8 +14,14 @@
 // All RHS of a group advance together; every scalar is per RHS on the device
 // and converged RHS are frozen by device-side masks, so a RHS's iterates do
 // not depend on the other RHS of its group.
+#include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstring>
+#include <deque>
 #include <functional>
+#include <memory>
+#include <thread>
 
 #include "internal.h"
 #include "solver.h"
@@ -208,6 +214,7 @@ struct CoarseSolver {
   cudaStream_t s = nullptr;
   const mglma_coarse_s* C = nullptr;
   int m = 16;
+  int cap_hint = 0;
   GcrWork w;
   struct Graphs {
     cudaGraphExec_t init = nullptr, cycle = nullptr;
@@ -267,7 +274,7 @@ struct CoarseSolver {
   // e1 = D1^-1 b1 to tol (or max_iter, rounded up to whole cycles)
   mglma_status solve(const Vec& b, Vec& x, double tol, int max_iter, long long* iters) {
     const int n = b.nrhs;
-    if (!w.cap) MG_CHECK(w.setup(ctx, s, b, n, m));
+    if (!w.cap) MG_CHECK(w.setup(ctx, s, b, std::max(n, cap_hint), m));
     if (n > w.cap) return fail(MGLMA_ERR_INVALID, "coarse solve: more RHS than the workspace holds");
     const int cycles = (max_iter + m - 1) / m;
     std::vector<int> hact;
@@ -343,6 +350,7 @@ struct TwoLevel {
   const mglma_coarse_s* C;
   const MgParams* p;
   long long coarse_iters = 0;
+  int cap = 0;  // RHS the scratch is sized for (0: the first call's count)
   Vec b1, e1, sv, tv;
   Scalars sc;
   CoarseSolver cs;
@@ -354,45 +362,52 @@ struct TwoLevel {
     dfree(ctx, tv.p, s);
   }
   mglma_status setup(const Vec& r) {
-    const int n = r.nrhs;
+    const int n = std::max(cap, r.nrhs);
+    cap = n;
     b1.prec = e1.prec = MGLMA_FP32;
     b1.nrhs = e1.nrhs = n;
     b1.n = e1.n = (size_t)C->geo.V1 * C->n2 * 2;
     MG_CHECK(dalloc(ctx, &b1.p, b1.bytes(), s));
     MG_CHECK(dalloc(ctx, &e1.p, e1.bytes(), s));
     sv = r;
-    tv = r;
+    sv.nrhs = n;
+    tv = sv;
     sv.p = tv.p = nullptr;
-    MG_CHECK(dalloc(ctx, &sv.p, r.bytes(), s));
-    MG_CHECK(dalloc(ctx, &tv.p, r.bytes(), s));
+    MG_CHECK(dalloc(ctx, &sv.p, sv.bytes(), s));
+    MG_CHECK(dalloc(ctx, &tv.p, tv.bytes(), s));
     MG_CHECK(sc.alloc(ctx, n, 1, 1, s));
     cs.ctx = ctx;
     cs.s = s;
     cs.C = C;
+    cs.cap_hint = n;
     ready = true;
     return MGLMA_OK;
   }
   mglma_status operator()(const Vec& r, Vec& z) {
-    if (!ready) MG_CHECK(setup(r));
+    if (!ready || r.nrhs > cap) {
+      if (ready) return fail(MGLMA_ERR_INVALID, "preconditioner: more RHS than its scratch holds");
+      MG_CHECK(setup(r));
+    }
     const int n = r.nrhs;
     const mglma_subspace_s* S = C->sub;
     const int64_t V = S->geo.V;
+    Vec b1n = b1, e1n = e1, svn = sv, tvn = tv;
+    b1n.nrhs = e1n.nrhs = svn.nrhs = tvn.nrhs = n;
     Spinor rs = as_spinor(r, V), zs = as_spinor(z, V);
-    MG_CHECK(restrict_fine(ctx, S, rs, b1.p, s));
-    MG_CHECK(cs.solve(b1, e1, p->coarse_tol, p->coarse_max_iter, &coarse_iters));
-    MG_CHECK(prolong_coarse(ctx, S, e1.p, zs, false, s));
+    MG_CHECK(restrict_fine(ctx, S, rs, b1n.p, s));
+    MG_CHECK(cs.solve(b1n, e1n, p->coarse_tol, p->coarse_max_iter, &coarse_iters));
+    MG_CHECK(prolong_coarse(ctx, S, e1n.p, zs, false, s));
     if (p->nu > 0) {
       // s = r - D z ; nu MR steps on D e = s, accumulated into z
-      Spinor ss = as_spinor(sv, V), ts = as_spinor(tv, V);
+      Spinor ss = as_spinor(svn, V), ts = as_spinor(tvn, V);
       MG_CHECK(dslash(ctx, G, zs, ts, false, false, s));
-      MG_CHECK(copy_vec(ctx, r, sv, s));
-      MG_CHECK(axpby(ctx, nullptr, CM1, tv, nullptr, C1, sv, s));
+      MG_CHECK(copy_vec(ctx, r, svn, s));
+      MG_CHECK(axpby(ctx, nullptr, CM1, tvn, nullptr, C1, svn, s));
       for (int k = 0; k < p->nu; ++k) {
         MG_CHECK(dslash(ctx, G, ss, ts, false, false, s));
-        MG_CHECK(cdot(ctx, tv, sv, sc.z, s));
-        MG_CHECK(norm2(ctx, tv, sc.d, s));
+        MG_CHECK(norm2_cdot(ctx, tvn, svn, sc.d, sc.z, s));  // |D s|^2 and <D s, s>
         MG_CHECK(mr_alpha(ctx, sc.z, sc.d, sc.z, n, s));
-        MG_CHECK(axpy2(ctx, sc.z, sv, z, tv, sv, s));
+        MG_CHECK(axpy2(ctx, sc.z, svn, z, tvn, svn, s));
       }
     }
     return MGLMA_OK;
@@ -535,4 +550,389 @@ mglma_status coarse_solve64(mglma_ctx ctx, const mglma_coarse_s* C, const void* 
   return fail(MGLMA_ERR_NOT_CONVERGED, "coarse solve: FP64 defect correction did not reach tol");
 }
 
+// ============================================================ continuous-batching engine
+// One resident lattice (gauge field, basis, coarse operator) and `cap` RHS
+// slots.  The engine runs the same mixed-precision solve as mg_solve, but a
+// slot can be filled or emptied at every restart boundary of the inner FGCR:
+// a new RHS starts its own FP64 defect correction there, a RHS whose inner
+// solve converged takes its FP64 update there, and a RHS that reached the
+// FP64 tolerance leaves.  Every RHS follows exactly the recurrence it would
+// follow alone (its own scalars, masks and restart points), so its result
+// does not depend on what else is in flight.
+static Vec vsub(const Vec& v, int r0, int n) {
+  Vec o = v;
+  o.p = (char*)v.p + (size_t)r0 * v.n * (v.prec == MGLMA_FP64 ? 8 : 4);
+  o.nrhs = n;
+  return o;
+}
+static Spinor ssub(const Spinor& v, int r0, int n) {
+  Spinor o = v;
+  o.p = (char*)v.p + (size_t)r0 * v.rhs_reals() * (v.prec == MGLMA_FP64 ? 8 : 4);
+  o.nrhs = n;
+  return o;
+}
+
+struct Engine {
+  struct Slot {
+    int req = -1;   // request index, -1 when free
+    int rhs = 0;    // RHS of the request held here
+    int inner = 0;  // FGCR iterations of the current inner solve
+    RhsStat st;
+    double bb = 0;
+  };
+  struct Done {
+    int slot, req, rhs;
+  };
+  mglma_ctx ctx = nullptr;
+  cudaStream_t s = nullptr;
+  const mglma_gauge_s* G = nullptr;
+  const mglma_coarse_s* C = nullptr;
+  MgParams p;
+  int cap = 0;
+  int64_t V = 0;
+  Spinor b64, x64, r64, w64, r32, e32;
+  double* dsc = nullptr;  // per slot: |r|^2 [cap], |r| [cap], 1/|r| [cap]
+  double* stage = nullptr;  // one canonical spinor: host requests pass through it
+  GcrWork gw;
+  TwoLevel K;
+  std::vector<Slot> slots;
+  FreeList* fl = nullptr;
+  static constexpr int kInnerCap = 400;
+
+  // device bytes one slot needs (FP64 b, x, r, D x; FP32 r, e, FGCR
+  // directions and images, preconditioner scratch)
+  static size_t slot_bytes(int64_t V, int m) { return (size_t)V * (4 * 192 + (size_t)(5 + 2 * m) * 96); }
+  static size_t fixed_bytes(int64_t V) { return (size_t)V * 192; }
+
+  ~Engine() { delete fl; }
+
+  mglma_status setup(mglma_ctx c, cudaStream_t st, const mglma_gauge_s* g, const mglma_coarse_s* co,
+                     const MgParams& prm, int capacity) {
+    ctx = c;
+    s = st;
+    G = g;
+    C = co;
+    p = prm;
+    cap = capacity;
+    V = g->g.V;
+    fl = new FreeList(ctx, s);
+    for (Spinor* f : {&b64, &x64, &r64, &w64}) {
+      MG_CHECK(alloc_spinor(ctx, *f, MGLMA_FP64, cap, V, s));
+      fl->add(f->p);
+    }
+    for (Spinor* f : {&r32, &e32}) {
+      MG_CHECK(alloc_spinor(ctx, *f, MGLMA_FP32, cap, V, s));
+      fl->add(f->p);
+    }
+    MG_CHECK(dalloc(ctx, (void**)&dsc, sizeof(double) * 3 * cap, s));
+    fl->add(dsc);
+    MG_CHECK(dalloc(ctx, (void**)&stage, (size_t)V * 24 * sizeof(double), s));
+    fl->add(stage);
+    MG_CHECK(gw.setup(ctx, s, as_vec(r32), cap, p.gcr_m));
+    K.ctx = ctx;
+    K.s = s;
+    K.G = G;
+    K.C = C;
+    K.p = &p;
+    K.cap = cap;
+    MG_CHECK(fill_int(gw.sc.active, 0, cap, s));
+    slots.assign(cap, Slot());
+    return MGLMA_OK;
+  }
+
+  int used_prefix() const {
+    int hi = 0;
+    for (int i = 0; i < cap; ++i)
+      if (slots[i].req >= 0) hi = i + 1;
+    return hi;
+  }
+  int first_free() const {
+    for (int i = 0; i < cap; ++i)
+      if (slots[i].req < 0) return i;
+    return -1;
+  }
+
+  // start the inner FP32 solve of slot i from its FP64 residual r64[i]
+  mglma_status start_inner(int i) {
+    std::vector<double> h;
+    MG_CHECK(norm2(ctx, as_vec(ssub(r64, i, 1)), dsc + i, s));
+    MG_CHECK(read_doubles(dsc + i, h, 1, s));
+    const double rn = std::sqrt(h[0]);
+    const double pr[2] = {rn, rn > 0 ? 1.0 / rn : 0.0};
+    MG_CUDA(cudaMemcpyAsync(dsc + cap + i, &pr[0], sizeof(double), cudaMemcpyHostToDevice, s));
+    MG_CUDA(cudaMemcpyAsync(dsc + 2 * cap + i, &pr[1], sizeof(double), cudaMemcpyHostToDevice, s));
+    Spinor rs = ssub(r32, i, 1);
+    MG_CHECK(convert_spinor(ctx, ssub(r64, i, 1), rs, s, dsc + 2 * cap + i, false));
+    Vec ri = vsub(as_vec(r32), i, 1), xi = vsub(as_vec(e32), i, 1);
+    Vec gr = vsub(gw.view(gw.rp, 0, cap), i, 1);
+    double* bb = gw.sc.d + (size_t)(gw.m + 1) * gw.cap;
+    MG_CHECK(zero_vec(ctx, xi, s));
+    MG_CHECK(copy_vec(ctx, ri, gr, s));
+    MG_CHECK(norm2(ctx, ri, bb + i, s));
+    MG_CHECK(fill_int(gw.sc.active + i, 1, 1, s));
+    slots[i].inner = 0;
+    return MGLMA_OK;
+  }
+
+  // a new RHS in slot i from a canonical device spinor; returns true in
+  // *finished when the source is zero (x = 0, nothing to iterate)
+  mglma_status admit(int i, int req, int rhs, const double* canon, bool* finished) {
+    Slot& sl = slots[i];
+    sl.req = req;
+    sl.rhs = rhs;
+    sl.st = RhsStat();
+    Spinor bi = ssub(b64, i, 1), ri = ssub(r64, i, 1);
+    MG_CHECK(pack_spinor(ctx, canon, bi, s));
+    Vec xv = as_vec(ssub(x64, i, 1));
+    MG_CHECK(zero_vec(ctx, xv, s));
+    Vec rv = as_vec(ri);
+    MG_CHECK(copy_vec(ctx, as_vec(bi), rv, s));
+    std::vector<double> h;
+    MG_CHECK(norm2(ctx, as_vec(bi), dsc + i, s));
+    MG_CHECK(read_doubles(dsc + i, h, 1, s));
+    sl.bb = h[0];
+    *finished = !(h[0] > 0);
+    if (*finished) {
+      sl.st.residual = 0;
+      sl.st.converged = true;
+      return MGLMA_OK;
+    }
+    return start_inner(i);
+  }
+
+  void release(int i) {
+    slots[i].req = -1;
+    fill_int(gw.sc.active + i, 0, 1, s);
+  }
+
+  // one restart cycle of the inner FGCR over the occupied prefix, then the
+  // FP64 updates of every slot whose inner solve finished
+  mglma_status cycle(std::vector<Done>& done) {
+    const int hi = used_prefix();
+    if (hi == 0) return MGLMA_OK;
+    OpFn A = [&](const Vec& in, Vec& o) {
+      Spinor a = as_spinor(in, V), bo = as_spinor(o, V);
+      return dslash(ctx, G, a, bo, false, false, s);
+    };
+    OpFn M = [&](const Vec& in, Vec& o) { return K(in, o); };
+    Vec x = vsub(as_vec(e32), 0, hi);
+    for (int k = 0; k < gw.m; ++k) MG_CHECK(gcr_iter(gw, A, &M, x, hi, k, p.inner_tol * p.inner_tol));
+    std::vector<int> act;
+    MG_CHECK(read_active(gw, hi, act));
+    for (int i = 0; i < hi; ++i) {
+      Slot& sl = slots[i];
+      if (sl.req < 0) continue;
+      sl.inner += gw.m;
+      if (act[i] && sl.inner < kInnerCap) continue;
+      // FP64 update: x += |r| e ; r = b - D x
+      Spinor xi = ssub(x64, i, 1), wi = ssub(w64, i, 1), ri = ssub(r64, i, 1);
+      MG_CHECK(convert_spinor(ctx, ssub(e32, i, 1), xi, s, dsc + cap + i, true));
+      MG_CHECK(dslash(ctx, G, xi, wi, false, false, s));
+      Vec rv = as_vec(ri);
+      MG_CHECK(copy_vec(ctx, as_vec(ssub(b64, i, 1)), rv, s));
+      MG_CHECK(axpby(ctx, nullptr, CM1, as_vec(wi), nullptr, C1, rv, s));
+      std::vector<double> h;
+      MG_CHECK(norm2(ctx, rv, dsc + i, s));
+      MG_CHECK(read_doubles(dsc + i, h, 1, s));
+      sl.st.outer++;
+      sl.st.iterations += sl.inner;
+      sl.st.residual = std::sqrt(h[0] / sl.bb);
+      if (!std::isfinite(sl.st.residual)) return fail(MGLMA_ERR_NUMERIC, "serve: non-finite residual");
+      sl.st.converged = sl.st.residual <= p.tol;
+      if (sl.st.converged || sl.st.outer >= 50 || sl.st.iterations >= p.max_iter) {
+        sl.st.coarse_iterations = K.coarse_iters;
+        done.push_back({i, sl.req, sl.rhs});
+      } else {
+        MG_CHECK(start_inner(i));
+      }
+    }
+    return MGLMA_OK;
+  }
+};
+
 }  // namespace mglma
+
+using namespace mglma;
+
+extern "C" mglma_status mglma_serve(mglma_ctx ctx, const mglma_serve_config* cfg, mglma_request_fn next,
+                                    mglma_done_fn done, void* user, mglma_serve_stats* out) {
+  if (!ctx || !cfg || !next || !cfg->lattices || cfg->nlattices < 1 || cfg->nlattices > 8)
+    return fail(MGLMA_ERR_INVALID, "serve: bad configuration");
+  if (cfg->max_slots < 1 || !(cfg->hbm_fraction > 0) || cfg->hbm_fraction > 1)
+    return fail(MGLMA_ERR_INVALID, "serve: max_slots >= 1 and 0 < hbm_fraction <= 1 required");
+  MG_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const mglma_solve_params* prm = &cfg->params;
+  MgParams mp;
+  mp.tol = prm->tol;
+  mp.max_iter = prm->max_iter;
+  mp.gcr_m = prm->gcr_m;
+  mp.nu = prm->nu;
+  mp.inner_tol = prm->inner_tol;
+  mp.coarse_tol = prm->coarse_tol;
+  mp.coarse_max_iter = prm->coarse_max_iter;
+  // admission by free HBM: the slots of each lattice take an equal share of
+  // hbm_fraction of the memory free now
+  size_t fr = 0, tot = 0;
+  MG_CUDA(cudaMemGetInfo(&fr, &tot));
+  const int NL = cfg->nlattices;
+  std::vector<std::unique_ptr<Engine>> eng(NL);
+  mglma_serve_stats st;
+  memset(&st, 0, sizeof(st));
+  for (int l = 0; l < NL; ++l) {
+    const mglma_serve_lattice& L = cfg->lattices[l];
+    if (!L.gauge || !L.coarse || L.coarse->sub->gauge != L.gauge)
+      return fail(MGLMA_ERR_INVALID, "serve: lattice entries need a gauge field and its coarse operator");
+    const size_t per = Engine::slot_bytes(L.gauge->g.V, mp.gcr_m);
+    const double share = cfg->hbm_fraction * (double)fr / NL - (double)Engine::fixed_bytes(L.gauge->g.V);
+    const int cap = share > 0 ? (int)std::min<size_t>((size_t)cfg->max_slots, (size_t)(share / per)) : 0;
+    if (cap < 1) return fail(MGLMA_ERR_OOM, "serve: not enough free HBM for one slot of lattice " + std::to_string(l));
+    eng[l].reset(new Engine());
+    MG_CHECK(eng[l]->setup(ctx, s, L.gauge, L.coarse, mp, cap));
+    st.slots[l] = cap;
+    st.slot_bytes[l] = (double)per;
+  }
+  MG_CUDA(cudaStreamSynchronize(s));
+  struct Req {
+    mglma_request r;
+    int next_rhs = 0, remaining = 0;
+    bool bhost = false, xhost = false;
+    std::vector<mglma_solve_stats> stats;
+    mglma_status status = MGLMA_OK;
+  };
+  std::vector<Req> reqs;
+  std::vector<std::deque<int>> queue(NL);
+  std::vector<double> lat;
+  auto t0 = std::chrono::steady_clock::now();
+  auto now = [&] { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+  bool ended = false;
+  long long rhs_done = 0;
+  mglma_status err = MGLMA_OK;
+  auto finish_req = [&](int q) {
+    Req& R = reqs[q];
+    cudaStreamSynchronize(s);
+    const double l = now() - R.r.arrival;
+    if (R.status == MGLMA_OK) lat.push_back(l);
+    if (done) done(user, &R.r, R.status, l, R.stats.data());
+  };
+  while (err == MGLMA_OK) {
+    // pull every request that has arrived
+    while (!ended) {
+      mglma_request rq;
+      memset(&rq, 0, sizeof(rq));
+      const int got = next(user, now(), &rq);
+      if (got < 0) ended = true;
+      if (got != 1) break;
+      Req R;
+      R.r = rq;
+      R.remaining = rq.nrhs;
+      R.stats.assign(std::max(rq.nrhs, 1), mglma_solve_stats());
+      const int l = rq.lattice;
+      const bool bad = l < 0 || l >= NL || rq.nrhs < 1 || !rq.b || !rq.x;
+      reqs.push_back(R);
+      const int q = (int)reqs.size() - 1;
+      st.requests++;
+      if (bad) {
+        reqs[q].status = MGLMA_ERR_INVALID;
+        st.rejected++;
+        if (done) done(user, &reqs[q].r, reqs[q].status, 0.0, reqs[q].stats.data());
+        continue;
+      }
+      queue[l].push_back(q);
+    }
+    bool active = false;
+    for (int l = 0; l < NL && err == MGLMA_OK; ++l) {
+      Engine& E = *eng[l];
+      // admit waiting RHS into free slots (a request may be spread over cycles)
+      while (!queue[l].empty() && err == MGLMA_OK) {
+        const int q = queue[l].front();
+        Req& R = reqs[q];
+        const size_t one = (size_t)E.V * 24;
+        if (R.next_rhs == 0) {
+          R.bhost = !is_device_pointer(R.r.b);
+          R.xhost = !is_device_pointer(R.r.x);
+        }
+        int slot;
+        while (R.next_rhs < R.r.nrhs && (slot = E.first_free()) >= 0) {
+          bool fin = false;
+          const int rhs = R.next_rhs++;
+          const double* src = R.r.b + (size_t)rhs * one;
+          if (R.bhost) {
+            cudaMemcpyAsync(E.stage, src, one * sizeof(double), cudaMemcpyHostToDevice, s);
+            src = E.stage;
+          }
+          err = E.admit(slot, q, rhs, src, &fin);
+          if (err != MGLMA_OK) break;
+          if (fin) {  // zero source: x = 0
+            if (R.xhost)
+              memset(R.r.x + (size_t)rhs * one, 0, one * sizeof(double));
+            else
+              cudaMemsetAsync(R.r.x + (size_t)rhs * one, 0, one * sizeof(double), s);
+            R.stats[rhs].converged = 1;
+            E.release(slot);
+            if (--R.remaining == 0) finish_req(q);
+          }
+        }
+        if (err != MGLMA_OK || R.next_rhs < R.r.nrhs) break;
+        queue[l].pop_front();
+      }
+      if (err != MGLMA_OK || E.used_prefix() == 0) continue;
+      active = true;
+      std::vector<Engine::Done> fin;
+      err = E.cycle(fin);
+      for (auto& d : fin) {
+        if (err != MGLMA_OK) break;
+        Req& R = reqs[d.req];
+        const Engine::Slot& sl = E.slots[d.slot];
+        Spinor xi = ssub(E.x64, d.slot, 1);
+        const size_t one = (size_t)E.V * 24;
+        if (R.xhost) {
+          err = unpack_spinor(ctx, xi, E.stage, s);
+          if (err == MGLMA_OK && cudaMemcpyAsync(R.r.x + (size_t)d.rhs * one, E.stage, one * sizeof(double),
+                                                 cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            err = fail(MGLMA_ERR_CUDA, "serve: copy of a solution to the host failed");
+          cudaStreamSynchronize(s);
+        } else {
+          err = unpack_spinor(ctx, xi, R.r.x + (size_t)d.rhs * one, s);
+        }
+        mglma_solve_stats& o = R.stats[d.rhs];
+        o.iterations = sl.st.iterations;
+        o.outer = sl.st.outer;
+        o.coarse_iterations = sl.st.coarse_iterations;
+        o.residual = sl.st.residual;
+        o.converged = sl.st.converged ? 1 : 0;
+        if (!sl.st.converged) R.status = MGLMA_ERR_NOT_CONVERGED;
+        E.release(d.slot);
+        rhs_done++;
+        if (--R.remaining == 0) finish_req(d.req);
+      }
+    }
+    if (err != MGLMA_OK) break;
+    if (!active) {
+      bool waiting = false;
+      for (auto& qd : queue) waiting = waiting || !qd.empty();
+      if (ended && !waiting) break;
+      if (!waiting) std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+  }
+  cudaStreamSynchronize(s);
+  const double wall = now();
+  if (out) {
+    st.rhs = rhs_done;
+    st.wall_s = wall;
+    st.solves_per_s = wall > 0 ? rhs_done / wall : 0;
+    if (!lat.empty()) {
+      std::vector<double> v = lat;
+      std::sort(v.begin(), v.end());
+      auto pct = [&](double q) { return v[std::min(v.size() - 1, (size_t)std::ceil(q * v.size()) - 1)]; };
+      st.p50_s = pct(0.50);
+      st.p99_s = pct(0.99);
+      st.max_s = v.back();
+      double sum = 0;
+      for (double x : v) sum += x;
+      st.mean_s = sum / v.size();
+    }
+    *out = st;
+  }
+  return err;
+}
