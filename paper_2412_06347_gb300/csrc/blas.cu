@@ -75,23 +75,32 @@ __global__ void axpy2_kernel(const typename Pair<R>::T* p, typename Pair<R>::T* 
   }
 }
 
-// y_r -= sum_{j<k} c[j][r] x_j,r  with x_j = x0 + j * jstride (vectors)
+// y_r -= sum_{j<k} c[j][r] x_j,r  with x_j = x0 + j * jstride (vectors); a
+// second pair (x0b, yb) with the same coefficients is updated in the same
+// pass when given (the GCR directions and their images).  The block's
+// coefficients sit in shared memory.
 template <typename R>
-__global__ void multi_axpy_kernel(const typename Pair<R>::T* __restrict__ x0, size_t jstride, int k,
-                                  typename Pair<R>::T* __restrict__ y, const double2* __restrict__ c, int nrhs,
-                                  size_t m) {
+__global__ void multi_axpy_kernel(const typename Pair<R>::T* __restrict__ x0, typename Pair<R>::T* __restrict__ y,
+                                  const typename Pair<R>::T* __restrict__ x0b, typename Pair<R>::T* __restrict__ yb,
+                                  size_t jstride, int k, const double2* __restrict__ c, int nrhs, size_t m) {
+  __shared__ double2 cs[64];
   const int r = blockIdx.y;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    const double2 v = c[(size_t)j * nrhs + r];
+    cs[j] = make_double2(-v.x, -v.y);
+  }
+  __syncthreads();
   const size_t off = (size_t)r * m;
   const double2 one = make_double2(1, 0);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
     auto acc = y[off + i];
-    for (int j = 0; j < k; ++j) {
-      double2 cj = c[(size_t)j * nrhs + r];
-      cj.x = -cj.x;
-      cj.y = -cj.y;
-      acc = lc(x0[j * jstride + off + i], acc, cj, one);
-    }
+    for (int j = 0; j < k; ++j) acc = lc(x0[j * jstride + off + i], acc, cs[j], one);
     y[off + i] = acc;
+    if (yb) {
+      auto accb = yb[off + i];
+      for (int j = 0; j < k; ++j) accb = lc(x0b[j * jstride + off + i], accb, cs[j], one);
+      yb[off + i] = accb;
+    }
   }
 }
 
@@ -241,21 +250,22 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const typename Pair<R>::T* _
   const size_t off = (size_t)r * m;
   const size_t step = (size_t)nb * RT;
   if (MODE == 1) {
-    for (int j = 0; j < k; ++j) {
-      RAcc<R> acc;
-      const auto* xj = x0 + j * jstride + off;
-      size_t i = (size_t)blockIdx.x * RT + threadIdx.x;
-      for (; i + 3 * step < m; i += 4 * step) {
-        const auto a0 = xj[i], a1 = xj[i + step], a2 = xj[i + 2 * step], a3 = xj[i + 3 * step];
-        const auto b0 = y[off + i], b1 = y[off + i + step], b2 = y[off + i + 2 * step], b3 = y[off + i + 3 * step];
-        acc.add_d(a0, b0);
-        acc.add_d(a1, b1);
-        acc.add_d(a2, b2);
-        acc.add_d(a3, b3);
+    // directions in chunks of up to 8 per pass over y
+    for (int j0 = 0; j0 < k; j0 += 8) {
+      const int nj = min(8, k - j0);
+      RAcc<R> acc[8];
+      for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < m; i += step) {
+        const auto yv = y[off + i];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          if (jj < nj) acc[jj].add_d(x0[(j0 + jj) * jstride + off + i], yv);
       }
-      for (; i < m; i += step) acc.add_d(xj[i], y[off + i]);
-      const double2 v = block_sum2<RT>(acc.dot());
-      if (threadIdx.x == 0) part[((size_t)j * nrhs + r) * nb + blockIdx.x] = v;
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        if (jj >= nj) break;
+        const double2 v = block_sum2<RT>(acc[jj].dot());
+        if (threadIdx.x == 0) part[((size_t)(j0 + jj) * nrhs + r) * nb + blockIdx.x] = v;
+      }
     }
   } else {
     RAcc<R> acc;
@@ -365,17 +375,20 @@ mglma_status axpy2(mglma_ctx ctx, const double2* a, const Vec& p, Vec& x, const 
 }
 
 mglma_status multi_axpy(mglma_ctx ctx, const Vec& x0, size_t jstride_reals, int k, Vec& y, const double2* c,
-                        cudaStream_t s) {
+                        cudaStream_t s, const Vec* x0b, Vec* yb) {
   if (k == 0) return MGLMA_OK;
-  ProfScope ps(ctx, K_BLAS, s, (k + 2.0) * y.bytes());
+  if (k > 64) return fail(MGLMA_ERR_INVALID, "multi_axpy: more than 64 directions");
+  ProfScope ps(ctx, K_BLAS, s, (k + 2.0) * y.bytes() * (yb ? 2.0 : 1.0));
   const size_t m = pairs(y);
   dim3 g = ew_grid(ctx, m, y.nrhs);
   if (y.prec == MGLMA_FP64)
-    multi_axpy_kernel<double><<<g, 256, 0, s>>>((const double2*)x0.p, jstride_reals / 2, k, (double2*)y.p, c,
-                                                y.nrhs, m);
+    multi_axpy_kernel<double><<<g, 256, 0, s>>>((const double2*)x0.p, (double2*)y.p,
+                                                x0b ? (const double2*)x0b->p : nullptr, yb ? (double2*)yb->p : nullptr,
+                                                jstride_reals / 2, k, c, y.nrhs, m);
   else
-    multi_axpy_kernel<float><<<g, 256, 0, s>>>((const float4*)x0.p, jstride_reals / 4, k, (float4*)y.p, c, y.nrhs,
-                                               m);
+    multi_axpy_kernel<float><<<g, 256, 0, s>>>((const float4*)x0.p, (float4*)y.p,
+                                               x0b ? (const float4*)x0b->p : nullptr, yb ? (float4*)yb->p : nullptr,
+                                               jstride_reals / 4, k, c, y.nrhs, m);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }

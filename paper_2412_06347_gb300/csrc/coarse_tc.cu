@@ -128,7 +128,77 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint32_t mma_phase = 0;
   const int ntiles = (nrhs + NT - 1) / NT;
   const int nv = n2 / 2;
+  // ---- B operand: each thread owns items w = tid + q*TC_THREADS of a work
+  // unit (site, RHS tile); item = (d, j octet, RHS r): 8 complex of X.
+  // The next unit's items are loaded into registers while the current
+  // unit's MMA runs.
+  constexpr int IT = (9 * 8 * NT + TC_THREADS - 1) / TC_THREADS;  // G <= 8
+  const int nitems = 9 * G * NT;
+  float4 xr[IT][4];
+  auto load_unit = [&](int64_t yy, int rt) {
+    int xx[4];
+    site_coords(q, yy, xx);
+    const int r0 = rt * NT;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int w = tid + it * TC_THREADS;
+      if (w >= nitems) break;
+      const int r = w % NT, jo = (w / NT) % G, d = w / (NT * G);
+      if (r0 + r < nrhs) {
+        const int64_t z = d == 8 ? yy : (d < 4 ? nbr_fwd(q, yy, xx, d) : nbr_bwd(q, yy, xx, d - 4));
+        const float4* src = reinterpret_cast<const float4*>(X + ((size_t)(r0 + r) * V1 + z) * n2 + jo * 8);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) xr[it][h] = __ldg(src + h);
+      } else {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) xr[it][h] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  };
+  auto store_unit = [&]() {
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int w = tid + it * TC_THREADS;
+      if (w >= nitems) break;
+      const int r = w % NT, jo = (w / NT) % G, d = w / (NT * G);
+      float re[8], im[8];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        re[2 * h] = xr[it][h].x;
+        im[2 * h] = xr[it][h].y;
+        re[2 * h + 1] = xr[it][h].z;
+        im[2 * h + 1] = xr[it][h].w;
+      }
+      if (dagger) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (jo * 8 + e >= nv) {
+            re[e] = -re[e];
+            im[e] = -im[e];
+          }
+      }
+      uint32_t pr[4], pim[4], nim[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        pr[e] = (uint32_t)bf16_bits(re[2 * e]) | ((uint32_t)bf16_bits(re[2 * e + 1]) << 16);
+        pim[e] = (uint32_t)bf16_bits(im[2 * e]) | ((uint32_t)bf16_bits(im[2 * e + 1]) << 16);
+        nim[e] = (uint32_t)bf16_bits(-im[2 * e]) | ((uint32_t)bf16_bits(-im[2 * e + 1]) << 16);
+      }
+      // k chunk of (d, part, jo): c = (d * 2 + part) * G + jo; columns r and NT + r
+      const int c0 = (d * 2) * G + jo, c1 = (d * 2 + 1) * G + jo;
+      auto put = [&](int c, int col, const uint32_t* v) {
+        uint4* p = reinterpret_cast<uint4*>(Bsm + ((size_t)c * (NN / 8) + col / 8) * 128 + (col % 8) * 16);
+        *p = make_uint4(v[0], v[1], v[2], v[3]);
+      };
+      put(c0, r, pr);        // Re X  -> Re Y column
+      put(c1, r, nim);       // -Im X -> Re Y column
+      put(c0, NT + r, pim);  // Im X  -> Im Y column
+      put(c1, NT + r, pr);   // Re X  -> Im Y column
+    }
+  };
+
   int t = 0;
+  if (y0 < V1) load_unit(y0, 0);
   for (int64_t y = y0; y < V1; y += gridDim.x, ++t) {
     const int buf = t & 1;
     const int64_t yn = y + gridDim.x;
@@ -136,55 +206,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       issue_copy(yn, buf ^ 1);
       pending[buf ^ 1] = true;
     }
-    int x[4];
-    site_coords(q, y, x);
     for (int rt = 0; rt < ntiles; ++rt) {
-      // ---- B tile: work item = (d, part-free j octet, column-pair r)
       const int r0 = rt * NT;
-      for (int w = tid; w < 9 * G * NT; w += TC_THREADS) {
-        const int r = w % NT, jo = (w / NT) % G, d = w / (NT * G);
-        const int64_t z = d == 8 ? y : (d < 4 ? nbr_fwd(q, y, x, d) : nbr_bwd(q, y, x, d - 4));
-        float re[8], im[8];
-        if (r0 + r < nrhs) {
-          const float4* src = reinterpret_cast<const float4*>(X + ((size_t)(r0 + r) * V1 + z) * n2 + jo * 8);
-#pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const float4 v = __ldg(src + h);
-            re[2 * h] = v.x;
-            im[2 * h] = v.y;
-            re[2 * h + 1] = v.z;
-            im[2 * h + 1] = v.w;
-          }
-          if (dagger) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-              if (jo * 8 + e >= nv) {
-                re[e] = -re[e];
-                im[e] = -im[e];
-              }
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) re[e] = im[e] = 0.f;
-        }
-        uint32_t pr[4], pim[4], nim[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          pr[e] = (uint32_t)bf16_bits(re[2 * e]) | ((uint32_t)bf16_bits(re[2 * e + 1]) << 16);
-          pim[e] = (uint32_t)bf16_bits(im[2 * e]) | ((uint32_t)bf16_bits(im[2 * e + 1]) << 16);
-          nim[e] = (uint32_t)bf16_bits(-im[2 * e]) | ((uint32_t)bf16_bits(-im[2 * e + 1]) << 16);
-        }
-        // k chunk of (d, part, jo): c = (d * 2 + part) * G + jo; column rows r and NT + r
-        const int c0 = (d * 2) * G + jo, c1 = (d * 2 + 1) * G + jo;
-        auto put = [&](int c, int col, const uint32_t* v) {
-          uint4* p = reinterpret_cast<uint4*>(Bsm + ((size_t)c * (NN / 8) + col / 8) * 128 + (col % 8) * 16);
-          *p = make_uint4(v[0], v[1], v[2], v[3]);
-        };
-        put(c0, r, pr);        // Re X  -> Re Y column
-        put(c1, r, nim);       // -Im X -> Re Y column
-        put(c0, NT + r, pim);  // Im X  -> Im Y column
-        put(c1, NT + r, pr);   // Re X  -> Im Y column
-      }
+      store_unit();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0 && !abort_flag) {
@@ -216,6 +240,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               smem_u32(bars + 2)));
         }
       }
+      // next unit's gather overlaps the MMA
+      if (rt + 1 < ntiles)
+        load_unit(y, rt + 1);
+      else if (yn < V1)
+        load_unit(yn, 0);
       __syncthreads();
       if (abort_flag) break;
       if (tid == 0) {

@@ -241,8 +241,9 @@ mglma_status caxpy(mglma_ctx, const double2* a, const Vec& x, Vec& y, cudaStream
 // x += a p ; r -= a w
 mglma_status axpy2(mglma_ctx, const double2* a, const Vec& p, Vec& x, const Vec& w, Vec& r, cudaStream_t s);
 // y -= sum_{j<k} c[j*nrhs + r] x_j  where x_j starts jstride reals after x_{j-1}
+// (x0b, yb optional: a second set updated with the same coefficients)
 mglma_status multi_axpy(mglma_ctx, const Vec& x0, size_t jstride_reals, int k, Vec& y, const double2* c,
-                        cudaStream_t s);
+                        cudaStream_t s, const Vec* x0b = nullptr, Vec* yb = nullptr);
 mglma_status copy_vec(mglma_ctx, const Vec& x, Vec& y, cudaStream_t s);
 mglma_status zero_vec(mglma_ctx, Vec& y, cudaStream_t s);
 // out[r] = <x_r, y_r> = sum conj(x) y (FP64 accumulation, deterministic)

@@ -146,8 +146,7 @@ static mglma_status gcr_iter(GcrWork& w, const OpFn& A, const OpFn* M, Vec& x, i
       ProfScope ps(ctx, K_SCALAR, s);
       gcr_coef_kernel<<<(k * n + 63) / 64, 64, 0, s>>>(dots, nw, coef, k, n);
     }
-    MG_CHECK(multi_axpy(ctx, W0, w.stride(), k, Wk, coef, s));
-    MG_CHECK(multi_axpy(ctx, Z0, w.stride(), k, Zk, coef, s));
+    MG_CHECK(multi_axpy(ctx, W0, w.stride(), k, Wk, coef, s, &Z0, &Zk));
   }
   MG_CHECK(norm2_cdot(ctx, Wk, r, nw + (size_t)k * n, num, s));
   {
@@ -173,8 +172,11 @@ static mglma_status read_active(GcrWork& w, int n, std::vector<int>& h) {
 // Batched flexible GCR(m): x = A^-1 b per RHS to |r| <= tol |b| (or max_iter).
 // M (nullable) is the right preconditioner.  poll_every > 0 reads the active
 // mask on the host every that many iterations and stops when all converged.
+// tol_scale (nullable, host, n entries): RHS r stops at |r| <= tol *
+// tol_scale[r] * |b_r| instead of tol * |b_r|.
 static mglma_status gcr(mglma_ctx ctx, cudaStream_t s, const OpFn& A, const OpFn* M, const Vec& b, Vec& x, int m,
-                        int max_iter, double tol, int poll_every, GcrResult& res) {
+                        int max_iter, double tol, int poll_every, GcrResult& res,
+                        const std::vector<double>* tol_scale = nullptr) {
   const int n = b.nrhs;
   res = GcrResult();
   res.per_rhs.assign(n, 0);
@@ -182,6 +184,15 @@ static mglma_status gcr(mglma_ctx ctx, cudaStream_t s, const OpFn& A, const OpFn
   GcrWork w;
   MG_CHECK(w.setup(ctx, s, b, n, m));
   MG_CHECK(gcr_init(w, b, x));
+  if (tol_scale) {
+    // the mask compares |r|^2 with tol^2 |b|^2: scale the stored |b|^2
+    double* bb = w.sc.d + (size_t)(w.m + 1) * w.cap;
+    std::vector<double> hb;
+    MG_CHECK(read_doubles(bb, hb, n, s));
+    for (int i = 0; i < n; ++i) hb[i] *= (*tol_scale)[i] * (*tol_scale)[i];
+    MG_CUDA(cudaMemcpyAsync(bb, hb.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+  }
   std::vector<int> hact, prev;
   if (poll_every == 1) MG_CHECK(read_active(w, n, prev));
   int it = 0;
@@ -414,6 +425,14 @@ struct TwoLevel {
   }
 };
 
+// Inner-tolerance factor for a RHS at FP64 relative residual `rel`: when
+// this cycle can reach the target (inner_tol * rel < 10 tol), the inner solve
+// aims at 0.3 tol / rel instead of inner_tol.
+static double final_cycle_scale(const MgParams& p, double rel) {
+  if (!(rel > 0) || p.inner_tol * rel >= 10.0 * p.tol) return 1.0;
+  return std::min(1.0, 0.3 * p.tol / (rel * p.inner_tol));
+}
+
 // x (FP64, zero on entry) = D^-1 b to p.tol in the FP64 residual.
 mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_s* C, const Spinor& b, Spinor& x,
                       const MgParams& p, std::vector<RhsStat>& out, cudaStream_t s) {
@@ -475,8 +494,12 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
     sqrt_kernel<<<nb, tb, 0, s>>>(rr, rn, n, 0);
     MG_CHECK(convert_spinor(ctx, r, r32, s, rinv, false));
     Vec v32 = as_vec(r32), e = as_vec(e32);
+    // a cycle that can finish a RHS aims a little below what it needs, so two
+    // cycles of inner_tol do not land just above the target
+    std::vector<double> scale(n, 1.0);
+    for (int i = 0; i < n; ++i) scale[i] = final_cycle_scale(p, out[i].residual);
     GcrResult gr;
-    MG_CHECK(gcr(ctx, s, A, &Kf, v32, e, p.gcr_m, p.max_iter - total_inner, p.inner_tol, 1, gr));
+    MG_CHECK(gcr(ctx, s, A, &Kf, v32, e, p.gcr_m, p.max_iter - total_inner, p.inner_tol, 1, gr, &scale));
     total_inner += gr.iterations;
     for (int i = 0; i < n; ++i) {
       out[i].iterations += gr.per_rhs[i];
@@ -668,8 +691,12 @@ struct Engine {
     double* bb = gw.sc.d + (size_t)(gw.m + 1) * gw.cap;
     MG_CHECK(zero_vec(ctx, xi, s));
     MG_CHECK(copy_vec(ctx, ri, gr, s));
-    MG_CHECK(norm2(ctx, ri, bb + i, s));
+    // |r32| = 1: the stopping reference is the squared inner-tolerance factor
+    const double sc = final_cycle_scale(p, slots[i].bb > 0 ? rn / std::sqrt(slots[i].bb) : 1.0);
+    const double ref = sc * sc;
+    MG_CUDA(cudaMemcpyAsync(bb + i, &ref, sizeof(double), cudaMemcpyHostToDevice, s));
     MG_CHECK(fill_int(gw.sc.active + i, 1, 1, s));
+    MG_CUDA(cudaStreamSynchronize(s));
     slots[i].inner = 0;
     return MGLMA_OK;
   }

@@ -232,7 +232,7 @@ void mglma_solve_params_default(mglma_solve_params* p, int method) {
   p->max_iter = method == MGLMA_SOLVER_CGNE ? 100000 : 4000;
   p->gcr_m = 8;
   p->nu = 2;
-  p->inner_tol = 1e-5;
+  p->inner_tol = 3e-6;
   p->coarse_tol = 0.02;
   p->coarse_max_iter = 100;
   p->check_every = method == MGLMA_SOLVER_CGNE ? 20 : 1;

@@ -70,7 +70,7 @@ struct MgParams {
   int max_iter = 2000;
   int gcr_m = 8;
   int nu = 2;
-  double inner_tol = 1e-5;
+  double inner_tol = 3e-6;
   double coarse_tol = 0.02;
   int coarse_max_iter = 100;
 };
