@@ -197,6 +197,9 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+COARSE_SOLVERS = {"gcr": 0, "minres": 1}
+
+
 def run_serving(m, torch, ctx, g, C, w, args, dev, stream):
     """Continuous-batching server on the resident lattice: Poisson arrivals
     (seed 4242, 20 requests/s), RHS per request uniform in 1..max, sources
@@ -213,7 +216,7 @@ def run_serving(m, torch, ctx, g, C, w, args, dev, stream):
         first += int(sizes[i])
         reqs.append(dict(lattice=0, b=b, x=torch.zeros_like(b), arrival=float(arrivals[i])))
     torch.cuda.synchronize()
-    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG)
+    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG, coarse_solver=COARSE_SOLVERS[args.coarse_solver])
     stats, res = m.mglma_serve(ctx, [(g, C)], reqs, prm, max_slots=32, hbm_fraction=0.6)
     ok = all(r["status"] == 0 for r in res)
     resid = max(s["residual"] for r in res for s in r["stats"])
@@ -308,6 +311,8 @@ def main():
     ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS))
     ap.add_argument("--group", type=int, default=0, help="sources per step (default: the workload's)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--coarse-solver", default="minres", choices=sorted(COARSE_SOLVERS),
+                    help="coarse solver inside the preconditioner")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-solver sample")
     ap.add_argument("--micro", default="", choices=["", "dslash32", "dslash64", "coarse", "transfer"],
                     help="time one kernel class on the workload lattice instead of the solve")
@@ -352,7 +357,7 @@ def main():
     sub = m.mglma_subspace_create(ctx, g, w["block"], w["nv"], w["n_smooth"], 2000 + w["cfg"], prec[w["sub_store"]],
                                   n_cg=w["n_cg"], cg_prec=m.MGLMA_FP32)
     C = m.mglma_coarse_build(ctx, g, sub, prec[w["coarse_store"]])
-    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG)
+    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG, coarse_solver=COARSE_SOLVERS[args.coarse_solver])
     stream = torch.cuda.Stream(device=dev)
 
     nsteps = args.warmup + args.steps
@@ -402,6 +407,7 @@ def main():
     value = solves / (ms / 1e3)
     resid = max(s["residual"] for s in all_stats)
     iters = [s["iterations"] for s in all_stats]
+    citers = [s["coarse_iterations"] for s in all_stats]
 
     # ---- end to end: pinned host buffers, copies inside the timed region
     # (each step's sources are placed in the pinned buffer before its timing)
@@ -483,10 +489,12 @@ def main():
             "config": {"workload": args.workload, "lattice": "x".join(map(str, L)), "eps": w["eps"],
                        "kappa": w["kappa"], "csw": w["csw"], "block": "x".join(map(str, w["block"])),
                        "Nv": w["nv"], "basis": w["sub_store"], "coarse_operator": w["coarse_store"],
+                       "coarse_solver": args.coarse_solver,
                        "setup": f"{w['n_smooth']} MR + {w['n_cg']} CG relaxation steps",
                        "rhs_per_step": G, "global_batch": G * world, "tol": 1e-10,
                        "l2": "inputs larger than L2 (each source 0.4 GB)", "parallelism": f"replicas x{world}"},
             "residual_max": resid, "fgcr_iterations": [min(iters), max(iters)],
+            "coarse_iterations": [min(citers), max(citers)],
             "e2e": e2e, "roofline": roofline, "dslash_fp32": dslash, "gpu_launches": launches, "clocks": clk,
             "serving": serving,
             "fp64_plain": fp64,

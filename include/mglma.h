@@ -209,9 +209,16 @@ void mglma_coarse_free(mglma_coarse c);
 mglma_status mglma_coarse_info(mglma_coarse c, int* nv, int Lb[4], int64_t* coarse_volume);
 /* Exports the FP64 stencil as complex128 [9][V1][2nv][2nv]. */
 mglma_status mglma_coarse_export(mglma_coarse c, double* dhat);
-/* out = D1 in for nrhs canonical coarse fields; compute MGLMA_FP64 uses the
- * FP64 operator, MGLMA_FP32 the stored low-precision copy. */
-mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse c, int nrhs, const double* in, double* out,
+/* out = op(D1) in for nrhs canonical coarse fields; compute MGLMA_FP64 uses
+ * the FP64 operator, MGLMA_FP32 the stored low-precision copy.  op:
+ *   MGLMA_OP_D     D1
+ *   MGLMA_OP_DDAG  D1^dag, applied as g5hat D1 g5hat (g5hat = +1 on the
+ *                  alpha = 0 dofs, -1 on alpha = 1): D1 inherits
+ *                  gamma5-hermiticity from D because the basis is split by
+ *                  chirality (Sec. 2, App. chirality)
+ *   MGLMA_OP_Q     Q1 = g5hat D1, the Hermitian coarse operator of Sec. 2
+ * MGLMA_OP_DDAGD is rejected with MGLMA_ERR_INVALID. */
+mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse c, mglma_op op, int nrhs, const double* in, double* out,
                                 mglma_prec compute, void* cuda_stream);
 
 /* ---------------------------------------------------------------- sources (Sec. 5) */
@@ -239,6 +246,15 @@ typedef enum {
                             T0 D1^-1 R0 plus MR smoothing */
 } mglma_solver;
 
+/* Solver of the coarse system inside the MG preconditioner. */
+typedef enum {
+  MGLMA_COARSE_GCR = 0,    /* restarted GCR(16) on D1 */
+  MGLMA_COARSE_MINRES = 1  /* MINRES on the Hermitian Q1 = g5hat D1 (Sec. 2),
+                              solving Q1 e = g5hat b: a three-term Lanczos
+                              recurrence, no restarts, about a third of the
+                              vector traffic of GCR per iteration */
+} mglma_coarse_solver;
+
 typedef struct {
   int method;           /* mglma_solver */
   double tol;           /* target FP64 ||b - D x|| / ||b|| (e.g. 1e-10) */
@@ -250,6 +266,7 @@ typedef struct {
   int coarse_max_iter;  /* cap on coarse iterations per preconditioner call */
   int check_every;      /* host polls residual norms every this many iterations */
   int max_batch;        /* RHS solved together (0: as many as free HBM allows, <= 64) */
+  int coarse_solver;    /* mglma_coarse_solver (MG) */
 } mglma_solve_params;
 
 typedef struct {

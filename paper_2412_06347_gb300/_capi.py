@@ -10,6 +10,7 @@ from . import build as _build
 
 MGLMA_FP64, MGLMA_FP32, MGLMA_BF16, MGLMA_FP16 = 0, 1, 2, 3
 MGLMA_OP_D, MGLMA_OP_DDAG, MGLMA_OP_Q, MGLMA_OP_DDAGD = 0, 1, 2, 3
+MGLMA_COARSE_GCR, MGLMA_COARSE_MINRES = 0, 1
 MGLMA_SOLVER_CGNE, MGLMA_SOLVER_MG = 0, 1
 MGLMA_SOURCE_Z2, MGLMA_SOURCE_Z4, MGLMA_SOURCE_POINT = 0, 1, 2
 _STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "NOT_CONVERGED", 6: "NUMERIC",
@@ -81,13 +82,14 @@ _sig("mglma_coarse_build", C.c_int, _vp, _vp, _vp, C.c_int, C.POINTER(_vp))
 _sig("mglma_coarse_free", None, _vp)
 _sig("mglma_coarse_info", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_i64))
 _sig("mglma_coarse_export", C.c_int, _vp, _vp)
-_sig("mglma_coarse_apply", C.c_int, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp)
+_sig("mglma_coarse_apply", C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp)
 
 
 class mglma_solve_params(C.Structure):
     _fields_ = [("method", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("gcr_m", C.c_int),
                 ("nu", C.c_int), ("inner_tol", C.c_double), ("coarse_tol", C.c_double),
-                ("coarse_max_iter", C.c_int), ("check_every", C.c_int), ("max_batch", C.c_int)]
+                ("coarse_max_iter", C.c_int), ("check_every", C.c_int), ("max_batch", C.c_int),
+                ("coarse_solver", C.c_int)]
 
 
 class mglma_solve_stats(C.Structure):
@@ -293,8 +295,9 @@ def mglma_coarse_export(c, dhat):
     _check(lib.mglma_coarse_export(c, ptr(dhat)))
 
 
-def mglma_coarse_apply(ctx, c, nrhs, inp, out, compute=MGLMA_FP64, stream=None):
-    _check(lib.mglma_coarse_apply(_h(ctx), c, int(nrhs), ptr(inp), ptr(out), int(compute), _stream_ptr(stream)))
+def mglma_coarse_apply(ctx, c, nrhs, inp, out, compute=MGLMA_FP64, stream=None, op=MGLMA_OP_D):
+    _check(lib.mglma_coarse_apply(_h(ctx), c, int(op), int(nrhs), ptr(inp), ptr(out), int(compute),
+                                  _stream_ptr(stream)))
 
 
 def mglma_solve_params_default(method=MGLMA_SOLVER_MG, **overrides):

@@ -329,6 +329,98 @@ __global__ void __launch_bounds__(RT) axpy2_norm_kernel(const typename Pair<R>::
   finish<0>(part, count, 1, nb, nrhs, nullptr, out1);
 }
 
+// ------------------------------------------------------------- MINRES (real scalars)
+__device__ __forceinline__ float4 rlc3(float4 x, float4 y, float4 z, double a, double b, double c) {
+  const float fa = (float)a, fb = (float)b, fc = (float)c;
+  return make_float4(fa * x.x + fb * y.x + fc * z.x, fa * x.y + fb * y.y + fc * z.y, fa * x.z + fb * y.z + fc * z.z,
+                     fa * x.w + fb * y.w + fc * z.w);
+}
+__device__ __forceinline__ double2 rlc3(double2 x, double2 y, double2 z, double a, double b, double c) {
+  return make_double2(a * x.x + b * y.x + c * z.x, a * x.y + b * y.y + c * z.y);
+}
+__device__ __forceinline__ float4 rlc2(float4 x, float4 y, double a, double b) {
+  const float fa = (float)a, fb = (float)b;
+  return make_float4(fa * x.x + fb * y.x, fa * x.y + fb * y.y, fa * x.z + fb * y.z, fa * x.w + fb * y.w);
+}
+__device__ __forceinline__ double2 rlc2(double2 x, double2 y, double a, double b) {
+  return make_double2(a * x.x + b * y.x, a * x.y + b * y.y);
+}
+__device__ __forceinline__ float4 rscale(float4 x, double a) {
+  const float f = (float)a;
+  return make_float4(f * x.x, f * x.y, f * x.z, f * x.w);
+}
+__device__ __forceinline__ double2 rscale(double2 x, double a) { return make_double2(a * x.x, a * x.y); }
+
+// Lanczos step z -= a_r v + b_r u with a_r = Re dot[r], b_r = beta[r], and
+// out1[r] = |z_r|^2; RHS with active[r] == 0 are left alone (out1 = 0).
+template <typename R>
+__global__ void __launch_bounds__(RT) lanczos_norm_kernel(const typename Pair<R>::T* __restrict__ v,
+                                                          const typename Pair<R>::T* __restrict__ u,
+                                                          typename Pair<R>::T* __restrict__ z,
+                                                          const double2* __restrict__ dot,
+                                                          const double* __restrict__ beta,
+                                                          const int* __restrict__ active, size_t m,
+                                                          double2* __restrict__ part, unsigned* __restrict__ count,
+                                                          double* out1) {
+  const int r = blockIdx.y, nrhs = gridDim.y, nb = gridDim.x;
+  const bool on = active[r] != 0;
+  const double a = on ? -dot[r].x : 0.0, b = on ? -beta[r] : 0.0;
+  const size_t off = (size_t)r * m;
+  RAcc<R> acc;
+  for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < m; i += (size_t)nb * RT) {
+    if (on) {
+      const auto nz = rlc3(z[off + i], v[off + i], u[off + i], 1.0, a, b);
+      z[off + i] = nz;
+      acc.add_n(nz);
+    }
+  }
+  const double2 t = block_sum2<RT>(make_double2(acc.norm(), 0));
+  if (threadIdx.x == 0) part[(size_t)r * nb + blockIdx.x] = t;
+  finish<0>(part, count, 1, nb, nrhs, nullptr, out1);
+}
+
+// w_new = cf0 v + cf1 w1 + cf2 w2 ; x += cf3 w_new ; z *= cf4, for RHS with
+// cf5 != 0 (cf_j[r] = cf[j * stride + r])
+template <typename R>
+__global__ void minres_update_kernel(const typename Pair<R>::T* __restrict__ v, const typename Pair<R>::T* __restrict__ w1,
+                                     const typename Pair<R>::T* __restrict__ w2, typename Pair<R>::T* __restrict__ wn,
+                                     typename Pair<R>::T* __restrict__ x, typename Pair<R>::T* __restrict__ z,
+                                     const double* __restrict__ cf, int stride, size_t m) {
+  const int r = blockIdx.y;
+  if (cf[5 * (size_t)stride + r] == 0.0) return;
+  const double c0 = cf[r], c1 = cf[stride + r], c2 = cf[2 * (size_t)stride + r], c3 = cf[3 * (size_t)stride + r],
+               c4 = cf[4 * (size_t)stride + r];
+  const size_t off = (size_t)r * m;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+    const auto w = rlc3(v[off + i], w1[off + i], w2[off + i], c0, c1, c2);
+    wn[off + i] = w;
+    x[off + i] = rlc2(x[off + i], w, 1.0, c3);
+    z[off + i] = rscale(z[off + i], c4);
+  }
+}
+
+// y_r = scale_r gamma5hat x_r on coarse fields (complex e of a RHS has dof
+// e mod n2; dofs >= nv change sign)
+template <typename R>
+__global__ void coarse_g5_scale_kernel(const typename Pair<R>::T* __restrict__ x, typename Pair<R>::T* __restrict__ y,
+                                       const double* __restrict__ scale, int n2, int nv, size_t m) {
+  const int r = blockIdx.y;
+  const double sc = scale[r];
+  constexpr int kc = Pair<R>::kCplx;
+  const size_t off = (size_t)r * m;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+    auto v = x[off + i];
+    R* e = reinterpret_cast<R*>(&v);
+#pragma unroll
+    for (int c = 0; c < kc; ++c) {
+      const R f = (R)(((i * kc + c) % (size_t)n2) >= (size_t)nv ? -sc : sc);
+      e[2 * c] *= f;
+      e[2 * c + 1] *= f;
+    }
+    y[off + i] = v;
+  }
+}
+
 // --------------------------------------------------------------- host side
 static inline size_t pairs(const Vec& v) { return v.prec == MGLMA_FP64 ? v.n / 2 : v.n / 4; }
 
@@ -505,6 +597,61 @@ mglma_status axpy2_norm(mglma_ctx ctx, const double2* a, const Vec& p, Vec& x, c
   else
     axpy2_norm_kernel<float><<<g, RT, 0, s>>>((const float4*)p.p, (float4*)x.p, (const float4*)w.p, (float4*)r.p, a,
                                               m, part, count, rr);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status lanczos_norm(mglma_ctx ctx, const double2* dot, const double* beta, const int* active, const Vec& v,
+                          const Vec& u, Vec& z, double* zz, cudaStream_t s) {
+  if (v.prec != z.prec || u.prec != z.prec || v.n != z.n || u.n != z.n)
+    return fail(MGLMA_ERR_INVALID, "lanczos_norm: mismatch");
+  if (z.nrhs == 0) return MGLMA_OK;
+  ProfScope ps(ctx, K_REDUCE, s, 4.0 * z.bytes());
+  const size_t m = pairs(z);
+  const int nb = reduce_blocks(m);
+  double2* part = nullptr;
+  unsigned* count = nullptr;
+  MG_CHECK(red_scratch(ctx, s, (size_t)nb * z.nrhs, z.nrhs, &part, &count));
+  dim3 g(nb, z.nrhs, 1);
+  if (z.prec == MGLMA_FP64)
+    lanczos_norm_kernel<double><<<g, RT, 0, s>>>((const double2*)v.p, (const double2*)u.p, (double2*)z.p, dot, beta,
+                                                 active, m, part, count, zz);
+  else
+    lanczos_norm_kernel<float><<<g, RT, 0, s>>>((const float4*)v.p, (const float4*)u.p, (float4*)z.p, dot, beta,
+                                                active, m, part, count, zz);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status minres_update(mglma_ctx ctx, const double* cf, int stride, const Vec& v, const Vec& w1, const Vec& w2,
+                           Vec& wn, Vec& x, Vec& z, cudaStream_t s) {
+  if (v.prec != x.prec || v.n != x.n || w1.n != x.n || w2.n != x.n || wn.n != x.n || z.n != x.n)
+    return fail(MGLMA_ERR_INVALID, "minres_update: mismatch");
+  if (x.nrhs == 0) return MGLMA_OK;
+  ProfScope ps(ctx, K_BLAS, s, 8.0 * x.bytes());
+  const size_t m = pairs(x);
+  dim3 g = ew_grid(ctx, m, x.nrhs);
+  if (x.prec == MGLMA_FP64)
+    minres_update_kernel<double><<<g, 256, 0, s>>>((const double2*)v.p, (const double2*)w1.p, (const double2*)w2.p,
+                                                   (double2*)wn.p, (double2*)x.p, (double2*)z.p, cf, stride, m);
+  else
+    minres_update_kernel<float><<<g, 256, 0, s>>>((const float4*)v.p, (const float4*)w1.p, (const float4*)w2.p,
+                                                  (float4*)wn.p, (float4*)x.p, (float4*)z.p, cf, stride, m);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status coarse_g5_scale(mglma_ctx ctx, const Vec& x, Vec& y, const double* scale, int n2, cudaStream_t s) {
+  if (x.prec != y.prec || x.n != y.n || x.nrhs != y.nrhs || n2 % 2 || x.n % (2 * (size_t)n2))
+    return fail(MGLMA_ERR_INVALID, "coarse_g5_scale: mismatch");
+  if (y.nrhs == 0) return MGLMA_OK;
+  ProfScope ps(ctx, K_BLAS, s, 2.0 * y.bytes());
+  const size_t m = pairs(y);
+  dim3 g = ew_grid(ctx, m, y.nrhs);
+  if (y.prec == MGLMA_FP64)
+    coarse_g5_scale_kernel<double><<<g, 256, 0, s>>>((const double2*)x.p, (double2*)y.p, scale, n2, n2 / 2, m);
+  else
+    coarse_g5_scale_kernel<float><<<g, 256, 0, s>>>((const float4*)x.p, (float4*)y.p, scale, n2, n2 / 2, m);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }

@@ -159,7 +159,7 @@ struct AL<__nv_bfloat162> {
 // grid (V1, RHS tiles); thread i < n2 owns row i of Y(y) for NRT RHS
 template <typename R, typename AT, int NRT>
 __global__ void coarse_apply_kernel(const AT* __restrict__ A, const Cx<R>* __restrict__ X, Cx<R>* __restrict__ Y,
-                                    LatIdx q, int n2, int nrhs, int dagger) {
+                                    LatIdx q, int n2, int nrhs, int mode) {
   extern __shared__ unsigned char smraw[];
   Cx<R>* xs = reinterpret_cast<Cx<R>*>(smraw);  // [9][n2][NRT]
   const int64_t y = blockIdx.x;
@@ -173,7 +173,7 @@ __global__ void coarse_apply_kernel(const AT* __restrict__ A, const Cx<R>* __res
     int64_t z = d == 8 ? y : (d < 4 ? nbr_fwd(q, y, x, d) : nbr_bwd(q, y, x, d - 4));
     Cx<R> v = cx<R>(0, 0);
     if (r0 + r < nrhs) v = X[((size_t)(r0 + r) * V1 + z) * n2 + j];
-    if (dagger && j >= nv) v = -v;
+    if ((mode & 1) && j >= nv) v = -v;
     xs[idx] = v;
   }
   __syncthreads();
@@ -191,14 +191,14 @@ __global__ void coarse_apply_kernel(const AT* __restrict__ A, const Cx<R>* __res
       for (int r = 0; r < NRT; ++r) cfma(acc[r], a, xr[r]);
     }
   }
-  const bool neg = dagger && i >= nv;
+  const bool neg = (mode & 2) && i >= nv;
 #pragma unroll
   for (int r = 0; r < NRT; ++r)
     if (r0 + r < nrhs) Y[((size_t)(r0 + r) * V1 + y) * n2 + i] = neg ? -acc[r] : acc[r];
 }
 
 template <typename R, typename AT, int NRT>
-static mglma_status launch_capply(const AT* A, const void* X, void* Y, const mglma_coarse_s* Cc, int nrhs, bool dag,
+static mglma_status launch_capply(const AT* A, const void* X, void* Y, const mglma_coarse_s* Cc, int nrhs, int mode,
                                   cudaStream_t s) {
   LatIdx q = make_latidx(Cc->geo.Lb);
   const int threads = ((Cc->n2 + 31) / 32) * 32;
@@ -210,13 +210,14 @@ static mglma_status launch_capply(const AT* A, const void* X, void* Y, const mgl
   }
   dim3 grid((unsigned)Cc->geo.V1, (unsigned)((nrhs + NRT - 1) / NRT), 1);
   coarse_apply_kernel<R, AT, NRT><<<grid, threads, smem, s>>>(A, (const Cx<R>*)X, (Cx<R>*)Y, q, Cc->n2, nrhs,
-                                                              dag ? 1 : 0);
+                                                              mode);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }
 
 mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X, void* Y, int nrhs, int prec,
-                          bool dagger, cudaStream_t s) {
+                          int mode, cudaStream_t s) {
+  if (mode < 0 || mode > 3) return fail(MGLMA_ERR_INVALID, "coarse apply: unknown gamma5 mode");
   if (nrhs == 0) return MGLMA_OK;
   // algorithmic traffic: the operator once (9 (2Nv)^2 complex per coarse
   // site) plus each RHS's input and output once; 8 flops per complex MAC
@@ -226,12 +227,12 @@ mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X
   ProfScope ps(ctx, K_COARSE, s, V1 * (9.0 * n2 * n2 * ca + 2.0 * N * n2 * cf), V1 * 9.0 * n2 * n2 * 8.0 * N);
   if (prec == MGLMA_FP64) {
     if (!Cc->A64) return fail(MGLMA_ERR_INVALID, "coarse apply: FP64 operator not kept");
-    return launch_capply<double, double2, 4>(Cc->A64, X, Y, Cc, nrhs, dagger, s);
+    return launch_capply<double, double2, 4>(Cc->A64, X, Y, Cc, nrhs, mode, s);
   }
-  if (Cc->Aimg) return coarse_apply_tc(ctx, Cc, (const float2*)X, (float2*)Y, nrhs, dagger, s);
-  if (Cc->A16) return launch_capply<float, __nv_bfloat162, 8>(Cc->A16, X, Y, Cc, nrhs, dagger, s);
-  if (Cc->A32) return launch_capply<float, float2, 8>(Cc->A32, X, Y, Cc, nrhs, dagger, s);
-  return launch_capply<float, double2, 8>(Cc->A64, X, Y, Cc, nrhs, dagger, s);
+  if (Cc->Aimg) return coarse_apply_tc(ctx, Cc, (const float2*)X, (float2*)Y, nrhs, mode, s);
+  if (Cc->A16) return launch_capply<float, __nv_bfloat162, 8>(Cc->A16, X, Y, Cc, nrhs, mode, s);
+  if (Cc->A32) return launch_capply<float, float2, 8>(Cc->A32, X, Y, Cc, nrhs, mode, s);
+  return launch_capply<float, double2, 8>(Cc->A64, X, Y, Cc, nrhs, mode, s);
 }
 
 mglma_status dslash_slot64_batch(mglma_ctx ctx, const mglma_gauge_s* G, const int block[4], const Spinor& in,
@@ -354,9 +355,12 @@ mglma_status mglma_coarse_export(mglma_coarse Cc, double* dhat) {
   return MGLMA_OK;
 }
 
-mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse Cc, int nrhs, const double* in, double* out,
+mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse Cc, mglma_op op, int nrhs, const double* in, double* out,
                                 mglma_prec compute, void* cuda_stream) {
   if (!ctx || !Cc || !in || !out) return fail(MGLMA_ERR_INVALID, "coarse_apply: NULL argument");
+  // gamma5hat on the input (bit 0) and on the output (bit 1)
+  const int mode = op == MGLMA_OP_D ? 0 : op == MGLMA_OP_DDAG ? 3 : op == MGLMA_OP_Q ? 2 : -1;
+  if (mode < 0) return fail(MGLMA_ERR_INVALID, "coarse_apply: op must be D, D^dag or Q");
   if (compute != MGLMA_FP64 && compute != MGLMA_FP32)
     return fail(MGLMA_ERR_INVALID, "coarse_apply: compute must be FP64 or FP32");
   if (nrhs <= 0) return nrhs == 0 ? MGLMA_OK : fail(MGLMA_ERR_INVALID, "coarse_apply: nrhs < 0");
@@ -374,7 +378,7 @@ mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse Cc, int nrhs, const 
   MG_CHECK(dalloc(ctx, &Y, n * cb, s));
   fl.add(Y);
   MG_CHECK(coarse_from_canonical(ctx, si.dev, n, X, compute, s));
-  MG_CHECK(coarse_apply(ctx, Cc, X, Y, nrhs, compute, false, s));
+  MG_CHECK(coarse_apply(ctx, Cc, X, Y, nrhs, compute, mode, s));
   MG_CHECK(coarse_tc_check(Cc, s));
   MG_CHECK(coarse_to_canonical(ctx, Y, compute, n, so.dev, s));
   MG_CHECK(stage_out_finish(out, n * sizeof(double2), s, so));

@@ -73,7 +73,7 @@ __device__ __forceinline__ uint16_t bf16_bits(float f) {
 template <int NT>  // right-hand sides per tile; the MMA N is 2 NT
 __global__ void __launch_bounds__(TC_THREADS, 1)
     coarse_tc_kernel(const uint8_t* __restrict__ Aimg, const float2* __restrict__ X, float2* __restrict__ Y, LatIdx q,
-                     int n2, int nrhs, int dagger, int* __restrict__ err) {
+                     int n2, int nrhs, int mode, int* __restrict__ err) {
   constexpr int NN = 2 * NT;
   extern __shared__ __align__(1024) uint8_t sm[];
   const int K = 18 * n2, NC = K / 8, G = n2 / 8;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         re[2 * h + 1] = xr[it][h].z;
         im[2 * h + 1] = xr[it][h].w;
       }
-      if (dagger) {
+      if (mode & 1) {
 #pragma unroll
         for (int e = 0; e < 8; ++e)
           if (jo * 8 + e >= nv) {
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int i = warp * 32 + lane;
         if (i < n2) {
-          const float sg = (dagger && i >= nv) ? -1.f : 1.f;
+          const float sg = ((mode & 2) && i >= nv) ? -1.f : 1.f;
 #pragma unroll
           for (int r = 0; r < NT; ++r)
             if (r0 + r < nrhs)
@@ -340,7 +340,7 @@ mglma_status coarse_tc_image(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s) {
 
 template <int NT>
 static mglma_status launch_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float2* X, float2* Y, int nrhs,
-                              bool dagger, int* err, cudaStream_t s) {
+                              int mode, int* err, cudaStream_t s) {
   const size_t smem = tc_smem(C->n2, NT);
   static size_t attr = 0;  // largest dynamic shared memory granted so far
   if (smem > attr) {
@@ -349,7 +349,7 @@ static mglma_status launch_tc(mglma_ctx ctx, const mglma_coarse_s* C, const floa
   }
   const unsigned grid = (unsigned)std::min<int64_t>(C->geo.V1, (int64_t)ctx->sm_count);
   coarse_tc_kernel<NT><<<grid, TC_THREADS, smem, s>>>((const uint8_t*)C->Aimg, X, Y, make_latidx(C->geo.Lb), C->n2,
-                                                      nrhs, dagger ? 1 : 0, err);
+                                                      nrhs, mode, err);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }
@@ -367,13 +367,13 @@ mglma_status coarse_tc_check(mglma_coarse_s* C, cudaStream_t s) {
 }
 
 mglma_status coarse_apply_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float2* X, float2* Y, int nrhs,
-                             bool dagger, cudaStream_t s) {
+                             int mode, cudaStream_t s) {
   if (!C->Aimg || !coarse_tc_supported(C->n2)) return fail(MGLMA_ERR_INVALID, "coarse_apply_tc: no tensor image");
   int* err = C->tc_err;
   const bool fit16 = tc_smem(C->n2, 16) <= 227 * 1024;
   const int nt = tuned(ctx, TUNE_COARSE_NT, nrhs, (nrhs <= 8 || !fit16) ? 8 : 16);
-  if (nt == 16 && fit16) return launch_tc<16>(ctx, C, X, Y, nrhs, dagger, err, s);
-  return launch_tc<8>(ctx, C, X, Y, nrhs, dagger, err, s);
+  if (nt == 16 && fit16) return launch_tc<16>(ctx, C, X, Y, nrhs, mode, err, s);
+  return launch_tc<8>(ctx, C, X, Y, nrhs, mode, err, s);
 }
 
 }  // namespace mglma

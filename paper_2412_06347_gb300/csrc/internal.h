@@ -262,5 +262,15 @@ mglma_status norm2_cdot(mglma_ctx, const Vec& x, const Vec& y, double* nrm, doub
 // x += a p ; r -= a w ; rr[r] = |r_r|^2 in one pass
 mglma_status axpy2_norm(mglma_ctx, const double2* a, const Vec& p, Vec& x, const Vec& w, Vec& r, double* rr,
                         cudaStream_t s);
+// MINRES: z -= Re(dot_r) v + beta_r u, zz[r] = |z_r|^2 (RHS with active[r] == 0
+// are left alone, zz = 0)
+mglma_status lanczos_norm(mglma_ctx, const double2* dot, const double* beta, const int* active, const Vec& v,
+                          const Vec& u, Vec& z, double* zz, cudaStream_t s);
+// MINRES: wn = c0 v + c1 w1 + c2 w2 ; x += c3 wn ; z *= c4 for RHS with c5 != 0,
+// c_j[r] = cf[j * stride + r] (real, device)
+mglma_status minres_update(mglma_ctx, const double* cf, int stride, const Vec& v, const Vec& w1, const Vec& w2,
+                           Vec& wn, Vec& x, Vec& z, cudaStream_t s);
+// y = scale_r gamma5hat x on coarse fields of n2 dofs per site (scale device, per RHS)
+mglma_status coarse_g5_scale(mglma_ctx, const Vec& x, Vec& y, const double* scale, int n2, cudaStream_t s);
 
 }  // namespace mglma

@@ -216,17 +216,168 @@ static mglma_status gcr(mglma_ctx ctx, cudaStream_t s, const OpFn& A, const OpFn
   return MGLMA_OK;
 }
 
-// Coarse solve of the preconditioner: GCR(m) on the coarse stencil with a
-// persistent workspace; one restart cycle of m iterations is captured as a
-// CUDA graph and replayed, with one host poll per cycle.  With profiling on,
+// ------------------------------------------------------------------ MINRES
+// Batched MINRES on the Hermitian coarse operator Qhat = g5hat Dhat, solving
+// Qhat e = g5hat b (the same e as Dhat e = b; g5hat is unitary, so the
+// recurrence's residual estimate |eta| is |b - Dhat e|).  Per RHS, iteration
+// k (v_0 = g5hat b / beta_1, beta_0 = 0, v_-1 = w_-1 = w_-2 = 0):
+//   Lanczos  z = Qhat v_k - alpha_k v_k - beta_k v_(k-1),  alpha_k = <v_k, Qhat v_k>,
+//            beta_(k+1) = |z|,  v_(k+1) = z / beta_(k+1)
+//   QR of the tridiagonal by Givens rotations (c, s):
+//            eps = s'' beta_k, d' = c'' beta_k, delta = c' d' + s' alpha_k,
+//            g' = c' alpha_k - s' d', gamma = hypot(g', beta_(k+1)),
+//            c = g' / gamma, s = beta_(k+1) / gamma
+//   update   w_k = (v_k - delta w_(k-1) - eps w_(k-2)) / gamma,
+//            e += c eta w_k,  eta <- -s eta
+// stopping at |eta| <= tol beta_1.  Vectors rotate through three slots
+// (v_j, w_j in slot j mod 3), so a captured cycle is a multiple of three
+// iterations long.
+enum {
+  MR_BETA1 = 0,
+  MR_ETA,
+  MR_BETA,
+  MR_C2,
+  MR_S2,
+  MR_C1,
+  MR_S1,
+  MR_BN2,
+  MR_BB,
+  MR_CF,  // six update coefficients (minres_update), MR_CF + 4 also scales v_0
+  MR_COUNT = MR_CF + 6
+};
+
+__global__ void minres_init_kernel(double* st, int* active, int cap, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  auto S = [&](int j) -> double& { return st[(size_t)j * cap + r]; };
+  const double b1 = sqrt(S(MR_BB));
+  const bool on = b1 > 0 && b1 < INFINITY;
+  S(MR_BETA1) = b1;
+  S(MR_ETA) = b1;
+  S(MR_BETA) = 0;
+  S(MR_C2) = S(MR_C1) = 1;
+  S(MR_S2) = S(MR_S1) = 0;
+  S(MR_CF + 4) = on ? 1.0 / b1 : 0.0;
+  active[r] = on ? 1 : 0;
+}
+
+__global__ void minres_scalar_kernel(double* st, const double2* dot, int* active, double tol, int cap, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  auto S = [&](int j) -> double& { return st[(size_t)j * cap + r]; };
+  S(MR_CF + 5) = 0;
+  if (!active[r]) return;
+  const double alpha = dot[r].x, beta = S(MR_BETA);
+  const double bn = sqrt(fmax(S(MR_BN2), 0.0));
+  const double eps = S(MR_S2) * beta, dp = S(MR_C2) * beta;
+  const double delta = S(MR_C1) * dp + S(MR_S1) * alpha;
+  const double gp = S(MR_C1) * alpha - S(MR_S1) * dp;
+  const double gamma = hypot(gp, bn);
+  if (!(gamma > 0) || !(gamma < INFINITY)) {  // breakdown: keep the iterate
+    active[r] = 0;
+    return;
+  }
+  const double c = gp / gamma, sn = bn / gamma;
+  S(MR_CF + 0) = 1.0 / gamma;
+  S(MR_CF + 1) = -delta / gamma;
+  S(MR_CF + 2) = -eps / gamma;
+  S(MR_CF + 3) = c * S(MR_ETA);
+  S(MR_CF + 4) = bn > 0 ? 1.0 / bn : 0.0;
+  S(MR_CF + 5) = 1;
+  S(MR_ETA) = -sn * S(MR_ETA);
+  S(MR_C2) = S(MR_C1);
+  S(MR_S2) = S(MR_S1);
+  S(MR_C1) = c;
+  S(MR_S1) = sn;
+  S(MR_BETA) = bn;
+  active[r] = (bn > 0 && fabs(S(MR_ETA)) > tol * S(MR_BETA1)) ? 1 : 0;
+}
+
+struct MinresWork {
+  mglma_ctx ctx = nullptr;
+  cudaStream_t s = nullptr;
+  int cap = 0;
+  Vec proto;
+  void *Vp = nullptr, *Wp = nullptr;  // three Lanczos vectors, three directions
+  Scalars sc;                         // d: MR_COUNT per RHS, z: <v, Qhat v>
+  ~MinresWork() {
+    if (ctx) {
+      dfree(ctx, Vp, s);
+      dfree(ctx, Wp, s);
+    }
+  }
+  mglma_status setup(mglma_ctx c, cudaStream_t st, const Vec& like, int capacity) {
+    ctx = c;
+    s = st;
+    cap = capacity;
+    proto = like;
+    proto.nrhs = cap;
+    MG_CHECK(dalloc(ctx, &Vp, proto.bytes() * 3, s));
+    MG_CHECK(dalloc(ctx, &Wp, proto.bytes() * 3, s));
+    MG_CHECK(sc.alloc(ctx, cap, MR_COUNT, 1, s));
+    return red_scratch_ready(ctx, s);
+  }
+  double* st(int j) const { return sc.d + (size_t)j * cap; }
+  Vec view(void* base, int j, int n) const {
+    Vec v = proto;
+    v.nrhs = n;
+    v.p = (char*)base + (size_t)j * proto.bytes();
+    return v;
+  }
+};
+
+static mglma_status minres_init(MinresWork& w, const mglma_coarse_s* C, const Vec& b, Vec& x) {
+  const int n = b.nrhs;
+  Vec v0 = w.view(w.Vp, 0, n), vm = w.view(w.Vp, 2, n), w1 = w.view(w.Wp, 1, n), w2 = w.view(w.Wp, 2, n);
+  MG_CHECK(zero_vec(w.ctx, x, w.s));
+  MG_CHECK(zero_vec(w.ctx, vm, w.s));
+  MG_CHECK(zero_vec(w.ctx, w1, w.s));
+  MG_CHECK(zero_vec(w.ctx, w2, w.s));
+  MG_CHECK(norm2(w.ctx, b, w.st(MR_BB), w.s));
+  {
+    ProfScope ps(w.ctx, K_SCALAR, w.s);
+    minres_init_kernel<<<(n + 63) / 64, 64, 0, w.s>>>(w.sc.d, w.sc.active, w.cap, n);
+    MG_LAUNCH_CHECK();
+  }
+  return coarse_g5_scale(w.ctx, b, v0, w.st(MR_CF + 4), C->n2, w.s);
+}
+
+static mglma_status minres_iter(MinresWork& w, const mglma_coarse_s* C, Vec& x, int n, int k, double tol) {
+  const int a = k % 3, b = (k + 1) % 3, c = (k + 2) % 3;
+  Vec v = w.view(w.Vp, a, n), vo = w.view(w.Vp, c, n), z = w.view(w.Vp, b, n);
+  Vec wn = w.view(w.Wp, a, n), w1 = w.view(w.Wp, c, n), w2 = w.view(w.Wp, b, n);
+  MG_CHECK(coarse_apply(w.ctx, C, v.p, z.p, n, MGLMA_FP32, CMODE_Q, w.s));
+  MG_CHECK(cdot(w.ctx, v, z, w.sc.z, w.s));
+  MG_CHECK(lanczos_norm(w.ctx, w.sc.z, w.st(MR_BETA), w.sc.active, v, vo, z, w.st(MR_BN2), w.s));
+  {
+    ProfScope ps(w.ctx, K_SCALAR, w.s);
+    minres_scalar_kernel<<<(n + 63) / 64, 64, 0, w.s>>>(w.sc.d, w.sc.z, w.sc.active, tol, w.cap, n);
+    MG_LAUNCH_CHECK();
+  }
+  return minres_update(w.ctx, w.st(MR_CF), w.cap, v, w1, w2, wn, x, z, w.s);
+}
+
+static mglma_status read_mask(const int* dev, int n, std::vector<int>& h, cudaStream_t s) {
+  h.resize(n);
+  MG_CUDA(cudaMemcpyAsync(h.data(), dev, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+  MG_CUDA(cudaStreamSynchronize(s));
+  return MGLMA_OK;
+}
+
+// Coarse solve of the preconditioner with a persistent workspace: MINRES on
+// Qhat (default) or GCR(m) on Dhat.  One cycle (m GCR iterations = one
+// restart; 12 MINRES iterations) is captured as a CUDA graph and replayed,
+// with one host poll of the convergence mask per cycle.  With profiling on,
 // a separately captured copy records event brackets around every launch.
 struct CoarseSolver {
   mglma_ctx ctx = nullptr;
   cudaStream_t s = nullptr;
   const mglma_coarse_s* C = nullptr;
+  int method = MGLMA_COARSE_MINRES;
   int m = 16;
   int cap_hint = 0;
   GcrWork w;
+  MinresWork mw;
   struct Graphs {
     cudaGraphExec_t init = nullptr, cycle = nullptr;
     int n = -1;
@@ -252,8 +403,18 @@ struct CoarseSolver {
       G.ev_cycle.clear();
     }
   }
+  bool minres() const { return method == MGLMA_COARSE_MINRES; }
+  int cycle_len() const { return minres() ? 12 : m; }
+  int capacity() const { return minres() ? mw.cap : w.cap; }
+  const int* active() const { return minres() ? mw.sc.active : w.sc.active; }
   OpFn op() {
-    return [this](const Vec& in, Vec& out) { return coarse_apply(ctx, C, in.p, out.p, in.nrhs, MGLMA_FP32, false, s); };
+    return [this](const Vec& in, Vec& out) {
+      return coarse_apply(ctx, C, in.p, out.p, in.nrhs, MGLMA_FP32, CMODE_D, s);
+    };
+  }
+  mglma_status init(const Vec& b, Vec& x) { return minres() ? minres_init(mw, C, b, x) : gcr_init(w, b, x); }
+  mglma_status iter(const OpFn& A, Vec& x, int n, int k, double tol) {
+    return minres() ? minres_iter(mw, C, x, n, k, tol) : gcr_iter(w, A, nullptr, x, n, k, tol * tol);
   }
   mglma_status capture(Graphs& G, const Vec& b, Vec& x, double tol, bool prof) {
     const int n = b.nrhs;
@@ -264,9 +425,9 @@ struct CoarseSolver {
       MG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
       mglma_status st = MGLMA_OK;
       if (part == 0) {
-        st = gcr_init(w, b, x);
+        st = init(b, x);
       } else {
-        for (int k = 0; k < m && st == MGLMA_OK; ++k) st = gcr_iter(w, A, nullptr, x, n, k, tol * tol);
+        for (int k = 0; k < cycle_len() && st == MGLMA_OK; ++k) st = iter(A, x, n, k, tol);
       }
       cudaError_t e = cudaStreamEndCapture(s, &graph);
       ctx->capture_events = nullptr;
@@ -285,19 +446,26 @@ struct CoarseSolver {
   // e1 = D1^-1 b1 to tol (or max_iter, rounded up to whole cycles)
   mglma_status solve(const Vec& b, Vec& x, double tol, int max_iter, long long* iters) {
     const int n = b.nrhs;
-    if (!w.cap) MG_CHECK(w.setup(ctx, s, b, std::max(n, cap_hint), m));
-    if (n > w.cap) return fail(MGLMA_ERR_INVALID, "coarse solve: more RHS than the workspace holds");
-    const int cycles = (max_iter + m - 1) / m;
+    if (!capacity()) {
+      const int c = std::max(n, cap_hint);
+      if (minres())
+        MG_CHECK(mw.setup(ctx, s, b, c));
+      else
+        MG_CHECK(w.setup(ctx, s, b, c, m));
+    }
+    if (n > capacity()) return fail(MGLMA_ERR_INVALID, "coarse solve: more RHS than the workspace holds");
+    const int L = cycle_len();
+    const int cycles = (max_iter + L - 1) / L;
     std::vector<int> hact;
     const bool prof = ctx->profile;
     if (!warmed) {
       // first use runs uncaptured (kernel attributes and scratch get set up)
       OpFn A = op();
-      MG_CHECK(gcr_init(w, b, x));
+      MG_CHECK(init(b, x));
       int c = 0;
       for (; c < cycles; ++c) {
-        for (int k = 0; k < m; ++k) MG_CHECK(gcr_iter(w, A, nullptr, x, n, k, tol * tol));
-        MG_CHECK(read_active(w, n, hact));
+        for (int k = 0; k < L; ++k) MG_CHECK(iter(A, x, n, k, tol));
+        MG_CHECK(read_mask(active(), n, hact, s));
         bool any = false;
         for (int v : hact) any = any || v;
         if (!any) {
@@ -305,7 +473,7 @@ struct CoarseSolver {
           break;
         }
       }
-      *iters += (long long)c * m;
+      *iters += (long long)c * L;
       warmed = true;
       return MGLMA_OK;
     }
@@ -328,8 +496,8 @@ struct CoarseSolver {
     int c = 0;
     for (; c < cycles; ++c) {
       MG_CUDA(cudaGraphLaunch(G.cycle, s));
-      MG_CHECK(read_active(w, n, hact));
-      if (prof) resolve_graph_events(ctx, c == 0 ? G.ev_init : std::vector<mglma_ctx_s::Pending>());
+      MG_CHECK(read_mask(active(), n, hact, s));
+      if (prof && c == 0) resolve_graph_events(ctx, G.ev_init);
       if (prof) resolve_graph_events(ctx, G.ev_cycle);
       bool any = false;
       for (int v : hact) any = any || v;
@@ -338,7 +506,7 @@ struct CoarseSolver {
         break;
       }
     }
-    *iters += (long long)c * m;
+    *iters += (long long)c * L;
     return MGLMA_OK;
   }
 };
@@ -390,6 +558,7 @@ struct TwoLevel {
     cs.ctx = ctx;
     cs.s = s;
     cs.C = C;
+    cs.method = p->coarse_solver;
     cs.cap_hint = n;
     ready = true;
     return MGLMA_OK;
@@ -544,7 +713,7 @@ mglma_status coarse_solve64(mglma_ctx ctx, const mglma_coarse_s* C, const void* 
   MG_CHECK(read_doubles(bb, hbb, n, s));
   MG_CHECK(zero_vec(ctx, vx, s));
   MG_CHECK(copy_vec(ctx, vb, vr, s));
-  OpFn Ac = [&](const Vec& in, Vec& out) { return coarse_apply(ctx, C, in.p, out.p, in.nrhs, MGLMA_FP32, false, s); };
+  OpFn Ac = [&](const Vec& in, Vec& out) { return coarse_apply(ctx, C, in.p, out.p, in.nrhs, MGLMA_FP32, CMODE_D, s); };
   const int tb = 64, nb = (n + tb - 1) / tb;
   for (int cycle = 0; cycle < 40; ++cycle) {
     MG_CHECK(norm2(ctx, vr, rr, s));
@@ -566,7 +735,7 @@ mglma_status coarse_solve64(mglma_ctx ctx, const mglma_coarse_s* C, const void* 
     GcrResult gr;
     MG_CHECK(gcr(ctx, s, Ac, nullptr, r32, e32, 24, 4000, 1e-6, 20, gr));
     MG_CHECK(coarse_scale_convert(ctx, e32.p, MGLMA_FP32, vx.p, MGLMA_FP64, rn, per, n, true, s));
-    MG_CHECK(coarse_apply(ctx, C, vx.p, vw.p, n, MGLMA_FP64, false, s));
+    MG_CHECK(coarse_apply(ctx, C, vx.p, vw.p, n, MGLMA_FP64, CMODE_D, s));
     MG_CHECK(copy_vec(ctx, vb, vr, s));
     MG_CHECK(axpby(ctx, nullptr, CM1, vw, nullptr, C1, vr, s));
   }
@@ -790,14 +959,7 @@ extern "C" mglma_status mglma_serve(mglma_ctx ctx, const mglma_serve_config* cfg
   MG_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = ctx->stream;
   const mglma_solve_params* prm = &cfg->params;
-  MgParams mp;
-  mp.tol = prm->tol;
-  mp.max_iter = prm->max_iter;
-  mp.gcr_m = prm->gcr_m;
-  mp.nu = prm->nu;
-  mp.inner_tol = prm->inner_tol;
-  mp.coarse_tol = prm->coarse_tol;
-  mp.coarse_max_iter = prm->coarse_max_iter;
+  const MgParams mp = mg_params(*prm);
   // admission by free HBM: the slots of each lattice take an equal share of
   // hbm_fraction of the memory free now
   size_t fr = 0, tot = 0;

@@ -223,6 +223,19 @@ mglma_status cgne64(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& b, Spin
 
 using namespace mglma;
 
+MgParams mglma::mg_params(const mglma_solve_params& p) {
+  MgParams mp;
+  mp.tol = p.tol;
+  mp.max_iter = p.max_iter;
+  mp.gcr_m = p.gcr_m;
+  mp.nu = p.nu;
+  mp.inner_tol = p.inner_tol;
+  mp.coarse_tol = p.coarse_tol;
+  mp.coarse_max_iter = p.coarse_max_iter;
+  mp.coarse_solver = p.coarse_solver;
+  return mp;
+}
+
 extern "C" {
 
 void mglma_solve_params_default(mglma_solve_params* p, int method) {
@@ -237,6 +250,7 @@ void mglma_solve_params_default(mglma_solve_params* p, int method) {
   p->coarse_max_iter = 100;
   p->check_every = method == MGLMA_SOLVER_CGNE ? 20 : 1;
   p->max_batch = 0;
+  p->coarse_solver = MGLMA_COARSE_MINRES;
 }
 
 mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, const mglma_solve_params* prm,
@@ -253,7 +267,9 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
   if (!(prm->tol > 0) || prm->max_iter < 1 || prm->check_every < 1 ||
       (prm->method == MGLMA_SOLVER_MG && (prm->gcr_m < 1 || prm->gcr_m > 64 || prm->nu < 0 ||
                                           !(prm->inner_tol > 0) || !(prm->coarse_tol > 0) ||
-                                          prm->coarse_max_iter < 1)))
+                                          prm->coarse_max_iter < 1 ||
+                                          (prm->coarse_solver != MGLMA_COARSE_GCR &&
+                                           prm->coarse_solver != MGLMA_COARSE_MINRES))))
     return fail(MGLMA_ERR_INVALID, "solve_batch: bad parameters");
   int total = 0;
   for (int g = 0; g < ngroups; ++g) {
@@ -298,14 +314,7 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
       ctl.check_every = prm->check_every;
       st = cgne64(ctx, G, B, X, ctl, rs, s);
     } else {
-      MgParams mp;
-      mp.tol = prm->tol;
-      mp.max_iter = prm->max_iter;
-      mp.gcr_m = prm->gcr_m;
-      mp.nu = prm->nu;
-      mp.inner_tol = prm->inner_tol;
-      mp.coarse_tol = prm->coarse_tol;
-      mp.coarse_max_iter = prm->coarse_max_iter;
+      const MgParams mp = mg_params(*prm);
       st = mg_solve(ctx, G, C, B, X, mp, rs, s);
     }
     if (st != MGLMA_OK && st != MGLMA_ERR_NOT_CONVERGED) return st;

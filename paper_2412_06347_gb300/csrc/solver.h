@@ -73,7 +73,11 @@ struct MgParams {
   double inner_tol = 3e-6;
   double coarse_tol = 0.02;
   int coarse_max_iter = 100;
+  int coarse_solver = MGLMA_COARSE_MINRES;
 };
+
+// the MG fields of the public parameter block
+MgParams mg_params(const mglma_solve_params& p);
 
 mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_s* C, const Spinor& b, Spinor& x,
                       const MgParams& p, std::vector<RhsStat>& out, cudaStream_t s);

@@ -59,11 +59,14 @@ mglma_status coarse_scale_convert(mglma_ctx ctx, const void* src, int sprec, voi
 bool coarse_tc_supported(int n2);
 mglma_status coarse_tc_image(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s);
 mglma_status coarse_apply_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float2* X, float2* Y, int nrhs,
-                             bool dagger, cudaStream_t s);
+                             int mode, cudaStream_t s);
 mglma_status coarse_tc_check(mglma_coarse_s* C, cudaStream_t s);
 // Y = Dhat X for nrhs coarse fields; prec of X/Y: FP64 (FP64 operator) or FP32
-// (FP32 or BF16 operator as stored)
+// (FP32 or BF16 operator as stored).  mode bit 0 applies gamma5hat to X, bit 1
+// to Y: 0 Dhat, 2 Qhat = gamma5hat Dhat, 3 gamma5hat Dhat gamma5hat = Dhat^dag
+// (gamma5hat-hermiticity, inherited from D by the chirality-split basis).
+constexpr int CMODE_D = 0, CMODE_Q = 2, CMODE_DDAG = 3;
 mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X, void* Y, int nrhs, int prec,
-                          bool dagger, cudaStream_t s);
+                          int mode, cudaStream_t s);
 
 }  // namespace mglma

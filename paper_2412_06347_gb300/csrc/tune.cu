@@ -97,7 +97,7 @@ mglma_status mglma_autotune(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, int nr
       if (st != MGLMA_OK) break;
       ctx->tune[TUNE_COARSE_NT * 1024 + bucket] = {nt, 0.0};
       double ms = 0;
-      st = time_ms(ctx, s, 5, [&] { return coarse_apply(ctx, C, X, Y, nrhs, MGLMA_FP32, false, s); }, &ms);
+      st = time_ms(ctx, s, 5, [&] { return coarse_apply(ctx, C, X, Y, nrhs, MGLMA_FP32, CMODE_D, s); }, &ms);
       if (st == MGLMA_OK && ms < best) {
         best = ms;
         choice = nt;

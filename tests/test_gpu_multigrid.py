@@ -90,6 +90,17 @@ def test_coarse_operator_and_apply(m, ctx, setup):
         assert rel_per_rhs(Y, ref).max() < 1e-12
         m.mglma_coarse_apply(ctx, C, 9, X, Y, m.MGLMA_FP32)
         assert rel_per_rhs(Y, ref).max() < tol
+        # Q1 = g5hat D1 and D1^dag = g5hat D1 g5hat against the oracle's
+        # stencil transpose (gamma5-hermiticity of the coarse operator)
+        g5 = MG.coarse_gamma5(s["nv"])
+        dag = MG.coarse_apply_dagger(Dhat_ref, X, Lb)
+        for op, want in ((m.MGLMA_OP_Q, g5 * ref), (m.MGLMA_OP_DDAG, dag)):
+            m.mglma_coarse_apply(ctx, C, 9, X, Y, m.MGLMA_FP64, op=op)
+            assert rel_per_rhs(Y, want).max() < 1e-11
+            m.mglma_coarse_apply(ctx, C, 9, X, Y, m.MGLMA_FP32, op=op)
+            assert rel_per_rhs(Y, want).max() < tol
+        with pytest.raises(m.MglmaError):
+            m.mglma_coarse_apply(ctx, C, 9, X, Y, m.MGLMA_FP64, op=m.MGLMA_OP_DDAGD)
         m.mglma_coarse_free(C)
 
 

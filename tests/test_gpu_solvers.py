@@ -57,11 +57,12 @@ def test_cgne_fp64(m, ctx, c1):
     assert np.linalg.norm(x[0] - xo) / np.linalg.norm(xo) < 1e-8
 
 
-def test_mg_mixed_solve_and_pieces(m, ctx, c1):
+@pytest.mark.parametrize("coarse_solver", [0, 1])  # GCR(16) on D1, MINRES on Q1
+def test_mg_mixed_solve_and_pieces(m, ctx, c1, coarse_solver):
     b = synthetic.z2_noise(c1["L"], 3, 3002)
     x = np.zeros_like(b)
     xc = np.zeros_like(b)
-    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG)
+    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG, coarse_solver=coarse_solver)
     _, st = m.mglma_solve_batch(ctx, c1["g"], c1["C"], prm, [3], b, x, xc)
     assert all(s["converged"] and s["residual"] <= 1e-10 for s in st)
     assert oracle_residual(c1, x, b).max() <= 1e-10
@@ -80,9 +81,10 @@ def test_mg_mixed_solve_and_pieces(m, ctx, c1):
     assert np.linalg.norm(g) < 1e-8 * np.linalg.norm(MG.restrict(phi, b[0], L, bl))
 
 
-def test_ragged_groups_equal_alone(m, ctx, c1):
+@pytest.mark.parametrize("coarse_solver", [0, 1])
+def test_ragged_groups_equal_alone(m, ctx, c1, coarse_solver):
     b = np.concatenate([synthetic.z2_noise(c1["L"], 4, 3003), synthetic.random_spinors(c1["L"], 2, 3004)])
-    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG)
+    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG, coarse_solver=coarse_solver)
     x = np.zeros_like(b)
     m.mglma_solve_batch(ctx, c1["g"], c1["C"], prm, [1, 3, 2], b, x)
     for i in (0, 2, 5):
