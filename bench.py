@@ -253,7 +253,7 @@ def run_micro(args, w):
     import paper_2412_06347_gb300 as m
     import synthetic
     hbm, _, _, peak_kind = peaks()
-    L = w["L"]
+    L = tuple(int(v) for v in args.micro_lattice.split("x")) if args.micro_lattice else w["L"]
     V = int(np.prod(L))
     ctx = m.Context(0)
     U = synthetic.gauge_links(L, w["eps"], 1000 + w["cfg"])
@@ -317,6 +317,7 @@ def main():
     ap.add_argument("--micro", default="", choices=["", "dslash32", "dslash64", "coarse", "transfer"],
                     help="time one kernel class on the workload lattice instead of the solve")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch in --micro mode")
+    ap.add_argument("--micro-lattice", default="", help="lattice of --micro mode, e.g. 32x32x32x16 (default: the workload's)")
     ap.add_argument("--serve-requests", type=int, default=6,
                     help="requests of the seeded Poisson stream served after the timed solves (0: skip)")
     ap.add_argument("--serve-max-rhs", type=int, default=4, help="RHS per request drawn uniformly in 1..this")

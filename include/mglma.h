@@ -277,7 +277,10 @@ typedef struct {
   int converged;               /* 1 if residual <= tol */
 } mglma_solve_stats;
 
-/* Fills *p with the library defaults for `method`. */
+/* Fills *p with the library defaults for `method`: tol 1e-10; MG: gcr_m 4,
+ * nu 7, inner_tol 3e-6, coarse_tol 0.02, coarse_max_iter 108 (whole cycles
+ * of 12 MINRES iterations), coarse_solver MINRES, check_every 1, max_batch 0;
+ * CGNE: max_iter 100000, check_every 20. */
 void mglma_solve_params_default(mglma_solve_params* p, int method);
 
 /* Solves D x = b (x = S b, the propagator of Sec. 2 applied to b) for
@@ -362,7 +365,7 @@ mglma_status mglma_serve(mglma_ctx ctx, const mglma_serve_config* cfg, mglma_req
  * events and keeps the fastest in the context (used by every later call
  * with an RHS count in the same power-of-two bucket):
  *   kernel 0: RHS per thread of the FP32 stencil (1, 2, 4), needs g;
- *   kernel 1: RHS per tile of the tensor-core coarse stencil (8, 16), needs c.
+ *   kernel 1: RHS per tile of the tensor-core coarse stencil (8, 16, 32), needs c.
  * g or c may be NULL to skip that kernel. */
 mglma_status mglma_autotune(mglma_ctx ctx, mglma_gauge g, mglma_coarse c, int nrhs);
 /* The tuned choice (0 if none) and its time in ms for kernel / nrhs. */

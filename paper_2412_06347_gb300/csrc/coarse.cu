@@ -216,7 +216,7 @@ static mglma_status launch_capply(const AT* A, const void* X, void* Y, const mgl
 }
 
 mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X, void* Y, int nrhs, int prec,
-                          int mode, cudaStream_t s) {
+                          int mode, cudaStream_t s, void* scratch, size_t scratch_bytes) {
   if (mode < 0 || mode > 3) return fail(MGLMA_ERR_INVALID, "coarse apply: unknown gamma5 mode");
   if (nrhs == 0) return MGLMA_OK;
   // algorithmic traffic: the operator once (9 (2Nv)^2 complex per coarse
@@ -229,7 +229,8 @@ mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X
     if (!Cc->A64) return fail(MGLMA_ERR_INVALID, "coarse apply: FP64 operator not kept");
     return launch_capply<double, double2, 4>(Cc->A64, X, Y, Cc, nrhs, mode, s);
   }
-  if (Cc->Aimg) return coarse_apply_tc(ctx, Cc, (const float2*)X, (float2*)Y, nrhs, mode, s);
+  if (Cc->Aimg)
+    return coarse_apply_tc(ctx, Cc, (const float2*)X, (float2*)Y, nrhs, mode, scratch, scratch_bytes, s);
   if (Cc->A16) return launch_capply<float, __nv_bfloat162, 8>(Cc->A16, X, Y, Cc, nrhs, mode, s);
   if (Cc->A32) return launch_capply<float, float2, 8>(Cc->A32, X, Y, Cc, nrhs, mode, s);
   return launch_capply<float, double2, 8>(Cc->A64, X, Y, Cc, nrhs, mode, s);

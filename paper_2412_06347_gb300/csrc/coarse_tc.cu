@@ -11,14 +11,22 @@
 //
 // Data layout: the BF16 operator of each site is stored in HBM already in the
 // no-swizzle K-major core-matrix order the MMA reads from shared memory
-// ([k chunk of 8][row group of 8][8 rows][8 values]), so a single bulk async
-// copy per site stages it; two stage buffers let the next site's operator
-// stream in while the current one is multiplied.  The MMA shape is M = 128
-// (rows >= n2 read neighbouring shared memory and are never stored).
+// ([k chunk of 8][row group of 8][8 rows][8 values]); the nine slots are nine
+// contiguous blocks.  A first kernel writes X once per call as the matching
+// B blocks (one per site and RHS tile, shared by the nine sites that use it).
+// The stencil kernel then only moves bytes with bulk async copies: a ring of
+// shared-memory stages, one stencil slot (A_d and B_d) per stage, filled by
+// one thread, drained by one MMA-issuing thread, with the accumulator of
+// consecutive work units alternating between two TMEM buffers so that the
+// epilogue of one unit overlaps the MMAs of the next.  Two CTAs share an SM,
+// so one CTA's copies proceed while the other waits for its MMAs to finish
+// reading a stage.  The MMA shape is
+// M = 128 (rows >= n2 read neighbouring shared memory and are never stored).
 //
 // Every mbarrier wait is bounded: on a timeout the kernel records an error,
-// stops issuing work, waits (bounded) for its own copies, frees its TMEM and
-// returns; the host reports MGLMA_ERR_TIMEOUT.
+// the other roles stop at their next wait, the copy thread waits (bounded)
+// for its copies in flight, the MMA thread for its MMAs, TMEM is freed and
+// the kernel returns; the host reports MGLMA_ERR_TIMEOUT.
 #include <algorithm>
 #include <string>
 
@@ -29,25 +37,33 @@
 
 namespace mglma {
 
-constexpr int TC_THREADS = 256;
-constexpr uint32_t TC_TMEM_COLS = 32;
+constexpr int TC_THREADS = 128;  // warps 0-1 epilogue, warp 2 copies, warp 3 MMA
+constexpr int TC_EPI_WARPS = 2;    // TMEM lanes 0..63 (rows i < n2 <= 48)
+constexpr int TC_MAX_STAGES = 16;
+constexpr uint32_t TC_PAD = 2048;  // M = 128 rows read past the n2 real rows
 constexpr long long TC_WAIT_LIMIT = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; gives up early when another role raised *abort
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
   for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
+    if (mbar_try(bar, parity)) return true;
+    if (abort && (it & 255) == 255 && *abort) return false;
   }
   return false;
 }
@@ -70,218 +86,257 @@ __device__ __forceinline__ uint16_t bf16_bits(float f) {
   return *reinterpret_cast<uint16_t*>(&h);
 }
 
-template <int NT>  // right-hand sides per tile; the MMA N is 2 NT
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    coarse_tc_kernel(const uint8_t* __restrict__ Aimg, const float2* __restrict__ X, float2* __restrict__ Y, LatIdx q,
-                     int n2, int nrhs, int mode, int* __restrict__ err) {
-  constexpr int NN = 2 * NT;
+// B-operand image of X for RHS tiles of NT: per (tile t, site z) the rows
+// k = (part, j) of one slot, 2 G chunks of 8, times N = 2 NT columns, in the
+// no-swizzle K-major order [chunk c][column group][8 columns][8 k] (16-byte
+// row (c, n) at index c N + n):
+//   part 0: column r <- Re X_j,r, column NT + r <- Im X_j,r
+//   part 1: column r <- -Im X_j,r, column NT + r <- Re X_j,r
+// RHS beyond nrhs are zero; mode bit 0 applies gamma5hat (j >= nv negated).
+__global__ void x_image_kernel(const float2* __restrict__ X, uint4* __restrict__ XB, int64_t V1, int n2, int nrhs,
+                               int NT, int mode) {
+  const int G = n2 / 8, N = 2 * NT, nv = n2 / 2;
+  const size_t rows = (size_t)2 * G * N;  // 16-byte rows per (tile, site)
+  const size_t ntiles = (size_t)(nrhs + NT - 1) / NT;
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= ntiles * V1 * rows) return;
+  const int n = (int)(tid % N);
+  const int c = (int)((tid / N) % (2 * G));
+  const int64_t z = (int64_t)((tid / rows) % V1);
+  const int t = (int)(tid / (rows * V1));
+  const int part = c / G, jo = c % G;
+  const bool imcol = n >= NT;
+  const int rr = t * NT + (imcol ? n - NT : n);
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
+  if (rr < nrhs) {
+    const float4* src = reinterpret_cast<const float4*>(X + ((size_t)rr * V1 + z) * n2 + jo * 8);
+    float re[8], im[8];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const float4 q = __ldg(src + h);
+      re[2 * h] = q.x;
+      im[2 * h] = q.y;
+      re[2 * h + 1] = q.z;
+      im[2 * h + 1] = q.w;
+    }
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float sg = ((mode & 1) && jo * 8 + e >= nv) ? -1.f : 1.f;
+      v[e] = sg * (part == 0 ? (imcol ? im[e] : re[e]) : (imcol ? re[e] : -im[e]));
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) w[e] = (uint32_t)bf16_bits(v[2 * e]) | ((uint32_t)bf16_bits(v[2 * e + 1]) << 16);
+  }
+  XB[tid] = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v);
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, uint32_t* v) {
+  tmem_ld<16>(taddr, v);
+  tmem_ld<16>(taddr + 16, v + 16);
+}
+template <>
+__device__ __forceinline__ void tmem_ld<64>(uint32_t taddr, uint32_t* v) {
+  tmem_ld<32>(taddr, v);
+  tmem_ld<32>(taddr + 32, v + 32);
+}
+
+// Warp-specialised persistent kernel: CTA b takes sites y = b, b + grid, ...
+// and every RHS tile of each; a work unit (site, tile) runs through nine
+// pipeline stages, one per stencil slot d, each holding the slot's operator
+// block A_d (n2 x 2 n2 BF16) and the B image of X at nbr_d(y).
+//   warp 2 (one lane): waits for a free stage, bulk-copies A_d and B_d into it
+//   warp 3 (one lane): waits for a full stage, issues the slot's MMAs into the
+//     unit's accumulator (two TMEM buffers, alternating by unit), commits the
+//     stage back to warp 2 and, after slot 8, the accumulator to the epilogue
+//   warps 0-1: read the accumulator (rows = TMEM lanes), release it, store Y
+template <int NT>
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    coarse_tc_kernel(const uint8_t* __restrict__ Aimg, const uint8_t* __restrict__ XB, float2* __restrict__ Y,
+                     LatIdx q, int n2, int nrhs, int mode, int nstages, int* __restrict__ err) {
+  constexpr int N = 2 * NT;
+  constexpr uint32_t TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;
   extern __shared__ __align__(1024) uint8_t sm[];
-  const int K = 18 * n2, NC = K / 8, G = n2 / 8;
-  const uint32_t abytes = (uint32_t)NC * G * 128;
-  uint8_t* Abuf0 = sm;
-  uint8_t* Bsm = sm + 2 * (size_t)abytes;
-  const uint32_t bbytes = (uint32_t)NC * (NN / 8) * 128;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Bsm + bbytes);  // full[0], full[1], mma
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
+  const int G = n2 / 8;
+  const uint32_t a_slot = (uint32_t)256 * G * G;  // 2 G chunks x G row groups x 128 B
+  const uint32_t b_slot = (uint32_t)32 * G * N;   // 2 G chunks x N/8 column groups x 128 B
+  const uint32_t stage_bytes = a_slot + b_slot;
+  const int S = nstages;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (size_t)S * stage_bytes + TC_PAD);
+  uint64_t* full = bars;                  // [S] copies landed
+  uint64_t* empty = bars + TC_MAX_STAGES;  // [S] MMAs done reading
+  uint64_t* accf = bars + 2 * TC_MAX_STAGES;
+  uint64_t* acce = accf + 2;
+  uint64_t* done = acce + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ int abort_flag;
+  volatile int* abrt = &abort_flag;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int64_t V1 = q.V;
+  const int ntiles = (nrhs + NT - 1) / NT;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TC_TMEM_COLS));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
     abort_flag = 0;
-    for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + b)));
+    for (int b = 0; b < S; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(full + b)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(empty + b)));
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(accf + b)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(acce + b)), "r"(TC_EPI_WARPS));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
-
-  auto issue_copy = [&](int64_t ysite, int buf) {
-    const uint32_t bar = smem_u32(bars + buf);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(abytes) : "memory");
-    const uint8_t* src = Aimg + (size_t)ysite * abytes;
-    const uint32_t dst = smem_u32(Abuf0 + (size_t)buf * abytes);
-    for (uint32_t off = 0; off < abytes; off += 32768) {
-      const uint32_t len = min(32768u, abytes - off);
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       dst + off),
-                   "l"(src + off), "r"(len), "r"(bar)
-                   : "memory");
-    }
+  auto give_up = [&](int code) {
+    abort_flag = 1;
+    atomicExch(err, code);
   };
 
-  const int64_t y0 = blockIdx.x;
-  bool pending[2] = {false, false};
-  uint32_t full_phase[2] = {0u, 0u};
-  if (tid == 0 && y0 < V1) {
-    issue_copy(y0, 0);
-    pending[0] = true;
-  }
-  const uint32_t idesc = idesc_bf16(128, NN);
-  const uint32_t lboA = (uint32_t)G * 128, lboB = (uint32_t)(NN / 8) * 128;
-  uint32_t mma_phase = 0;
-  const int ntiles = (nrhs + NT - 1) / NT;
-  const int nv = n2 / 2;
-  // ---- B operand: each thread owns items w = tid + q*TC_THREADS of a work
-  // unit (site, RHS tile); item = (d, j octet, RHS r): 8 complex of X.
-  // The next unit's items are loaded into registers while the current
-  // unit's MMA runs.
-  constexpr int IT = (9 * 8 * NT + TC_THREADS - 1) / TC_THREADS;  // G <= 8
-  const int nitems = 9 * G * NT;
-  float4 xr[IT][4];
-  auto load_unit = [&](int64_t yy, int rt) {
-    int xx[4];
-    site_coords(q, yy, xx);
-    const int r0 = rt * NT;
+  if (warp == 2) {
+    // ------------------------------------------------------------ copies
+    uint32_t it = 0;
+    if (lane == 0) {
+      bool ok = true;
+      for (int64_t y = blockIdx.x; y < V1 && ok; y += gridDim.x) {
+        int xx[4];
+        site_coords(q, y, xx);
+        int64_t nb[9];
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int w = tid + it * TC_THREADS;
-      if (w >= nitems) break;
-      const int r = w % NT, jo = (w / NT) % G, d = w / (NT * G);
-      if (r0 + r < nrhs) {
-        const int64_t z = d == 8 ? yy : (d < 4 ? nbr_fwd(q, yy, xx, d) : nbr_bwd(q, yy, xx, d - 4));
-        const float4* src = reinterpret_cast<const float4*>(X + ((size_t)(r0 + r) * V1 + z) * n2 + jo * 8);
-#pragma unroll
-        for (int h = 0; h < 4; ++h) xr[it][h] = __ldg(src + h);
-      } else {
-#pragma unroll
-        for (int h = 0; h < 4; ++h) xr[it][h] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-  };
-  auto store_unit = [&]() {
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int w = tid + it * TC_THREADS;
-      if (w >= nitems) break;
-      const int r = w % NT, jo = (w / NT) % G, d = w / (NT * G);
-      float re[8], im[8];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        re[2 * h] = xr[it][h].x;
-        im[2 * h] = xr[it][h].y;
-        re[2 * h + 1] = xr[it][h].z;
-        im[2 * h + 1] = xr[it][h].w;
-      }
-      if (mode & 1) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          if (jo * 8 + e >= nv) {
-            re[e] = -re[e];
-            im[e] = -im[e];
-          }
-      }
-      uint32_t pr[4], pim[4], nim[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        pr[e] = (uint32_t)bf16_bits(re[2 * e]) | ((uint32_t)bf16_bits(re[2 * e + 1]) << 16);
-        pim[e] = (uint32_t)bf16_bits(im[2 * e]) | ((uint32_t)bf16_bits(im[2 * e + 1]) << 16);
-        nim[e] = (uint32_t)bf16_bits(-im[2 * e]) | ((uint32_t)bf16_bits(-im[2 * e + 1]) << 16);
-      }
-      // k chunk of (d, part, jo): c = (d * 2 + part) * G + jo; columns r and NT + r
-      const int c0 = (d * 2) * G + jo, c1 = (d * 2 + 1) * G + jo;
-      auto put = [&](int c, int col, const uint32_t* v) {
-        uint4* p = reinterpret_cast<uint4*>(Bsm + ((size_t)c * (NN / 8) + col / 8) * 128 + (col % 8) * 16);
-        *p = make_uint4(v[0], v[1], v[2], v[3]);
-      };
-      put(c0, r, pr);        // Re X  -> Re Y column
-      put(c1, r, nim);       // -Im X -> Re Y column
-      put(c0, NT + r, pim);  // Im X  -> Im Y column
-      put(c1, NT + r, pr);   // Re X  -> Im Y column
-    }
-  };
-
-  int t = 0;
-  if (y0 < V1) load_unit(y0, 0);
-  for (int64_t y = y0; y < V1; y += gridDim.x, ++t) {
-    const int buf = t & 1;
-    const int64_t yn = y + gridDim.x;
-    if (tid == 0 && yn < V1) {
-      issue_copy(yn, buf ^ 1);
-      pending[buf ^ 1] = true;
-    }
-    for (int rt = 0; rt < ntiles; ++rt) {
-      const int r0 = rt * NT;
-      store_unit();
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0 && !abort_flag) {
-        bool ok = true;
-        if (rt == 0) {
-          ok = mbar_wait(smem_u32(bars + buf), full_phase[buf]);
-          if (ok) {
-            full_phase[buf] ^= 1u;
-            pending[buf] = false;
-          }
+        for (int d = 0; d < 4; ++d) {
+          nb[d] = nbr_fwd(q, y, xx, d);
+          nb[4 + d] = nbr_bwd(q, y, xx, d);
         }
-        if (!ok) {
-          abort_flag = 1;
-          atomicExch(err, 1);
-        } else {
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t a0 = smem_u32(Abuf0 + (size_t)buf * abytes), b0 = smem_u32(Bsm);
-          for (int s = 0; s < K / 16; ++s) {
-            const uint64_t ad = smem_desc(a0 + s * 2 * lboA, lboA, 128);
-            const uint64_t bd = smem_desc(b0 + s * 2 * lboB, lboB, 128);
-            const uint32_t acc = s > 0 ? 1u : 0u;
+        nb[8] = y;
+        for (int t = 0; t < ntiles && ok; ++t) {
+          for (int d = 0; d < 9; ++d, ++it) {
+            const int st = (int)(it % S);
+            const uint32_t ph = (it / S) & 1u;
+            if (!mbar_wait(smem_u32(empty + st), ph ^ 1u, abrt)) {
+              if (!*abrt) give_up(1);
+              ok = false;
+              break;
+            }
+            const uint32_t bar = smem_u32(full + st);
+            const uint32_t dst = smem_u32(sm + (size_t)st * stage_bytes);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(stage_bytes)
+                         : "memory");
+            const uint8_t* srcA = Aimg + ((size_t)y * 9 + d) * a_slot;
+            const uint8_t* srcB = XB + ((size_t)t * V1 + nb[d]) * b_slot;
             asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "setp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                "l"(srcA), "r"(a_slot), "r"(bar)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    dst + a_slot),
+                "l"(srcB), "r"(b_slot), "r"(bar)
+                : "memory");
           }
+        }
+      }
+      // copies still in flight (after an abort): wait for each stage's last
+      // fill, bounded and regardless of the abort flag
+      for (uint32_t st = 0; st < (uint32_t)S && st < it; ++st) {
+        const uint32_t fills = (it - st + S - 1) / S;
+        mbar_wait(smem_u32(full + st), (fills - 1) & 1u, nullptr);
+      }
+    }
+  } else if (warp == 3) {
+    // ------------------------------------------------------------ MMA
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, N);
+      const uint32_t lboA = (uint32_t)G * 128, lboB = (uint32_t)(N / 8) * 128;
+      uint32_t it = 0, u = 0;
+      bool ok = true;
+      for (int64_t y = blockIdx.x; y < V1 && ok; y += gridDim.x) {
+        for (int t = 0; t < ntiles && ok; ++t, ++u) {
+          const uint32_t b = u & 1u, aph = (u >> 1) & 1u;
+          if (!mbar_wait(smem_u32(acce + b), aph ^ 1u, abrt)) {
+            if (!*abrt) give_up(2);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t dcol = tmem + b * N;
+          for (int d = 0; d < 9; ++d, ++it) {
+            const int st = (int)(it % S);
+            const uint32_t ph = (it / S) & 1u;
+            if (!mbar_wait(smem_u32(full + st), ph, abrt)) {
+              if (!*abrt) give_up(3);
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a0 = smem_u32(sm + (size_t)st * stage_bytes), b0 = a0 + a_slot;
+            for (int kk = 0; kk < G; ++kk) {
+              const uint64_t ad = smem_desc(a0 + kk * 2 * lboA, lboA, 128);
+              const uint64_t bd = smem_desc(b0 + kk * 2 * lboB, lboB, 128);
+              const uint32_t acc = (d > 0 || kk > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\t"
+                  "setp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(empty + st)));
+          }
+          if (!ok) break;
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(bars + 2)));
+              smem_u32(accf + b)));
         }
       }
-      // next unit's gather overlaps the MMA
-      if (rt + 1 < ntiles)
-        load_unit(y, rt + 1);
-      else if (yn < V1)
-        load_unit(yn, 0);
-      __syncthreads();
-      if (abort_flag) break;
-      if (tid == 0) {
-        if (!mbar_wait(smem_u32(bars + 2), mma_phase)) {
-          atomicExch(err, 2);
-          abort_flag = 1;
+      // every MMA issued by this thread has completed before TMEM is freed
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(done)));
+      mbar_wait(smem_u32(done), 0u, nullptr);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    uint32_t u = 0;
+    const int i = warp * 32 + lane;
+    const float sg = ((mode & 2) && i >= n2 / 2) ? -1.f : 1.f;
+    bool ok = true;
+    for (int64_t y = blockIdx.x; y < V1 && ok; y += gridDim.x) {
+      for (int t = 0; t < ntiles; ++t, ++u) {
+        const uint32_t b = u & 1u, aph = (u >> 1) & 1u;
+        // every lane waits; the warp proceeds only if all saw the phase
+        const bool mine = mbar_wait(smem_u32(accf + b), aph, abrt);
+        if (!__all_sync(0xffffffffu, mine)) {
+          if (lane == 0 && !*abrt) give_up(4);
+          ok = false;
+          break;
         }
-        mma_phase ^= 1u;
-      }
-      __syncthreads();
-      if (abort_flag) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      // ---- epilogue: warps 0..3 own TMEM lanes 0..127; rows >= n2 are padding
-      if (warp < 4 && warp * 32 < n2) {
-        uint32_t v[NN];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        if constexpr (NN == 16) {
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-              : "r"(taddr));
-        } else {
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-                "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-                "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-                "=r"(v[30]), "=r"(v[31])
-              : "r"(taddr));
-        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        uint32_t v[N];
+        tmem_ld<N>(tmem + ((uint32_t)(warp * 32) << 16) + b * N, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int i = warp * 32 + lane;
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acce + b)) : "memory");
         if (i < n2) {
-          const float sg = ((mode & 2) && i >= nv) ? -1.f : 1.f;
+          const int r0 = t * NT;
 #pragma unroll
           for (int r = 0; r < NT; ++r)
             if (r0 + r < nrhs)
@@ -289,19 +344,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   make_float2(sg * __uint_as_float(v[r]), sg * __uint_as_float(v[NT + r]));
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-      if (abort_flag) break;
     }
-    if (abort_flag) break;
   }
-  // copies still in flight (only after an abort): wait for them, bounded
-  if (tid == 0) {
-    for (int b = 0; b < 2; ++b)
-      if (pending[b]) mbar_wait(smem_u32(bars + b), full_phase[b]);
-  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 // operator image for the kernel: per site [c][g][8 rows][8 bf16] with
@@ -322,9 +369,23 @@ __global__ void a_image_kernel(const double2* __restrict__ A64, uint16_t* __rest
 
 bool coarse_tc_supported(int n2) { return n2 % 8 == 0 && n2 >= 8 && n2 <= 48; }
 
+static uint32_t tc_stage_bytes(int n2, int NT) {
+  const uint32_t G = n2 / 8;
+  return 256 * G * G + 32 * G * 2 * NT;
+}
+static int tc_stages(int n2, int NT) {
+  // two CTAs per SM (half of 227 KB each), less the pad, the barriers and
+  // 1 KB of static shared memory
+  const size_t avail = 113 * 1024 - 1024 - TC_PAD - (2 * TC_MAX_STAGES + 5) * 8 - 16;
+  return (int)std::min<size_t>(TC_MAX_STAGES, avail / tc_stage_bytes(n2, NT));
+}
 static size_t tc_smem(int n2, int NT) {
-  const size_t K = 18 * (size_t)n2, abytes = K * n2 * 2, bbytes = K * 2 * NT * 2;
-  return 2 * abytes + bbytes + 3 * 8 + 16;
+  return (size_t)tc_stages(n2, NT) * tc_stage_bytes(n2, NT) + TC_PAD + (2 * TC_MAX_STAGES + 5) * 8 + 16;
+}
+
+size_t coarse_tc_scratch_bytes(const mglma_coarse_s* C, int nrhs) {
+  // B images of X for RHS rounded up to the widest tile (32)
+  return (size_t)((nrhs + 31) / 32 * 32) * C->geo.V1 * C->n2 * 8;
 }
 
 mglma_status coarse_tc_image(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s) {
@@ -339,17 +400,26 @@ mglma_status coarse_tc_image(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s) {
 }
 
 template <int NT>
-static mglma_status launch_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float2* X, float2* Y, int nrhs,
-                              int mode, int* err, cudaStream_t s) {
-  const size_t smem = tc_smem(C->n2, NT);
+static mglma_status launch_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float2* X, float2* Y, int nrhs, int mode,
+                              void* xb, int* err, cudaStream_t s) {
+  const int n2 = C->n2;
+  const int64_t V1 = C->geo.V1;
+  {
+    const size_t rows = (size_t)((nrhs + NT - 1) / NT) * V1 * 2 * (n2 / 8) * 2 * NT;
+    x_image_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(X, (uint4*)xb, V1, n2, nrhs, NT, mode);
+    MG_LAUNCH_CHECK();
+  }
+  const size_t smem = tc_smem(n2, NT);
   static size_t attr = 0;  // largest dynamic shared memory granted so far
   if (smem > attr) {
     MG_CUDA(cudaFuncSetAttribute(coarse_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = smem;
   }
-  const unsigned grid = (unsigned)std::min<int64_t>(C->geo.V1, (int64_t)ctx->sm_count);
-  coarse_tc_kernel<NT><<<grid, TC_THREADS, smem, s>>>((const uint8_t*)C->Aimg, X, Y, make_latidx(C->geo.Lb), C->n2,
-                                                      nrhs, mode, err);
+  // two resident CTAs per SM: while one waits for its MMAs to release a
+  // stage, the other's copies and MMAs proceed
+  const unsigned grid = (unsigned)std::min<int64_t>(V1, 2 * (int64_t)ctx->sm_count);
+  coarse_tc_kernel<NT><<<grid, TC_THREADS, smem, s>>>((const uint8_t*)C->Aimg, (const uint8_t*)xb, Y,
+                                                      make_latidx(C->geo.Lb), n2, nrhs, mode, tc_stages(n2, NT), err);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }
@@ -366,14 +436,33 @@ mglma_status coarse_tc_check(mglma_coarse_s* C, cudaStream_t s) {
   return MGLMA_OK;
 }
 
-mglma_status coarse_apply_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float2* X, float2* Y, int nrhs,
-                             int mode, cudaStream_t s) {
+int coarse_tc_default_nt(int nrhs) { return nrhs <= 8 ? 8 : (nrhs <= 24 ? 16 : 32); }
+
+mglma_status coarse_apply_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float2* X, float2* Y, int nrhs, int mode,
+                             void* scratch, size_t scratch_bytes, cudaStream_t s) {
   if (!C->Aimg || !coarse_tc_supported(C->n2)) return fail(MGLMA_ERR_INVALID, "coarse_apply_tc: no tensor image");
   int* err = C->tc_err;
-  const bool fit16 = tc_smem(C->n2, 16) <= 227 * 1024;
-  const int nt = tuned(ctx, TUNE_COARSE_NT, nrhs, (nrhs <= 8 || !fit16) ? 8 : 16);
-  if (nt == 16 && fit16) return launch_tc<16>(ctx, C, X, Y, nrhs, mode, err, s);
-  return launch_tc<8>(ctx, C, X, Y, nrhs, mode, err, s);
+  const int nt = tuned(ctx, TUNE_COARSE_NT, nrhs, coarse_tc_default_nt(nrhs));
+  const size_t need = coarse_tc_scratch_bytes(C, nrhs);
+  void* xb = scratch;
+  void* own = nullptr;
+  if (!xb || scratch_bytes < need) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(MGLMA_ERR_INVALID, "coarse_apply_tc: scratch too small inside a graph capture");
+    MG_CHECK(dalloc(ctx, &own, need, s));
+    xb = own;
+  }
+  mglma_status st;
+  if (nt == 32)
+    st = launch_tc<32>(ctx, C, X, Y, nrhs, mode, xb, err, s);
+  else if (nt == 16)
+    st = launch_tc<16>(ctx, C, X, Y, nrhs, mode, xb, err, s);
+  else
+    st = launch_tc<8>(ctx, C, X, Y, nrhs, mode, xb, err, s);
+  if (own) dfree(ctx, own, s);
+  return st;
 }
 
 }  // namespace mglma

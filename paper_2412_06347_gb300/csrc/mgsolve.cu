@@ -342,11 +342,12 @@ static mglma_status minres_init(MinresWork& w, const mglma_coarse_s* C, const Ve
   return coarse_g5_scale(w.ctx, b, v0, w.st(MR_CF + 4), C->n2, w.s);
 }
 
-static mglma_status minres_iter(MinresWork& w, const mglma_coarse_s* C, Vec& x, int n, int k, double tol) {
+static mglma_status minres_iter(MinresWork& w, const mglma_coarse_s* C, Vec& x, int n, int k, double tol,
+                                void* scr, size_t scr_bytes) {
   const int a = k % 3, b = (k + 1) % 3, c = (k + 2) % 3;
   Vec v = w.view(w.Vp, a, n), vo = w.view(w.Vp, c, n), z = w.view(w.Vp, b, n);
   Vec wn = w.view(w.Wp, a, n), w1 = w.view(w.Wp, c, n), w2 = w.view(w.Wp, b, n);
-  MG_CHECK(coarse_apply(w.ctx, C, v.p, z.p, n, MGLMA_FP32, CMODE_Q, w.s));
+  MG_CHECK(coarse_apply(w.ctx, C, v.p, z.p, n, MGLMA_FP32, CMODE_Q, w.s, scr, scr_bytes));
   MG_CHECK(cdot(w.ctx, v, z, w.sc.z, w.s));
   MG_CHECK(lanczos_norm(w.ctx, w.sc.z, w.st(MR_BETA), w.sc.active, v, vo, z, w.st(MR_BN2), w.s));
   {
@@ -378,6 +379,8 @@ struct CoarseSolver {
   int cap_hint = 0;
   GcrWork w;
   MinresWork mw;
+  void* scr = nullptr;  // tensor-core apply work space (B images of X)
+  size_t scr_bytes = 0;
   struct Graphs {
     cudaGraphExec_t init = nullptr, cycle = nullptr;
     int n = -1;
@@ -387,7 +390,10 @@ struct CoarseSolver {
   void* gx = nullptr;
   double gtol = -1;
   bool warmed = false;
-  ~CoarseSolver() { reset(); }
+  ~CoarseSolver() {
+    reset();
+    if (scr) dfree(ctx, scr, s);
+  }
   void reset() {
     for (auto& G : g) {
       if (G.init) cudaGraphExecDestroy(G.init);
@@ -409,12 +415,12 @@ struct CoarseSolver {
   const int* active() const { return minres() ? mw.sc.active : w.sc.active; }
   OpFn op() {
     return [this](const Vec& in, Vec& out) {
-      return coarse_apply(ctx, C, in.p, out.p, in.nrhs, MGLMA_FP32, CMODE_D, s);
+      return coarse_apply(ctx, C, in.p, out.p, in.nrhs, MGLMA_FP32, CMODE_D, s, scr, scr_bytes);
     };
   }
   mglma_status init(const Vec& b, Vec& x) { return minres() ? minres_init(mw, C, b, x) : gcr_init(w, b, x); }
   mglma_status iter(const OpFn& A, Vec& x, int n, int k, double tol) {
-    return minres() ? minres_iter(mw, C, x, n, k, tol) : gcr_iter(w, A, nullptr, x, n, k, tol * tol);
+    return minres() ? minres_iter(mw, C, x, n, k, tol, scr, scr_bytes) : gcr_iter(w, A, nullptr, x, n, k, tol * tol);
   }
   mglma_status capture(Graphs& G, const Vec& b, Vec& x, double tol, bool prof) {
     const int n = b.nrhs;
@@ -452,6 +458,10 @@ struct CoarseSolver {
         MG_CHECK(mw.setup(ctx, s, b, c));
       else
         MG_CHECK(w.setup(ctx, s, b, c, m));
+      if (C->Aimg) {
+        scr_bytes = coarse_tc_scratch_bytes(C, c);
+        MG_CHECK(dalloc(ctx, &scr, scr_bytes, s));
+      }
     }
     if (n > capacity()) return fail(MGLMA_ERR_INVALID, "coarse solve: more RHS than the workspace holds");
     const int L = cycle_len();

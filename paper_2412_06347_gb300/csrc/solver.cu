@@ -243,11 +243,11 @@ void mglma_solve_params_default(mglma_solve_params* p, int method) {
   p->method = method;
   p->tol = 1e-10;
   p->max_iter = method == MGLMA_SOLVER_CGNE ? 100000 : 4000;
-  p->gcr_m = 8;
-  p->nu = 2;
+  p->gcr_m = 4;
+  p->nu = 7;
   p->inner_tol = 3e-6;
   p->coarse_tol = 0.02;
-  p->coarse_max_iter = 100;
+  p->coarse_max_iter = 108;
   p->check_every = method == MGLMA_SOLVER_CGNE ? 20 : 1;
   p->max_batch = 0;
   p->coarse_solver = MGLMA_COARSE_MINRES;

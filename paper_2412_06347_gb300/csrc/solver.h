@@ -68,11 +68,11 @@ mglma_status mr_alpha(mglma_ctx ctx, const double2* num, const double* den, doub
 struct MgParams {
   double tol = 1e-10;
   int max_iter = 2000;
-  int gcr_m = 8;
-  int nu = 2;
+  int gcr_m = 4;
+  int nu = 7;
   double inner_tol = 3e-6;
   double coarse_tol = 0.02;
-  int coarse_max_iter = 100;
+  int coarse_max_iter = 108;
   int coarse_solver = MGLMA_COARSE_MINRES;
 };
 

@@ -58,15 +58,20 @@ mglma_status coarse_scale_convert(mglma_ctx ctx, const void* src, int sprec, voi
 // tensor-core path (coarse_tc.cu)
 bool coarse_tc_supported(int n2);
 mglma_status coarse_tc_image(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s);
+// scratch: B images of X (coarse_tc_scratch_bytes); NULL or too small ->
+// allocated for the call (refused inside a graph capture)
 mglma_status coarse_apply_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float2* X, float2* Y, int nrhs,
-                             int mode, cudaStream_t s);
+                             int mode, void* scratch, size_t scratch_bytes, cudaStream_t s);
+size_t coarse_tc_scratch_bytes(const mglma_coarse_s* C, int nrhs);
+int coarse_tc_default_nt(int nrhs);
 mglma_status coarse_tc_check(mglma_coarse_s* C, cudaStream_t s);
 // Y = Dhat X for nrhs coarse fields; prec of X/Y: FP64 (FP64 operator) or FP32
 // (FP32 or BF16 operator as stored).  mode bit 0 applies gamma5hat to X, bit 1
 // to Y: 0 Dhat, 2 Qhat = gamma5hat Dhat, 3 gamma5hat Dhat gamma5hat = Dhat^dag
 // (gamma5hat-hermiticity, inherited from D by the chirality-split basis).
 constexpr int CMODE_D = 0, CMODE_Q = 2, CMODE_DDAG = 3;
+// scratch (optional): work space of the tensor-core path, see coarse_apply_tc
 mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X, void* Y, int nrhs, int prec,
-                          int mode, cudaStream_t s);
+                          int mode, cudaStream_t s, void* scratch = nullptr, size_t scratch_bytes = 0);
 
 }  // namespace mglma

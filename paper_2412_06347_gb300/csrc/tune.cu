@@ -1,5 +1,5 @@
 // Autotuner of the RHS tile widths: the stencil's RHS per thread (1, 2, 4)
-// and the tensor-core coarse kernel's RHS per tile (8, 16) are timed with
+// and the tensor-core coarse kernel's RHS per tile (8, 16, 32) are timed with
 // CUDA events on the context stream for a given RHS count, and the fastest
 // is kept per (kernel, RHS bucket) in the context; the table can be saved to
 // and loaded from a text file keyed by GPU name.
@@ -93,8 +93,8 @@ mglma_status mglma_autotune(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, int nr
     if (st == MGLMA_OK) MG_CUDA(cudaMemsetAsync(X, 0, n * sizeof(float2), s));
     double best = 1e30;
     int choice = 8;
-    for (int nt : {8, 16}) {
-      if (st != MGLMA_OK) break;
+    for (int nt : {8, 16, 32}) {
+      if (st != MGLMA_OK || (nt > 8 && nt >= 2 * nrhs)) break;  // tiles mostly padding
       ctx->tune[TUNE_COARSE_NT * 1024 + bucket] = {nt, 0.0};
       double ms = 0;
       st = time_ms(ctx, s, 5, [&] { return coarse_apply(ctx, C, X, Y, nrhs, MGLMA_FP32, CMODE_D, s); }, &ms);
@@ -146,7 +146,8 @@ mglma_status mglma_autotune_load(mglma_ctx ctx, const char* path) {
     int k, b, c;
     double ms;
     if (!(is >> g >> k >> b >> c >> ms) || g != gpu) continue;
-    const bool ok = (k == TUNE_DSLASH32_NR && (c == 1 || c == 2 || c == 4)) || (k == TUNE_COARSE_NT && (c == 8 || c == 16));
+    const bool ok = (k == TUNE_DSLASH32_NR && (c == 1 || c == 2 || c == 4)) || 
+                    (k == TUNE_COARSE_NT && (c == 8 || c == 16 || c == 32));
     if (ok && b >= 1 && b <= 64) ctx->tune[k * 1024 + b] = {c, ms};
   }
   return MGLMA_OK;
