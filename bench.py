@@ -138,7 +138,8 @@ class Clocks:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
-KINDS = ("dslash64", "dslash32", "blas", "reduce", "restrict", "prolong", "coarse", "pack", "setup", "scalar")
+KINDS = ("dslash64", "dslash32", "blas", "reduce", "restrict", "prolong", "coarse", "pack", "setup", "scalar", "cblas",
+         "creduce")
 
 
 def profile_snapshot(m, ctx):
@@ -247,6 +248,13 @@ def micro_dslash(m, torch, ctx, g, V, nrhs, prec, reps, stream):
             "bytes_per_launch": by / n, "tflops": round(fl / (ms / 1e3) / 1e12, 2)}
 
 
+def set_tile(m, ctx, args, nrhs):
+    """--tile NR,RW fixes the FP32 stencil's tile shape for nrhs RHS."""
+    if args.tile:
+        nr, rw = (int(v) for v in args.tile.split(","))
+        m.mglma_autotune_set(ctx, 0, nrhs, m.dslash32_tile_code(nr, rw))
+
+
 def run_micro(args, w):
     """One kernel class alone on the workload lattice (inputs larger than L2)."""
     import torch
@@ -259,6 +267,7 @@ def run_micro(args, w):
     U = synthetic.gauge_links(L, w["eps"], 1000 + w["cfg"])
     g = m.mglma_gauge_load(ctx, L, U, w["kappa"], w["csw"])
     del U
+    set_tile(m, ctx, args, args.nrhs)
     stream = torch.cuda.current_stream()
     reps = max(args.steps, 1)
     if args.micro in ("dslash32", "dslash64"):
@@ -295,7 +304,7 @@ def run_micro(args, w):
         m.mglma_subspace_free(sub)
     if "achieved" in r:
         r["frac"] = round(r["achieved"] / hbm, 4)
-    r.update({"micro": args.micro, "workload": args.workload, "lattice": "x".join(map(str, L)), "peak": hbm,
+    r.update({"micro": args.micro, "workload": args.workload, "tile": args.tile or "default", "lattice": "x".join(map(str, L)), "peak": hbm,
               "peak_source": f"{peak_kind} hbm_gbs"})
     print(json.dumps(r), flush=True)
     m.mglma_gauge_free(g)
@@ -317,6 +326,8 @@ def main():
     ap.add_argument("--micro", default="", choices=["", "dslash32", "dslash64", "coarse", "transfer"],
                     help="time one kernel class on the workload lattice instead of the solve")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch in --micro mode")
+    ap.add_argument("--tile", default="", help="FP32 stencil tile NR,RW (RHS per thread, RHS tiles per CTA); "
+                                                "default: the library's choice")
     ap.add_argument("--micro-lattice", default="", help="lattice of --micro mode, e.g. 32x32x32x16 (default: the workload's)")
     ap.add_argument("--serve-requests", type=int, default=6,
                     help="requests of the seeded Poisson stream served after the timed solves (0: skip)")
@@ -360,6 +371,7 @@ def main():
     C = m.mglma_coarse_build(ctx, g, sub, prec[w["coarse_store"]])
     prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG, coarse_solver=COARSE_SOLVERS[args.coarse_solver])
     stream = torch.cuda.Stream(device=dev)
+    set_tile(m, ctx, args, G)
 
     nsteps = args.warmup + args.steps
     # every rank solves its own sources (replicas): rank r starts at source r*G*steps
@@ -445,7 +457,9 @@ def main():
                 "dslash32": {"achieved": round(dsl[2] / (dsl[1] / 1e3) / 1e9, 1) if dsl[1] else None,
                              "frac": round(dsl[2] / (dsl[1] / 1e3) / 1e9 / hbm, 4) if dsl[1] else None,
                              "launches": dsl[0]}}
-    launches = sum(v[0] for v in prof.values()) + prof.get("reduce", (0,))[0]  # reductions are two kernels
+    # every class is one launch per record except the tensor-core coarse apply,
+    # which writes the B image of X in a first kernel
+    launches = sum(v[0] for v in prof.values()) + prof.get("coarse", (0,))[0]
 
     # ---- the stencil alone at N = 1 and N = G (the "dslash GB/s vs HBM peak" part of the metric)
     dslash = {}

@@ -92,7 +92,9 @@ const char* mglma_version(void);
 mglma_status mglma_profile(mglma_ctx ctx, int enable, int reset);
 /* Fetches the accumulated launches, milliseconds, algorithmic bytes and
  * algorithmic flops of kernel class `name` ("dslash64", "dslash32", "blas",
- * "reduce", "restrict", "prolong", "coarse", "pack", "setup").  Algorithmic
+ * "reduce", "restrict", "prolong", "coarse", "pack", "setup", "scalar",
+ * "cblas", "creduce"; the last two are BLAS-1 and reductions on coarse
+ * fields inside coarse solves, "blas" and "reduce" the fine-level ones).  Algorithmic
  * bytes count every operand read once and every result written once (for
  * the stencil: links, clover, input and output spinors).  Waits for the
  * recorded events.  Any output pointer may be NULL. */
@@ -364,10 +366,16 @@ mglma_status mglma_serve(mglma_ctx ctx, const mglma_serve_config* cfg, mglma_req
 /* Times the candidate RHS tile widths for nrhs right-hand sides with CUDA
  * events and keeps the fastest in the context (used by every later call
  * with an RHS count in the same power-of-two bucket):
- *   kernel 0: RHS per thread of the FP32 stencil (1, 2, 4), needs g;
+ *   kernel 0: tile shape of the FP32 stencil, needs g: NR right-hand sides
+ *     per thread (1, 2, 4) and RW RHS tiles per 128-thread CTA (1, 2, 4;
+ *     a CTA then covers 128 / RW sites), coded NR + 16 (RW - 1) (NR = 4 only
+ *     with RW = 1);
  *   kernel 1: RHS per tile of the tensor-core coarse stencil (8, 16, 32), needs c.
  * g or c may be NULL to skip that kernel. */
 mglma_status mglma_autotune(mglma_ctx ctx, mglma_gauge g, mglma_coarse c, int nrhs);
+/* Sets the choice for kernel / the RHS bucket of nrhs by hand (codes as
+ * above); MGLMA_ERR_INVALID for an unknown kernel or choice. */
+mglma_status mglma_autotune_set(mglma_ctx ctx, int kernel, int nrhs, int choice);
 /* The tuned choice (0 if none) and its time in ms for kernel / nrhs. */
 mglma_status mglma_autotune_get(mglma_ctx ctx, int kernel, int nrhs, int* choice, double* ms);
 /* Text cache of the tuned table, one line per entry, keyed by GPU name;

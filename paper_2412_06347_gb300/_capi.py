@@ -101,6 +101,7 @@ _sig("mglma_sources", C.c_int, _vp, C.POINTER(mglma_lattice), C.c_int, C.c_int, 
      C.POINTER(_i64), C.POINTER(C.c_int), C.c_int, _vp, _vp)
 _sig("mglma_autotune", C.c_int, _vp, _vp, _vp, C.c_int)
 _sig("mglma_autotune_get", C.c_int, _vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double))
+_sig("mglma_autotune_set", C.c_int, _vp, C.c_int, C.c_int, C.c_int)
 _sig("mglma_autotune_save", C.c_int, _vp, C.c_char_p)
 _sig("mglma_autotune_load", C.c_int, _vp, C.c_char_p)
 _sig("mglma_solve_params_default", None, C.POINTER(mglma_solve_params), C.c_int)
@@ -339,6 +340,15 @@ def mglma_autotune_get(ctx, kernel, nrhs):
     ms = C.c_double()
     _check(lib.mglma_autotune_get(_h(ctx), int(kernel), int(nrhs), C.byref(c), C.byref(ms)))
     return c.value, ms.value
+
+
+def mglma_autotune_set(ctx, kernel, nrhs, choice):
+    _check(lib.mglma_autotune_set(_h(ctx), int(kernel), int(nrhs), int(choice)))
+
+
+def dslash32_tile_code(nr, rw):
+    """Tile code of the FP32 stencil: NR RHS per thread, RW RHS tiles per CTA."""
+    return int(nr) + 16 * (int(rw) - 1)
 
 
 def mglma_autotune_save(ctx, path):

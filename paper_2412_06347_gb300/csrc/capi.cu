@@ -19,8 +19,15 @@ mglma_status fail(mglma_status st, const std::string& msg) {
   return st;
 }
 
-static const char* kKindNames[K_NKINDS] = {"dslash64", "dslash32", "blas",  "reduce", "restrict",
-                                           "prolong",  "coarse",   "pack",  "setup", "scalar"};
+static const char* kKindNames[K_NKINDS] = {"dslash64", "dslash32", "blas",  "reduce", "restrict", "prolong",
+                                           "coarse",   "pack",     "setup", "scalar", "cblas",    "creduce"};
+
+CoarseLevelScope::CoarseLevelScope(mglma_ctx c) : ctx(c), prev(c ? c->coarse_level : false) {
+  if (ctx) ctx->coarse_level = true;
+}
+CoarseLevelScope::~CoarseLevelScope() {
+  if (ctx) ctx->coarse_level = prev;
+}
 const char* kernel_kind_name(int k) { return (k >= 0 && k < K_NKINDS) ? kKindNames[k] : "?"; }
 
 void resolve_profile(mglma_ctx ctx);
@@ -38,6 +45,10 @@ static cudaEvent_t take_event(mglma_ctx ctx) {
 
 ProfScope::ProfScope(mglma_ctx c, int k, cudaStream_t st, double bytes_, double flops_)
     : ctx(c), kind(k), s(st), bytes(bytes_), flops(flops_) {
+  if (ctx && ctx->coarse_level) {
+    if (kind == K_BLAS) kind = K_CBLAS;
+    if (kind == K_REDUCE) kind = K_CREDUCE;
+  }
   if (ctx && ctx->profile) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cs);

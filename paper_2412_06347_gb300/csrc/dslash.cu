@@ -269,17 +269,24 @@ struct DslashArgs {
 
 // out = op(in) for NR right-hand sides per thread.  DAG selects D^dag
 // (projectors 1 +- gamma swap); g5out multiplies the result by gamma5.
-template <typename R, int NR, bool DAG>
+// A CTA of 128 threads covers 128 / RW consecutive sites for RW RHS tiles of
+// NR: thread t takes site t mod (128 / RW) of the CTA's block and RHS tile
+// t / (128 / RW), so with RW > 1 the warps of one CTA read the same links and
+// clover entries and all but the first find them in L1.
+template <typename R, int NR, bool DAG, int RW>
 __global__ void __launch_bounds__(128) dslash_kernel(const void* __restrict__ in, void* __restrict__ out,
                                                      const void* __restrict__ U, const void* __restrict__ C,
                                                      DslashArgs a) {
+  constexpr int SW = 128 / RW;  // sites per CTA
   const int64_t V = a.q.V;
-  // RHS tiles run fastest in launch order, so the CTAs that share a block of
-  // sites are resident together and its links and clover come from L2
+  // RHS tile groups run fastest in launch order, so the CTAs that share a
+  // block of sites are resident together and its links and clover come from L2
   const int ntile = (a.nrhs + NR - 1) / NR;
-  const int64_t site = (int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x;
-  if (site >= V) return;
-  const int r0 = (blockIdx.x % ntile) * NR;
+  const int ngrp = (ntile + RW - 1) / RW;
+  const int64_t site = (int64_t)(blockIdx.x / ngrp) * SW + threadIdx.x % SW;
+  const int tile = (int)(blockIdx.x % ngrp) * RW + (int)threadIdx.x / SW;
+  if (site >= V || tile >= ntile) return;
+  const int r0 = tile * NR;
   int x[4];
   site_coords(a.q, site, x);
   const R sF = DAG ? R(1) : R(-1);  // forward hop carries (1 + sF gamma)
@@ -659,15 +666,42 @@ mglma_status convert_spinor(mglma_ctx ctx, const Spinor& src, Spinor& dst, cudaS
   return MGLMA_OK;
 }
 
-template <typename R, int NR, bool DAG>
+template <typename R, int NR, int RW>
 static void launch_dslash(const Spinor& in, Spinor& out, const void* U, const void* C, const DslashArgs& a,
-                          cudaStream_t s) {
-  const size_t tiles = (size_t)((in.V + 127) / 128) * ((in.nrhs + NR - 1) / NR);
-  dslash_kernel<R, NR, DAG><<<(unsigned)tiles, 128, 0, s>>>(in.p, out.p, U, C, a);
+                          bool dagger, cudaStream_t s) {
+  constexpr int SW = 128 / RW;
+  const int ntile = (in.nrhs + NR - 1) / NR;
+  const size_t ctas = (size_t)((in.V + SW - 1) / SW) * ((ntile + RW - 1) / RW);
+  if (dagger)
+    dslash_kernel<R, NR, true, RW><<<(unsigned)ctas, 128, 0, s>>>(in.p, out.p, U, C, a);
+  else
+    dslash_kernel<R, NR, false, RW><<<(unsigned)ctas, 128, 0, s>>>(in.p, out.p, U, C, a);
 }
 
-// RHS per thread: 1 unless the autotuner (tune.cu) measured a better width
-// for this RHS count on this context
+// FP32 tile shape (RHS per thread NR, RHS tiles per CTA RW) encoded as
+// NR + 16 (RW - 1); the autotuner (tune.cu) may replace the default below
+// for an RHS count on a context.
+int dslash32_default_tile(int nrhs) { return nrhs >= 4 ? dslash32_tile_code(1, 1) : dslash32_tile_code(1, 1); }
+
+static void launch_dslash32(int code, const Spinor& in, Spinor& out, const void* U, const void* C,
+                            const DslashArgs& a, bool dagger, cudaStream_t s) {
+  int nr = dslash32_tile_nr(code), rw = dslash32_tile_rw(code);
+  if (in.nrhs < nr) nr = in.nrhs >= 2 ? 2 : 1;
+  if (nr == 4)
+    launch_dslash<float, 4, 1>(in, out, U, C, a, dagger, s);
+  else if (nr == 2 && rw == 4)
+    launch_dslash<float, 2, 4>(in, out, U, C, a, dagger, s);
+  else if (nr == 2 && rw == 2)
+    launch_dslash<float, 2, 2>(in, out, U, C, a, dagger, s);
+  else if (nr == 2)
+    launch_dslash<float, 2, 1>(in, out, U, C, a, dagger, s);
+  else if (rw == 4)
+    launch_dslash<float, 1, 4>(in, out, U, C, a, dagger, s);
+  else if (rw == 2)
+    launch_dslash<float, 1, 2>(in, out, U, C, a, dagger, s);
+  else
+    launch_dslash<float, 1, 1>(in, out, U, C, a, dagger, s);
+}
 
 mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, bool dagger,
                     bool gamma5_out, cudaStream_t s) {
@@ -686,26 +720,11 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
   const double flops = 1896.0 * V * N;
   if (in.prec == MGLMA_FP64) {
     ProfScope ps(ctx, K_DSLASH64, s, V * (1152.0 + 384.0 * N), flops);
-    const int nr = 1;
-    if (nr == 2)
-      dagger ? launch_dslash<double, 2, true>(in, out, G->U64, G->C64, a, s)
-             : launch_dslash<double, 2, false>(in, out, G->U64, G->C64, a, s);
-    else
-      dagger ? launch_dslash<double, 1, true>(in, out, G->U64, G->C64, a, s)
-             : launch_dslash<double, 1, false>(in, out, G->U64, G->C64, a, s);
+    launch_dslash<double, 1, 1>(in, out, G->U64, G->C64, a, dagger, s);
   } else {
     ProfScope ps(ctx, K_DSLASH32, s, V * (480.0 + 192.0 * N), flops);
-    int nr = tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, 1);
-    if (in.nrhs < nr) nr = in.nrhs >= 2 ? 2 : 1;
-    if (nr == 4)
-      dagger ? launch_dslash<float, 4, true>(in, out, G->U32, G->C32, a, s)
-             : launch_dslash<float, 4, false>(in, out, G->U32, G->C32, a, s);
-    else if (nr == 2)
-      dagger ? launch_dslash<float, 2, true>(in, out, G->U32, G->C32, a, s)
-             : launch_dslash<float, 2, false>(in, out, G->U32, G->C32, a, s);
-    else
-      dagger ? launch_dslash<float, 1, true>(in, out, G->U32, G->C32, a, s)
-             : launch_dslash<float, 1, false>(in, out, G->U32, G->C32, a, s);
+    launch_dslash32(tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, dslash32_default_tile(in.nrhs)), in, out, G->U32, G->C32,
+                    a, dagger, s);
   }
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
@@ -831,19 +850,16 @@ extern "C" mglma_status mglma_dirac_apply_noalloc(mglma_ctx ctx, mglma_gauge G, 
   else
     pack_kernel<float><<<pg, 256, 0, s>>>(in, a.p, a.V, nrhs);
   const bool dag1 = op == MGLMA_OP_DDAG;
-  if (dp) {
-    dag1 ? launch_dslash<double, 1, true>(a, b, G->U64, G->C64, da, s)
-         : launch_dslash<double, 1, false>(a, b, G->U64, G->C64, da, s);
-  } else {
-    dag1 ? launch_dslash<float, 1, true>(a, b, G->U32, G->C32, da, s)
-         : launch_dslash<float, 1, false>(a, b, G->U32, G->C32, da, s);
-  }
+  if (dp)
+    launch_dslash<double, 1, 1>(a, b, G->U64, G->C64, da, dag1, s);
+  else
+    launch_dslash<float, 1, 1>(a, b, G->U32, G->C32, da, dag1, s);
   const Spinor* res = &b;
   if (op == MGLMA_OP_DDAGD) {  // second pass D^dag back into a
     if (dp)
-      launch_dslash<double, 1, true>(b, a, G->U64, G->C64, da, s);
+      launch_dslash<double, 1, 1>(b, a, G->U64, G->C64, da, true, s);
     else
-      launch_dslash<float, 1, true>(b, a, G->U32, G->C32, da, s);
+      launch_dslash<float, 1, 1>(b, a, G->U32, G->C32, da, true, s);
     res = &a;
   }
   if (dp)

@@ -106,6 +106,7 @@ struct mglma_ctx_s {
   // external event-record nodes listed here (resolved after each replay)
   std::vector<Pending>* capture_events = nullptr;
   std::vector<cudaEvent_t> event_cache;
+  bool coarse_level = false;  // see CoarseLevelScope
   mglma::KernelStat stats[16];
 };
 
@@ -136,6 +137,16 @@ inline int tuned(const mglma_ctx_s* ctx, int kernel, int nrhs, int dflt) {
   auto it = ctx->tune.find(kernel * 1024 + rhs_bucket(nrhs));
   return it == ctx->tune.end() ? dflt : it->second.first;
 }
+// FP32 stencil tile codes: NR RHS per thread (1, 2, 4) and RW RHS tiles per
+// CTA (1, 2, 4), code = NR + 16 (RW - 1); codes 1, 2, 4 are RW = 1
+inline int dslash32_tile_code(int nr, int rw) { return nr + 16 * (rw - 1); }
+inline int dslash32_tile_nr(int code) { return code & 15; }
+inline int dslash32_tile_rw(int code) { return 1 + (code >> 4); }
+inline bool dslash32_tile_valid(int code) {
+  const int nr = dslash32_tile_nr(code), rw = dslash32_tile_rw(code);
+  return code > 0 && (nr == 1 || nr == 2 || nr == 4) && (rw == 1 || rw == 2 || rw == 4) && (nr < 4 || rw == 1);
+}
+int dslash32_default_tile(int nrhs);
 
 // kernel-statistics kinds (timing is optional, see mglma_profile)
 enum KernelKind {
@@ -149,7 +160,17 @@ enum KernelKind {
   K_PACK = 7,
   K_SETUP = 8,
   K_SCALAR = 9,
-  K_NKINDS = 10
+  K_CBLAS = 10,    // BLAS-1 on coarse fields (inside a coarse solve)
+  K_CREDUCE = 11,  // reductions on coarse fields
+  K_NKINDS = 12
+};
+// While alive, BLAS and reduction launches on the context count as coarse-level
+// work in the per-kernel statistics.
+struct CoarseLevelScope {
+  mglma_ctx ctx;
+  bool prev;
+  explicit CoarseLevelScope(mglma_ctx c);
+  ~CoarseLevelScope();
 };
 const char* kernel_kind_name(int k);
 

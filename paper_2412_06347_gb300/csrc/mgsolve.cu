@@ -451,6 +451,7 @@ struct CoarseSolver {
   }
   // e1 = D1^-1 b1 to tol (or max_iter, rounded up to whole cycles)
   mglma_status solve(const Vec& b, Vec& x, double tol, int max_iter, long long* iters) {
+    CoarseLevelScope level(ctx);
     const int n = b.nrhs;
     if (!capacity()) {
       const int c = std::max(n, cap_hint);
@@ -698,6 +699,7 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
 // around FP32 coarse GCR.
 mglma_status coarse_solve64(mglma_ctx ctx, const mglma_coarse_s* C, const void* b1, void* X, int n, double tol,
                             cudaStream_t s) {
+  CoarseLevelScope level(ctx);
   const size_t per = (size_t)C->geo.V1 * C->n2;  // complex per RHS
   FreeList fl(ctx, s);
   Vec vb, vx, vr, vw, r32, e32;

@@ -1,5 +1,6 @@
-// Autotuner of the RHS tile widths: the stencil's RHS per thread (1, 2, 4)
-// and the tensor-core coarse kernel's RHS per tile (8, 16, 32) are timed with
+// Autotuner of the RHS tile widths: the stencil's tile shape (RHS per thread
+// 1, 2, 4 times RHS tiles per CTA 1, 2, 4) and the tensor-core coarse
+// kernel's RHS per tile (8, 16, 32) are timed with
 // CUDA events on the context stream for a given RHS count, and the fastest
 // is kept per (kernel, RHS bucket) in the context; the table can be saved to
 // and loaded from a text file keyed by GPU name.
@@ -70,14 +71,17 @@ mglma_status mglma_autotune(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, int nr
     if (st == MGLMA_OK) MG_CUDA(cudaMemsetAsync(a.p, 0, a.bytes(), s));
     double best = 1e30;
     int choice = 1;
-    for (int nr : {1, 2, 4}) {
-      if (st != MGLMA_OK || (nr > 1 && nr > nrhs)) break;
-      ctx->tune[TUNE_DSLASH32_NR * 1024 + bucket] = {nr, 0.0};
+    const int shapes[][2] = {{1, 1}, {2, 1}, {4, 1}, {1, 2}, {1, 4}, {2, 2}, {2, 4}};
+    for (const auto& sh : shapes) {
+      if (st != MGLMA_OK) break;
+      if (sh[0] * sh[1] > 1 && sh[0] * sh[1] > nrhs) continue;  // tiles mostly idle
+      const int code = dslash32_tile_code(sh[0], sh[1]);
+      ctx->tune[TUNE_DSLASH32_NR * 1024 + bucket] = {code, 0.0};
       double ms = 0;
       st = time_ms(ctx, s, 5, [&] { return dslash(ctx, G, a, b, false, false, s); }, &ms);
       if (st == MGLMA_OK && ms < best) {
         best = ms;
-        choice = nr;
+        choice = code;
       }
     }
     ctx->tune[TUNE_DSLASH32_NR * 1024 + bucket] = {choice, best};
@@ -123,6 +127,15 @@ mglma_status mglma_autotune_get(mglma_ctx ctx, int kernel, int nrhs, int* choice
   return MGLMA_OK;
 }
 
+mglma_status mglma_autotune_set(mglma_ctx ctx, int kernel, int nrhs, int choice) {
+  if (!ctx || nrhs < 1) return fail(MGLMA_ERR_INVALID, "autotune_set: bad arguments");
+  const bool ok = (kernel == TUNE_DSLASH32_NR && dslash32_tile_valid(choice)) ||
+                  (kernel == TUNE_COARSE_NT && (choice == 8 || choice == 16 || choice == 32));
+  if (!ok) return fail(MGLMA_ERR_INVALID, "autotune_set: unknown kernel or choice");
+  ctx->tune[kernel * 1024 + rhs_bucket(nrhs)] = {choice, 0.0};
+  return MGLMA_OK;
+}
+
 mglma_status mglma_autotune_save(mglma_ctx ctx, const char* path) {
   if (!ctx || !path) return fail(MGLMA_ERR_INVALID, "autotune_save: NULL argument");
   std::ofstream f(path);
@@ -146,7 +159,7 @@ mglma_status mglma_autotune_load(mglma_ctx ctx, const char* path) {
     int k, b, c;
     double ms;
     if (!(is >> g >> k >> b >> c >> ms) || g != gpu) continue;
-    const bool ok = (k == TUNE_DSLASH32_NR && (c == 1 || c == 2 || c == 4)) || 
+    const bool ok = (k == TUNE_DSLASH32_NR && dslash32_tile_valid(c)) ||
                     (k == TUNE_COARSE_NT && (c == 8 || c == 16 || c == 32));
     if (ok && b >= 1 && b <= 64) ctx->tune[k * 1024 + b] = {c, ms};
   }

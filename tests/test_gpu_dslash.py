@@ -82,6 +82,36 @@ def test_dirac_fp32_parity(m, ctx, L, nrhs):
     m.mglma_gauge_free(g)
 
 
+TILES = [(1, 1), (2, 1), (4, 1), (1, 2), (1, 4), (2, 2), (2, 4)]
+
+
+@pytest.mark.parametrize("nr,rw", TILES)
+def test_dirac_fp32_tile_shapes(m, ctx, nr, rw):
+    """Every FP32 tile shape (RHS per thread x RHS tiles per CTA) against the
+    oracle, with RHS counts that leave partial tiles and partial tile groups
+    and a volume (6x3x5x2 = 180) that is not a multiple of any CTA's sites."""
+    kappa, csw = 0.125, 1.7
+    L = (6, 3, 5, 2)
+    U, g = load(m, ctx, L, 0.2, 1002, kappa, csw)
+    c = m.Context(0)
+    for nrhs in (1, 5, 11):
+        m.mglma_autotune_set(c, 0, nrhs, m.dslash32_tile_code(nr, rw))
+        psi = synthetic.random_spinors(L, nrhs, 60 + nrhs)
+        for op in (0, 1, 2, 3):
+            out = np.zeros_like(psi)
+            m.mglma_dirac_apply(c, g, op, nrhs, psi, out, m.MGLMA_FP32)
+            assert rel_per_rhs(out, oracle_op(U, psi, kappa, csw, op)).max() < 2e-6, (nrhs, op)
+    c.close()
+    m.mglma_gauge_free(g)
+
+
+def test_autotune_set_rejects_unknown(m, ctx):
+    with pytest.raises(m.MglmaError):
+        m.mglma_autotune_set(ctx, 0, 4, m.dslash32_tile_code(4, 2))
+    with pytest.raises(m.MglmaError):
+        m.mglma_autotune_set(ctx, 1, 4, 12)
+
+
 def test_periodic_time_bc_and_free_field(m, ctx):
     L = (4, 4, 4, 4)
     U = synthetic.free_links(L)
