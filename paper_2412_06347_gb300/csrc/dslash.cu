@@ -273,8 +273,14 @@ struct DslashArgs {
 // NR: thread t takes site t mod (128 / RW) of the CTA's block and RHS tile
 // t / (128 / RW), so with RW > 1 the warps of one CTA read the same links and
 // clover entries and all but the first find them in L1.
+// resident CTAs per SM the register allocation must allow (128 threads each)
+template <typename R, int NR, int RW>
+constexpr int dslash_min_ctas() {
+  return sizeof(R) == 8 ? 3 : (NR == 1 ? (RW == 1 ? 6 : 5) : (NR == 2 ? 4 : 3));
+}
+
 template <typename R, int NR, bool DAG, int RW>
-__global__ void __launch_bounds__(128) dslash_kernel(const void* __restrict__ in, void* __restrict__ out,
+__global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kernel(const void* __restrict__ in, void* __restrict__ out,
                                                      const void* __restrict__ U, const void* __restrict__ C,
                                                      DslashArgs a) {
   constexpr int SW = 128 / RW;  // sites per CTA
@@ -282,11 +288,19 @@ __global__ void __launch_bounds__(128) dslash_kernel(const void* __restrict__ in
   // RHS tile groups run fastest in launch order, so the CTAs that share a
   // block of sites are resident together and its links and clover come from L2
   const int ntile = (a.nrhs + NR - 1) / NR;
-  const int ngrp = (ntile + RW - 1) / RW;
-  const int64_t site = (int64_t)(blockIdx.x / ngrp) * SW + threadIdx.x % SW;
-  const int tile = (int)(blockIdx.x % ngrp) * RW + (int)threadIdx.x / SW;
-  if (site >= V || tile >= ntile) return;
-  const int r0 = tile * NR;
+  int64_t site;
+  int r0;
+  if constexpr (RW == 1) {
+    site = (int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x;
+    if (site >= V) return;
+    r0 = (blockIdx.x % ntile) * NR;
+  } else {
+    const int ngrp = (ntile + RW - 1) / RW;
+    const int tile = (int)(blockIdx.x % ngrp) * RW + (int)threadIdx.x / SW;
+    site = (int64_t)(blockIdx.x / ngrp) * SW + threadIdx.x % SW;
+    if (site >= V || tile >= ntile) return;
+    r0 = tile * NR;
+  }
   int x[4];
   site_coords(a.q, site, x);
   const R sF = DAG ? R(1) : R(-1);  // forward hop carries (1 + sF gamma)
