@@ -113,6 +113,18 @@ mglma_status mglma_profile_get(mglma_ctx ctx, const char* name, long long* launc
  *   relies on it; larger deviations give MGLMA_ERR_INVALID. */
 mglma_status mglma_gauge_load(mglma_ctx ctx, const mglma_lattice* lat, const double* links, int64_t t_begin,
                               int64_t t_count, double kappa, double csw, mglma_gauge* inout);
+/* Generates the synthetic gauge field of the benchmark configurations on the
+ * device and loads it as mglma_gauge_load would: link (x, mu) is
+ * P_SU3(exp(i eps H)) with H = sum_a h_a lambda_a / 2, h_a ~ N(0, 1) the
+ * Gaussians 8 n .. 8 n + 7 (n = 4 x + mu) of the SplitMix64 counter stream
+ * (seed, tag 1), Box-Muller pairs; exp by an order-18 Taylor series, then
+ * row Gram-Schmidt and row2 = conj(row0 x row1).  This is an input
+ * generator, not part of the paper's method: it reproduces the library's
+ * Python input generator to rounding (CUDA's log / sin / cos), so that
+ * lattices too large to generate on the host (96x48^3, 128x64^3) can be set
+ * up.  Works in time slabs of at most 512 MB; *out receives a new handle. */
+mglma_status mglma_gauge_random(mglma_ctx ctx, const mglma_lattice* lat, double eps, uint64_t seed, double kappa,
+                                double csw, mglma_gauge* out);
 void mglma_gauge_free(mglma_gauge g);
 /* Lattice extents and V of a gauge handle. */
 mglma_status mglma_gauge_info(mglma_gauge g, int L[4], int64_t* volume);

@@ -59,6 +59,8 @@ _sig("mglma_profile_get", C.c_int, _vp, C.c_char_p, C.POINTER(C.c_longlong), C.P
      C.POINTER(C.c_double), C.POINTER(C.c_double))
 _sig("mglma_gauge_load", C.c_int, _vp, C.POINTER(mglma_lattice), _vp, _i64, _i64, C.c_double, C.c_double,
      C.POINTER(_vp))
+_sig("mglma_gauge_random", C.c_int, _vp, C.POINTER(mglma_lattice), C.c_double, C.c_uint64, C.c_double, C.c_double,
+     C.POINTER(_vp))
 _sig("mglma_gauge_free", None, _vp)
 _sig("mglma_gauge_info", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(_i64))
 _sig("mglma_dirac_apply", C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp)
@@ -195,6 +197,15 @@ def mglma_gauge_load(ctx, L, links, kappa, csw, t_bc=-1, t_begin=0, t_count=None
         t_count = int(L[0]) - t_begin
     _check(lib.mglma_gauge_load(_h(ctx), C.byref(lat), ptr(links), int(t_begin), int(t_count), float(kappa),
                                 float(csw), C.byref(h)))
+    return h.value
+
+
+def mglma_gauge_random(ctx, L, eps, seed, kappa, csw, t_bc=-1):
+    """Gauge field from the seeded link recipe, generated on the device."""
+    lat = mglma_lattice((C.c_int * 4)(*[int(v) for v in L]), int(t_bc))
+    h = _vp()
+    _check(lib.mglma_gauge_random(_h(ctx), C.byref(lat), float(eps), int(seed), float(kappa), float(csw),
+                                  C.byref(h)))
     return h.value
 
 

@@ -112,6 +112,24 @@ def test_autotune_set_rejects_unknown(m, ctx):
         m.mglma_autotune_set(ctx, 1, 4, 12)
 
 
+@pytest.mark.parametrize("L,eps,seed,t_bc", [((8, 8, 8, 8), 0.3, 1001, -1), ((6, 4, 2, 10), 0.15, 1004, 1)])
+def test_device_gauge_generator_matches_host(m, ctx, L, eps, seed, t_bc):
+    """mglma_gauge_random draws the links of synthetic.gauge_links on the
+    device; D built from them equals D from the host links to rounding."""
+    kappa, csw = 0.1266, 1.9
+    U = synthetic.gauge_links(L, eps, seed)
+    g_host = m.mglma_gauge_load(ctx, L, U, kappa, csw, t_bc=t_bc)
+    g_dev = m.mglma_gauge_random(ctx, L, eps, seed, kappa, csw, t_bc=t_bc)
+    psi = synthetic.random_spinors(L, 2, 9)
+    a, b = np.zeros_like(psi), np.zeros_like(psi)
+    m.mglma_dirac_apply(ctx, g_host, 0, 2, psi, a, m.MGLMA_FP64)
+    m.mglma_dirac_apply(ctx, g_dev, 0, 2, psi, b, m.MGLMA_FP64)
+    assert rel_per_rhs(b, a).max() < 1e-13
+    assert rel_per_rhs(a, oracle_op(U, psi, kappa, csw, 0, t_bc=float(t_bc))).max() < 1e-12
+    m.mglma_gauge_free(g_host)
+    m.mglma_gauge_free(g_dev)
+
+
 def test_periodic_time_bc_and_free_field(m, ctx):
     L = (4, 4, 4, 4)
     U = synthetic.free_links(L)
