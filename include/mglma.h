@@ -184,6 +184,15 @@ mglma_status mglma_subspace_build(mglma_ctx ctx, mglma_gauge g, const int block[
  * low right singular vectors of D -- the low modes of Q (App. chirality) that
  * the paper's basis is built from.  mglma_subspace_build is this call with
  * n_cg = 0. */
+/* lean_group > 0 selects the memory-lean set-up for large lattices: the
+ * test vectors are stored in FP32 and relaxed lean_group at a time (MR and
+ * CG in FP32, so cg_prec is ignored), the per-(block, chirality)
+ * orthonormalisation runs in FP64 on chunks of blocks, and only the store
+ * copy (MGLMA_FP32 or MGLMA_FP16) is kept -- no FP64 basis.  Peak device
+ * memory is about (nv x 96 + lean_group x 480) bytes per site instead of
+ * about nv x 670.  FP64 R0 / T0 and the coarse build then read the stored
+ * copy in FP64 arithmetic; the propagator pieces (which need the FP64 basis)
+ * are refused.  0 = the standard FP64 set-up. */
 typedef struct {
   int block[4];
   int nv;
@@ -192,6 +201,7 @@ typedef struct {
   int cg_prec;
   uint64_t seed;
   int store;
+  int lean_group;
 } mglma_subspace_params;
 mglma_status mglma_subspace_create(mglma_ctx ctx, mglma_gauge g, const mglma_subspace_params* params,
                                    mglma_subspace* out);
@@ -202,7 +212,8 @@ mglma_status mglma_subspace_load(mglma_ctx ctx, mglma_gauge g, const int block[4
 void mglma_subspace_free(mglma_subspace s);
 mglma_status mglma_subspace_info(mglma_subspace s, int* nv, int Lb[4], int64_t* coarse_volume);
 /* Exports the FP64 basis as complex128 [V1][2][nv][|B|][4][3] (spins of the
- * other chirality are zero); sites of a block in site-in-block order. */
+ * other chirality are zero); sites of a block in site-in-block order.  A lean
+ * subspace exports its stored FP32 / FP16 copy (scale applied). */
 mglma_status mglma_subspace_export(mglma_subspace s, double* phi);
 /* R0 (Eq. res_mg): out[rhs][y][alpha nv + c] = sum_{x in B_y} phi^dag psi(x).
  * in: nrhs canonical spinors; out: nrhs canonical coarse fields. */
@@ -216,10 +227,16 @@ mglma_status mglma_prolong(mglma_ctx ctx, mglma_subspace s, int nrhs, const doub
 /* Builds D1 = R0 D T0 in FP64 as the nine-slot stencil of dense
  * (2nv x 2nv) blocks; store selects the copy used by the solvers' coarse
  * applications: MGLMA_BF16 (FP32 accumulation), MGLMA_FP32 or MGLMA_FP64.
- * The FP64 operator is always kept (export, FP64 coarse residuals). */
+ * The FP64 operator is kept (export, FP64 coarse residuals) until
+ * mglma_coarse_release_fp64.  With a lean subspace the operator is R0 D T0
+ * of the stored FP32 / FP16 basis, computed in FP64 arithmetic. */
 mglma_status mglma_coarse_build(mglma_ctx ctx, mglma_gauge g, mglma_subspace s, mglma_prec store,
                                 mglma_coarse* out);
 void mglma_coarse_free(mglma_coarse c);
+/* Frees the FP64 copy of D1 when a low-precision copy exists (store BF16 or
+ * FP32), e.g. to keep large lattices resident for serving; FP64 coarse
+ * applications, export and the propagator pieces are refused afterwards. */
+mglma_status mglma_coarse_release_fp64(mglma_coarse c);
 mglma_status mglma_coarse_info(mglma_coarse c, int* nv, int Lb[4], int64_t* coarse_volume);
 /* Exports the FP64 stencil as complex128 [9][V1][2nv][2nv]. */
 mglma_status mglma_coarse_export(mglma_coarse c, double* dhat);

@@ -70,7 +70,7 @@ _sig("mglma_subspace_build", C.c_int, _vp, _vp, C.POINTER(C.c_int), C.c_int, C.c
      C.POINTER(_vp))
 class mglma_subspace_params(C.Structure):
     _fields_ = [("block", C.c_int * 4), ("nv", C.c_int), ("n_smooth", C.c_int), ("n_cg", C.c_int),
-                ("cg_prec", C.c_int), ("seed", C.c_uint64), ("store", C.c_int)]
+                ("cg_prec", C.c_int), ("seed", C.c_uint64), ("store", C.c_int), ("lean_group", C.c_int)]
 
 
 _sig("mglma_subspace_create", C.c_int, _vp, _vp, C.POINTER(mglma_subspace_params), C.POINTER(_vp))
@@ -82,6 +82,7 @@ _sig("mglma_restrict", C.c_int, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp)
 _sig("mglma_prolong", C.c_int, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp)
 _sig("mglma_coarse_build", C.c_int, _vp, _vp, _vp, C.c_int, C.POINTER(_vp))
 _sig("mglma_coarse_free", None, _vp)
+_sig("mglma_coarse_release_fp64", C.c_int, _vp)
 _sig("mglma_coarse_info", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_i64))
 _sig("mglma_coarse_export", C.c_int, _vp, _vp)
 _sig("mglma_coarse_apply", C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp)
@@ -248,8 +249,10 @@ def mglma_subspace_build(ctx, g, block, nv, n_smooth, seed, store=MGLMA_FP32):
     return h.value
 
 
-def mglma_subspace_create(ctx, g, block, nv, n_smooth, seed, store=MGLMA_FP32, n_cg=0, cg_prec=MGLMA_FP64):
-    p = mglma_subspace_params(_block(block), int(nv), int(n_smooth), int(n_cg), int(cg_prec), int(seed), int(store))
+def mglma_subspace_create(ctx, g, block, nv, n_smooth, seed, store=MGLMA_FP32, n_cg=0, cg_prec=MGLMA_FP64,
+                          lean_group=0):
+    p = mglma_subspace_params(_block(block), int(nv), int(n_smooth), int(n_cg), int(cg_prec), int(seed), int(store),
+                              int(lean_group))
     h = _vp()
     _check(lib.mglma_subspace_create(_h(ctx), g, C.byref(p), C.byref(h)))
     return h.value
@@ -301,6 +304,10 @@ def mglma_coarse_info(c):
     V1 = _i64()
     _check(lib.mglma_coarse_info(c, C.byref(nv), Lb, C.byref(V1)))
     return nv.value, tuple(Lb), V1.value
+
+
+def mglma_coarse_release_fp64(c):
+    _check(lib.mglma_coarse_release_fp64(c))
 
 
 def mglma_coarse_export(c, dhat):

@@ -249,7 +249,7 @@ mglma_status mglma_coarse_build(mglma_ctx ctx, mglma_gauge G, mglma_subspace S, 
                                 mglma_coarse* out) {
   if (!ctx || !G || !S || !out) return fail(MGLMA_ERR_INVALID, "coarse_build: NULL argument");
   if (S->gauge != G) return fail(MGLMA_ERR_INVALID, "coarse_build: subspace belongs to another gauge field");
-  if (!S->phi64) return fail(MGLMA_ERR_INVALID, "coarse_build: the subspace's FP64 basis was released");
+  if (!S->phi64 && !S->lean) return fail(MGLMA_ERR_INVALID, "coarse_build: the subspace's FP64 basis was released");
   if (store != MGLMA_FP64 && store != MGLMA_FP32 && store != MGLMA_BF16)
     return fail(MGLMA_ERR_INVALID, "coarse_build: store must be FP64, FP32 or BF16");
   MG_CUDA(cudaSetDevice(ctx->device));
@@ -326,6 +326,17 @@ mglma_status mglma_coarse_build(mglma_ctx ctx, mglma_gauge G, mglma_subspace S, 
     return st;
   }
   *out = Cc;
+  return MGLMA_OK;
+}
+
+mglma_status mglma_coarse_release_fp64(mglma_coarse Cc) {
+  if (!Cc) return fail(MGLMA_ERR_INVALID, "coarse_release_fp64: NULL handle");
+  if (!Cc->A32 && !Cc->A16 && !Cc->Aimg)
+    return fail(MGLMA_ERR_INVALID, "coarse_release_fp64: the FP64 operator is the only copy");
+  if (Cc->ctx) MG_CUDA(cudaSetDevice(Cc->ctx->device));
+  MG_CUDA(cudaDeviceSynchronize());
+  cudaFree(Cc->A64);
+  Cc->A64 = nullptr;
   return MGLMA_OK;
 }
 

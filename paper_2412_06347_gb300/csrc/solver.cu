@@ -264,6 +264,7 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
     return fail(MGLMA_ERR_INVALID, "solve_batch: the MG method and the pieces need a coarse operator");
   if (C && C->sub->gauge != G) return fail(MGLMA_ERR_INVALID, "solve_batch: coarse operator of another gauge field");
   if (x_coarse && !C->sub->phi64) return fail(MGLMA_ERR_INVALID, "solve_batch: pieces need the FP64 basis");
+  if (x_coarse && !C->A64) return fail(MGLMA_ERR_INVALID, "solve_batch: pieces need the FP64 coarse operator");
   if (!(prm->tol > 0) || prm->max_iter < 1 || prm->check_every < 1 ||
       (prm->method == MGLMA_SOLVER_MG && (prm->gcr_m < 1 || prm->gcr_m > 64 || prm->nu < 0 ||
                                           !(prm->inner_tol > 0) || !(prm->coarse_tol > 0) ||

@@ -93,6 +93,28 @@ __global__ void random_starts_kernel(double2* __restrict__ out, int64_t V, int n
   }
 }
 
+// The same Gaussians rounded to FP32 in the FP32 internal layout, for the
+// vectors c0 .. c0 + ng - 1 (lean set-up).
+__global__ void random_starts32_kernel(float4* __restrict__ out, int64_t V, int ng, int c0, uint64_t key) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (s >= V || c >= ng) return;
+  for (int k2 = 0; k2 < 6; ++k2) {
+    float v[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint64_t n = ((uint64_t)(c0 + c) * V + s) * 12 + 2 * k2 + h;
+      const double u1 = u53(mix64(key + 2 * n)), u2 = u53(mix64(key + 2 * n + 1));
+      const double r = sqrt(-2.0 * log(u1));
+      double sn, cs;
+      sincospi(2.0 * u2, &sn, &cs);
+      v[2 * h] = (float)(r * cs);
+      v[2 * h + 1] = (float)(r * sn);
+    }
+    out[((size_t)c * 6 + k2) * V + s] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
 // ------------------------------------------------------------ basis IO
 template <typename B>
 struct BIO;
@@ -314,6 +336,39 @@ __global__ void split_kernel(const double2* __restrict__ vecs, int nv, BlockGeo 
     for (int q = 0; q < 6; ++q)
       phi[(((size_t)y * 2 * nv + j) * 6 + q) * g.nB + k] = vecs[((size_t)c * 12 + 6 * alpha + q) * g.V + site];
   }
+}
+
+// The same from FP32 vectors ([c][6 float4 chunks][V]) for blocks y0 + blockIdx.x,
+// written to a chunk buffer that starts at block y0.
+__global__ void split32_kernel(const float4* __restrict__ vecs, int nv, BlockGeo g, int64_t y0,
+                               double2* __restrict__ phi) {
+  const int64_t yl = blockIdx.x;
+  const int j = blockIdx.y;
+  const int alpha = j / nv, c = j % nv;
+  for (int k = threadIdx.x; k < g.nB; k += blockDim.x) {
+    const int64_t site = block_site(g, y0 + yl, k);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const int cidx = 6 * alpha + q;  // complex component (spin, colour)
+      const float4 v = vecs[((size_t)c * 6 + cidx / 2) * g.V + site];
+      phi[(((size_t)yl * 2 * nv + j) * 6 + q) * g.nB + k] =
+          (cidx & 1) ? make_double2(v.z, v.w) : make_double2(v.x, v.y);
+    }
+  }
+}
+
+// stored FP32 / FP16 basis -> FP64 layout (export of a lean subspace)
+template <typename B>
+__global__ void basis_widen_kernel(const void* __restrict__ src, const float* __restrict__ scale,
+                                   double2* __restrict__ p64, size_t nyj, int nB) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over nyj * nB
+  if (i >= nyj * nB) return;
+  const size_t yj = i / nB;
+  const int k = (int)(i % nB);
+  Cx<double> o[6];
+  BIO<B>::template load<double>(src, scale, yj, nB, k, o);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) p64[(yj * 6 + q) * nB + k] = make_double2(o[q].re, o[q].im);
 }
 
 // ------------------------------------------------------------ CholeskyQR2 per (block, chirality)
@@ -548,8 +603,10 @@ mglma_status restrict_fine(mglma_ctx ctx, const mglma_subspace_s* S, const Spino
                            cudaStream_t s) {
   ProfScope ps(ctx, K_RESTRICT, s, transfer_bytes(S, in.prec, in.nrhs), 8.0 * S->geo.V * 12.0 * S->nv * in.nrhs);
   if (in.prec == MGLMA_FP64) {
-    if (!S->phi64) return fail(MGLMA_ERR_INVALID, "restrict: FP64 needs a subspace stored in FP64");
-    return launch_restrict<double, double, 2>(S, in.p, in.nrhs, S->phi64, out_coarse, s);
+    if (S->phi64) return launch_restrict<double, double, 2>(S, in.p, in.nrhs, S->phi64, out_coarse, s);
+    if (!S->lean) return fail(MGLMA_ERR_INVALID, "restrict: FP64 needs a subspace stored in FP64");
+    if (S->phi16) return launch_restrict<double, __half, 2>(S, in.p, in.nrhs, S->phi16, out_coarse, s);
+    return launch_restrict<double, float, 2>(S, in.p, in.nrhs, S->phi32, out_coarse, s);
   }
   if (S->phi16) return launch_restrict<float, __half, 4>(S, in.p, in.nrhs, S->phi16, out_coarse, s);
   return launch_restrict<float, float, 4>(S, in.p, in.nrhs, S->phi32, out_coarse, s);
@@ -559,8 +616,10 @@ mglma_status prolong_coarse(mglma_ctx ctx, const mglma_subspace_s* S, const void
                             bool accumulate, cudaStream_t s) {
   ProfScope ps(ctx, K_PROLONG, s, transfer_bytes(S, out.prec, out.nrhs), 8.0 * S->geo.V * 12.0 * S->nv * out.nrhs);
   if (out.prec == MGLMA_FP64) {
-    if (!S->phi64) return fail(MGLMA_ERR_INVALID, "prolong: FP64 needs a subspace stored in FP64");
-    return launch_prolong<double, double, 2>(S, in_coarse, out.nrhs, S->phi64, out.p, accumulate, s);
+    if (S->phi64) return launch_prolong<double, double, 2>(S, in_coarse, out.nrhs, S->phi64, out.p, accumulate, s);
+    if (!S->lean) return fail(MGLMA_ERR_INVALID, "prolong: FP64 needs a subspace stored in FP64");
+    if (S->phi16) return launch_prolong<double, __half, 2>(S, in_coarse, out.nrhs, S->phi16, out.p, accumulate, s);
+    return launch_prolong<double, float, 2>(S, in_coarse, out.nrhs, S->phi32, out.p, accumulate, s);
   }
   if (S->phi16) return launch_prolong<float, __half, 4>(S, in_coarse, out.nrhs, S->phi16, out.p, accumulate, s);
   return launch_prolong<float, float, 4>(S, in_coarse, out.nrhs, S->phi32, out.p, accumulate, s);
@@ -610,13 +669,85 @@ static mglma_status finish_basis(mglma_ctx ctx, mglma_subspace_s* S, const Spino
   return MGLMA_OK;
 }
 
-mglma_status mr_smooth64(mglma_ctx ctx, const mglma_gauge_s* G, Spinor& v, int n_smooth, cudaStream_t s) {
+mglma_status cg_relax(mglma_ctx ctx, const mglma_gauge_s* G, Spinor& v, int n_cg, cudaStream_t s);
+
+// Lean variant: test vectors in FP32; CholeskyQR2 in FP64 on chunks of
+// blocks; only the store copy (FP32 or FP16 + scales) is kept.
+static mglma_status finish_basis_lean(mglma_ctx ctx, mglma_subspace_s* S, const Spinor& vecs, cudaStream_t s) {
+  const BlockGeo g = S->geo;
+  const int nv = S->nv;
+  const size_t nyj = (size_t)g.V1 * 2 * nv;
+  const size_t n3 = nyj * 3 * g.nB;
+  const bool half = S->store == MGLMA_FP16;
+  if (half) {
+    MG_CUDA(cudaMalloc(&S->scale16, nyj * sizeof(float)));
+    MG_CUDA(cudaMalloc(&S->phi16, n3 * sizeof(uint2)));
+  } else {
+    MG_CUDA(cudaMalloc(&S->phi32, n3 * sizeof(float4)));
+  }
+  // chunks of blocks whose FP64 copy takes at most 1 GiB
+  const size_t per_block = (size_t)2 * nv * 6 * g.nB * sizeof(double2);
+  const int64_t cb = std::max<int64_t>(1, std::min<int64_t>(g.V1, ((size_t)1 << 30) / per_block));
+  FreeList fl(ctx, s);
+  double2* p64 = nullptr;
+  MG_CHECK(dalloc(ctx, (void**)&p64, (size_t)cb * per_block, s));
+  fl.add(p64);
+  int* flag = nullptr;
+  MG_CHECK(dalloc(ctx, (void**)&flag, sizeof(int), s));
+  fl.add(flag);
+  MG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  const int smem = (2 * nv * nv + GS_TR * nv) * (int)sizeof(double2);
+  cudaFuncSetAttribute(cholqr2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  for (int64_t y0 = 0; y0 < g.V1; y0 += cb) {
+    const int64_t nyc = std::min<int64_t>(cb, g.V1 - y0);
+    ProfScope ps(ctx, K_SETUP, s);
+    split32_kernel<<<dim3((unsigned)nyc, 2 * nv, 1), 128, 0, s>>>((const float4*)vecs.p, nv, g, y0, p64);
+    cholqr2_kernel<<<dim3((unsigned)nyc, 2, 1), GS_THREADS, smem, s>>>(p64, nv, g, 1e-6, flag);
+    const size_t cyj = (size_t)nyc * 2 * nv, c3 = cyj * 3 * g.nB, off = (size_t)y0 * 2 * nv;
+    if (half) {
+      basis_scale_kernel<<<(unsigned)cyj, 128, 0, s>>>(p64, S->scale16 + off, g.nB);
+      basis_to16_kernel<<<(unsigned)((c3 + 255) / 256), 256, 0, s>>>(p64, S->scale16 + off,
+                                                                     S->phi16 + off * 3 * g.nB, cyj, g.nB);
+    } else {
+      basis_to32_kernel<<<(unsigned)((c3 + 255) / 256), 256, 0, s>>>(p64, S->phi32 + off * 3 * g.nB, cyj, g.nB);
+    }
+    MG_LAUNCH_CHECK();
+  }
+  int hflag = 0;
+  MG_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MG_CUDA(cudaStreamSynchronize(s));
+  if (hflag) return fail(MGLMA_ERR_RANK, "subspace: a block basis vector is linearly dependent on earlier ones");
+  return MGLMA_OK;
+}
+
+// Lean set-up: FP32 test vectors relaxed `group` at a time in place.
+static mglma_status build_lean(mglma_ctx ctx, const mglma_gauge_s* G, mglma_subspace_s* S,
+                               const mglma_subspace_params* prm, uint64_t key, cudaStream_t s) {
+  const int nv = S->nv, grp = prm->lean_group;
+  Spinor all;
+  FreeList fl(ctx, s);
+  MG_CHECK(alloc_spinor(ctx, all, MGLMA_FP32, nv, G->g.V, s));
+  fl.add(all.p);
+  for (int c0 = 0; c0 < nv; c0 += grp) {
+    Spinor v = all;
+    v.nrhs = std::min(grp, nv - c0);
+    v.p = static_cast<float*>(all.p) + (size_t)c0 * all.rhs_reals();
+    random_starts32_kernel<<<dim3((unsigned)((G->g.V + 127) / 128), v.nrhs, 1), 128, 0, s>>>(
+        (float4*)v.p, G->g.V, v.nrhs, c0, key);
+    MG_LAUNCH_CHECK();
+    MG_CHECK(mr_smooth(ctx, G, v, prm->n_smooth, s));
+    MG_CHECK(cg_relax(ctx, G, v, prm->n_cg, s));
+  }
+  return finish_basis_lean(ctx, S, all, s);
+}
+
+mglma_status mr_smooth(mglma_ctx ctx, const mglma_gauge_s* G, Spinor& v, int n_smooth, cudaStream_t s) {
   const int n = v.nrhs;
   FreeList fr(ctx, s);
   Spinor r, w;
-  MG_CHECK(alloc_spinor(ctx, r, MGLMA_FP64, n, v.V, s));
+  MG_CHECK(alloc_spinor(ctx, r, v.prec, n, v.V, s));
   fr.add(r.p);
-  MG_CHECK(alloc_spinor(ctx, w, MGLMA_FP64, n, v.V, s));
+  MG_CHECK(alloc_spinor(ctx, w, v.prec, n, v.V, s));
   fr.add(w.p);
   Scalars sc;
   MG_CHECK(sc.alloc(ctx, n, 1, 1, s));
@@ -708,6 +839,7 @@ mglma_status mglma_subspace_build(mglma_ctx ctx, mglma_gauge G, const int block[
   p.cg_prec = MGLMA_FP64;
   p.seed = seed;
   p.store = store;
+  p.lean_group = 0;
   return mglma_subspace_create(ctx, G, &p, out);
 }
 
@@ -726,24 +858,38 @@ mglma_status mglma_subspace_create(mglma_ctx ctx, mglma_gauge G, const mglma_sub
   }
   MG_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = ctx->stream;
+  const uint64_t key = [&] {
+    // key = mix64(mix64(seed) ^ tag), tag 3 = start vectors
+    auto h = [](uint64_t z) {
+      z += 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      return z ^ (z >> 31);
+    };
+    return h(h(seed) ^ 3ull);
+  }();
+  if (prm->lean_group != 0) {
+    if (prm->lean_group < 0 || (store != MGLMA_FP32 && store != MGLMA_FP16)) {
+      delete S;
+      return fail(MGLMA_ERR_INVALID, "subspace: the lean set-up needs lean_group > 0 and store FP32 or FP16");
+    }
+    S->lean = true;
+    mglma_status st = build_lean(ctx, G, S, prm, key, s);
+    if (st != MGLMA_OK) {
+      mglma_subspace_free(S);
+      return st;
+    }
+    *out = S;
+    return MGLMA_OK;
+  }
   Spinor v;
   mglma_status st = alloc_spinor(ctx, v, MGLMA_FP64, nv, G->g.V, s);
   if (st == MGLMA_OK) {
-    const uint64_t key = [&] {
-      // key = mix64(mix64(seed) ^ tag), tag 3 = start vectors
-      auto h = [](uint64_t z) {
-        z += 0x9E3779B97F4A7C15ull;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        return z ^ (z >> 31);
-      };
-      return h(h(seed) ^ 3ull);
-    }();
     random_starts_kernel<<<dim3((unsigned)((G->g.V + 127) / 128), nv, 1), 128, 0, s>>>((double2*)v.p, G->g.V, nv,
                                                                                        key);
     if (cudaGetLastError() != cudaSuccess) st = fail(MGLMA_ERR_CUDA, "random starts launch failed");
   }
-  if (st == MGLMA_OK) st = mr_smooth64(ctx, G, v, n_smooth, s);
+  if (st == MGLMA_OK) st = mr_smooth(ctx, G, v, n_smooth, s);
   if (st == MGLMA_OK && prm->n_cg > 0) {
     if (prm->cg_prec == MGLMA_FP64) {
       st = cg_relax(ctx, G, v, prm->n_cg, s);
@@ -813,7 +959,8 @@ mglma_status mglma_subspace_info(mglma_subspace S, int* nv, int Lb[4], int64_t* 
 
 mglma_status mglma_subspace_export(mglma_subspace S, double* phi) {
   if (!S || !phi) return fail(MGLMA_ERR_INVALID, "subspace_export: NULL argument");
-  if (!S->phi64) return fail(MGLMA_ERR_INVALID, "subspace_export: FP64 basis released (store FP64 keeps it)");
+  if (!S->phi64 && !S->lean)
+    return fail(MGLMA_ERR_INVALID, "subspace_export: FP64 basis released (store FP64 keeps it)");
   mglma_ctx ctx = S->ctx;
   MG_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = ctx->stream;
@@ -822,7 +969,19 @@ mglma_status mglma_subspace_export(mglma_subspace S, double* phi) {
   Staged o;
   MG_CHECK(stage_out_alloc(ctx, phi, bytes, s, o));
   const size_t n = nyj * S->geo.nB;
-  basis_export_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S->phi64, (double2*)o.dev, S->nv, S->geo.nB, nyj);
+  const double2* src = S->phi64;
+  FreeList fl(ctx, s);
+  if (!src) {  // lean: widen the stored copy
+    double2* w = nullptr;
+    MG_CHECK(dalloc(ctx, (void**)&w, n * 6 * sizeof(double2), s));
+    fl.add(w);
+    if (S->phi16)
+      basis_widen_kernel<__half><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S->phi16, S->scale16, w, nyj, S->geo.nB);
+    else
+      basis_widen_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S->phi32, nullptr, w, nyj, S->geo.nB);
+    src = w;
+  }
+  basis_export_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, (double2*)o.dev, S->nv, S->geo.nB, nyj);
   MG_LAUNCH_CHECK();
   MG_CHECK(stage_out_finish(phi, bytes, s, o));
   MG_CUDA(cudaStreamSynchronize(s));

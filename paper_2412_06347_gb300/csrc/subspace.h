@@ -24,6 +24,7 @@ struct mglma_subspace_s {
   float4* phi32 = nullptr;   // [V1][2Nv][3][nB]
   uint2* phi16 = nullptr;    // [V1][2Nv][3][nB], halves
   float* scale16 = nullptr;  // [V1][2Nv]
+  bool lean = false;         // built without an FP64 copy (phi64 stays NULL)
 };
 
 struct mglma_coarse_s {
@@ -45,7 +46,8 @@ mglma_status restrict_fine(mglma_ctx ctx, const mglma_subspace_s* S, const Spino
                            cudaStream_t s);
 mglma_status prolong_coarse(mglma_ctx ctx, const mglma_subspace_s* S, const void* in_coarse, Spinor& out,
                             bool accumulate, cudaStream_t s);
-mglma_status mr_smooth64(mglma_ctx ctx, const mglma_gauge_s* G, Spinor& v, int n_smooth, cudaStream_t s);
+// n_smooth MR steps on D v = 0 in the precision of v
+mglma_status mr_smooth(mglma_ctx ctx, const mglma_gauge_s* G, Spinor& v, int n_smooth, cudaStream_t s);
 
 // coarse fields: internal [rhs][V1][n2] float2 (FP32) or double2 (FP64)
 mglma_status coarse_to_canonical(mglma_ctx ctx, const void* c, int prec, size_t ncplx, double* canon,

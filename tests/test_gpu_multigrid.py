@@ -213,3 +213,57 @@ def test_coarse_tensor_core_full_size_properties(m, ctx):
     m.mglma_coarse_free(C)
     m.mglma_subspace_free(sub)
     m.mglma_gauge_free(g)
+
+
+@pytest.mark.parametrize("store,btol", [("fp32", 1e-4), ("fp16", 3e-3)])
+def test_lean_subspace_coarse_and_solve(m, ctx, store, btol):
+    """Memory-lean set-up (FP32 test vectors relaxed three at a time, FP64
+    orthonormalisation on chunks of blocks, no FP64 basis copy): the stored
+    basis is the oracle's recipe to the storage precision and orthonormal per
+    (block, chirality); FP64 R0 / T0 and the coarse operator built from it
+    equal the oracle's definitions applied to the same stored basis; after
+    the FP64 operator is released the MG solve still reaches 1e-10."""
+    from oracle import solvers as S
+    prec = {"fp32": m.MGLMA_FP32, "fp16": m.MGLMA_FP16}[store]
+    L, b, nv, kappa, csw = (8, 8, 8, 8), (2, 2, 2, 2), 8, 0.125, 1.7
+    U = synthetic.gauge_links(L, 0.2, 71)
+    g = m.mglma_gauge_load(ctx, L, U, kappa, csw)
+    sub = m.mglma_subspace_create(ctx, g, b, nv, 3, 72, prec, n_cg=4, lean_group=3)
+    ref = MG.subspace(U, synthetic.gaussian_start_vectors(L, nv, 72), kappa, csw, b, 3, n_cg=4)
+    phi = np.zeros_like(ref)
+    m.mglma_subspace_export(sub, phi)
+    assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < btol
+    V1, nB = phi.shape[0], phi.shape[3]
+    for y in (0, V1 // 2, V1 - 1):
+        for a in range(2):
+            Q = phi[y, a].reshape(nv, -1)
+            assert np.abs(Q.conj() @ Q.T - np.eye(nv)).max() < 4 * btol
+    # FP64 transfers on the stored basis
+    psi = synthetic.random_spinors(L, 2, 73)
+    out = np.zeros((2, V1, 2 * nv), dtype=np.complex128)
+    m.mglma_restrict(ctx, sub, 2, psi, out, m.MGLMA_FP64)
+    assert rel_per_rhs(out, MG.restrict(phi, psi, L, b)).max() < 1e-12
+    f = np.zeros_like(psi)
+    m.mglma_prolong(ctx, sub, 2, out, f, m.MGLMA_FP64)
+    assert rel_per_rhs(f, MG.prolong(phi, out, L, b)).max() < 1e-12
+    # coarse operator of the stored basis
+    C = m.mglma_coarse_build(ctx, g, sub, m.MGLMA_BF16)
+    Dh = np.zeros((9, V1, 2 * nv, 2 * nv), dtype=np.complex128)
+    m.mglma_coarse_export(C, Dh)
+    Dref = MG.coarse_operator(U, phi, kappa, csw, b)
+    assert np.linalg.norm(Dh - Dref) / np.linalg.norm(Dref) < 1e-12
+    m.mglma_coarse_release_fp64(C)
+    with pytest.raises(m.MglmaError):
+        m.mglma_coarse_export(C, Dh)
+    bsrc = synthetic.z2_noise(L, 3, 74)
+    x = np.zeros_like(bsrc)
+    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG)
+    _, st = m.mglma_solve_batch(ctx, g, C, prm, [3], bsrc, x)
+    assert all(s["converged"] for s in st)
+    A = D.clover_matrix(U, kappa, csw)
+    assert max(S.true_residual(U, xi, bi, kappa, csw, A=A) for xi, bi in zip(x, bsrc)) <= 1e-10
+    with pytest.raises(m.MglmaError):  # the pieces need the FP64 basis
+        m.mglma_solve_batch(ctx, g, C, prm, [3], bsrc, x, x_coarse=np.zeros((3, V1, 2 * nv), np.complex128))
+    m.mglma_coarse_free(C)
+    m.mglma_subspace_free(sub)
+    m.mglma_gauge_free(g)
