@@ -365,7 +365,8 @@ typedef struct {
   int nlattices;                        /* 1..8 */
   const mglma_serve_lattice* lattices;
   int max_slots;                        /* RHS in flight per lattice, upper bound */
-  double hbm_fraction;                  /* share of the HBM free at start the slots may take */
+  double hbm_fraction;                  /* share of the HBM free at start the slots may take;
+                                           lattices split it in proportion to their volume */
   mglma_solve_params params;            /* MGLMA_SOLVER_MG parameters (tol, gcr_m, nu, ...) */
 } mglma_serve_config;
 

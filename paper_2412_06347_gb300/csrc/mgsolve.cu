@@ -794,7 +794,7 @@ struct Engine {
   MgParams p;
   int cap = 0;
   int64_t V = 0;
-  Spinor b64, x64, r64, w64, r32, e32;
+  Spinor b64, x64, r64, r32, e32;
   double* dsc = nullptr;  // per slot: |r|^2 [cap], |r| [cap], 1/|r| [cap]
   double* stage = nullptr;  // one canonical spinor: host requests pass through it
   GcrWork gw;
@@ -803,9 +803,10 @@ struct Engine {
   FreeList* fl = nullptr;
   static constexpr int kInnerCap = 400;
 
-  // device bytes one slot needs (FP64 b, x, r, D x; FP32 r, e, FGCR
-  // directions and images, preconditioner scratch)
-  static size_t slot_bytes(int64_t V, int m) { return (size_t)V * (4 * 192 + (size_t)(5 + 2 * m) * 96); }
+  // device bytes one slot needs (FP64 b, x, r -- r also holds D x while the
+  // residual is formed; FP32 r, e, FGCR directions and images, preconditioner
+  // scratch)
+  static size_t slot_bytes(int64_t V, int m) { return (size_t)V * (3 * 192 + (size_t)(5 + 2 * m) * 96); }
   static size_t fixed_bytes(int64_t V) { return (size_t)V * 192; }
 
   ~Engine() { delete fl; }
@@ -820,7 +821,7 @@ struct Engine {
     cap = capacity;
     V = g->g.V;
     fl = new FreeList(ctx, s);
-    for (Spinor* f : {&b64, &x64, &r64, &w64}) {
+    for (Spinor* f : {&b64, &x64, &r64}) {
       MG_CHECK(alloc_spinor(ctx, *f, MGLMA_FP64, cap, V, s));
       fl->add(f->p);
     }
@@ -933,12 +934,11 @@ struct Engine {
       sl.inner += gw.m;
       if (act[i] && sl.inner < kInnerCap) continue;
       // FP64 update: x += |r| e ; r = b - D x
-      Spinor xi = ssub(x64, i, 1), wi = ssub(w64, i, 1), ri = ssub(r64, i, 1);
+      Spinor xi = ssub(x64, i, 1), ri = ssub(r64, i, 1);
       MG_CHECK(convert_spinor(ctx, ssub(e32, i, 1), xi, s, dsc + cap + i, true));
-      MG_CHECK(dslash(ctx, G, xi, wi, false, false, s));
+      MG_CHECK(dslash(ctx, G, xi, ri, false, false, s));  // r = D x, then r = b - r
       Vec rv = as_vec(ri);
-      MG_CHECK(copy_vec(ctx, as_vec(ssub(b64, i, 1)), rv, s));
-      MG_CHECK(axpby(ctx, nullptr, CM1, as_vec(wi), nullptr, C1, rv, s));
+      MG_CHECK(axpby(ctx, nullptr, C1, as_vec(ssub(b64, i, 1)), nullptr, CM1, rv, s));
       std::vector<double> h;
       MG_CHECK(norm2(ctx, rv, dsc + i, s));
       MG_CHECK(read_doubles(dsc + i, h, 1, s));
@@ -972,11 +972,15 @@ extern "C" mglma_status mglma_serve(mglma_ctx ctx, const mglma_serve_config* cfg
   cudaStream_t s = ctx->stream;
   const mglma_solve_params* prm = &cfg->params;
   const MgParams mp = mg_params(*prm);
-  // admission by free HBM: the slots of each lattice take an equal share of
-  // hbm_fraction of the memory free now
+  // admission by free HBM: the slots of each lattice take a share of
+  // hbm_fraction of the memory free now in proportion to its volume (a slot's
+  // size is proportional to the volume)
   size_t fr = 0, tot = 0;
   MG_CUDA(cudaMemGetInfo(&fr, &tot));
   const int NL = cfg->nlattices;
+  double vsum = 0;
+  for (int l = 0; l < NL; ++l)
+    if (cfg->lattices[l].gauge) vsum += (double)cfg->lattices[l].gauge->g.V;
   std::vector<std::unique_ptr<Engine>> eng(NL);
   mglma_serve_stats st;
   memset(&st, 0, sizeof(st));
@@ -985,7 +989,8 @@ extern "C" mglma_status mglma_serve(mglma_ctx ctx, const mglma_serve_config* cfg
     if (!L.gauge || !L.coarse || L.coarse->sub->gauge != L.gauge)
       return fail(MGLMA_ERR_INVALID, "serve: lattice entries need a gauge field and its coarse operator");
     const size_t per = Engine::slot_bytes(L.gauge->g.V, mp.gcr_m);
-    const double share = cfg->hbm_fraction * (double)fr / NL - (double)Engine::fixed_bytes(L.gauge->g.V);
+    const double share =
+        cfg->hbm_fraction * (double)fr * ((double)L.gauge->g.V / vsum) - (double)Engine::fixed_bytes(L.gauge->g.V);
     const int cap = share > 0 ? (int)std::min<size_t>((size_t)cfg->max_slots, (size_t)(share / per)) : 0;
     if (cap < 1) return fail(MGLMA_ERR_OOM, "serve: not enough free HBM for one slot of lattice " + std::to_string(l));
     eng[l].reset(new Engine());
