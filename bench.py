@@ -50,6 +50,13 @@ WORKLOADS = {
 }
 
 
+# The serving stream of the 2, 3 and 4 fm boxes: lattices generated on the
+# device, lean set-up (FP32 test vectors relaxed 4 at a time, FP16 basis, no
+# FP64 basis), BF16 coarse operator with its FP64 copy released.
+C5 = dict(shapes=[(128, 64, 64, 64), (96, 48, 48, 48), (64, 32, 32, 32)], eps=0.15, kappa=0.1266, csw=1.9,
+          block=(4, 4, 4, 4), nv=24, n_smooth=5, n_cg=60, lean_group=4, cfg=5)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -229,6 +236,102 @@ def run_serving(m, torch, ctx, g, C, w, args, dev, stream):
             "residual_max": resid}
 
 
+def run_c5(args):
+    """Serving stream over resident 64x32^3, 96x48^3 and 128x64^3 lattices
+    (eps 0.15, kappa 0.1266, csw 1.9, 4^4 blocks, Nv 24 FP16 basis, BF16
+    coarse operator): Poisson arrivals (20 requests/s, seed 4242), lattice
+    shape uniform over the three, RHS per request uniform in 1..max, Z2
+    sources generated on the device.  Reports p50/p99 latency, solves/s and
+    the sequential FP64 plain (CGNE) service time per shape, the latter from
+    timed iterations times the iteration count of a full CGNE solve on the
+    smallest shape (labelled extrapolated)."""
+    import torch
+    import paper_2412_06347_gb300 as m
+    import synthetic
+    w = C5
+    ctx = m.Context(0)
+    lats, setup = [], {}
+    for i, L in enumerate(w["shapes"]):  # largest first: its set-up has the most room
+        t0 = time.perf_counter()
+        g = m.mglma_gauge_random(ctx, L, w["eps"], 1000 + 10 * w["cfg"] + i, w["kappa"], w["csw"])
+        sub = m.mglma_subspace_create(ctx, g, w["block"], w["nv"], w["n_smooth"], 2000 + 10 * w["cfg"] + i,
+                                      m.MGLMA_FP16, n_cg=w["n_cg"], cg_prec=m.MGLMA_FP32, lean_group=w["lean_group"])
+        C = m.mglma_coarse_build(ctx, g, sub, m.MGLMA_BF16)
+        m.mglma_coarse_release_fp64(C)
+        torch.cuda.synchronize()
+        free, total = torch.cuda.mem_get_info()
+        setup["x".join(map(str, L))] = {"setup_s": round(time.perf_counter() - t0, 1),
+                                        "free_gb_after": round(free / 1e9, 1)}
+        lats.append(dict(L=L, V=int(np.prod(L)), g=g, sub=sub, C=C))
+    n = args.serve_requests
+    arrivals = synthetic.poisson_arrivals(n, 20.0, 4242)
+    shape = synthetic.uniform_ints(n, 0, len(lats) - 1, 4242, synthetic.TAG_FIELD)
+    sizes = synthetic.uniform_ints(n, 1, args.serve_max_rhs, 4242, synthetic.TAG_GROUPS)
+    reqs = []
+    for i in range(n):
+        lt = lats[int(shape[i])]
+        b = torch.empty((int(sizes[i]), lt["V"], 12), dtype=torch.complex128, device="cuda")
+        m.mglma_sources(ctx, lt["L"], m.MGLMA_SOURCE_Z2, int(sizes[i]), 3000 + w["cfg"], b, first=100 * i)
+        reqs.append(dict(lattice=int(shape[i]), b=b, x=torch.zeros_like(b), arrival=float(arrivals[i])))
+    torch.cuda.synchronize()
+    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG)
+    stats, res = m.mglma_serve(ctx, [(lt["g"], lt["C"]) for lt in lats], reqs, prm, max_slots=8,
+                               hbm_fraction=args.serve_hbm)
+    per_shape = {}
+    for i, r in enumerate(res):
+        key = "x".join(map(str, lats[reqs[i]["lattice"]]["L"]))
+        d = per_shape.setdefault(key, {"requests": 0, "rhs": 0, "latency_s": [], "residual_max": 0.0,
+                                       "iterations": []})
+        d["requests"] += 1
+        d["rhs"] += len(r["stats"])
+        d["latency_s"].append(round(r["latency"], 2))
+        d["residual_max"] = max([d["residual_max"]] + [s["residual"] for s in r["stats"]])
+        d["iterations"] += [s["iterations"] for s in r["stats"]]
+    for lt in reqs:
+        lt["b"] = lt["x"] = None
+    # sequential FP64 plain service time per shape: 20 timed CGNE iterations
+    # x the iteration count of a full CGNE solve on the smallest shape
+    small = lats[-1]
+    pc = m.mglma_solve_params_default(m.MGLMA_SOLVER_CGNE)
+    b1 = torch.empty((1, small["V"], 12), dtype=torch.complex128, device="cuda")
+    m.mglma_sources(ctx, small["L"], m.MGLMA_SOURCE_Z2, 1, 3000 + w["cfg"], b1)
+    x1 = torch.zeros_like(b1)
+    _, s1 = m.mglma_solve_batch(ctx, small["g"], None, pc, [1], b1, x1, raise_on_error=False)
+    full_iters = s1[0]["iterations"]
+    seq = {}
+    pc.max_iter = 20
+    for lt in lats:
+        b1 = torch.empty((1, lt["V"], 12), dtype=torch.complex128, device="cuda")
+        m.mglma_sources(ctx, lt["L"], m.MGLMA_SOURCE_Z2, 1, 3000 + w["cfg"], b1)
+        x1 = torch.zeros_like(b1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.mglma_solve_batch(ctx, lt["g"], None, pc, [1], b1, x1, raise_on_error=False)
+        torch.cuda.synchronize()
+        t_it = (time.perf_counter() - t0) / 20
+        seq["x".join(map(str, lt["L"]))] = {"s_per_iteration": round(t_it, 4),
+                                            "solve_s_extrapolated": round(t_it * full_iters, 2)}
+        del b1, x1
+    shares = [stats["slots"][i] for i in range(len(lats))]
+    mean_seq = float(np.mean([seq["x".join(map(str, lats[int(k)]["L"]))]["solve_s_extrapolated"] for k in shape]))
+    line = {"workload": "c5", "metric": METRIC, "unit": "solves/s", "value": round(stats["solves_per_s"], 4),
+            "p50_s": round(stats["p50_s"], 2), "p99_s": round(stats["p99_s"], 2), "wall_s": round(stats["wall_s"], 1),
+            "requests": stats["requests"], "rhs": stats["rhs"], "rejected": stats["rejected"],
+            "all_ok": all(r["status"] == 0 for r in res),
+            "offered": f"Poisson 20 requests/s (seed 4242), shape uniform, RHS uniform in 1..{args.serve_max_rhs}",
+            "slots": dict(zip(["x".join(map(str, lt["L"])) for lt in lats], shares)),
+            "slot_gb": [round(b / 1e9, 1) for b in stats["slot_bytes"][:len(lats)]], "per_shape": per_shape,
+            "setup": setup, "fp64_plain_sequential": seq, "cgne_iterations_smallest": full_iters,
+            "fp64_plain_solves_per_s_extrapolated": round(1.0 / mean_seq, 4) if mean_seq > 0 else None,
+            "dtype": "f32 inner / f64 outer / bf16 coarse / fp16 basis", "data": "synthetic (device-generated)"}
+    print(json.dumps(line), flush=True)
+    for lt in lats:
+        m.mglma_coarse_free(lt["C"])
+        m.mglma_subspace_free(lt["sub"])
+        m.mglma_gauge_free(lt["g"])
+    ctx.close()
+
+
 def micro_dslash(m, torch, ctx, g, V, nrhs, prec, reps, stream):
     """FP32/FP64 stencil on nrhs fields, launch-level timing from the
     library's CUDA events on the launching stream."""
@@ -317,7 +420,10 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mglma", choices=["mglma", "reference"])
-    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS) + ["c5"],
+                    help="c4: 64x32^3 solves (default); c2: 32x16^3 single-RHS; c5: serving stream over the "
+                         "64x32^3, 96x48^3 and 128x64^3 lattices")
+    ap.add_argument("--serve-hbm", type=float, default=0.9, help="c5: share of free HBM the serving slots take")
     ap.add_argument("--group", type=int, default=0, help="sources per step (default: the workload's)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--coarse-solver", default="minres", choices=sorted(COARSE_SOLVERS),
@@ -333,6 +439,13 @@ def main():
                     help="requests of the seeded Poisson stream served after the timed solves (0: skip)")
     ap.add_argument("--serve-max-rhs", type=int, default=4, help="RHS per request drawn uniformly in 1..this")
     args = ap.parse_args()
+    if args.workload == "c5":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "c5 has no oracle arm: the oracle cannot hold "
+                                                                  "128x64^3 fields within a bounded sample"}))
+            return
+        run_c5(args)
+        return
     w = dict(WORKLOADS[args.workload])
     if args.group:
         w["group"] = args.group

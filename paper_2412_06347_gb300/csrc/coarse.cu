@@ -276,32 +276,34 @@ mglma_status mglma_coarse_build(mglma_ctx ctx, mglma_gauge G, mglma_subspace S, 
   int NB = (int)std::min<size_t>((size_t)n2, std::max<size_t>(1, fr / 3 / per_col));
   NB = std::min(NB, 16);
   mglma_status st = MGLMA_OK;
-  FreeList fl(ctx, s);
-  double2 *U1 = nullptr, *C = nullptr;
-  Spinor Phi, H;
-  st = dalloc(ctx, (void**)&U1, (size_t)NB * g.V1 * n2 * sizeof(double2), s);
-  fl.add(U1);
-  if (st == MGLMA_OK) st = dalloc(ctx, (void**)&C, (size_t)NB * g.V1 * n2 * sizeof(double2), s);
-  fl.add(C);
-  if (st == MGLMA_OK) st = alloc_spinor(ctx, Phi, MGLMA_FP64, NB, g.V, s);
-  fl.add(Phi.p);
-  if (st == MGLMA_OK) st = alloc_spinor(ctx, H, MGLMA_FP64, NB, g.V, s);
-  fl.add(H.p);
-  for (int j0 = 0; st == MGLMA_OK && j0 < n2; j0 += NB) {
-    const int nb = std::min(NB, n2 - j0);
-    Phi.nrhs = H.nrhs = nb;
-    const size_t nu = (size_t)nb * g.V1 * n2;
-    {
-      ProfScope ps(ctx, K_SETUP, s);
-      unit_columns_kernel<<<(unsigned)((nu + 255) / 256), 256, 0, s>>>(U1, nb, g.V1, n2, j0);
-    }
-    st = prolong_coarse(ctx, S, U1, Phi, false, s);
-    for (int d = 0; st == MGLMA_OK && d < 9; ++d) {
-      st = dslash_slot64_batch(ctx, G, g.b, Phi, H, d, s);
-      if (st == MGLMA_OK) st = restrict_fine(ctx, S, H, C, s);
-      if (st == MGLMA_OK) {
+  {  // column work fields, returned to the pool at the end of this scope
+    FreeList fl(ctx, s);
+    double2 *U1 = nullptr, *C = nullptr;
+    Spinor Phi, H;
+    st = dalloc(ctx, (void**)&U1, (size_t)NB * g.V1 * n2 * sizeof(double2), s);
+    fl.add(U1);
+    if (st == MGLMA_OK) st = dalloc(ctx, (void**)&C, (size_t)NB * g.V1 * n2 * sizeof(double2), s);
+    fl.add(C);
+    if (st == MGLMA_OK) st = alloc_spinor(ctx, Phi, MGLMA_FP64, NB, g.V, s);
+    fl.add(Phi.p);
+    if (st == MGLMA_OK) st = alloc_spinor(ctx, H, MGLMA_FP64, NB, g.V, s);
+    fl.add(H.p);
+    for (int j0 = 0; st == MGLMA_OK && j0 < n2; j0 += NB) {
+      const int nb = std::min(NB, n2 - j0);
+      Phi.nrhs = H.nrhs = nb;
+      const size_t nu = (size_t)nb * g.V1 * n2;
+      {
         ProfScope ps(ctx, K_SETUP, s);
-        scatter_columns_kernel<<<(unsigned)((nu + 255) / 256), 256, 0, s>>>(C, Cc->A64, nb, g.V1, n2, j0, d);
+        unit_columns_kernel<<<(unsigned)((nu + 255) / 256), 256, 0, s>>>(U1, nb, g.V1, n2, j0);
+      }
+      st = prolong_coarse(ctx, S, U1, Phi, false, s);
+      for (int d = 0; st == MGLMA_OK && d < 9; ++d) {
+        st = dslash_slot64_batch(ctx, G, g.b, Phi, H, d, s);
+        if (st == MGLMA_OK) st = restrict_fine(ctx, S, H, C, s);
+        if (st == MGLMA_OK) {
+          ProfScope ps(ctx, K_SETUP, s);
+          scatter_columns_kernel<<<(unsigned)((nu + 255) / 256), 256, 0, s>>>(C, Cc->A64, nb, g.V1, n2, j0, d);
+        }
       }
     }
   }
@@ -320,6 +322,7 @@ mglma_status mglma_coarse_build(mglma_ctx ctx, mglma_gauge G, mglma_subspace S, 
     if (e != cudaSuccess) st = fail(MGLMA_ERR_OOM, "coarse_build: cannot allocate the low-precision operator");
   }
   cudaError_t e = cudaStreamSynchronize(s);
+  cudaMemPoolTrimTo(ctx->pool, 0);  // hand the build's work fields back to the device
   if (st == MGLMA_OK && e != cudaSuccess) st = fail(MGLMA_ERR_CUDA, cudaGetErrorString(e));
   if (st != MGLMA_OK) {
     mglma_coarse_free(Cc);

@@ -190,6 +190,8 @@ extern "C" mglma_status mglma_gauge_random(mglma_ctx ctx, const mglma_lattice* l
     st = mglma_gauge_load(ctx, lat, (const double*)buf, t0, tc, kappa, csw, &G);
   }
   dfree(ctx, buf, s);
+  cudaStreamSynchronize(s);
+  cudaMemPoolTrimTo(ctx->pool, 0);
   if (st != MGLMA_OK) {
     mglma_gauge_free(G);
     return st;

@@ -807,7 +807,15 @@ struct Engine {
   // residual is formed; FP32 r, e, FGCR directions and images, preconditioner
   // scratch)
   static size_t slot_bytes(int64_t V, int m) { return (size_t)V * (3 * 192 + (size_t)(5 + 2 * m) * 96); }
-  static size_t fixed_bytes(int64_t V) { return (size_t)V * 192; }
+  // one canonical spinor that host requests pass through, allocated on the
+  // first host request (device requests need none)
+  static size_t fixed_bytes(int64_t) { return 0; }
+  mglma_status ensure_stage() {
+    if (stage) return MGLMA_OK;
+    MG_CHECK(dalloc(ctx, (void**)&stage, (size_t)V * 24 * sizeof(double), s));
+    fl->add(stage);
+    return MGLMA_OK;
+  }
 
   ~Engine() { delete fl; }
 
@@ -831,8 +839,6 @@ struct Engine {
     }
     MG_CHECK(dalloc(ctx, (void**)&dsc, sizeof(double) * 3 * cap, s));
     fl->add(dsc);
-    MG_CHECK(dalloc(ctx, (void**)&stage, (size_t)V * 24 * sizeof(double), s));
-    fl->add(stage);
     MG_CHECK(gw.setup(ctx, s, as_vec(r32), cap, p.gcr_m));
     K.ctx = ctx;
     K.s = s;
@@ -976,6 +982,8 @@ extern "C" mglma_status mglma_serve(mglma_ctx ctx, const mglma_serve_config* cfg
   // hbm_fraction of the memory free now in proportion to its volume (a slot's
   // size is proportional to the volume)
   size_t fr = 0, tot = 0;
+  MG_CUDA(cudaStreamSynchronize(s));
+  MG_CUDA(cudaMemPoolTrimTo(ctx->pool, 0));  // cached set-up blocks count as free
   MG_CUDA(cudaMemGetInfo(&fr, &tot));
   const int NL = cfg->nlattices;
   double vsum = 0;
@@ -1057,6 +1065,10 @@ extern "C" mglma_status mglma_serve(mglma_ctx ctx, const mglma_serve_config* cfg
         if (R.next_rhs == 0) {
           R.bhost = !is_device_pointer(R.r.b);
           R.xhost = !is_device_pointer(R.r.x);
+          if (R.bhost || R.xhost) {
+            err = E.ensure_stage();
+            if (err != MGLMA_OK) break;
+          }
         }
         int slot;
         while (R.next_rhs < R.r.nrhs && (slot = E.first_free()) >= 0) {

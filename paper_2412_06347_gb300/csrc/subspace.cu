@@ -875,6 +875,8 @@ mglma_status mglma_subspace_create(mglma_ctx ctx, mglma_gauge G, const mglma_sub
     }
     S->lean = true;
     mglma_status st = build_lean(ctx, G, S, prm, key, s);
+    cudaStreamSynchronize(s);
+    cudaMemPoolTrimTo(ctx->pool, 0);  // hand the set-up's work fields back to the device
     if (st != MGLMA_OK) {
       mglma_subspace_free(S);
       return st;
@@ -904,6 +906,8 @@ mglma_status mglma_subspace_create(mglma_ctx ctx, mglma_gauge G, const mglma_sub
   }
   if (st == MGLMA_OK) st = finish_basis(ctx, S, v, s);
   dfree(ctx, v.p, s);
+  cudaStreamSynchronize(s);
+  cudaMemPoolTrimTo(ctx->pool, 0);  // hand the set-up's work fields back to the device
   if (st != MGLMA_OK) {
     mglma_subspace_free(S);
     return st;
