@@ -77,3 +77,42 @@ def test_serve_device_buffers_and_request_larger_than_slots(m, ctx):
     m.mglma_coarse_free(A["C"])
     m.mglma_subspace_free(A["sub"])
     m.mglma_gauge_free(A["g"])
+
+
+def test_serve_lean_device_generated_lattices(m, ctx):
+    """The serving set-up used for the large boxes, on small lattices: links
+    generated on the device, lean FP16 basis (test vectors relaxed in groups,
+    no FP64 copy), BF16 coarse operator with its FP64 copy released, slots
+    sized by volume share.  Every result reaches 1e-10 in the oracle's FP64
+    residual (computed with the host generator's links) and equals the solve
+    of the same sources alone."""
+    spec_l = [((8, 8, 8, 8), 0.15, 1051), ((8, 4, 4, 8), 0.2, 1052)]
+    kappa, csw = 0.125, 1.7
+    lats = []
+    for L, eps, seed in spec_l:
+        g = m.mglma_gauge_random(ctx, L, eps, seed, kappa, csw)
+        sub = m.mglma_subspace_create(ctx, g, (2, 2, 2, 2), 6, 5, seed + 1, m.MGLMA_FP16, n_cg=20,
+                                      cg_prec=m.MGLMA_FP32, lean_group=4)
+        C = m.mglma_coarse_build(ctx, g, sub, m.MGLMA_BF16)
+        m.mglma_coarse_release_fp64(C)
+        lats.append(dict(L=L, U=synthetic.gauge_links(L, eps, seed), g=g, sub=sub, C=C))
+    spec = [(0, 1, 0.0), (1, 2, 0.0), (0, 2, 0.01), (1, 1, 0.02), (0, 1, 0.03)]
+    reqs = []
+    for i, (l, n, t) in enumerate(spec):
+        b = synthetic.z2_noise(lats[l]["L"], n, 5200 + i)
+        reqs.append(dict(lattice=l, b=b, x=np.zeros_like(b), arrival=t))
+    prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG)
+    stats, res = m.mglma_serve(ctx, [(lt["g"], lt["C"]) for lt in lats], reqs, prm, max_slots=2, hbm_fraction=0.5)
+    assert stats["rejected"] == 0 and stats["rhs"] == sum(n for _, n, _ in spec)
+    for i, r in enumerate(reqs):
+        assert res[i]["status"] == 0
+        lt = lats[r["lattice"]]
+        xa = np.zeros_like(r["b"])
+        m.mglma_solve_batch(ctx, lt["g"], lt["C"], prm, [r["b"].shape[0]], r["b"], xa)
+        for j in range(r["b"].shape[0]):
+            assert np.linalg.norm(r["x"][j] - xa[j]) <= 1e-9 * np.linalg.norm(xa[j])
+            assert S.true_residual(lt["U"], r["x"][j], r["b"][j], kappa, csw) <= 1e-10
+    for lt in lats:
+        m.mglma_coarse_free(lt["C"])
+        m.mglma_subspace_free(lt["sub"])
+        m.mglma_gauge_free(lt["g"])
