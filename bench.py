@@ -367,9 +367,8 @@ def run_micro(args, w):
     L = tuple(int(v) for v in args.micro_lattice.split("x")) if args.micro_lattice else w["L"]
     V = int(np.prod(L))
     ctx = m.Context(0)
-    U = synthetic.gauge_links(L, w["eps"], 1000 + w["cfg"])
-    g = m.mglma_gauge_load(ctx, L, U, w["kappa"], w["csw"])
-    del U
+    # the seeded link recipe, generated on the device
+    g = m.mglma_gauge_random(ctx, L, w["eps"], 1000 + w["cfg"], w["kappa"], w["csw"])
     set_tile(m, ctx, args, args.nrhs)
     stream = torch.cuda.current_stream()
     reps = max(args.steps, 1)
@@ -476,9 +475,8 @@ def main():
     V = int(np.prod(L))
     G = w["group"]
     ctx = m.Context(local)
-    U = synthetic.gauge_links(L, w["eps"], 1000 + w["cfg"])
-    g = m.mglma_gauge_load(ctx, L, U, w["kappa"], w["csw"])
-    del U
+    # the seeded link recipe, generated on the device
+    g = m.mglma_gauge_random(ctx, L, w["eps"], 1000 + w["cfg"], w["kappa"], w["csw"])
     sub = m.mglma_subspace_create(ctx, g, w["block"], w["nv"], w["n_smooth"], 2000 + w["cfg"], prec[w["sub_store"]],
                                   n_cg=w["n_cg"], cg_prec=m.MGLMA_FP32)
     C = m.mglma_coarse_build(ctx, g, sub, prec[w["coarse_store"]])

@@ -241,7 +241,12 @@ struct RAcc<double> {
   __device__ __forceinline__ double2 dot() { return make_double2(DR, DI); }
 };
 
-template <typename R, int MODE>
+// Plain grid-stride loops: a four-way unrolled variant with loads one grid
+// stride apart reached only 40-60 % of the HBM copy rate on GB300, the plain
+// loop (as in the streaming updates) reaches it.  JM accumulators per pass
+// over y (MODE 1) keep the register count, and so the occupancy, low for the
+// usual one to four directions.
+template <typename R, int MODE, int JM>
 __global__ void __launch_bounds__(RT) reduce_kernel(const typename Pair<R>::T* __restrict__ x0, size_t jstride, int k,
                                                     const typename Pair<R>::T* __restrict__ y, size_t m,
                                                     double2* __restrict__ part, unsigned* __restrict__ count,
@@ -250,18 +255,18 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const typename Pair<R>::T* _
   const size_t off = (size_t)r * m;
   const size_t step = (size_t)nb * RT;
   if (MODE == 1) {
-    // directions in chunks of up to 8 per pass over y
-    for (int j0 = 0; j0 < k; j0 += 8) {
-      const int nj = min(8, k - j0);
-      RAcc<R> acc[8];
+    // directions in chunks of up to JM per pass over y
+    for (int j0 = 0; j0 < k; j0 += JM) {
+      const int nj = min(JM, k - j0);
+      RAcc<R> acc[JM];
       for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < m; i += step) {
         const auto yv = y[off + i];
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
+        for (int jj = 0; jj < JM; ++jj)
           if (jj < nj) acc[jj].add_d(x0[(j0 + jj) * jstride + off + i], yv);
       }
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
+      for (int jj = 0; jj < JM; ++jj) {
         if (jj >= nj) break;
         const double2 v = block_sum2<RT>(acc[jj].dot());
         if (threadIdx.x == 0) part[((size_t)(j0 + jj) * nrhs + r) * nb + blockIdx.x] = v;
@@ -270,23 +275,7 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const typename Pair<R>::T* _
   } else {
     RAcc<R> acc;
     const auto* x = x0 + off;
-    size_t i = (size_t)blockIdx.x * RT + threadIdx.x;
-    for (; i + 3 * step < m; i += 4 * step) {
-      const auto a0 = x[i], a1 = x[i + step], a2 = x[i + 2 * step], a3 = x[i + 3 * step];
-      if (MODE == 2) {
-        const auto b0 = y[off + i], b1 = y[off + i + step], b2 = y[off + i + 2 * step], b3 = y[off + i + 3 * step];
-        acc.add_nd(a0, b0);
-        acc.add_nd(a1, b1);
-        acc.add_nd(a2, b2);
-        acc.add_nd(a3, b3);
-      } else {
-        acc.add_n(a0);
-        acc.add_n(a1);
-        acc.add_n(a2);
-        acc.add_n(a3);
-      }
-    }
-    for (; i < m; i += step) {
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < m; i += step) {
       if (MODE == 2)
         acc.add_nd(x[i], y[off + i]);
       else
@@ -551,12 +540,24 @@ static mglma_status reduce_impl(mglma_ctx ctx, const Vec& x0, size_t jstride_rea
   unsigned* count = nullptr;
   MG_CHECK(red_scratch(ctx, s, (size_t)nb * x0.nrhs * nslot, x0.nrhs, &part, &count));
   dim3 g(nb, x0.nrhs, 1);
-  if (x0.prec == MGLMA_FP64)
-    reduce_kernel<double, MODE><<<g, RT, 0, s>>>((const double2*)x0.p, jstride_reals / 2, k,
-                                                 y ? (const double2*)y->p : nullptr, m, part, count, out2, out1);
-  else
-    reduce_kernel<float, MODE><<<g, RT, 0, s>>>((const float4*)x0.p, jstride_reals / 4, k,
-                                                y ? (const float4*)y->p : nullptr, m, part, count, out2, out1);
+  const int jm = MODE != 1 ? 1 : (k <= 1 ? 1 : (k <= 2 ? 2 : (k <= 4 ? 4 : 8)));
+  if (x0.prec == MGLMA_FP64) {
+    const double2* xp = (const double2*)x0.p;
+    const double2* yp = y ? (const double2*)y->p : nullptr;
+    const size_t js = jstride_reals / 2;
+    if (jm == 1) reduce_kernel<double, MODE, 1><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+    if (jm == 2) reduce_kernel<double, MODE, 2><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+    if (jm == 4) reduce_kernel<double, MODE, 4><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+    if (jm == 8) reduce_kernel<double, MODE, 8><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+  } else {
+    const float4* xp = (const float4*)x0.p;
+    const float4* yp = y ? (const float4*)y->p : nullptr;
+    const size_t js = jstride_reals / 4;
+    if (jm == 1) reduce_kernel<float, MODE, 1><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+    if (jm == 2) reduce_kernel<float, MODE, 2><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+    if (jm == 4) reduce_kernel<float, MODE, 4><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+    if (jm == 8) reduce_kernel<float, MODE, 8><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+  }
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }

@@ -95,19 +95,19 @@ __device__ __forceinline__ uint16_t bf16_bits(float f) {
 // RHS beyond nrhs are zero; mode bit 0 applies gamma5hat (j >= nv negated).
 __global__ void x_image_kernel(const float2* __restrict__ X, uint4* __restrict__ XB, int64_t V1, int n2, int nrhs,
                                int NT, int mode) {
+  // one thread per (tile t, site z, group jo of 8 dofs, RHS r of the tile):
+  // reads the group's 64 bytes of X once and writes its four 16-byte rows
   const int G = n2 / 8, N = 2 * NT, nv = n2 / 2;
   const size_t rows = (size_t)2 * G * N;  // 16-byte rows per (tile, site)
   const size_t ntiles = (size_t)(nrhs + NT - 1) / NT;
-  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= ntiles * V1 * rows) return;
-  const int n = (int)(tid % N);
-  const int c = (int)((tid / N) % (2 * G));
-  const int64_t z = (int64_t)((tid / rows) % V1);
-  const int t = (int)(tid / (rows * V1));
-  const int part = c / G, jo = c % G;
-  const bool imcol = n >= NT;
-  const int rr = t * NT + (imcol ? n - NT : n);
-  uint32_t w[4] = {0u, 0u, 0u, 0u};
+  const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= ntiles * V1 * G * NT) return;
+  const int ri = (int)(u % NT);
+  const int jo = (int)((u / NT) % G);
+  const int64_t z = (int64_t)((u / ((size_t)NT * G)) % V1);
+  const int t = (int)(u / ((size_t)NT * G * V1));
+  const int rr = t * NT + ri;
+  uint32_t w[4][4] = {};  // rows: (part 0, Re col), (part 0, Im col), (part 1, Re col), (part 1, Im col)
   if (rr < nrhs) {
     const float4* src = reinterpret_cast<const float4*>(X + ((size_t)rr * V1 + z) * n2 + jo * 8);
     float re[8], im[8];
@@ -119,16 +119,25 @@ __global__ void x_image_kernel(const float2* __restrict__ X, uint4* __restrict__
       re[2 * h + 1] = q.z;
       im[2 * h + 1] = q.w;
     }
-    float v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const float sg = ((mode & 1) && jo * 8 + e >= nv) ? -1.f : 1.f;
-      v[e] = sg * (part == 0 ? (imcol ? im[e] : re[e]) : (imcol ? re[e] : -im[e]));
+      re[e] *= sg;
+      im[e] *= sg;
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) w[e] = (uint32_t)bf16_bits(v[2 * e]) | ((uint32_t)bf16_bits(v[2 * e + 1]) << 16);
+    for (int e = 0; e < 4; ++e) {
+      w[0][e] = (uint32_t)bf16_bits(re[2 * e]) | ((uint32_t)bf16_bits(re[2 * e + 1]) << 16);
+      w[1][e] = (uint32_t)bf16_bits(im[2 * e]) | ((uint32_t)bf16_bits(im[2 * e + 1]) << 16);
+      w[2][e] = (uint32_t)bf16_bits(-im[2 * e]) | ((uint32_t)bf16_bits(-im[2 * e + 1]) << 16);
+      w[3][e] = w[0][e];
+    }
   }
-  XB[tid] = make_uint4(w[0], w[1], w[2], w[3]);
+  uint4* dst = XB + ((size_t)t * V1 + z) * rows;
+  dst[(size_t)jo * N + ri] = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
+  dst[(size_t)jo * N + NT + ri] = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+  dst[(size_t)(G + jo) * N + ri] = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
+  dst[(size_t)(G + jo) * N + NT + ri] = make_uint4(w[3][0], w[3][1], w[3][2], w[3][3]);
 }
 
 template <int N>
@@ -405,8 +414,8 @@ static mglma_status launch_tc(mglma_ctx ctx, const mglma_coarse_s* C, const floa
   const int n2 = C->n2;
   const int64_t V1 = C->geo.V1;
   {
-    const size_t rows = (size_t)((nrhs + NT - 1) / NT) * V1 * 2 * (n2 / 8) * 2 * NT;
-    x_image_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(X, (uint4*)xb, V1, n2, nrhs, NT, mode);
+    const size_t groups = (size_t)((nrhs + NT - 1) / NT) * V1 * (n2 / 8) * NT;
+    x_image_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, s>>>(X, (uint4*)xb, V1, n2, nrhs, NT, mode);
     MG_LAUNCH_CHECK();
   }
   const size_t smem = tc_smem(n2, NT);
