@@ -241,11 +241,9 @@ struct RAcc<double> {
   __device__ __forceinline__ double2 dot() { return make_double2(DR, DI); }
 };
 
-// Plain grid-stride loops: a four-way unrolled variant with loads one grid
-// stride apart reached only 40-60 % of the HBM copy rate on GB300, the plain
-// loop (as in the streaming updates) reaches it.  JM accumulators per pass
-// over y (MODE 1) keep the register count, and so the occupancy, low for the
-// usual one to four directions.
+// Grid-stride loops over 16-byte loads.  JM accumulators per pass over y
+// (MODE 1) keep the register count, and so the occupancy, low for the usual
+// one to four directions.
 template <typename R, int MODE, int JM>
 __global__ void __launch_bounds__(RT) reduce_kernel(const typename Pair<R>::T* __restrict__ x0, size_t jstride, int k,
                                                     const typename Pair<R>::T* __restrict__ y, size_t m,
