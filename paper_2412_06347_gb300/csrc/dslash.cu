@@ -279,10 +279,15 @@ constexpr int dslash_min_ctas() {
   return sizeof(R) == 8 ? 3 : (NR == 1 ? (RW == 1 ? 6 : 5) : (NR == 2 ? 4 : 3));
 }
 
-template <typename R, int NR, bool DAG, int RW>
+// RED (FP32, one RHS per thread, one RHS tile per CTA only) also reduces, per
+// CTA, |t|^2 and <t, in> = sum conj(t) in over the CTA's 128 sites of t = op(in)
+// into part[(rhs * nblk + block) * 3 + {0, 1, 2}] (|t|^2, Re, Im) in FP64,
+// summed over the blocks in a fixed order by dot_finish_kernel.
+template <typename R, int NR, bool DAG, int RW, bool RED = false>
 __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kernel(const void* __restrict__ in, void* __restrict__ out,
                                                      const void* __restrict__ U, const void* __restrict__ C,
-                                                     DslashArgs a) {
+                                                     DslashArgs a, double* __restrict__ part = nullptr) {
+  static_assert(!RED || (NR == 1 && RW == 1 && sizeof(R) == 4), "fused reduction: FP32 tile 1,1 only");
   constexpr int SW = 128 / RW;  // sites per CTA
   const int64_t V = a.q.V;
   // RHS tile groups run fastest in launch order, so the CTAs that share a
@@ -290,9 +295,14 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
   const int ntile = (a.nrhs + NR - 1) / NR;
   int64_t site;
   int r0;
+  bool valid = true;  // with RED every thread reaches the block reduction
   if constexpr (RW == 1) {
     site = (int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x;
-    if (site >= V) return;
+    if (site >= V) {
+      if constexpr (!RED) return;
+      valid = false;
+      site = V - 1;
+    }
     r0 = (blockIdx.x % ntile) * NR;
   } else {
     const int ngrp = (ntile + RW - 1) / RW;
@@ -353,13 +363,79 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
   }
 #pragma unroll
   for (int r = 0; r < NR; ++r)
-    if (r0 + r < a.nrhs) {
+    if (r0 + r < a.nrhs && valid) {
       if (a.g5out) {
 #pragma unroll
         for (int k = 6; k < 12; ++k) acc[r][k] = -acc[r][k];
       }
       IO<R>::store(out, V, r0 + r, site, acc[r]);
     }
+  if constexpr (RED) {
+    float nn = 0.f, dr = 0.f, di = 0.f;
+    if (valid) {
+      Cx<R> sv[12];
+      IO<R>::load(in, V, r0, site, sv);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const Cx<R> t = acc[0][k];
+        nn += t.re * t.re + t.im * t.im;
+        dr += t.re * sv[k].re + t.im * sv[k].im;
+        di += t.re * sv[k].im - t.im * sv[k].re;
+      }
+    }
+    double v0 = nn, v1 = dr, v2 = di;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v0 += __shfl_down_sync(0xffffffffu, v0, o);
+      v1 += __shfl_down_sync(0xffffffffu, v1, o);
+      v2 += __shfl_down_sync(0xffffffffu, v2, o);
+    }
+    __shared__ double wsum[4][3];
+    const int w = threadIdx.x / 32;
+    if (threadIdx.x % 32 == 0) {
+      wsum[w][0] = v0;
+      wsum[w][1] = v1;
+      wsum[w][2] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      const int64_t nblk = (V + 127) / 128;
+      const int c = threadIdx.x;
+      part[((size_t)r0 * nblk + blockIdx.x / ntile) * 3 + c] =
+          ((wsum[0][c] + wsum[1][c]) + wsum[2][c]) + wsum[3][c];
+    }
+  }
+}
+
+// nrm[r] = sum_b part[r][b][0], dot[r] = sum_b (part[r][b][1], part[r][b][2]):
+// one CTA per RHS, fixed order (strided partial sums, then a fixed tree)
+__global__ void __launch_bounds__(256) dot_finish_kernel(const double* __restrict__ part, int64_t nblk,
+                                                         double* __restrict__ nrm, double2* __restrict__ dot) {
+  const int r = blockIdx.x;
+  double a = 0, b = 0, c = 0;
+  for (int64_t i = threadIdx.x; i < nblk; i += 256) {
+    const double* p = part + ((size_t)r * nblk + i) * 3;
+    a += p[0];
+    b += p[1];
+    c += p[2];
+  }
+  __shared__ double sh[3][256];
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = b;
+  sh[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + h];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + h];
+      sh[2][threadIdx.x] += sh[2][threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    nrm[r] = sh[0][0];
+    dot[r] = make_double2(sh[1][0], sh[2][0]);
+  }
 }
 
 // ------------------------------------------------------------ hop-slot pieces (FP64, setup)
@@ -739,6 +815,35 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
     ProfScope ps(ctx, K_DSLASH32, s, V * (480.0 + 192.0 * N), flops);
     launch_dslash32(tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, dslash32_default_tile(in.nrhs)), in, out, G->U32, G->C32,
                     a, dagger, s);
+  }
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+size_t dslash_dot_part_doubles(int64_t V, int nrhs) { return (size_t)3 * nrhs * (size_t)((V + 127) / 128); }
+
+mglma_status dslash_dot(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, double* part,
+                        double* nrm, double2* dot, cudaStream_t s) {
+  if (in.prec != MGLMA_FP32 || out.prec != MGLMA_FP32 || in.V != G->g.V || out.V != G->g.V || in.nrhs != out.nrhs)
+    return fail(MGLMA_ERR_INVALID, "dslash_dot: FP32 fields of the gauge field's volume needed");
+  if (in.p == out.p) return fail(MGLMA_ERR_INVALID, "dslash_dot: in and out must differ");
+  if (in.nrhs == 0) return MGLMA_OK;
+  DslashArgs a;
+  a.q = make_latidx(G->g.L);
+  a.bc = (double)G->g.t_bc;
+  a.nrhs = in.nrhs;
+  a.g5out = 0;
+  const double V = (double)in.V, N = (double)in.nrhs;
+  const int64_t nblk = (in.V + 127) / 128;
+  {
+    ProfScope ps(ctx, K_DSLASH32, s, V * (480.0 + 192.0 * N), 1896.0 * V * N);
+    dslash_kernel<float, 1, false, 1, true><<<(unsigned)(nblk * in.nrhs), 128, 0, s>>>(in.p, out.p, G->U32, G->C32,
+                                                                                       a, part);
+  }
+  MG_LAUNCH_CHECK();
+  {
+    ProfScope ps(ctx, K_REDUCE, s, (double)dslash_dot_part_doubles(in.V, in.nrhs) * 8.0);
+    dot_finish_kernel<<<in.nrhs, 256, 0, s>>>(part, nblk, nrm, dot);
   }
   MG_LAUNCH_CHECK();
   return MGLMA_OK;

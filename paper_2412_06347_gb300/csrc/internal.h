@@ -228,6 +228,12 @@ mglma_status convert_spinor(mglma_ctx, const Spinor& src, Spinor& dst, cudaStrea
 // fine operator application: out = op(in), op in {D, D^dag, gamma5 D, gamma5 D^dag}
 mglma_status dslash(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, bool dagger,
                     bool gamma5_out, cudaStream_t s);
+// FP32 t = D in with, per RHS, nrm = |t|^2 and dot = <t, in> = sum conj(t) in
+// reduced in the same pass (FP64 partials per 128-site block in `part`, at
+// least dslash_dot_part_doubles(V, nrhs) doubles, summed in a fixed order).
+mglma_status dslash_dot(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, double* part, double* nrm,
+                        double2* dot, cudaStream_t s);
+size_t dslash_dot_part_doubles(int64_t V, int nrhs);
 // single hop-slot pieces of D in FP64, used to assemble the coarse operator:
 // slot d < 8: the hop term of slot d at sites whose hop leaves their block
 // (zero elsewhere); slot 8: clover term plus every hop that stays in the block.

@@ -542,6 +542,7 @@ struct TwoLevel {
   long long coarse_iters = 0;
   int cap = 0;  // RHS the scratch is sized for (0: the first call's count)
   Vec b1, e1, sv, tv;
+  double* part = nullptr;  // per-block partial sums of the fused MR reductions
   Scalars sc;
   CoarseSolver cs;
   bool ready = false;
@@ -550,6 +551,7 @@ struct TwoLevel {
     dfree(ctx, e1.p, s);
     dfree(ctx, sv.p, s);
     dfree(ctx, tv.p, s);
+    dfree(ctx, part, s);
   }
   mglma_status setup(const Vec& r) {
     const int n = std::max(cap, r.nrhs);
@@ -565,6 +567,7 @@ struct TwoLevel {
     sv.p = tv.p = nullptr;
     MG_CHECK(dalloc(ctx, &sv.p, sv.bytes(), s));
     MG_CHECK(dalloc(ctx, &tv.p, tv.bytes(), s));
+    MG_CHECK(dalloc(ctx, (void**)&part, dslash_dot_part_doubles(C->sub->geo.V, n) * sizeof(double), s));
     MG_CHECK(sc.alloc(ctx, n, 1, 1, s));
     cs.ctx = ctx;
     cs.s = s;
@@ -595,8 +598,8 @@ struct TwoLevel {
       MG_CHECK(copy_vec(ctx, r, svn, s));
       MG_CHECK(axpby(ctx, nullptr, CM1, tvn, nullptr, C1, svn, s));
       for (int k = 0; k < p->nu; ++k) {
-        MG_CHECK(dslash(ctx, G, ss, ts, false, false, s));
-        MG_CHECK(norm2_cdot(ctx, tvn, svn, sc.d, sc.z, s));  // |D s|^2 and <D s, s>
+        // t = D s with |D s|^2 and <D s, s> reduced in the same pass
+        MG_CHECK(dslash_dot(ctx, G, ss, ts, part, sc.d, sc.z, s));
         MG_CHECK(mr_alpha(ctx, sc.z, sc.d, sc.z, n, s));
         MG_CHECK(axpy2(ctx, sc.z, svn, z, tvn, svn, s));
       }
