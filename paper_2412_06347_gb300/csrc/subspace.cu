@@ -206,28 +206,51 @@ __global__ void __launch_bounds__(RP_THREADS) restrict_kernel(const void* __rest
 #pragma unroll
     for (int r = 0; r < NRT; ++r) acc[a][r] = cx<R>(0, 0);
 
+  __shared__ int64_t site_of[RP_CHUNK];
+  const int nv = n2 / 2;
   for (int k0 = 0; k0 < g.nB; k0 += RP_CHUNK) {
     const int ck = min(RP_CHUNK, g.nB - k0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < NRT * 12 * ck; idx += RP_THREADS) {
-      const int kk = idx % ck, q = (idx / ck) % 12, r = idx / (ck * 12);
-      Cx<R> v = cx<R>(0, 0);
-      if (r0 + r < nrhs) v = fine_get<R>(fine, g.V, r0 + r, block_site(g, y, k0 + kk), q);
-      sm[(r * 12 + q) * RP_CHUNK + kk] = v;
+    for (int kk = threadIdx.x; kk < ck; kk += RP_THREADS) site_of[kk] = block_site(g, y, k0 + kk);
+    __syncthreads();
+    if constexpr (sizeof(R) == 4) {  // 16-byte loads: two complex components per load
+      for (int idx = threadIdx.x; idx < NRT * 6 * ck; idx += RP_THREADS) {
+        const int kk = idx % ck, c = (idx / ck) % 6, r = idx / (ck * 6);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r0 + r < nrhs) v = __ldg(reinterpret_cast<const float4*>(fine) + ((size_t)(r0 + r) * 6 + c) * g.V + site_of[kk]);
+        sm[(r * 12 + 2 * c) * RP_CHUNK + kk] = cx<R>(v.x, v.y);
+        sm[(r * 12 + 2 * c + 1) * RP_CHUNK + kk] = cx<R>(v.z, v.w);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < NRT * 12 * ck; idx += RP_THREADS) {
+        const int kk = idx % ck, q = (idx / ck) % 12, r = idx / (ck * 12);
+        Cx<R> v = cx<R>(0, 0);
+        if (r0 + r < nrhs) v = fine_get<R>(fine, g.V, r0 + r, site_of[kk], q);
+        sm[(r * 12 + q) * RP_CHUNK + kk] = v;
+      }
     }
     __syncthreads();
+    // per site of the lane and chirality: the spinor components once into
+    // registers, then every dof of this warp with that chirality
+    for (int kk = lane; kk < ck; kk += 32) {
 #pragma unroll
-    for (int a = 0; a < MAXJ; ++a) {
-      const int j = warp + a * NW;
-      if (j >= n2) break;
-      const int qa = j < n2 / 2 ? 0 : 6;
-      for (int kk = lane; kk < ck; kk += 32) {
-        Cx<R> ph[6];
-        BIO<B>::template load<R>(basis, scale, (size_t)y * n2 + j, g.nB, k0 + kk, ph);
+      for (int al = 0; al < 2; ++al) {
+        Cx<R> ps[NRT][6];
 #pragma unroll
         for (int r = 0; r < NRT; ++r)
 #pragma unroll
-          for (int q = 0; q < 6; ++q) cfma_conj(acc[a][r], ph[q], sm[(r * 12 + qa + q) * RP_CHUNK + kk]);
+          for (int q = 0; q < 6; ++q) ps[r][q] = sm[(r * 12 + 6 * al + q) * RP_CHUNK + kk];
+#pragma unroll
+        for (int a = 0; a < MAXJ; ++a) {
+          const int j = warp + a * NW;
+          if (j >= n2 || (j >= nv) != (al == 1)) continue;
+          Cx<R> ph[6];
+          BIO<B>::template load<R>(basis, scale, (size_t)y * n2 + j, g.nB, k0 + kk, ph);
+#pragma unroll
+          for (int r = 0; r < NRT; ++r)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) cfma_conj(acc[a][r], ph[q], ps[r][q]);
+        }
       }
     }
   }
