@@ -189,8 +189,9 @@ mglma_status mglma_subspace_build(mglma_ctx ctx, mglma_gauge g, const int block[
  * CG in FP32, so cg_prec is ignored), the per-(block, chirality)
  * orthonormalisation runs in FP64 on chunks of blocks, and only the store
  * copy (MGLMA_FP32 or MGLMA_FP16) is kept -- no FP64 basis.  Peak device
- * memory is about (nv x 96 + lean_group x 480) bytes per site instead of
- * about nv x 670.  FP64 R0 / T0 and the coarse build then read the stored
+ * memory is about 96 nv + 384 lean_group bytes per site, plus the stored
+ * copy (48 nv for FP16, 96 nv for FP32) and a 1 GiB chunk buffer, instead of
+ * about 670 nv.  FP64 R0 / T0 and the coarse build then read the stored
  * copy in FP64 arithmetic; the propagator pieces (which need the FP64 basis)
  * are refused.  0 = the standard FP64 set-up. */
 typedef struct {
