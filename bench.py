@@ -57,6 +57,13 @@ C5 = dict(shapes=[(128, 64, 64, 64), (96, 48, 48, 48), (64, 32, 32, 32)], eps=0.
           block=(4, 4, 4, 4), nv=24, n_smooth=5, n_cg=60, lean_group=4, cfg=5)
 
 
+# DRAM traffic per lattice site of one launch of a kernel class at a given
+# RHS count, from ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
+# capture divided by the captured lattice's volume; traffic grows with the
+# volume).  The capture and its command are summarised under profiles/.
+NCU_TRAFFIC_PER_SITE = {}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -561,8 +568,11 @@ def main():
     achieved = kbytes / (kms / 1e3) / 1e9
     share = {k: round(v[1] / ms, 4) for k, v in prof.items() if v[0]}
     dsl = prof.get("dslash32", (0, 0, 0, 0))
+    tps = NCU_TRAFFIC_PER_SITE.get((kname, G))
     roofline = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
-                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": round(tps * V) if tps else None,
+                "bytes_per_launch": round(kbytes / max(kl, 1)),
                 "peak_source": f"{peak_kind} hbm_gbs", "launches": kl, "avg_launch_ms": kms / max(kl, 1),
                 "time_share": share,
                 "dslash32": {"achieved": round(dsl[2] / (dsl[1] / 1e3) / 1e9, 1) if dsl[1] else None,
