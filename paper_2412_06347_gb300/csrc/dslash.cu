@@ -281,8 +281,9 @@ constexpr int dslash_min_ctas() {
 
 // RED (FP32, one RHS per thread, one RHS tile per CTA only) also reduces, per
 // CTA, |t|^2 and <t, in> = sum conj(t) in over the CTA's 128 sites of t = op(in)
-// into part[(rhs * nblk + block) * 3 + {0, 1, 2}] (|t|^2, Re, Im) in FP64,
-// summed over the blocks in a fixed order by dot_finish_kernel.
+// into part[(rhs * nblk + block) * 3 + {0, 1, 2}] (|t|^2, Re, Im): FP32 over
+// each warp's 32 sites, FP64 from there on, summed over the blocks in a fixed
+// order by dot_finish_kernel.
 template <typename R, int NR, bool DAG, int RW, bool RED = false>
 __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kernel(const void* __restrict__ in, void* __restrict__ out,
                                                      const void* __restrict__ U, const void* __restrict__ C,
@@ -383,26 +384,27 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
         di += t.re * sv[k].im - t.im * sv[k].re;
       }
     }
-    double v0 = nn, v1 = dr, v2 = di;
+    // FP32 within a warp (32 sites), FP64 from the warp partials on: the
+    // FP64 pipe of GB300 is too narrow for a per-thread FP64 tree
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      v0 += __shfl_down_sync(0xffffffffu, v0, o);
-      v1 += __shfl_down_sync(0xffffffffu, v1, o);
-      v2 += __shfl_down_sync(0xffffffffu, v2, o);
+      nn += __shfl_down_sync(0xffffffffu, nn, o);
+      dr += __shfl_down_sync(0xffffffffu, dr, o);
+      di += __shfl_down_sync(0xffffffffu, di, o);
     }
-    __shared__ double wsum[4][3];
+    __shared__ float wsum[4][3];
     const int w = threadIdx.x / 32;
     if (threadIdx.x % 32 == 0) {
-      wsum[w][0] = v0;
-      wsum[w][1] = v1;
-      wsum[w][2] = v2;
+      wsum[w][0] = nn;
+      wsum[w][1] = dr;
+      wsum[w][2] = di;
     }
     __syncthreads();
     if (threadIdx.x < 3) {
       const int64_t nblk = (V + 127) / 128;
       const int c = threadIdx.x;
       part[((size_t)r0 * nblk + blockIdx.x / ntile) * 3 + c] =
-          ((wsum[0][c] + wsum[1][c]) + wsum[2][c]) + wsum[3][c];
+          (((double)wsum[0][c] + (double)wsum[1][c]) + (double)wsum[2][c]) + (double)wsum[3][c];
     }
   }
 }

@@ -229,8 +229,9 @@ mglma_status convert_spinor(mglma_ctx, const Spinor& src, Spinor& dst, cudaStrea
 mglma_status dslash(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, bool dagger,
                     bool gamma5_out, cudaStream_t s);
 // FP32 t = D in with, per RHS, nrm = |t|^2 and dot = <t, in> = sum conj(t) in
-// reduced in the same pass (FP64 partials per 128-site block in `part`, at
-// least dslash_dot_part_doubles(V, nrhs) doubles, summed in a fixed order).
+// reduced in the same pass (FP32 per warp of 32 sites, then FP64 partials per
+// 128-site block in `part`, at least dslash_dot_part_doubles(V, nrhs)
+// doubles, summed in a fixed order).
 mglma_status dslash_dot(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, double* part, double* nrm,
                         double2* dot, cudaStream_t s);
 size_t dslash_dot_part_doubles(int64_t V, int nrhs);
