@@ -153,7 +153,7 @@ class Clocks:
 
 
 KINDS = ("dslash64", "dslash32", "blas", "reduce", "restrict", "prolong", "coarse", "pack", "setup", "scalar", "cblas",
-         "creduce")
+         "creduce", "contract")
 
 
 def profile_snapshot(m, ctx):
@@ -382,6 +382,24 @@ def run_micro(args, w):
     if args.micro in ("dslash32", "dslash64"):
         prec = m.MGLMA_FP32 if args.micro == "dslash32" else m.MGLMA_FP64
         r = micro_dslash(m, torch, ctx, g, V, args.nrhs, prec, reps, stream)
+    elif args.micro == "contract":
+        # the estimator's time-slice contraction (Eq. C_stoch2): 4 FP64
+        # canonical fields per RHS read once
+        n = args.nrhs
+        a = torch.randn(n, 3, V, 24, dtype=torch.float64, device="cuda")
+        b = torch.randn(n, V, 24, dtype=torch.float64, device="cuda")
+        out = torch.empty(n, L[0], 2, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            m.mglma_contract(ctx, L, n, a, b, out, stream=stream)
+        torch.cuda.synchronize()
+        m.mglma_profile(ctx, True, True)
+        for _ in range(reps):
+            m.mglma_contract(ctx, L, n, a, b, out, stream=stream)
+        nl, ms, by, fl = m.mglma_profile_get(ctx, "contract")
+        m.mglma_profile(ctx, False, True)
+        r = {"kernel": "contract", "nrhs": n, "launches": nl, "avg_launch_ms": ms / nl,
+             "achieved": round(by / (ms / 1e3) / 1e9, 1), "unit": "GB/s", "bytes_per_launch": by / nl,
+             "fp64_tflops": round(fl / (ms / 1e3) / 1e12, 3)}
     else:
         prec = {"fp16": m.MGLMA_FP16, "fp32": m.MGLMA_FP32, "bf16": m.MGLMA_BF16}
         sub = m.mglma_subspace_build(ctx, g, w["block"], w["nv"], 1, 2000 + w["cfg"], prec[w["sub_store"]])
@@ -435,7 +453,7 @@ def main():
     ap.add_argument("--coarse-solver", default="minres", choices=sorted(COARSE_SOLVERS),
                     help="coarse solver inside the preconditioner")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-solver sample")
-    ap.add_argument("--micro", default="", choices=["", "dslash32", "dslash64", "coarse", "transfer"],
+    ap.add_argument("--micro", default="", choices=["", "dslash32", "dslash64", "coarse", "transfer", "contract"],
                     help="time one kernel class on the workload lattice instead of the solve")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch in --micro mode")
     ap.add_argument("--tile", default="", help="FP32 stencil tile NR,RW (RHS per thread, RHS tiles per CTA); "

@@ -93,8 +93,9 @@ mglma_status mglma_profile(mglma_ctx ctx, int enable, int reset);
 /* Fetches the accumulated launches, milliseconds, algorithmic bytes and
  * algorithmic flops of kernel class `name` ("dslash64", "dslash32", "blas",
  * "reduce", "restrict", "prolong", "coarse", "pack", "setup", "scalar",
- * "cblas", "creduce"; the last two are BLAS-1 and reductions on coarse
- * fields inside coarse solves, "blas" and "reduce" the fine-level ones).  Algorithmic
+ * "cblas", "creduce", "contract"; "cblas" and "creduce" are BLAS-1 and
+ * reductions on coarse fields inside coarse solves, "blas" and "reduce" the
+ * fine-level ones).  Algorithmic
  * bytes count every operand read once and every result written once (for
  * the stencil: links, clover, input and output spinors).  Waits for the
  * recorded events.  Any output pointer may be NULL. */
@@ -269,6 +270,27 @@ typedef enum { MGLMA_SOURCE_Z2 = 0, MGLMA_SOURCE_Z4 = 1, MGLMA_SOURCE_POINT = 2 
 mglma_status mglma_sources(mglma_ctx ctx, const mglma_lattice* lat, int kind, int nrhs, uint64_t seed,
                            int64_t first, const int64_t* point_sites, const int* point_sc, int t_slice, double* out,
                            void* cuda_stream);
+
+/* ---------------------------------------------------------------- contractions (Sec. 5) */
+/* Time-slice contraction of the stochastic estimator, Eq. C_stoch2: for each
+ * RHS r and time slice x0,
+ *   out[r][x0] = -(1 / (3 L1 L2 L3)) sum_{k=1}^{3} sum_{x in slice x0}
+ *                < a[r][k-1](x), gamma5 gamma_k b[r](x) >
+ * with <u, v> = sum over spin and colour of conj(u) v.  For a noise source
+ * eta on slice y0, a[r][k-1] = S_j gamma5 gamma_k^dag eta and b[r] = S_i eta
+ * give G_ij(x0, y0) (gamma_k is Hermitian in the chiral basis, so the
+ * sources are mglma_gamma5_gamma of eta).
+ *   a: nrhs x 3 canonical spinors ([r][k-1][site][spin][colour]);
+ *   b: nrhs canonical spinors; out: nrhs x L0 complex128 ([r][x0]).
+ * Host or device pointers.  Sums in FP64 in a fixed order (one CTA per RHS
+ * and time slice), so the result does not depend on the batch. */
+mglma_status mglma_contract(mglma_ctx ctx, const mglma_lattice* lat, int nrhs, const double* a, const double* b,
+                            double* out, void* cuda_stream);
+/* out = gamma5 gamma_k in for nrhs canonical spinors, k = 1, 2, 3 (chiral
+ * basis: gamma5 gamma_k = [[0, -i sigma_k], [-i sigma_k, 0]]); the sources
+ * of the a fields of mglma_contract.  in and out must differ. */
+mglma_status mglma_gamma5_gamma(mglma_ctx ctx, const mglma_lattice* lat, int k, int nrhs, const double* in,
+                                double* out, void* cuda_stream);
 
 /* ---------------------------------------------------------------- solves (Sec. 2, Sec. 5) */
 typedef enum {

@@ -24,6 +24,10 @@ without blocking, fusion or reordering beyond what the definition states:
 * ``solvers``   -- CG on the normal equations, dense solves, and the
                    propagator pieces S1 = T Q1^-1 R gamma5 and S0 = S - S1
                    (Sec. 2, App. chirality).
+* ``contract``  -- the time-slice contraction of the stochastic estimator
+                   (Sec. 5, Eq. C_stoch2), the correlator from a dense
+                   propagator (Eq. tmr) and the translation average (Eq.
+                   timetrans).
 
 Parity pins (tests/test_oracle_*.py) tie each part to facts that do not come
 from this package: the free-field momentum-space spectrum, an abelian
@@ -31,4 +35,4 @@ constant-field clover, gamma5-hermiticity, gauge covariance, QR factorisation,
 brute-force dense matrices, dense LU inverses, and the eigenvalue alignment of
 App. spectra.  No function here is "parity unpinned".
 """
-from . import lattice, dirac, multigrid, solvers  # noqa: F401
+from . import lattice, dirac, multigrid, solvers, contract  # noqa: F401

@@ -104,6 +104,8 @@ _sig("mglma_sources", C.c_int, _vp, C.POINTER(mglma_lattice), C.c_int, C.c_int, 
      C.POINTER(_i64), C.POINTER(C.c_int), C.c_int, _vp, _vp)
 _sig("mglma_autotune", C.c_int, _vp, _vp, _vp, C.c_int)
 _sig("mglma_autotune_get", C.c_int, _vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double))
+_sig("mglma_contract", C.c_int, _vp, C.POINTER(mglma_lattice), C.c_int, _vp, _vp, _vp, _vp)
+_sig("mglma_gamma5_gamma", C.c_int, _vp, C.POINTER(mglma_lattice), C.c_int, C.c_int, _vp, _vp, _vp)
 _sig("mglma_autotune_set", C.c_int, _vp, C.c_int, C.c_int, C.c_int)
 _sig("mglma_autotune_save", C.c_int, _vp, C.c_char_p)
 _sig("mglma_autotune_load", C.c_int, _vp, C.c_char_p)
@@ -347,6 +349,17 @@ def mglma_sources(ctx, L, kind, nrhs, seed, out, first=0, point_sites=None, poin
     pc = (C.c_int * nrhs)(*[int(v) for v in point_sc]) if point_sc is not None else None
     _check(lib.mglma_sources(_h(ctx), C.byref(lat), int(kind), int(nrhs), int(seed), int(first), ps, pc,
                              int(t_slice), ptr(out), _stream_ptr(stream)))
+
+
+def mglma_contract(ctx, L, nrhs, a, b, out, stream=None):
+    """out[r][x0] = -(1/(3 L^3)) sum_k sum_{x in x0} <a[r][k-1](x), gamma5 gamma_k b[r](x)> (Eq. C_stoch2)."""
+    lat = mglma_lattice((C.c_int * 4)(*[int(v) for v in L]), -1)
+    _check(lib.mglma_contract(_h(ctx), C.byref(lat), int(nrhs), ptr(a), ptr(b), ptr(out), _stream_ptr(stream)))
+
+
+def mglma_gamma5_gamma(ctx, L, k, nrhs, inp, out, stream=None):
+    lat = mglma_lattice((C.c_int * 4)(*[int(v) for v in L]), -1)
+    _check(lib.mglma_gamma5_gamma(_h(ctx), C.byref(lat), int(k), int(nrhs), ptr(inp), ptr(out), _stream_ptr(stream)))
 
 
 def mglma_autotune(ctx, g=None, coarse=None, nrhs=1):

@@ -20,7 +20,8 @@ mglma_status fail(mglma_status st, const std::string& msg) {
 }
 
 static const char* kKindNames[K_NKINDS] = {"dslash64", "dslash32", "blas",  "reduce", "restrict", "prolong",
-                                           "coarse",   "pack",     "setup", "scalar", "cblas",    "creduce"};
+                                           "coarse",   "pack",     "setup", "scalar", "cblas",    "creduce",
+                                           "contract"};
 
 CoarseLevelScope::CoarseLevelScope(mglma_ctx c) : ctx(c), prev(c ? c->coarse_level : false) {
   if (ctx) ctx->coarse_level = true;

@@ -162,7 +162,8 @@ enum KernelKind {
   K_SCALAR = 9,
   K_CBLAS = 10,    // BLAS-1 on coarse fields (inside a coarse solve)
   K_CREDUCE = 11,  // reductions on coarse fields
-  K_NKINDS = 12
+  K_CONTRACT = 12, // time-slice contractions
+  K_NKINDS = 13
 };
 // While alive, BLAS and reduction launches on the context count as coarse-level
 // work in the per-kernel statistics.
