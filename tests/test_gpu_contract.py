@@ -35,9 +35,12 @@ def test_contract_parity(m, ctx, L, nrhs):
     for r in range(nrhs):
         ref = K.slice_correlator(a[r], b[r])
         assert np.abs(out[r] - ref).max() <= 1e-12 * np.abs(ref).max()
-    # device buffers give the same bits
+    # device buffers give the same bits (written in order on the context's
+    # stream: wait for it before reading)
+    import torch
     od = to_device(np.zeros_like(out))
     m.mglma_contract(ctx, L, nrhs, to_device(a), to_device(b), od)
+    torch.cuda.synchronize()
     assert np.array_equal(od.cpu().numpy(), out)
 
 
