@@ -156,6 +156,27 @@ KINDS = ("dslash64", "dslash32", "blas", "reduce", "restrict", "prolong", "coars
          "creduce", "contract")
 
 
+def replica_source_base(rank, rhs_per_step, nsteps):
+    """First source index of a rank: the replicas solve disjoint ranges of the
+    workload's sources (weak scaling, no data-path collective)."""
+    return rank * rhs_per_step * nsteps
+
+
+def max_over_ranks(dist, x):
+    """The slowest rank's value (the job's time); x itself on one rank."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(rhs_per_step, steps, world, seconds):
+    """Whole-job solves/s: the RHS all ranks solved over the slowest rank's time."""
+    return rhs_per_step * steps * world / seconds
+
+
 def profile_snapshot(m, ctx):
     out = {}
     for k in KINDS:
@@ -510,8 +531,8 @@ def main():
     set_tile(m, ctx, args, G)
 
     nsteps = args.warmup + args.steps
-    # every rank solves its own sources (replicas): rank r starts at source r*G*steps
-    base = rank * G * nsteps
+    # every rank solves its own sources (replicas)
+    base = replica_source_base(rank, G, nsteps)
     dev_b = []
     for i in range(nsteps):
         b = torch.empty((G, V, 12), dtype=torch.complex128, device=dev)
@@ -548,12 +569,9 @@ def main():
     clk = clocks.stop()
     prof = profile_snapshot(m, ctx)
     m.mglma_profile(ctx, False, True)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, ms)
     solves = G * args.steps * world
-    value = solves / (ms / 1e3)
+    value = job_throughput(G, args.steps, world, ms / 1e3)
     resid = max(s["residual"] for s in all_stats)
     iters = [s["iterations"] for s in all_stats]
     citers = [s["coarse_iterations"] for s in all_stats]
@@ -573,11 +591,8 @@ def main():
         step(0, pin_b, pin_x)
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": solves / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": G * V * 24 * 8,
+    e2e_s = max_over_ranks(dist, e2e_s)
+    e2e = {"value": job_throughput(G, args.steps, world, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": G * V * 24 * 8,
            "d2h_bytes_per_step": G * V * 24 * 8}
 
     # ---- roofline of the dominant kernel class in the timed region
