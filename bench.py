@@ -187,29 +187,78 @@ def profile_snapshot(m, ctx):
     return out
 
 
-def cpu_baseline(w, gpu_cgne_iters, budget_slices=4):
+_ORACLE_JOB = None
+
+
+def _oracle_worker_init(job):
+    global _ORACLE_JOB
+    _ORACLE_JOB = job
+
+
+def _oracle_worker_run(iters):
+    """One worker process: `iters` CGNE iterations of the oracle on its own
+    copy of the slab problem; returns the seconds they took."""
+    from oracle import solvers as S
+    U, A, b, kappa, csw = _ORACLE_JOB
+    t0 = time.perf_counter()
+    S.solve_fine(U, b, kappa, csw, tol=1e-300, maxiter=iters, A=A)
+    return time.perf_counter() - t0
+
+
+def _oracle_all_cores(job, procs, iters):
+    """Per-iteration seconds of the oracle with every core busy: `procs`
+    spawned processes (one BLAS/OpenMP thread each) run the slab problem
+    concurrently; the median worker time / iters."""
+    import multiprocessing as mp
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in keys}
+    try:
+        for k in keys:
+            os.environ[k] = "1"
+        with mp.get_context("spawn").Pool(procs, initializer=_oracle_worker_init, initargs=(job,)) as pool:
+            times = pool.map(_oracle_worker_run, [iters] * procs, chunksize=1)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return float(np.median(times)) / iters
+
+
+def cpu_baseline(w, gpu_cgne_iters, budget_slices=4, procs=None):
     """The FP64 oracle on the host cores: plain CG on the normal equations
     (the oracle's solver), timed for two iterations on a budget_slices x
     L1 x L2 x L3 slab of the same operator and extrapolated to one full
     solve: per-iteration time x (V / V_slab) x the iteration count the GPU's
-    FP64 CGNE needed on this workload.  The clover build is set-up, untimed
-    (as the GPU's gauge load is)."""
+    FP64 CGNE needed on this workload.  Timed in one spawned single-threaded
+    process (one core), and on all host cores as `procs` concurrent such
+    processes (spawned, so safe after CUDA use) whose slab throughput adds up
+    as a time-slab decomposition of the full lattice would.  The clover build is set-up, untimed (as the GPU's gauge
+    load is)."""
     import synthetic
     from oracle import dirac as D
-    from oracle import solvers as S
     L = (budget_slices,) + tuple(w["L"][1:])
     U = synthetic.gauge_links(L, w["eps"], 1000 + w["cfg"])
     A = D.clover_matrix(U, w["kappa"], w["csw"])
     b = synthetic.z2_noise(L, 1, 3000 + w["cfg"])[0]
-    t0 = time.perf_counter()
-    S.solve_fine(U, b, w["kappa"], w["csw"], tol=1e-300, maxiter=2, A=A)
-    t_iter = (time.perf_counter() - t0) / 2
+    job = (U, A, b, w["kappa"], w["csw"])
+    t_iter = _oracle_all_cores(job, 1, 2)  # one process, one thread
     scale = np.prod(w["L"]) / np.prod(L)
-    t_solve = t_iter * scale * gpu_cgne_iters
-    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+    one = 1.0 / (t_iter * scale * gpu_cgne_iters)
+    procs = procs if procs is not None else (os.cpu_count() or 1)
+    if procs > 1:
+        t_busy = _oracle_all_cores(job, procs, 2)
+        value = procs / (t_busy * scale * gpu_cgne_iters)
+        how = (f"; all cores: {procs} spawned processes on copies of the slab, {t_busy:.2f} s/iteration each "
+               f"under full load, throughput summed")
+    else:
+        value, how = one, ""
+    return {"value": value, "unit": "solves/s", "cores": procs, "kind": "oracle",
+            "one_core": {"value": one, "cores": 1, "s_per_iteration": round(t_iter, 3)},
             "sample": (f"2 FP64 CGNE iterations of the numpy oracle on a {'x'.join(map(str, L))} slab "
-                       f"({t_iter:.2f} s/iteration), scaled by volume x{scale:.0f} and by the "
-                       f"{gpu_cgne_iters} iterations the GPU FP64 CGNE took")}
+                       f"({t_iter:.2f} s/iteration on one core), scaled by volume x{scale:.0f} and by the "
+                       f"{gpu_cgne_iters} iterations the GPU FP64 CGNE took" + how)}
 
 
 def run_reference(args, w):

@@ -61,3 +61,13 @@ def test_reference_arm_only_on_rank_zero(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(args, dict(bench.WORKLOADS["c2"]))
     assert buf.getvalue() == ""
+
+
+def test_cpu_baseline_fields_one_and_all_cores():
+    """The oracle CPU baseline (spawned single-threaded processes) reports the
+    cores it used and the one-core figure beside the all-cores one."""
+    w = dict(bench.WORKLOADS["c2"])
+    r = bench.cpu_baseline(w, 100, budget_slices=1, procs=2)
+    assert r["kind"] == "oracle" and r["cores"] == 2 and r["unit"] == "solves/s"
+    assert r["one_core"]["cores"] == 1 and r["one_core"]["value"] > 0 and r["value"] > 0
+    assert "1x16x16x16" in r["sample"]
