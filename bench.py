@@ -188,6 +188,7 @@ def profile_snapshot(m, ctx):
 
 
 _ORACLE_JOB = None
+_SLAB_JOBS = {}
 
 
 def _oracle_worker_init(job):
@@ -236,13 +237,16 @@ def cpu_baseline(w, gpu_cgne_iters, budget_slices=4, procs=None):
     processes (spawned, so safe after CUDA use) whose slab throughput adds up
     as a time-slab decomposition of the full lattice would.  The clover build is set-up, untimed (as the GPU's gauge
     load is)."""
-    import synthetic
-    from oracle import dirac as D
     L = (budget_slices,) + tuple(w["L"][1:])
-    U = synthetic.gauge_links(L, w["eps"], 1000 + w["cfg"])
-    A = D.clover_matrix(U, w["kappa"], w["csw"])
-    b = synthetic.z2_noise(L, 1, 3000 + w["cfg"])[0]
-    job = (U, A, b, w["kappa"], w["csw"])
+    key = (L, w["eps"], w["kappa"], w["csw"], w["cfg"])
+    if key not in _SLAB_JOBS:  # the slab problem is set-up, built once per process
+        import synthetic
+        from oracle import dirac as D
+        U = synthetic.gauge_links(L, w["eps"], 1000 + w["cfg"])
+        A = D.clover_matrix(U, w["kappa"], w["csw"])
+        b = synthetic.z2_noise(L, 1, 3000 + w["cfg"])[0]
+        _SLAB_JOBS[key] = (U, A, b, w["kappa"], w["csw"])
+    job = _SLAB_JOBS[key]
     t_iter = _oracle_all_cores(job, 1, 2)  # one process, one thread
     scale = np.prod(w["L"]) / np.prod(L)
     one = 1.0 / (t_iter * scale * gpu_cgne_iters)
