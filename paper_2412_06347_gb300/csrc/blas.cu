@@ -526,6 +526,22 @@ mglma_status red_scratch_ready(mglma_ctx ctx, cudaStream_t s) {
   return red_scratch(ctx, s, 1, 1, &p, &c);
 }
 
+// accumulators per pass (jm) only matter for MODE 1 (several directions)
+template <typename R, int MODE>
+static void launch_reduce(dim3 g, int jm, const typename Pair<R>::T* xp, size_t js, int k,
+                          const typename Pair<R>::T* yp, size_t m, double2* part, unsigned* count, double2* out2,
+                          double* out1, cudaStream_t s) {
+  if constexpr (MODE == 1) {
+    if (jm == 1) reduce_kernel<R, MODE, 1><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+    if (jm == 2) reduce_kernel<R, MODE, 2><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+    if (jm == 4) reduce_kernel<R, MODE, 4><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+    if (jm == 8) reduce_kernel<R, MODE, 8><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+  } else {
+    (void)jm;
+    reduce_kernel<R, MODE, 1><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
+  }
+}
+
 template <int MODE>
 static mglma_status reduce_impl(mglma_ctx ctx, const Vec& x0, size_t jstride_reals, int k, const Vec* y,
                                 double2* out2, double* out1, cudaStream_t s) {
@@ -538,24 +554,13 @@ static mglma_status reduce_impl(mglma_ctx ctx, const Vec& x0, size_t jstride_rea
   unsigned* count = nullptr;
   MG_CHECK(red_scratch(ctx, s, (size_t)nb * x0.nrhs * nslot, x0.nrhs, &part, &count));
   dim3 g(nb, x0.nrhs, 1);
-  const int jm = MODE != 1 ? 1 : (k <= 1 ? 1 : (k <= 2 ? 2 : (k <= 4 ? 4 : 8)));
-  if (x0.prec == MGLMA_FP64) {
-    const double2* xp = (const double2*)x0.p;
-    const double2* yp = y ? (const double2*)y->p : nullptr;
-    const size_t js = jstride_reals / 2;
-    if (jm == 1) reduce_kernel<double, MODE, 1><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
-    if (jm == 2) reduce_kernel<double, MODE, 2><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
-    if (jm == 4) reduce_kernel<double, MODE, 4><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
-    if (jm == 8) reduce_kernel<double, MODE, 8><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
-  } else {
-    const float4* xp = (const float4*)x0.p;
-    const float4* yp = y ? (const float4*)y->p : nullptr;
-    const size_t js = jstride_reals / 4;
-    if (jm == 1) reduce_kernel<float, MODE, 1><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
-    if (jm == 2) reduce_kernel<float, MODE, 2><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
-    if (jm == 4) reduce_kernel<float, MODE, 4><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
-    if (jm == 8) reduce_kernel<float, MODE, 8><<<g, RT, 0, s>>>(xp, js, k, yp, m, part, count, out2, out1);
-  }
+  const int jm = k <= 1 ? 1 : (k <= 2 ? 2 : (k <= 4 ? 4 : 8));
+  if (x0.prec == MGLMA_FP64)
+    launch_reduce<double, MODE>(g, jm, (const double2*)x0.p, jstride_reals / 2, k,
+                                y ? (const double2*)y->p : nullptr, m, part, count, out2, out1, s);
+  else
+    launch_reduce<float, MODE>(g, jm, (const float4*)x0.p, jstride_reals / 4, k,
+                               y ? (const float4*)y->p : nullptr, m, part, count, out2, out1, s);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }

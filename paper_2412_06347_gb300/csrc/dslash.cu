@@ -772,8 +772,9 @@ static void launch_dslash(const Spinor& in, Spinor& out, const void* U, const vo
 
 // FP32 tile shape (RHS per thread NR, RHS tiles per CTA RW) encoded as
 // NR + 16 (RW - 1); the autotuner (tune.cu) may replace the default below
-// for an RHS count on a context.
-int dslash32_default_tile(int nrhs) { return nrhs >= 4 ? dslash32_tile_code(1, 1) : dslash32_tile_code(1, 1); }
+// for an RHS count on a context.  Measured on GB300 (64x32^3, 1-16 RHS),
+// one RHS per thread and one RHS tile per CTA was fastest at every count.
+int dslash32_default_tile(int) { return dslash32_tile_code(1, 1); }
 
 static void launch_dslash32(int code, const Spinor& in, Spinor& out, const void* U, const void* C,
                             const DslashArgs& a, bool dagger, cudaStream_t s) {
