@@ -69,3 +69,17 @@ def test_free_field_reflection_and_translation():
         assert abs(c[t] - c[L[0] - t]) < 1e-13
     assert np.abs(K.translation_average(Cm) - c).max() < 1e-13
     assert np.all(c.real < 0)  # the sign Eq. tmr gives in the chiral basis
+
+
+def test_correlator_gauge_invariant():
+    """C(x0, y0) of Eq. tmr is a colour trace of gauge-covariant propagators:
+    a random gauge transformation of the links leaves it unchanged (a dropped
+    or misplaced colour index in the trace would not be invariant)."""
+    L = (4, 2, 2, 2)
+    U = synthetic.gauge_links(L, 0.4, 21)
+    g = synthetic.random_su3(L, 1.0, 22)
+    Ug = D.gauge_transform_links(U, g)
+    for y0 in (0, 2):
+        C = K.correlator_from_propagator(_dense_S(L, U, 0.125, 1.3), L, y0)
+        Cg = K.correlator_from_propagator(_dense_S(L, Ug, 0.125, 1.3), L, y0)
+        assert np.abs(Cg - C).max() < 1e-12 * np.abs(C).max()
