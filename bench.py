@@ -18,6 +18,9 @@ consecutive groups of those sources.  The JSON line reports:
 * clocks      -- nvidia-smi samples taken during the timed region.
 
 `--impl reference` runs the oracle alone as the reference arm.
+`--workload c5` serves a seeded Poisson stream over the resident 64x32^3,
+96x48^3 and 128x64^3 lattices; `--micro dslash32|dslash64|coarse|transfer|
+contract` times one kernel class alone.
 Multi-GPU (--gpus N under torchrun): independent replicas, each solving its
 own sources (weak scaling); no collective on the data path.
 """
