@@ -292,30 +292,39 @@ def run_reference(args, w):
 COARSE_SOLVERS = {"gcr": 0, "minres": 1}
 
 
-def run_serving(m, torch, ctx, g, C, w, args, dev, stream):
+def run_serving(m, torch, ctx, g, C, w, args, dev, src_all):
     """Continuous-batching server on the resident lattice: Poisson arrivals
-    (seed 4242, 20 requests/s), RHS per request uniform in 1..max, sources
-    generated on the device, latency from arrival to completion."""
+    (seed 4242, 20 requests/s), RHS per request uniform in 1..max, latency
+    from arrival to completion.  A request of n RHS takes n consecutive
+    sources of the workload's resident set (source buffers are read-only and
+    may be shared); the solutions of every request go to one shared sink of
+    max RHS (the server checks each RHS's FP64 residual itself), so the
+    stream's memory stays bounded however many requests it has."""
     import synthetic
     n = args.serve_requests
     arrivals = synthetic.poisson_arrivals(n, 20.0, 4242)
-    sizes = synthetic.uniform_ints(n, 1, args.serve_max_rhs, 4242, synthetic.TAG_GROUPS)
-    V = int(np.prod(w["L"]))
-    reqs, first = [], 5000
+    sizes = [int(v) for v in synthetic.uniform_ints(n, 1, args.serve_max_rhs, 4242, synthetic.TAG_GROUPS)]
+    nsrc = src_all.shape[0]
+    sink = torch.zeros((max(sizes), src_all.shape[1], 12), dtype=torch.complex128, device=dev)
+    reqs, k = [], 0
     for i in range(n):
-        b = torch.empty((int(sizes[i]), V, 12), dtype=torch.complex128, device=dev)
-        make_sources(m, ctx, w, first, int(sizes[i]), b)
-        first += int(sizes[i])
-        reqs.append(dict(lattice=0, b=b, x=torch.zeros_like(b), arrival=float(arrivals[i])))
+        q = min(sizes[i], nsrc)
+        k0 = k % (nsrc - q + 1)
+        reqs.append(dict(lattice=0, b=src_all[k0:k0 + q], x=sink[:q], arrival=float(arrivals[i])))
+        k += q
     torch.cuda.synchronize()
     prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG, coarse_solver=COARSE_SOLVERS[args.coarse_solver])
     stats, res = m.mglma_serve(ctx, [(g, C)], reqs, prm, max_slots=32, hbm_fraction=0.6)
+    del sink
     ok = all(r["status"] == 0 for r in res)
     resid = max(s["residual"] for r in res for s in r["stats"])
+    offered_rhs = 20.0 * float(np.mean(sizes))
     return {"requests": stats["requests"], "rhs": stats["rhs"], "p50_s": round(stats["p50_s"], 3),
-            "p99_s": round(stats["p99_s"], 3), "mean_s": round(stats["mean_s"], 3),
+            "p99_s": round(stats["p99_s"], 3), "mean_s": round(stats["mean_s"], 3), "max_s": round(stats["max_s"], 3),
             "solves_per_s": round(stats["solves_per_s"], 4), "wall_s": round(stats["wall_s"], 2),
             "offered": "Poisson 20 requests/s (seed 4242), RHS per request uniform in 1.." + str(args.serve_max_rhs),
+            "offered_rhs_per_s": round(offered_rhs, 1), "achieved_rhs_per_s": round(stats["solves_per_s"], 3),
+            "arrival_span_s": round(float(arrivals[-1]), 2),
             "slots": stats["slots"][0], "slot_gb": round(stats["slot_bytes"][0] / 1e9, 2), "all_ok": ok,
             "residual_max": resid}
 
@@ -536,9 +545,13 @@ def main():
     ap.add_argument("--tile", default="", help="FP32 stencil tile NR,RW (RHS per thread, RHS tiles per CTA); "
                                                 "default: the library's choice")
     ap.add_argument("--micro-lattice", default="", help="lattice of --micro mode, e.g. 32x32x32x16 (default: the workload's)")
-    ap.add_argument("--serve-requests", type=int, default=6,
+    ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests of the seeded Poisson stream served after the timed solves (0: skip)")
-    ap.add_argument("--serve-max-rhs", type=int, default=4, help="RHS per request drawn uniformly in 1..this")
+    ap.add_argument("--serve-max-rhs", type=int, default=32, help="RHS per request drawn uniformly in 1..this")
+    ap.add_argument("--prof-steps", type=int, default=2, help="profiled steps after the timed region")
+    ap.add_argument("--e2e-steps", type=int, default=6, help="steps of the end-to-end (host buffer) measurement")
+    ap.add_argument("--cg-batch-iters", type=int, default=40,
+                    help="FP64 CGNE iterations timed on the step's batch (like-for-like plain baseline)")
     args = ap.parse_args()
     if args.workload == "c5":
         if args.impl == "reference":
@@ -587,13 +600,14 @@ def main():
     set_tile(m, ctx, args, G)
 
     nsteps = args.warmup + args.steps
-    # every rank solves its own sources (replicas)
-    base = replica_source_base(rank, G, nsteps)
-    dev_b = []
-    for i in range(nsteps):
-        b = torch.empty((G, V, 12), dtype=torch.complex128, device=dev)
-        make_sources(m, ctx, w, base + i * G, G, b, stream=stream)
-        dev_b.append(b)
+    # The workload's sources, resident in HBM for the whole run: n_sources /
+    # G groups of G (96 / 16 = 6 at 64x32^3, 6.4 GB each); step i solves group
+    # i mod ngroups.  Every rank solves its own sources (replicas).
+    ngroups = max(1, w["n_sources"] // G)
+    base = replica_source_base(rank, G, ngroups)
+    src_all = torch.empty((ngroups * G, V, 12), dtype=torch.complex128, device=dev)
+    make_sources(m, ctx, w, base, ngroups * G, src_all, stream=stream)
+    dev_b = [src_all[i * G:(i + 1) * G] for i in range(ngroups)]
     dev_x = torch.zeros_like(dev_b[0])
     torch.cuda.synchronize()
 
@@ -605,71 +619,93 @@ def main():
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
-            step(i, dev_b[i], dev_x)
+            step(i, dev_b[i % ngroups], dev_x)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    # ---- timed region: sources resident in HBM
+    # ---- timed region: sources resident in HBM, per-launch profiling off
     clocks = Clocks(local)
     clocks.start()
-    m.mglma_profile(ctx, True, True)
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     all_stats = []
     torch.cuda.synchronize()
     t_start.record(stream)
     for i in range(args.warmup, nsteps):
-        all_stats += step(i, dev_b[i], dev_x)
+        all_stats += step(i, dev_b[i % ngroups], dev_x)
     t_end.record(stream)
     torch.cuda.synchronize()
     ms = t_start.elapsed_time(t_end)
     clk = clocks.stop()
-    prof = profile_snapshot(m, ctx)
-    m.mglma_profile(ctx, False, True)
     ms = max_over_ranks(dist, ms)
-    solves = G * args.steps * world
     value = job_throughput(G, args.steps, world, ms / 1e3)
     resid = max(s["residual"] for s in all_stats)
     iters = [s["iterations"] for s in all_stats]
     citers = [s["coarse_iterations"] for s in all_stats]
+    batch = sorted({s["batch"] for s in all_stats})
+
+    # ---- profiled pass (after the timed region): per-launch CUDA events on
+    # the launching stream give the kernel classes' times and algorithmic
+    # bytes; one step with profiling on first, so the profiled coarse graphs
+    # are captured before the measured steps
+    m.mglma_profile(ctx, True, True)
+    with torch.cuda.stream(stream):
+        step(0, dev_b[0], dev_x)
+    torch.cuda.synchronize()
+    m.mglma_profile(ctx, True, True)
+    p_start, p_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p_start.record(stream)
+    for i in range(args.prof_steps):
+        step(i, dev_b[(i + 1) % ngroups], dev_x)
+    p_end.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = p_start.elapsed_time(p_end)
+    prof = profile_snapshot(m, ctx)
+    m.mglma_profile(ctx, False, True)
 
     # ---- end to end: pinned host buffers, copies inside the timed region
     # (each step's sources are placed in the pinned buffer before its timing)
+    e2e_steps = min(args.steps, args.e2e_steps)
     pin_b = torch.empty((G, V, 12), dtype=torch.complex128).pin_memory()
     pin_x = torch.empty_like(pin_b).pin_memory()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e2e_s = 0.0
-    for i in range(args.warmup, nsteps):
-        pin_b.copy_(dev_b[i].cpu())
+    for i in range(e2e_steps):
+        pin_b.copy_(dev_b[i % ngroups].cpu())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         step(0, pin_b, pin_x)
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
     e2e_s = max_over_ranks(dist, e2e_s)
-    e2e = {"value": job_throughput(G, args.steps, world, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": G * V * 24 * 8,
-           "d2h_bytes_per_step": G * V * 24 * 8}
+    e2e = {"value": job_throughput(G, e2e_steps, world, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": G * V * 24 * 8,
+           "d2h_bytes_per_step": G * V * 24 * 8, "steps": e2e_steps}
+    del pin_b, pin_x
 
-    # ---- roofline of the dominant kernel class in the timed region
+    # ---- roofline of the dominant kernel class (profiled pass)
     top = max(((k, v) for k, v in prof.items() if k != "setup"), key=lambda kv: kv[1][1])
     kname, (kl, kms, kbytes, kflops) = top
     achieved = kbytes / (kms / 1e3) / 1e9
-    share = {k: round(v[1] / ms, 4) for k, v in prof.items() if v[0]}
+    share = {k: round(v[1] / prof_ms, 4) for k, v in prof.items() if v[0]}
     dsl = prof.get("dslash32", (0, 0, 0, 0))
-    tps = NCU_TRAFFIC_PER_SITE.get((kname, G))
+    tps = NCU_TRAFFIC_PER_SITE.get((kname, batch[-1]))
     roofline = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": round(tps * V) if tps else None,
                 "bytes_per_launch": round(kbytes / max(kl, 1)),
                 "peak_source": f"{peak_kind} hbm_gbs", "launches": kl, "avg_launch_ms": kms / max(kl, 1),
+                "measured": f"CUDA events on the launching stream, {args.prof_steps} profiled steps after the timed region",
                 "time_share": share,
                 "dslash32": {"achieved": round(dsl[2] / (dsl[1] / 1e3) / 1e9, 1) if dsl[1] else None,
                              "frac": round(dsl[2] / (dsl[1] / 1e3) / 1e9 / hbm, 4) if dsl[1] else None,
-                             "launches": dsl[0]}}
-    # every class is one launch per record except the tensor-core coarse apply,
-    # which writes the B image of X in a first kernel
-    launches = sum(v[0] for v in prof.values()) + prof.get("coarse", (0,))[0]
+                             "launches": dsl[0], "bytes_per_launch": round(dsl[2] / max(dsl[0], 1))}}
+    # launches of the library's kernels in the timed region, from the
+    # profiled steps' count per step: every class is one launch per record
+    # except the tensor-core coarse apply, which writes the B image of X in a
+    # first kernel
+    per_step = (sum(v[0] for v in prof.values()) + prof.get("coarse", (0,))[0]) / max(args.prof_steps, 1)
+    launches = int(round(per_step * args.steps))
 
     # ---- the stencil alone at N = 1 and N = G (the "dslash GB/s vs HBM peak" part of the metric)
     dslash = {}
@@ -682,9 +718,10 @@ def main():
     # ---- serving: a bounded prefix of the seeded Poisson request stream
     serving = None
     if args.serve_requests > 0 and rank == 0:
-        serving = run_serving(m, torch, ctx, g, C, w, args, dev, stream)
+        serving = run_serving(m, torch, ctx, g, C, w, args, dev, src_all)
 
-    # ---- plain FP64 solver on the GPU (bounded sample: one source)
+    # ---- plain FP64 solver on the GPU: one full solve of the first source,
+    # and the same G-RHS batch as a step for a bounded number of iterations
     fp64 = None
     cg_iters = 720 if args.workload == "c4" else 460
     if not args.no_fp64 and rank == 0:
@@ -699,8 +736,26 @@ def main():
         torch.cuda.synchronize()
         t1 = e0.elapsed_time(e1) / 1e3
         cg_iters = s1[0]["iterations"]
+        del b1, x1
+        # like for like: FP64 CGNE on the step's G-RHS batch, cg_batch_iters
+        # iterations timed, extrapolated to the full solve's iteration count
+        pb = m.mglma_solve_params_default(m.MGLMA_SOLVER_CGNE, max_iter=args.cg_batch_iters,
+                                          check_every=args.cg_batch_iters)
+        xb = torch.zeros_like(dev_b[0])
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m.mglma_solve_batch(ctx, g, None, pb, [G], dev_b[0], xb, stream=stream, raise_on_error=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1) / 1e3
+        del xb
+        per_it = tb / args.cg_batch_iters
         fp64 = {"value": 1.0 / t1, "unit": "solves/s", "iterations": cg_iters, "residual": s1[0]["residual"],
-                "sample": "first source of the workload, FP64 CG on the normal equations"}
+                "sample": "first source of the workload, FP64 CG on the normal equations, full solve",
+                "batch": {"value": G / (per_it * cg_iters), "unit": "solves/s", "rhs": G,
+                          "s_per_iteration": round(per_it, 4),
+                          "sample": f"FP64 CGNE on the step's {G}-RHS batch: {args.cg_batch_iters} iterations timed "
+                                    f"(CUDA events), extrapolated to the {cg_iters} iterations of the full solve"}}
     cpu = None
     if not args.no_cpu and rank == 0:
         cpu = cpu_baseline(w, cg_iters)
@@ -717,13 +772,15 @@ def main():
                        "coarse_solver": args.coarse_solver,
                        "setup": f"{w['n_smooth']} MR + {w['n_cg']} CG relaxation steps",
                        "rhs_per_step": G, "global_batch": G * world, "tol": 1e-10,
-                       "l2": "inputs larger than L2 (each source 0.4 GB)", "parallelism": f"replicas x{world}"},
+                       "l2": "inputs larger than L2 (each source 0.4 GB)", "parallelism": f"replicas x{world}",
+                       "sources_resident": f"{ngroups * G} ({ngroups} groups of {G}; step i solves group i mod {ngroups})"},
             "residual_max": resid, "fgcr_iterations": [min(iters), max(iters)],
-            "coarse_iterations": [min(citers), max(citers)],
+            "coarse_iterations": [min(citers), max(citers)], "lockstep_batch": batch,
             "e2e": e2e, "roofline": roofline, "dslash_fp32": dslash, "gpu_launches": launches, "clocks": clk,
             "serving": serving,
             "fp64_plain": fp64,
             "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
+            "speedup_vs_fp64_batch": (value / world / fp64["batch"]["value"]) if fp64 else None,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -319,7 +319,9 @@ typedef struct {
   double coarse_tol;    /* relative tolerance of the preconditioner's coarse solve */
   int coarse_max_iter;  /* cap on coarse iterations per preconditioner call */
   int check_every;      /* host polls residual norms every this many iterations */
-  int max_batch;        /* RHS solved together (0: as many as free HBM allows, <= 64) */
+  int max_batch;        /* RHS solved together (0: as many as 70 % of the memory the
+                           context can use allows -- free HBM plus its pool's idle
+                           cached blocks -- at most 64, split into equal batches) */
   int coarse_solver;    /* mglma_coarse_solver (MG) */
 } mglma_solve_params;
 
@@ -329,6 +331,8 @@ typedef struct {
   long long coarse_iterations; /* coarse-solver iterations (MG) */
   double residual;             /* final FP64 ||b - D x|| / ||b|| */
   int converged;               /* 1 if residual <= tol */
+  int batch;                   /* RHS in the lockstep batch this RHS was solved in
+                                  (mglma_solve_batch); 0 from mglma_serve */
 } mglma_solve_stats;
 
 /* Fills *p with the library defaults for `method`: tol 1e-10; MG: gcr_m 4,

@@ -97,7 +97,7 @@ class mglma_solve_params(C.Structure):
 
 class mglma_solve_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("outer", C.c_int), ("coarse_iterations", C.c_longlong),
-                ("residual", C.c_double), ("converged", C.c_int)]
+                ("residual", C.c_double), ("converged", C.c_int), ("batch", C.c_int)]
 
 
 _sig("mglma_sources", C.c_int, _vp, C.POINTER(mglma_lattice), C.c_int, C.c_int, C.c_uint64, _i64,
@@ -339,7 +339,7 @@ def mglma_solve_batch(ctx, g, coarse, params, group_nrhs, b, x, x_coarse=None, s
     if status != 0 and raise_on_error:
         _check(status)
     out = [dict(iterations=s.iterations, outer=s.outer, coarse_iterations=s.coarse_iterations,
-                residual=s.residual, converged=bool(s.converged)) for s in st[:sum(groups)]]
+                residual=s.residual, converged=bool(s.converged), batch=s.batch) for s in st[:sum(groups)]]
     return status, out
 
 

@@ -126,6 +126,28 @@ void dfree(mglma_ctx, void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
 
+size_t device_room(mglma_ctx ctx, cudaStream_t s) {
+  cudaStreamSynchronize(s);
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  uint64_t reserved = 0, used = 0;
+  if (cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+      cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+    cudaGetLastError();
+    return fr;
+  }
+  return fr + (reserved > used ? (size_t)(reserved - used) : 0);
+}
+
+mglma_status check_gauge_device(mglma_ctx ctx, const mglma_gauge_s* G, const char* who) {
+  if (!G->ctx || G->ctx->device != ctx->device)
+    return fail(MGLMA_ERR_INVALID, std::string(who) + ": gauge field was loaded on another device");
+  return MGLMA_OK;
+}
+
 bool is_device_pointer(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -368,6 +390,7 @@ mglma_status mglma_dirac_apply(mglma_ctx ctx, mglma_gauge G, mglma_op op, int nr
                                mglma_prec compute, void* cuda_stream) {
   if (!ctx || !G || !in || !out) return fail(MGLMA_ERR_INVALID, "mglma_dirac_apply: NULL argument");
   if (!G->ready) return fail(MGLMA_ERR_INVALID, "mglma_dirac_apply: gauge field incomplete");
+  MG_CHECK(check_gauge_device(ctx, G, "mglma_dirac_apply"));
   if (nrhs < 0) return fail(MGLMA_ERR_INVALID, "mglma_dirac_apply: nrhs < 0");
   if (op < MGLMA_OP_D || op > MGLMA_OP_DDAGD) return fail(MGLMA_ERR_INVALID, "mglma_dirac_apply: bad op");
   if (compute != MGLMA_FP64 && compute != MGLMA_FP32)

@@ -758,6 +758,14 @@ mglma_status convert_spinor(mglma_ctx ctx, const Spinor& src, Spinor& dst, cudaS
   return MGLMA_OK;
 }
 
+// algorithmic traffic of one stencil launch: links + clover once, spinor in
+// and out once per RHS (FP32: 4 x 48 B reconstruct-12 links + 288 B clover;
+// FP64: 4 x 144 B links + 576 B clover); 1896 flops per site per RHS
+static double dslash_bytes(int64_t V, int nrhs, bool fp64) {
+  return (double)V * (fp64 ? 1152.0 + 384.0 * nrhs : 480.0 + 192.0 * nrhs);
+}
+static double dslash_flops(int64_t V, int nrhs) { return 1896.0 * (double)V * nrhs; }
+
 template <typename R, int NR, int RW>
 static void launch_dslash(const Spinor& in, Spinor& out, const void* U, const void* C, const DslashArgs& a,
                           bool dagger, cudaStream_t s) {
@@ -806,16 +814,12 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
   a.bc = (double)G->g.t_bc;
   a.nrhs = in.nrhs;
   a.g5out = gamma5_out ? 1 : 0;
-  // algorithmic traffic per site: links + clover once, spinor in and out once
-  // per RHS (FP32: 4 x 48 B reconstruct-12 links + 288 B clover; FP64: 4 x
-  // 144 B links + 576 B clover); 1896 flops per site per RHS
-  const double V = (double)in.V, N = (double)in.nrhs;
-  const double flops = 1896.0 * V * N;
+  const double flops = dslash_flops(in.V, in.nrhs);
   if (in.prec == MGLMA_FP64) {
-    ProfScope ps(ctx, K_DSLASH64, s, V * (1152.0 + 384.0 * N), flops);
+    ProfScope ps(ctx, K_DSLASH64, s, dslash_bytes(in.V, in.nrhs, true), flops);
     launch_dslash<double, 1, 1>(in, out, G->U64, G->C64, a, dagger, s);
   } else {
-    ProfScope ps(ctx, K_DSLASH32, s, V * (480.0 + 192.0 * N), flops);
+    ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(in.V, in.nrhs, false), flops);
     launch_dslash32(tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, dslash32_default_tile(in.nrhs)), in, out, G->U32, G->C32,
                     a, dagger, s);
   }
@@ -836,10 +840,9 @@ mglma_status dslash_dot(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in,
   a.bc = (double)G->g.t_bc;
   a.nrhs = in.nrhs;
   a.g5out = 0;
-  const double V = (double)in.V, N = (double)in.nrhs;
   const int64_t nblk = (in.V + 127) / 128;
   {
-    ProfScope ps(ctx, K_DSLASH32, s, V * (480.0 + 192.0 * N), 1896.0 * V * N);
+    ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(in.V, in.nrhs, false), dslash_flops(in.V, in.nrhs));
     dslash_kernel<float, 1, false, 1, true><<<(unsigned)(nblk * in.nrhs), 128, 0, s>>>(in.p, out.p, G->U32, G->C32,
                                                                                        a, part);
   }
@@ -936,6 +939,7 @@ extern "C" mglma_status mglma_dirac_apply_noalloc(mglma_ctx ctx, mglma_gauge G, 
   using namespace mglma;
   if (!ctx || !G || !in || !out) return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: NULL argument");
   if (!G->ready) return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: gauge field incomplete");
+  MG_CHECK(check_gauge_device(ctx, G, "dirac_apply_noalloc"));
   if (nrhs < 0) return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: nrhs < 0");
   if (op < MGLMA_OP_D || op > MGLMA_OP_DDAGD) return fail(MGLMA_ERR_INVALID, "dirac_apply_noalloc: bad op");
   if (compute != MGLMA_FP64 && compute != MGLMA_FP32)
@@ -967,27 +971,38 @@ extern "C" mglma_status mglma_dirac_apply_noalloc(mglma_ctx ctx, mglma_gauge G, 
   da.g5out = op == MGLMA_OP_Q ? 1 : 0;
   const dim3 pg = site_grid(G->g.V, 256, nrhs);
   const bool dp = compute == MGLMA_FP64;
-  if (dp)
-    pack_kernel<double><<<pg, 256, 0, s>>>(in, a.p, a.V, nrhs);
-  else
-    pack_kernel<float><<<pg, 256, 0, s>>>(in, a.p, a.V, nrhs);
+  const int kd = dp ? K_DSLASH64 : K_DSLASH32;
+  {
+    ProfScope ps(ctx, K_PACK, s);
+    if (dp)
+      pack_kernel<double><<<pg, 256, 0, s>>>(in, a.p, a.V, nrhs);
+    else
+      pack_kernel<float><<<pg, 256, 0, s>>>(in, a.p, a.V, nrhs);
+  }
   const bool dag1 = op == MGLMA_OP_DDAG;
-  if (dp)
-    launch_dslash<double, 1, 1>(a, b, G->U64, G->C64, da, dag1, s);
-  else
-    launch_dslash<float, 1, 1>(a, b, G->U32, G->C32, da, dag1, s);
+  {
+    ProfScope ps(ctx, kd, s, dslash_bytes(G->g.V, nrhs, dp), dslash_flops(G->g.V, nrhs));
+    if (dp)
+      launch_dslash<double, 1, 1>(a, b, G->U64, G->C64, da, dag1, s);
+    else
+      launch_dslash<float, 1, 1>(a, b, G->U32, G->C32, da, dag1, s);
+  }
   const Spinor* res = &b;
   if (op == MGLMA_OP_DDAGD) {  // second pass D^dag back into a
+    ProfScope ps(ctx, kd, s, dslash_bytes(G->g.V, nrhs, dp), dslash_flops(G->g.V, nrhs));
     if (dp)
       launch_dslash<double, 1, 1>(b, a, G->U64, G->C64, da, true, s);
     else
       launch_dslash<float, 1, 1>(b, a, G->U32, G->C32, da, true, s);
     res = &a;
   }
-  if (dp)
-    unpack_kernel<double><<<pg, 256, 0, s>>>(res->p, out, res->V, nrhs);
-  else
-    unpack_kernel<float><<<pg, 256, 0, s>>>(res->p, out, res->V, nrhs);
+  {
+    ProfScope ps(ctx, K_PACK, s);
+    if (dp)
+      unpack_kernel<double><<<pg, 256, 0, s>>>(res->p, out, res->V, nrhs);
+    else
+      unpack_kernel<float><<<pg, 256, 0, s>>>(res->p, out, res->V, nrhs);
+  }
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }

@@ -191,6 +191,12 @@ struct ProfScope {
 mglma_status dalloc(mglma_ctx ctx, void** p, size_t bytes, cudaStream_t s);
 void dfree(mglma_ctx ctx, void* p, cudaStream_t s);
 bool is_device_pointer(const void* p);
+// Bytes the context can still allocate: the device's free memory plus the
+// blocks its pool holds cached but unused (waits for stream s first, so
+// stream-ordered frees have returned to the pool).
+size_t device_room(mglma_ctx ctx, cudaStream_t s);
+// MGLMA_ERR_INVALID unless the gauge field was loaded on ctx's device.
+mglma_status check_gauge_device(mglma_ctx ctx, const mglma_gauge_s* G, const char* who);
 
 // host-or-device staging of one canonical buffer (capi.cu)
 struct Staged {

@@ -394,20 +394,22 @@ struct CoarseSolver {
     reset();
     if (scr) dfree(ctx, scr, s);
   }
+  // destroys one graph set (both execs, its event brackets) and marks it empty
+  static void drop(Graphs& G) {
+    if (G.init) cudaGraphExecDestroy(G.init);
+    if (G.cycle) cudaGraphExecDestroy(G.cycle);
+    G.init = G.cycle = nullptr;
+    G.n = -1;
+    for (auto* L : {&G.ev_init, &G.ev_cycle})
+      for (auto& p : *L) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+      }
+    G.ev_init.clear();
+    G.ev_cycle.clear();
+  }
   void reset() {
-    for (auto& G : g) {
-      if (G.init) cudaGraphExecDestroy(G.init);
-      if (G.cycle) cudaGraphExecDestroy(G.cycle);
-      G.init = G.cycle = nullptr;
-      G.n = -1;
-      for (auto* L : {&G.ev_init, &G.ev_cycle})
-        for (auto& p : *L) {
-          cudaEventDestroy(p.a);
-          cudaEventDestroy(p.b);
-        }
-      G.ev_init.clear();
-      G.ev_cycle.clear();
-    }
+    for (auto& G : g) drop(G);
   }
   bool minres() const { return method == MGLMA_COARSE_MINRES; }
   int cycle_len() const { return minres() ? 12 : m; }
@@ -422,7 +424,18 @@ struct CoarseSolver {
   mglma_status iter(const OpFn& A, Vec& x, int n, int k, double tol) {
     return minres() ? minres_iter(mw, C, x, n, k, tol, scr, scr_bytes) : gcr_iter(w, A, nullptr, x, n, k, tol * tol);
   }
+  // captures the init and cycle graphs of n RHS into G; on any failure G is
+  // left empty (no half-built set survives to be launched)
   mglma_status capture(Graphs& G, const Vec& b, Vec& x, double tol, bool prof) {
+    drop(G);
+    const mglma_status st = capture_parts(G, b, x, tol, prof);
+    if (st != MGLMA_OK) {
+      cudaGetLastError();
+      drop(G);
+    }
+    return st;
+  }
+  mglma_status capture_parts(Graphs& G, const Vec& b, Vec& x, double tol, bool prof) {
     const int n = b.nrhs;
     OpFn A = op();
     for (int part = 0; part < 2; ++part) {
@@ -442,9 +455,11 @@ struct CoarseSolver {
         return st;
       }
       if (e != cudaSuccess) return fail(MGLMA_ERR_CUDA, std::string("coarse graph capture: ") + cudaGetErrorString(e));
-      e = cudaGraphInstantiate(part == 0 ? &G.init : &G.cycle, graph, 0);
+      cudaGraphExec_t ex = nullptr;
+      e = cudaGraphInstantiate(&ex, graph, 0);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return fail(MGLMA_ERR_CUDA, std::string("coarse graph instantiate: ") + cudaGetErrorString(e));
+      (part == 0 ? G.init : G.cycle) = ex;
     }
     G.n = n;
     return MGLMA_OK;
@@ -495,14 +510,7 @@ struct CoarseSolver {
       gtol = tol;
     }
     Graphs& G = g[prof ? 1 : 0];
-    if (G.n != n) {
-      if (G.init) {
-        cudaGraphExecDestroy(G.init);
-        cudaGraphExecDestroy(G.cycle);
-        G.init = G.cycle = nullptr;
-      }
-      MG_CHECK(capture(G, b, x, tol, prof));
-    }
+    if (G.n != n || !G.init || !G.cycle) MG_CHECK(capture(G, b, x, tol, prof));
     MG_CUDA(cudaGraphLaunch(G.init, s));
     int c = 0;
     for (; c < cycles; ++c) {

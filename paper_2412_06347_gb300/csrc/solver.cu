@@ -258,6 +258,7 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
                                mglma_solve_stats* stats, void* cuda_stream) {
   if (!ctx || !G || !prm || !group_nrhs || !b || !x) return fail(MGLMA_ERR_INVALID, "solve_batch: NULL argument");
   if (!G->ready) return fail(MGLMA_ERR_INVALID, "solve_batch: gauge field incomplete");
+  MG_CHECK(check_gauge_device(ctx, G, "solve_batch"));
   if (prm->method != MGLMA_SOLVER_CGNE && prm->method != MGLMA_SOLVER_MG)
     return fail(MGLMA_ERR_INVALID, "solve_batch: unknown method");
   if ((prm->method == MGLMA_SOLVER_MG || x_coarse) && !C)
@@ -286,15 +287,19 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
   MG_CHECK(stage_in(ctx, b, per * total, s, sb));
   MG_CHECK(stage_out_alloc(ctx, x, per * total, s, sx));
   if (x_coarse) MG_CHECK(stage_out_alloc(ctx, x_coarse, per * total, s, sxc));
-  // ragged groups are merged into lockstep batches sized by free HBM
+  // Ragged groups are merged into lockstep batches sized by the memory the
+  // context can still use: free HBM plus the blocks its own pool holds cached
+  // (a batch must not shrink because the library's cache grew).
   int cap = prm->max_batch > 0 ? prm->max_batch : 64;
   if (prm->max_batch <= 0) {
-    size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
+    const size_t room = device_room(ctx, s);
     const size_t per_site = prm->method == MGLMA_SOLVER_CGNE ? 6 * 192 : 4 * 192 + (size_t)(6 + 2 * prm->gcr_m) * 96;
     const size_t per_rhs = per_site * (size_t)V;
-    cap = (int)std::max<size_t>(1, std::min<size_t>(64, (size_t)(0.7 * (double)fr) / per_rhs));
+    cap = (int)std::max<size_t>(1, std::min<size_t>(64, (size_t)(0.7 * (double)room) / per_rhs));
   }
+  // equal lockstep batches: ceil(total / cap) batches of nearly equal size
+  const int nbatch = (total + cap - 1) / cap;
+  cap = (total + nbatch - 1) / nbatch;
   bool all_conv = true;
   for (int off = 0; off < total;) {
     const int n = std::min(cap, total - off);
@@ -342,6 +347,7 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
         o.coarse_iterations = rs[i].coarse_iterations;
         o.residual = rs[i].residual;
         o.converged = rs[i].converged ? 1 : 0;
+        o.batch = n;
       }
     }
     off += n;

@@ -156,6 +156,7 @@ def test_device_pointers_stream_and_slabs(m, ctx):
     dpsi = to_device(psi)
     dout = torch.zeros_like(dpsi)
     s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())  # the copies and the zero fill come first
     with torch.cuda.stream(s):
         m.mglma_dirac_apply(ctx, g2, 0, 3, dpsi, dout, m.MGLMA_FP64, stream=s)
     s.synchronize()

@@ -41,8 +41,10 @@ def test_noalloc_matches_regular_two_calls(env, op, compute, tol):
         psi = torch.from_numpy(synthetic.random_spinors(L, nrhs, seed)).cuda()
         ref = torch.zeros_like(psi)
         got = torch.full_like(psi, float("nan"))
-        m.mglma_dirac_apply(ctx, g, op, nrhs, psi, ref, compute)
-        m.mglma_dirac_apply_noalloc(ctx, g, op, nrhs, psi, got, compute)
+        # both calls run on torch's current stream, after the fills above
+        stream = torch.cuda.current_stream().cuda_stream
+        m.mglma_dirac_apply(ctx, g, op, nrhs, psi, ref, compute, stream=stream)
+        m.mglma_dirac_apply_noalloc(ctx, g, op, nrhs, psi, got, compute, stream=stream)
         torch.cuda.synchronize()
         r, o = ref.cpu().numpy(), got.cpu().numpy()
         err = np.linalg.norm((o - r).reshape(nrhs, -1), axis=1) / np.linalg.norm(r.reshape(nrhs, -1), axis=1)
