@@ -254,6 +254,47 @@ mglma_status mglma_coarse_export(mglma_coarse c, double* dhat);
 mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse c, mglma_op op, int nrhs, const double* in, double* out,
                                 mglma_prec compute, void* cuda_stream);
 
+/* ---------------------------------------------------------------- deeper levels (Sec. "Multigrid decompositions") */
+/* Builds the operator of the next level of the nested block hierarchy,
+ * D_{l+1} = R_l D_l T_l, from the level-l operator `parent` (a handle of
+ * mglma_coarse_build for l = 1, or of this call).  For l >= 1 the paper's
+ * restrictor of a coarse field psi_l on the level-l grid is
+ *   (R_l psi_l)_{alpha c}(y) = sqrt(V_{l+1} / V_l) sum_{z in B_y} psi_{l, alpha c}(z)
+ * (blocks of side block[mu] in level-l sites, each dividing the parent's
+ * grid extent), and T_l = R_l^dag; the Hermitian Q_{l+1} = R_l Q_l T_l of the
+ * paper equals g5hat D_{l+1} because R_l acts per (alpha, c).  D_{l+1} is
+ * again a nine-slot stencil of (2nv x 2nv) blocks on the grid L_l / block
+ * (same slot rules as D1 when an extent is 1 or 2) and every coarse call
+ * (apply, export, info, free) accepts it; store as in mglma_coarse_build.
+ * The parent's FP64 operator must still be held; the new handle refers to
+ * the parent (free the children first).  A grid of one site is the LMA
+ * limit of the hierarchy. */
+mglma_status mglma_coarse_build_next(mglma_ctx ctx, mglma_coarse parent, const int block[4], mglma_prec store,
+                                     mglma_coarse* out);
+/* R_l and T_l between the grid of level l (the parent of `level`) and that
+ * of `level` (level l+1 >= 2): in / out are nrhs canonical coarse fields of
+ * the respective grids (complex128 [rhs][site][2nv], host or device), FP64
+ * arithmetic.  MGLMA_ERR_INVALID for a level-1 handle (use mglma_restrict /
+ * mglma_prolong there). */
+mglma_status mglma_coarse_restrict(mglma_ctx ctx, mglma_coarse level, int nrhs, const double* in, double* out,
+                                   void* cuda_stream);
+mglma_status mglma_coarse_prolong(mglma_ctx ctx, mglma_coarse level, int nrhs, const double* in, double* out,
+                                  void* cuda_stream);
+/* The coarse-level pieces of the telescoping decomposition S = S_0 + ... +
+ * S_{N-1} (Sec. "Multigrid decompositions", Eq. mglma:decomp) for nrhs
+ * sources b: psi[l-1] = calT_l D_l^-1 calR_l b for l = 1 .. nlevels with
+ * calR_l = R_{l-1} ... R_0 and calT_l = T_0 ... T_{l-1} (App. chirality:
+ * calT_l Q_l^-1 calR_l gamma5 = calT_l D_l^-1 calR_l).  levels[0] is a
+ * level-1 operator of g's basis and levels[k] the mglma_coarse_build_next
+ * child of levels[k-1]; each D_l^-1 is solved to relative residual tol by
+ * FP64 defect correction around FP32 GCR on that level's stored operator.
+ * With x = D^-1 b from mglma_solve_batch: S_0 b = x - psi[0], S_l b =
+ * psi[l-1] - psi[l], S_{N-1} b = psi[N-2] (N = nlevels + 1 levels in all).
+ *   b: nrhs canonical spinors; psi: nlevels x nrhs canonical spinors
+ *   ([level][rhs][site][spin][colour]); host or device. */
+mglma_status mglma_pieces(mglma_ctx ctx, mglma_gauge g, const mglma_coarse* levels, int nlevels, int nrhs,
+                          const double* b, double* psi, double tol, void* cuda_stream);
+
 /* ---------------------------------------------------------------- sources (Sec. 5) */
 typedef enum { MGLMA_SOURCE_Z2 = 0, MGLMA_SOURCE_Z4 = 1, MGLMA_SOURCE_POINT = 2 } mglma_source_kind;
 /* Writes nrhs canonical sources to out (host or device):

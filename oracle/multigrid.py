@@ -24,6 +24,17 @@ infrastructure only).
   on application); slot 8 collects the clover term and every hop that stays
   inside B_y.
 
+* Inner levels (Sec. "Multigrid decompositions"): for l >= 1 the restrictor
+  R_l of a coarse field psi_l on the grid Lambda_l sums the components of
+  equal (alpha, c) over the level-l sites z whose block of the next level is
+  y, times sqrt(V_{l+1} / V_l); the prolongator T_l copies psi_{l+1}(y) to
+  every such z with the same factor.  The coarse operator of the next level
+  is Q_{l+1} = R_l Q_l T_l; with Q_l = g5hat D_l and R_l acting per (alpha, c)
+  this is g5hat D_{l+1}, D_{l+1} = R_l D_l T_l, again a nine-slot stencil:
+  slot d < 8 of y collects the slot-d blocks of the sites z of B_y whose
+  slot-d neighbour lies outside B_y, slot 8 the self blocks and every block
+  whose neighbour stays inside, all times V_{l+1} / V_l.
+
 Arrays: the basis is phi[y, alpha, c, k, spin, colour] over the |B| sites k of
 block y (site-in-block order) with the spins of the other chirality zero;
 coarse fields are (V1, 2 N_v) with dof index alpha*N_v + c; a coarse batch
@@ -252,3 +263,77 @@ def dense_prolongator(phi: np.ndarray, L, b) -> np.ndarray:
         e[j] = 1
         cols.append(prolong(phi, e.reshape(V1, n), L, b).reshape(-1))
     return np.stack(cols, axis=1)
+
+
+# ------------------------------------------------------------------ inner levels
+def restrict_level(X: np.ndarray, Lb, b) -> np.ndarray:
+    """R_l X for a coarse field X (V_l, n) on the grid Lb, blocks of side b
+    (in level-l sites): sqrt(V_{l+1}/V_l) times the sum over each block."""
+    if X.ndim == 3:
+        return np.stack([restrict_level(x, Lb, b) for x in X])
+    sites = _lat.block_sites(Lb, b)  # (V_{l+1}, |B|)
+    f = np.sqrt(sites.shape[0] / _lat.volume(Lb))
+    return f * X[sites].sum(axis=1)
+
+
+def prolong_level(Y: np.ndarray, Lb, b) -> np.ndarray:
+    """T_l Y for a field Y (V_{l+1}, n) of the next level: sqrt(V_{l+1}/V_l)
+    times Y at the block of every level-l site."""
+    if Y.ndim == 3:
+        return np.stack([prolong_level(y, Lb, b) for y in Y])
+    blk = _lat.block_of_site(Lb, b)
+    f = np.sqrt(_lat.volume(_lat.block_grid(Lb, b)) / _lat.volume(Lb))
+    return f * Y[blk]
+
+
+def coarse_operator_next(Dhat: np.ndarray, Lb, b) -> np.ndarray:
+    """D_{l+1} = R_l D_l T_l as the nine-slot stencil on the next grid, from
+    the slot-wise stencil Dhat (9, V_l, n, n) of D_l (module docstring)."""
+    Lb = tuple(int(v) for v in Lb)
+    Lb2 = _lat.block_grid(Lb, b)
+    V1, V2 = _lat.volume(Lb), _lat.volume(Lb2)
+    n = Dhat.shape[2]
+    blk = _lat.block_of_site(Lb, b)
+    out = np.zeros((9, V2, n, n), dtype=np.complex128)
+    f = V2 / V1
+    leaves = [_crossing_mask(Lb, b, d).reshape(-1) for d in range(8)]
+    for z in range(V1):
+        y = blk[z]
+        out[8, y] += f * Dhat[8, z]
+        for d in range(8):
+            # a hop that crosses the face of the next-level block keeps its
+            # slot (the neighbour block may be y itself when the next grid has
+            # extent 1 or 2 in that direction); one that stays inside is self
+            out[d if leaves[d][z] else 8, y] += f * Dhat[d, z]
+    return out
+
+
+def dense_restrict_level(Lb, b) -> np.ndarray:
+    """The (V_{l+1} n x V_l n) matrix of R_l for n = 1 (kron with 1_n for n
+    dofs), row y, column z: sqrt(V_{l+1}/V_l) when z lies in B_y."""
+    Lb2 = _lat.block_grid(Lb, b)
+    V1, V2 = _lat.volume(Lb), _lat.volume(Lb2)
+    R = np.zeros((V2, V1))
+    R[_lat.block_of_site(Lb, b), np.arange(V1)] = np.sqrt(V2 / V1)
+    return R
+
+
+def multilevel_pieces(Dhats, Lbs, blocks, phi, L, b0, eta, tol=1e-13):
+    """psi_l = T_l-compound D_l^-1 R_l-compound eta for l = 1 .. N-1 (Sec.
+    "Multigrid decompositions", with Q_l^-1 R gamma5 replaced by D_l^-1 R by
+    App. chirality): Dhats[l-1], Lbs[l-1] are the stencil and grid of level
+    l, blocks[l-1] the blocking from level l to l+1 (len N-2), phi and b0 the
+    level-1 basis and fine blocking.  The telescoping pieces are
+    S_0 eta = x - psi_1, S_l eta = psi_l - psi_{l+1}, S_{N-1} eta = psi_{N-1}."""
+    from . import solvers as _s
+    r = restrict(phi, eta, L, b0)
+    chain = [r]
+    for l in range(1, len(Dhats)):
+        chain.append(restrict_level(chain[-1], Lbs[l - 1], blocks[l - 1]))
+    out = []
+    for l in range(len(Dhats)):
+        X, _, _ = _s.solve_coarse(Dhats[l], chain[l], Lbs[l], tol=tol)
+        for k in range(l, 0, -1):
+            X = prolong_level(X, Lbs[k - 1], blocks[k - 1])
+        out.append(prolong(phi, X, L, b0))
+    return out

@@ -71,6 +71,48 @@ def true_residual(U, x, b, kappa, csw, bc_t=-1.0, A=None) -> float:
     return float(np.sqrt(_norm2(r) / _norm2(b)))
 
 
+def _slab_slices(L0: int, t0: int, t1: int) -> np.ndarray:
+    """Time slices t0 - 1 .. t1 (mod L0): the slab [t0, t1) with one halo
+    slice on each side."""
+    return np.arange(t0 - 1, t1 + 1) % L0
+
+
+def dirac_slab(U, psi, kappa, csw, t0: int, t1: int, bc_t=-1.0) -> np.ndarray:
+    """(D psi)(x) for the time slices t0 <= x0 < t1 of one field, from the
+    links and spinors of slices t0 - 1 .. t1 only.  Every term of D at x
+    (the clover leaves and the hops) touches slices x0 - 1 .. x0 + 1, so D is
+    evaluated by ``dirac`` on the extended slab taken as periodic, and the two
+    halo results -- the only ones that see the artificial wrap -- are dropped.
+    The fermion boundary sign is carried by the halo spinors instead: a halo
+    slice that lies across the lattice's time boundary (t0 = 0 below, t1 = L0
+    above) enters multiplied by bc_t, and the slab is then applied with
+    periodic hops."""
+    L0 = U.shape[0]
+    idx = _slab_slices(L0, t0, t1)
+    Us = U[idx]
+    ps = psi[idx].copy()
+    if t0 == 0:
+        ps[0] *= bc_t
+    if t1 == L0:
+        ps[-1] *= bc_t
+    out = _d.dirac(Us, ps, kappa, csw, 1.0)
+    return out[1:-1]
+
+
+def residual_slabs(U, x, b, kappa, csw, bc_t=-1.0, slab=4) -> float:
+    """||b - D x|| / ||b|| in FP64 for one field, D evaluated ``slab`` time
+    slices at a time (``dirac_slab``), so the clover term and the work arrays
+    never cover more than slab + 2 slices: the oracle's check of a solution
+    on lattices too large for ``true_residual``."""
+    L0 = U.shape[0]
+    rr = 0.0
+    for t0 in range(0, L0, slab):
+        t1 = min(L0, t0 + slab)
+        r = b[t0:t1] - dirac_slab(U, x, kappa, csw, t0, t1, bc_t)
+        rr += _norm2(r)
+    return float(np.sqrt(rr / _norm2(b)))
+
+
 def pieces(U, phi, Dhat, eta, kappa, csw, b, bc_t=-1.0, tol=1e-11):
     """(psi, psi1, psi0) for one source eta: psi = D^-1 eta,
     psi1 = T D1^-1 R eta, psi0 = psi - psi1."""

@@ -86,6 +86,10 @@ _sig("mglma_coarse_release_fp64", C.c_int, _vp)
 _sig("mglma_coarse_info", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_i64))
 _sig("mglma_coarse_export", C.c_int, _vp, _vp)
 _sig("mglma_coarse_apply", C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp)
+_sig("mglma_coarse_build_next", C.c_int, _vp, _vp, C.POINTER(C.c_int), C.c_int, C.POINTER(_vp))
+_sig("mglma_coarse_restrict", C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp)
+_sig("mglma_coarse_prolong", C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp)
+_sig("mglma_pieces", C.c_int, _vp, _vp, C.POINTER(_vp), C.c_int, C.c_int, _vp, _vp, C.c_double, _vp)
 
 
 class mglma_solve_params(C.Structure):
@@ -319,6 +323,28 @@ def mglma_coarse_export(c, dhat):
 def mglma_coarse_apply(ctx, c, nrhs, inp, out, compute=MGLMA_FP64, stream=None, op=MGLMA_OP_D):
     _check(lib.mglma_coarse_apply(_h(ctx), c, int(op), int(nrhs), ptr(inp), ptr(out), int(compute),
                                   _stream_ptr(stream)))
+
+
+def mglma_coarse_build_next(ctx, parent, block, store=MGLMA_BF16):
+    """D_{l+1} = R_l D_l T_l on the grid of the parent's coarse sites blocked by `block`."""
+    out = _vp()
+    _check(lib.mglma_coarse_build_next(_h(ctx), parent, _block(block), int(store), C.byref(out)))
+    return out.value
+
+
+def mglma_coarse_restrict(ctx, level, nrhs, inp, out, stream=None):
+    _check(lib.mglma_coarse_restrict(_h(ctx), level, int(nrhs), ptr(inp), ptr(out), _stream_ptr(stream)))
+
+
+def mglma_coarse_prolong(ctx, level, nrhs, inp, out, stream=None):
+    _check(lib.mglma_coarse_prolong(_h(ctx), level, int(nrhs), ptr(inp), ptr(out), _stream_ptr(stream)))
+
+
+def mglma_pieces(ctx, g, levels, nrhs, b, psi, tol=1e-10, stream=None):
+    """psi[l-1] = calT_l D_l^-1 calR_l b for the chain of coarse levels."""
+    arr = (_vp * len(levels))(*levels)
+    _check(lib.mglma_pieces(_h(ctx), g, arr, len(levels), int(nrhs), ptr(b), ptr(psi), float(tol),
+                            _stream_ptr(stream)))
 
 
 def mglma_solve_params_default(method=MGLMA_SOLVER_MG, **overrides):

@@ -239,6 +239,26 @@ mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X
 mglma_status dslash_slot64_batch(mglma_ctx ctx, const mglma_gauge_s* G, const int block[4], const Spinor& in,
                                  Spinor& out, int slot, cudaStream_t s);
 
+mglma_status coarse_store_copies(mglma_ctx ctx, mglma_coarse_s* Cc, int store, cudaStream_t s) {
+  const size_t na = (size_t)Cc->geo.V1 * 9 * Cc->n2 * Cc->n2;
+  cudaError_t e = cudaSuccess;
+  if (store == MGLMA_FP32) {
+    e = cudaMalloc(&Cc->A32, na * sizeof(float2));
+    if (e == cudaSuccess) a_to32_kernel<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(Cc->A64, Cc->A32, na);
+  } else if (store == MGLMA_BF16 && coarse_tc_supported(Cc->n2)) {
+    MG_CHECK(coarse_tc_image(ctx, Cc, s));  // tensor-core operand image
+  } else if (store == MGLMA_BF16) {
+    e = cudaMalloc(&Cc->A16, na * sizeof(__nv_bfloat162));
+    if (e == cudaSuccess) a_to16_kernel<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(Cc->A64, Cc->A16, na);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MGLMA_ERR_OOM, "coarse operator: cannot allocate the low-precision copy");
+  }
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
 }  // namespace mglma
 
 using namespace mglma;
@@ -308,19 +328,7 @@ mglma_status mglma_coarse_build(mglma_ctx ctx, mglma_gauge G, mglma_subspace S, 
     }
   }
   if (st == MGLMA_OK && cudaGetLastError() != cudaSuccess) st = fail(MGLMA_ERR_CUDA, "coarse_build: launch failed");
-  if (st == MGLMA_OK) {
-    cudaError_t e = cudaSuccess;
-    if (store == MGLMA_FP32) {
-      e = cudaMalloc(&Cc->A32, na * sizeof(float2));
-      if (e == cudaSuccess) a_to32_kernel<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(Cc->A64, Cc->A32, na);
-    } else if (store == MGLMA_BF16 && coarse_tc_supported(n2)) {
-      st = coarse_tc_image(ctx, Cc, s);  // tensor-core operand image
-    } else if (store == MGLMA_BF16) {
-      e = cudaMalloc(&Cc->A16, na * sizeof(__nv_bfloat162));
-      if (e == cudaSuccess) a_to16_kernel<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(Cc->A64, Cc->A16, na);
-    }
-    if (e != cudaSuccess) st = fail(MGLMA_ERR_OOM, "coarse_build: cannot allocate the low-precision operator");
-  }
+  if (st == MGLMA_OK) st = coarse_store_copies(ctx, Cc, store, s);
   cudaError_t e = cudaStreamSynchronize(s);
   cudaMemPoolTrimTo(ctx->pool, 0);  // hand the build's work fields back to the device
   if (st == MGLMA_OK && e != cudaSuccess) st = fail(MGLMA_ERR_CUDA, cudaGetErrorString(e));

@@ -38,6 +38,12 @@ struct mglma_coarse_s {
   __nv_bfloat162* A16 = nullptr; // same layout, BF16 (re, im)
   uint16_t* Aimg = nullptr;      // BF16 tensor-core image, see coarse_tc.cu
   int* tc_err = nullptr;         // device error flag of the tensor-core kernel
+  // level of the hierarchy: 1 for D1 = R0 D T0 (geo: fine lattice -> block
+  // grid); l >= 2 for D_l = R_{l-1} D_{l-1} T_{l-1}, built by aggregation
+  // from `parent` (geo: level l-1 grid -> level l grid, geo.V = V_{l-1},
+  // geo.V1 = V_l; sub is the level-1 basis of the chain)
+  int level = 1;
+  const mglma_coarse_s* parent = nullptr;
 };
 
 namespace mglma {
@@ -75,5 +81,16 @@ constexpr int CMODE_D = 0, CMODE_Q = 2, CMODE_DDAG = 3;
 // scratch (optional): work space of the tensor-core path, see coarse_apply_tc
 mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X, void* Y, int nrhs, int prec,
                           int mode, cudaStream_t s, void* scratch = nullptr, size_t scratch_bytes = 0);
+// the copy the FP32 solvers read (FP32, BF16 tensor-core image or BF16 plain)
+// from the FP64 master A64
+mglma_status coarse_store_copies(mglma_ctx ctx, mglma_coarse_s* Cc, int store, cudaStream_t s);
+// inner-level transfers between the grids of Cc->parent (level l-1) and Cc
+// (level l), FP64 or FP32 internal coarse fields [rhs][V][n2]:
+//   restrict: out(y) = sqrt(V_l / V_{l-1}) sum_{z in B_y} in(z)
+//   prolong:  out(z) = sqrt(V_l / V_{l-1}) in(y(z)) (+ out when accumulate)
+mglma_status restrict_level(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* in, void* out, int nrhs, int prec,
+                            cudaStream_t s);
+mglma_status prolong_level(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* in, void* out, int nrhs, int prec,
+                           bool accumulate, cudaStream_t s);
 
 }  // namespace mglma

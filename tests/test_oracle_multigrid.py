@@ -216,3 +216,37 @@ def test_cg_relaxation_filters_towards_low_modes():
     assert frac[0] < frac[1] < frac[2] and frac[2] > 0.8
     # zero steps is the identity; the step is the CG minimiser along the first direction
     assert np.array_equal(MG.cg_relax(U, x0, kappa, csw, 0), x0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_cg_relaxation_is_the_krylov_minimiser(n):
+    """CG on the normal equations D^dag D x = 0 from x0 is, after n steps, the
+    unique minimiser of ||D x|| over x0 + K_n(D^dag D, D^dag D x0) -- the
+    defining property of CG (it minimises the D^dag D-norm of the error, and
+    the solution is 0).  The minimiser is computed independently: an
+    orthonormal basis of the Krylov space from the dense D, then least
+    squares.  A wrong step length, a wrong beta or a dropped direction gives
+    another point of the affine space and fails."""
+    L = (4, 2, 2, 2)
+    U = synthetic.gauge_links(L, 0.3, 83)
+    kappa, csw = 0.125, 1.2
+    M = D.dense_dirac(U, kappa, csw)
+    x0 = synthetic.gaussian_start_vectors(L, 1, 84)[0].reshape(-1)
+    N = M.conj().T @ M
+    # Arnoldi (two Gram-Schmidt passes per vector) on N from N x0: an
+    # orthonormal basis of K_n without the power basis's ill-conditioning
+    Qk = np.empty((x0.size, n), dtype=np.complex128)
+    v = N @ x0
+    for j in range(n):
+        for _ in range(2):
+            v = v - Qk[:, :j] @ (Qk[:, :j].conj().T @ v)
+        Qk[:, j] = v / np.linalg.norm(v)
+        v = N @ Qk[:, j]
+    c, *_ = np.linalg.lstsq(M @ Qk, -(M @ x0), rcond=None)
+    x_min = x0 + Qk @ c
+    x_cg = MG.cg_relax(U, x0.reshape(L + (4, 3)), kappa, csw, n).reshape(-1)
+    assert np.linalg.norm(x_cg - x_min) / np.linalg.norm(x_min) < 1e-12
+    # and it is a strict improvement on the previous step's minimiser
+    if n > 1:
+        x_prev = MG.cg_relax(U, x0.reshape(L + (4, 3)), kappa, csw, n - 1).reshape(-1)
+        assert np.linalg.norm(M @ x_cg) < np.linalg.norm(M @ x_prev)
