@@ -289,7 +289,7 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
-COARSE_SOLVERS = {"gcr": 0, "minres": 1}
+COARSE_SOLVERS = {"gcr": 0, "minres": 1, "minres_eo": 2}
 
 
 def run_serving(m, torch, ctx, g, C, w, args, dev, src_all):
@@ -446,7 +446,9 @@ def micro_dslash(m, torch, ctx, g, V, nrhs, prec, reps, stream):
 
 def set_tile(m, ctx, args, nrhs):
     """--tile NR,RW fixes the FP32 stencil's tile shape for nrhs RHS."""
-    if args.tile:
+    if args.tile.startswith("s"):
+        m.mglma_autotune_set(ctx, 0, nrhs, m.dslash32_staged_code(int(args.tile[1:])))
+    elif args.tile:
         nr, rw = (int(v) for v in args.tile.split(","))
         m.mglma_autotune_set(ctx, 0, nrhs, m.dslash32_tile_code(nr, rw))
 
@@ -542,7 +544,8 @@ def main():
     ap.add_argument("--micro", default="", choices=["", "dslash32", "dslash64", "coarse", "transfer", "contract"],
                     help="time one kernel class on the workload lattice instead of the solve")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch in --micro mode")
-    ap.add_argument("--tile", default="", help="FP32 stencil tile NR,RW (RHS per thread, RHS tiles per CTA); "
+    ap.add_argument("--tile", default="", help="FP32 stencil tile NR,RW (RHS per thread, RHS tiles per CTA) or sNRT "
+                                                "(staged-tile kernel, 32 sites x NRT RHS per CTA, NRT 4, 8, 16); "
                                                 "default: the library's choice")
     ap.add_argument("--micro-lattice", default="", help="lattice of --micro mode, e.g. 32x32x32x16 (default: the workload's)")
     ap.add_argument("--serve-requests", type=int, default=40,

@@ -68,10 +68,13 @@ typedef enum {
 typedef enum { MGLMA_FP64 = 0, MGLMA_FP32 = 1, MGLMA_BF16 = 2, MGLMA_FP16 = 3 } mglma_prec;
 
 typedef enum {
-  MGLMA_OP_D = 0,     /* D                 */
-  MGLMA_OP_DDAG = 1,  /* D^dag = g5 D g5   */
-  MGLMA_OP_Q = 2,     /* Q = gamma5 D (Sec. 2) */
-  MGLMA_OP_DDAGD = 3  /* D^dag D           */
+  MGLMA_OP_D = 0,        /* D                 */
+  MGLMA_OP_DDAG = 1,     /* D^dag = g5 D g5   */
+  MGLMA_OP_Q = 2,        /* Q = gamma5 D (Sec. 2) */
+  MGLMA_OP_DDAGD = 3,    /* D^dag D           */
+  MGLMA_OP_SCHUR = 4,    /* coarse only: S_ee = D_ee - D_eo D_oo^-1 D_oe, the
+                            even-odd preconditioned operator on the even sites */
+  MGLMA_OP_SCHUR_Q = 5   /* coarse only: g5hat S_ee (Hermitian) */
 } mglma_op;
 
 typedef struct {
@@ -250,6 +253,13 @@ mglma_status mglma_coarse_export(mglma_coarse c, double* dhat);
  *                  gamma5-hermiticity from D because the basis is split by
  *                  chirality (Sec. 2, App. chirality)
  *   MGLMA_OP_Q     Q1 = g5hat D1, the Hermitian coarse operator of Sec. 2
+ *   MGLMA_OP_SCHUR / MGLMA_OP_SCHUR_Q
+ *                  S_ee = D_ee - D_eo D_oo^-1 D_oe (or g5hat S_ee) of the
+ *                  even-odd decomposition (sites of even y0 + y1 + y2 + y3):
+ *                  reads the even sites of in, writes the even sites of out
+ *                  and zero on the odd ones.  Every coarse extent must be
+ *                  even; the first such call forms the self-block inverses
+ *                  from the FP64 operator (which must be held).
  * MGLMA_OP_DDAGD is rejected with MGLMA_ERR_INVALID. */
 mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse c, mglma_op op, int nrhs, const double* in, double* out,
                                 mglma_prec compute, void* cuda_stream);
@@ -294,6 +304,32 @@ mglma_status mglma_coarse_prolong(mglma_ctx ctx, mglma_coarse level, int nrhs, c
  *   ([level][rhs][site][spin][colour]); host or device. */
 mglma_status mglma_pieces(mglma_ctx ctx, mglma_gauge g, const mglma_coarse* levels, int nlevels, int nrhs,
                           const double* b, double* psi, double tol, void* cuda_stream);
+
+/* ---------------------------------------------------------------- exact coarsest level (Sec. "Exact estimator on the coarsest grid") */
+/* Coarse matrices of gamma5 gamma_k with an open fine time index (Eq.
+ * coarse:gamma):  Gam_k(x0) = calR gamma5 gamma_k P_{x0} calT on the grid of
+ * `level` (calR, calT the compound transfers from the fine lattice), k = 1,
+ * 2, 3.  They are block-diagonal over coarse sites: out receives complex128
+ * [L0][V_c][2nv][2nv], block y of slice x0 (zero when block y does not meet
+ * the fine time slice x0), host or device.  Level 1 computes them from the
+ * basis (phi_i^dag gamma5 gamma_k phi_j summed over the block's sites on the
+ * slice); deeper levels sum them over a block times V_{l+1} / V_l. */
+mglma_status mglma_coarse_gamma5_gamma(mglma_ctx ctx, mglma_coarse level, int k, double* out);
+/* Q_c^-1 of the Hermitian coarse operator Q_c = g5hat D_c of `level` as a
+ * dense complex128 n x n matrix (n = V_c 2nv <= 16384, row index
+ * site * 2nv + dof), formed in FP64 by Gauss-Jordan elimination with partial
+ * pivoting on the device (n^3 complex multiply-adds; the level's FP64
+ * operator must be held).  MGLMA_ERR_NUMERIC if Q_c is singular. */
+mglma_status mglma_coarse_dense_inverse(mglma_ctx ctx, mglma_coarse level, double* out);
+/* The exact estimator of the coarsest level's correlator (Eq. G_LL:exact):
+ *   corr[x0][y0] = -(1 / (3 L1 L2 L3)) sum_{k=1}^{3} tr{Gam_k(y0) Q_c^-1 Gam_k(x0) Q_c^-1}
+ *   G[t]         = (1 / L0) sum_{y0} corr[(t + y0) mod L0][y0]   (Eq. timetrans)
+ * complex128, corr [L0][L0] and G [L0] (either may be NULL), host or device.
+ * This is C_ll of the level's coarse propagator calT D_c^-1 calR (App.
+ * chirality), averaged over the whole lattice with no noise; Q_c^-1 as in
+ * mglma_coarse_dense_inverse (n <= 16384, at most 80 dofs per site).  Sums
+ * run in a fixed order. */
+mglma_status mglma_exact_correlator(mglma_ctx ctx, mglma_coarse level, double* corr, double* G);
 
 /* ---------------------------------------------------------------- sources (Sec. 5) */
 typedef enum { MGLMA_SOURCE_Z2 = 0, MGLMA_SOURCE_Z4 = 1, MGLMA_SOURCE_POINT = 2 } mglma_source_kind;
@@ -343,11 +379,20 @@ typedef enum {
 
 /* Solver of the coarse system inside the MG preconditioner. */
 typedef enum {
-  MGLMA_COARSE_GCR = 0,    /* restarted GCR(16) on D1 */
-  MGLMA_COARSE_MINRES = 1  /* MINRES on the Hermitian Q1 = g5hat D1 (Sec. 2),
-                              solving Q1 e = g5hat b: a three-term Lanczos
-                              recurrence, no restarts, about a third of the
-                              vector traffic of GCR per iteration */
+  MGLMA_COARSE_GCR = 0,       /* restarted GCR(16) on D1 */
+  MGLMA_COARSE_MINRES = 1,    /* MINRES on the Hermitian Q1 = g5hat D1 (Sec. 2),
+                                 solving Q1 e = g5hat b: a three-term Lanczos
+                                 recurrence, no restarts, about a third of the
+                                 vector traffic of GCR per iteration */
+  MGLMA_COARSE_MINRES_EO = 2  /* MINRES on g5hat S_ee, the even-odd (Schur)
+                                 preconditioned coarse operator S_ee = D_ee -
+                                 D_eo D_oo^-1 D_oe on the even coarse sites, the
+                                 odd sites by back-substitution (the paper's
+                                 coarse solves use the even-odd preconditioned
+                                 coarse operator, Sec. "Comparison of the
+                                 cost"); every coarse extent must be even and
+                                 the FP64 coarse operator held (the self-block
+                                 inverses are formed from it on first use) */
 } mglma_coarse_solver;
 
 typedef struct {
@@ -364,6 +409,10 @@ typedef struct {
                            context can use allows -- free HBM plus its pool's idle
                            cached blocks -- at most 64, split into equal batches) */
   int coarse_solver;    /* mglma_coarse_solver (MG) */
+  int autotune;         /* MG: 1 = the first lockstep batch of each (lattice, RHS
+                           bucket) tunes the stencil and coarse tile shapes
+                           (mglma_autotune) before it runs; 0 = use the table as
+                           it stands (defaults where empty) */
 } mglma_solve_params;
 
 typedef struct {
@@ -378,8 +427,8 @@ typedef struct {
 
 /* Fills *p with the library defaults for `method`: tol 1e-10; MG: gcr_m 4,
  * nu 7, inner_tol 3e-6, coarse_tol 0.02, coarse_max_iter 108 (whole cycles
- * of 12 MINRES iterations), coarse_solver MINRES, check_every 1, max_batch 0;
- * CGNE: max_iter 100000, check_every 20. */
+ * of 12 MINRES iterations), coarse_solver MINRES, check_every 1, max_batch 0,
+ * autotune 1; CGNE: max_iter 100000, check_every 20, autotune 0. */
 void mglma_solve_params_default(mglma_solve_params* p, int method);
 
 /* Solves D x = b (x = S b, the propagator of Sec. 2 applied to b) for
@@ -462,12 +511,15 @@ mglma_status mglma_serve(mglma_ctx ctx, const mglma_serve_config* cfg, mglma_req
 
 /* ---------------------------------------------------------------- autotuning */
 /* Times the candidate RHS tile widths for nrhs right-hand sides with CUDA
- * events and keeps the fastest in the context (used by every later call
- * with an RHS count in the same power-of-two bucket):
+ * events and keeps the fastest in the context, per lattice volume (used by
+ * every later call on a lattice of that volume with an RHS count in the same
+ * power-of-two bucket):
  *   kernel 0: tile shape of the FP32 stencil, needs g: NR right-hand sides
  *     per thread (1, 2, 4) and RW RHS tiles per 128-thread CTA (1, 2, 4;
  *     a CTA then covers 128 / RW sites), coded NR + 16 (RW - 1) (NR = 4 only
- *     with RW = 1);
+ *     with RW = 1); or the staged-tile kernel, 32 sites x NRT RHS per CTA
+ *     with each site's links and clover staged once in shared memory, coded
+ *     64 + NRT (NRT = 4, 8, 16);
  *   kernel 1: RHS per tile of the tensor-core coarse stencil (8, 16, 32), needs c.
  * g or c may be NULL to skip that kernel. */
 mglma_status mglma_autotune(mglma_ctx ctx, mglma_gauge g, mglma_coarse c, int nrhs);
@@ -476,8 +528,12 @@ mglma_status mglma_autotune(mglma_ctx ctx, mglma_gauge g, mglma_coarse c, int nr
 mglma_status mglma_autotune_set(mglma_ctx ctx, int kernel, int nrhs, int choice);
 /* The tuned choice (0 if none) and its time in ms for kernel / nrhs. */
 mglma_status mglma_autotune_get(mglma_ctx ctx, int kernel, int nrhs, int* choice, double* ms);
-/* Text cache of the tuned table, one line per entry, keyed by GPU name;
- * entries of other GPUs are ignored on load. */
+/* Text cache of the tuned table, one line per entry (GPU name, kernel, RHS
+ * bucket, lattice volume -- 0 for entries set by mglma_autotune_set --,
+ * choice, ms); entries of other GPUs are ignored on load.  When the
+ * environment variable MGLMA_TUNE_CACHE names a file, mglma_create loads it
+ * (if it exists) and the solver saves the table there after each automatic
+ * tuning. */
 mglma_status mglma_autotune_save(mglma_ctx ctx, const char* path);
 mglma_status mglma_autotune_load(mglma_ctx ctx, const char* path);
 

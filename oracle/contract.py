@@ -23,6 +23,22 @@ gamma5); the pin in tests/test_oracle_contract.py checks that identity.
 
 Eq. timetrans: the translation average G(t) = (1 / L0) sum_{y0} C(t + y0, y0)
 (``translation_average``), with x0 taken modulo L0.
+
+Sec. "Exact estimator on the coarsest grid" (Eq. G_LL:exact): on a coarse
+level small enough to invert densely, the level's contribution to G(t) is
+
+    G(t) = -(1 / (3 L0 L^3)) sum_k sum_{y0} tr{ Gam_k(y0 + t) Q_c^-1 Gam_k(y0) Q_c^-1 }
+
+with Q_c = g5hat D_c the Hermitian coarse operator and the coarse matrices
+Gam_k(x0) = calR gamma5 gamma_k P_{x0} calT (P_{x0} keeps fine time slice
+x0), the open-index analogue of Eq. coarse:gamma.  On level 1 they are
+block-diagonal over coarse sites: Gam_k(x0)[y] = sum_{x in B_y, time x0}
+phi_i(x)^dag gamma5 gamma_k phi_j(x); an inner-level transfer keeps them
+block-diagonal, Gam(x0)[y] on level l + 1 = (V_{l+1} / V_l) sum_{z in B_y}
+Gam(x0)[z] on level l.  ``exact_coarse_correlator`` evaluates the trace
+formula from the dense inverse; the pin in tests/test_oracle_exact.py
+compares it with C_11 of Eq. lma:ee summed from the dense coarse-level
+propagator calT D_c^-1 calR (App. chirality) on the fine lattice.
 """
 from __future__ import annotations
 
@@ -82,3 +98,62 @@ def translation_average(C: np.ndarray) -> np.ndarray:
     indexed [x0, y0]."""
     L0 = C.shape[0]
     return np.array([sum(C[(t + y0) % L0, y0] for y0 in range(L0)) / L0 for t in range(L0)])
+
+
+def coarse_gamma5_gamma(phi: np.ndarray, L, b, k: int) -> np.ndarray:
+    """Gam_k(x0) on level 1 for every fine time slice x0: array (L0, V1, n, n),
+    block y of slice x0 = sum over the sites x of B_y on slice x0 of
+    phi_i(x)^dag gamma5 gamma_k phi_j(x) (zero when B_y misses x0); phi as in
+    ``multigrid.build_basis``."""
+    from . import lattice as _lat
+    L = tuple(int(v) for v in L)
+    V1, _, nv = phi.shape[:3]
+    n = 2 * nv
+    sites = _lat.block_sites(L, b)  # (V1, nB)
+    x0_of = _lat.coords(L)[:, 0]
+    G5k = gamma5_gamma(k)
+    out = np.zeros((L[0], V1, n, n), dtype=np.complex128)
+    ph = phi.reshape(V1, n, phi.shape[3], 4, 3)  # (y, i, site-in-block, spin, colour)
+    for y in range(V1):
+        gphi = np.einsum("st,jktc->jksc", G5k, ph[y])
+        for kk, site in enumerate(sites[y]):
+            x0 = x0_of[site]
+            out[x0, y] += np.einsum("isc,jsc->ij", np.conj(ph[y][:, kk]), gphi[:, kk])
+    return out
+
+
+def coarse_gamma_next(Gam: np.ndarray, Lb, b) -> np.ndarray:
+    """Gam(x0) on the next level: (V_{l+1} / V_l) times the sum of the blocks
+    of the level-l sites of each next-level block."""
+    from . import lattice as _lat
+    Lb2 = _lat.block_grid(Lb, b)
+    V1, V2 = _lat.volume(Lb), _lat.volume(Lb2)
+    blk = _lat.block_of_site(Lb, b)
+    out = np.zeros((Gam.shape[0], V2) + Gam.shape[2:], dtype=np.complex128)
+    for z in range(V1):
+        out[:, blk[z]] += Gam[:, z]
+    return out * (V2 / V1)
+
+
+def exact_coarse_correlator(Dhat: np.ndarray, Lb, Gams, L) -> tuple:
+    """(C, G): C[x0, y0] = -(1 / (3 L^3)) sum_k tr{Gam_k(y0) Q^-1 Gam_k(x0) Q^-1}
+    and its translation average G(t) (Eq. G_LL:exact), Q = g5hat D_c dense,
+    Gams[k-1] = Gam_k as from ``coarse_gamma5_gamma`` / ``coarse_gamma_next``."""
+    from . import multigrid as _mg
+    L = tuple(int(v) for v in L)
+    n = Dhat.shape[2]
+    V1 = Dhat.shape[1]
+    g5 = np.tile(_mg.coarse_gamma5(n // 2), V1)
+    Qi = np.linalg.inv(g5[:, None] * _mg.dense_coarse(Dhat, Lb))
+    L0 = L[0]
+    C = np.zeros((L0, L0), dtype=np.complex128)
+    for Gam in Gams:
+        dense = [np.zeros((V1 * n, V1 * n), dtype=np.complex128) for _ in range(L0)]
+        for t in range(L0):
+            for y in range(V1):
+                dense[t][y * n:(y + 1) * n, y * n:(y + 1) * n] = Gam[t, y]
+        for x0 in range(L0):
+            for y0 in range(L0):
+                C[x0, y0] += np.trace(dense[y0] @ Qi @ dense[x0] @ Qi)
+    C *= -1.0 / (3.0 * (int(np.prod(L)) // L0))
+    return C, translation_average(C)

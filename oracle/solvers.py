@@ -77,7 +77,7 @@ def _slab_slices(L0: int, t0: int, t1: int) -> np.ndarray:
     return np.arange(t0 - 1, t1 + 1) % L0
 
 
-def dirac_slab(U, psi, kappa, csw, t0: int, t1: int, bc_t=-1.0) -> np.ndarray:
+def dirac_slab(U, psi, kappa, csw, t0: int, t1: int, bc_t=-1.0, A=None) -> np.ndarray:
     """(D psi)(x) for the time slices t0 <= x0 < t1 of one field, from the
     links and spinors of slices t0 - 1 .. t1 only.  Every term of D at x
     (the clover leaves and the hops) touches slices x0 - 1 .. x0 + 1, so D is
@@ -86,7 +86,8 @@ def dirac_slab(U, psi, kappa, csw, t0: int, t1: int, bc_t=-1.0) -> np.ndarray:
     The fermion boundary sign is carried by the halo spinors instead: a halo
     slice that lies across the lattice's time boundary (t0 = 0 below, t1 = L0
     above) enters multiplied by bc_t, and the slab is then applied with
-    periodic hops."""
+    periodic hops.  A (optional) is the clover matrix of the extended slab's
+    links, ``dirac.clover_matrix(U[slices t0 - 1 .. t1])``."""
     L0 = U.shape[0]
     idx = _slab_slices(L0, t0, t1)
     Us = U[idx]
@@ -95,22 +96,27 @@ def dirac_slab(U, psi, kappa, csw, t0: int, t1: int, bc_t=-1.0) -> np.ndarray:
         ps[0] *= bc_t
     if t1 == L0:
         ps[-1] *= bc_t
-    out = _d.dirac(Us, ps, kappa, csw, 1.0)
+    out = _d.dirac(Us, ps, kappa, csw, 1.0, A)
     return out[1:-1]
 
 
-def residual_slabs(U, x, b, kappa, csw, bc_t=-1.0, slab=4) -> float:
-    """||b - D x|| / ||b|| in FP64 for one field, D evaluated ``slab`` time
-    slices at a time (``dirac_slab``), so the clover term and the work arrays
-    never cover more than slab + 2 slices: the oracle's check of a solution
-    on lattices too large for ``true_residual``."""
+def residual_slabs(U, x, b, kappa, csw, bc_t=-1.0, slab=4):
+    """||b - D x|| / ||b|| in FP64, D evaluated ``slab`` time slices at a
+    time (``dirac_slab``), so the clover term and the work arrays never cover
+    more than slab + 2 slices: the oracle's check of a solution on lattices
+    too large for ``true_residual``.  x, b: one field, or a batch (n, L...,
+    4, 3) sharing each slab's clover term; returns a float, or n floats."""
+    one = x.ndim == 6
+    xs, bs = (x[None], b[None]) if one else (x, b)
     L0 = U.shape[0]
-    rr = 0.0
+    rr = np.zeros(len(xs))
     for t0 in range(0, L0, slab):
         t1 = min(L0, t0 + slab)
-        r = b[t0:t1] - dirac_slab(U, x, kappa, csw, t0, t1, bc_t)
-        rr += _norm2(r)
-    return float(np.sqrt(rr / _norm2(b)))
+        A = _d.clover_matrix(U[_slab_slices(L0, t0, t1)], kappa, csw)
+        for i in range(len(xs)):
+            rr[i] += _norm2(bs[i][t0:t1] - dirac_slab(U, xs[i], kappa, csw, t0, t1, bc_t, A))
+    res = np.sqrt(rr / np.array([_norm2(v) for v in bs]))
+    return float(res[0]) if one else res
 
 
 def pieces(U, phi, Dhat, eta, kappa, csw, b, bc_t=-1.0, tol=1e-11):
@@ -122,3 +128,40 @@ def pieces(U, phi, Dhat, eta, kappa, csw, b, bc_t=-1.0, tol=1e-11):
     X, _, _ = solve_coarse(Dhat, _mg.restrict(phi, eta, L, b), Lb, tol * 0.1)
     psi1 = _mg.prolong(phi, X, L, b)
     return psi, psi1, psi - psi1
+
+
+# ------------------------------------------------------------------ even-odd (Schur) preconditioning
+def parity(L) -> np.ndarray:
+    """(x0 + x1 + x2 + x3) mod 2 of every site, flat site order."""
+    from . import lattice as _lat
+    return (_lat.coords(L).sum(axis=1) % 2).astype(np.int64)
+
+
+def eo_blocks(M: np.ndarray, par: np.ndarray, ndof: int):
+    """The four parity blocks (ee, eo, oe, oo) of a dense operator M on sites
+    with `ndof` components each (site-major), sites ordered as in `par`."""
+    e = np.repeat(par == 0, ndof)
+    o = ~e
+    return M[np.ix_(e, e)], M[np.ix_(e, o)], M[np.ix_(o, e)], M[np.ix_(o, o)]
+
+
+def schur_even(M: np.ndarray, par: np.ndarray, ndof: int) -> np.ndarray:
+    """S_ee = M_ee - M_eo M_oo^-1 M_oe, the Schur complement on the even sites
+    (the even-odd preconditioned operator when every hop joins sites of
+    opposite parity, which holds when every lattice extent is even; the paper
+    applies it to the coarse operator, Sec. "Comparison of the cost")."""
+    Mee, Meo, Moe, Moo = eo_blocks(M, par, ndof)
+    return Mee - Meo @ np.linalg.solve(Moo, Moe)
+
+
+def solve_eo(M: np.ndarray, par: np.ndarray, ndof: int, b: np.ndarray) -> np.ndarray:
+    """x = M^-1 b through the Schur complement: S_ee x_e = b_e - M_eo M_oo^-1 b_o,
+    then x_o = M_oo^-1 (b_o - M_oe x_e) (dense solves)."""
+    Mee, Meo, Moe, Moo = eo_blocks(M, par, ndof)
+    e = np.repeat(par == 0, ndof)
+    be, bo = b[e], b[~e]
+    xe = np.linalg.solve(Mee - Meo @ np.linalg.solve(Moo, Moe), be - Meo @ np.linalg.solve(Moo, bo))
+    xo = np.linalg.solve(Moo, bo - Moe @ xe)
+    x = np.empty_like(b)
+    x[e], x[~e] = xe, xo
+    return x

@@ -9,8 +9,8 @@ import numpy as np
 from . import build as _build
 
 MGLMA_FP64, MGLMA_FP32, MGLMA_BF16, MGLMA_FP16 = 0, 1, 2, 3
-MGLMA_OP_D, MGLMA_OP_DDAG, MGLMA_OP_Q, MGLMA_OP_DDAGD = 0, 1, 2, 3
-MGLMA_COARSE_GCR, MGLMA_COARSE_MINRES = 0, 1
+MGLMA_OP_D, MGLMA_OP_DDAG, MGLMA_OP_Q, MGLMA_OP_DDAGD, MGLMA_OP_SCHUR, MGLMA_OP_SCHUR_Q = 0, 1, 2, 3, 4, 5
+MGLMA_COARSE_GCR, MGLMA_COARSE_MINRES, MGLMA_COARSE_MINRES_EO = 0, 1, 2
 MGLMA_SOLVER_CGNE, MGLMA_SOLVER_MG = 0, 1
 MGLMA_SOURCE_Z2, MGLMA_SOURCE_Z4, MGLMA_SOURCE_POINT = 0, 1, 2
 _STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "NOT_CONVERGED", 6: "NUMERIC",
@@ -90,13 +90,16 @@ _sig("mglma_coarse_build_next", C.c_int, _vp, _vp, C.POINTER(C.c_int), C.c_int, 
 _sig("mglma_coarse_restrict", C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp)
 _sig("mglma_coarse_prolong", C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp)
 _sig("mglma_pieces", C.c_int, _vp, _vp, C.POINTER(_vp), C.c_int, C.c_int, _vp, _vp, C.c_double, _vp)
+_sig("mglma_coarse_gamma5_gamma", C.c_int, _vp, _vp, C.c_int, _vp)
+_sig("mglma_coarse_dense_inverse", C.c_int, _vp, _vp, _vp)
+_sig("mglma_exact_correlator", C.c_int, _vp, _vp, _vp, _vp)
 
 
 class mglma_solve_params(C.Structure):
     _fields_ = [("method", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("gcr_m", C.c_int),
                 ("nu", C.c_int), ("inner_tol", C.c_double), ("coarse_tol", C.c_double),
                 ("coarse_max_iter", C.c_int), ("check_every", C.c_int), ("max_batch", C.c_int),
-                ("coarse_solver", C.c_int)]
+                ("coarse_solver", C.c_int), ("autotune", C.c_int)]
 
 
 class mglma_solve_stats(C.Structure):
@@ -347,6 +350,21 @@ def mglma_pieces(ctx, g, levels, nrhs, b, psi, tol=1e-10, stream=None):
                             _stream_ptr(stream)))
 
 
+def mglma_coarse_gamma5_gamma(ctx, level, k, out):
+    """Gam_k(x0) of the level, complex128 [L0][V_c][2nv][2nv]."""
+    _check(lib.mglma_coarse_gamma5_gamma(_h(ctx), level, int(k), ptr(out)))
+
+
+def mglma_coarse_dense_inverse(ctx, level, out):
+    """Q_c^-1 of the level, complex128 [n][n]."""
+    _check(lib.mglma_coarse_dense_inverse(_h(ctx), level, ptr(out)))
+
+
+def mglma_exact_correlator(ctx, level, corr=None, G=None):
+    """corr[x0][y0] and G[t] of the exact estimator on the level (complex128)."""
+    _check(lib.mglma_exact_correlator(_h(ctx), level, ptr(corr), ptr(G)))
+
+
 def mglma_solve_params_default(method=MGLMA_SOLVER_MG, **overrides):
     p = mglma_solve_params()
     lib.mglma_solve_params_default(C.byref(p), int(method))
@@ -406,6 +424,11 @@ def mglma_autotune_set(ctx, kernel, nrhs, choice):
 def dslash32_tile_code(nr, rw):
     """Tile code of the FP32 stencil: NR RHS per thread, RW RHS tiles per CTA."""
     return int(nr) + 16 * (int(rw) - 1)
+
+
+def dslash32_staged_code(nrt):
+    """Tile code of the FP32 staged-tile stencil: 32 sites x nrt (4, 8, 16) RHS per CTA."""
+    return 64 + int(nrt)
 
 
 def mglma_autotune_save(ctx, path):

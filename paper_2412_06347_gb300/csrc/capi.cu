@@ -3,6 +3,7 @@
 // live here; all arithmetic runs in the kernels of the other units.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -237,6 +238,14 @@ mglma_status mglma_create(int device, mglma_ctx* out) {
   cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   for (int k = 0; k < K_NKINDS; ++k) c->stats[k].name = kernel_kind_name(k);
+  if (const char* cache = getenv("MGLMA_TUNE_CACHE")) {
+    c->tune_cache = cache;
+    FILE* f = fopen(cache, "r");
+    if (f) {
+      fclose(f);
+      mglma_autotune_load(c, cache);  // entries of other GPUs are skipped
+    }
+  }
   *out = c;
   return MGLMA_OK;
 }

@@ -354,6 +354,8 @@ mglma_status mglma_coarse_release_fp64(mglma_coarse Cc) {
 void mglma_coarse_free(mglma_coarse Cc) {
   if (!Cc) return;
   if (Cc->ctx) cudaSetDevice(Cc->ctx->device);
+  cudaFree(Cc->Sinv64);
+  cudaFree(Cc->Sinv_img);
   cudaFree(Cc->A64);
   cudaFree(Cc->A32);
   cudaFree(Cc->A16);
@@ -382,8 +384,10 @@ mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse Cc, mglma_op op, int
                                 mglma_prec compute, void* cuda_stream) {
   if (!ctx || !Cc || !in || !out) return fail(MGLMA_ERR_INVALID, "coarse_apply: NULL argument");
   // gamma5hat on the input (bit 0) and on the output (bit 1)
-  const int mode = op == MGLMA_OP_D ? 0 : op == MGLMA_OP_DDAG ? 3 : op == MGLMA_OP_Q ? 2 : -1;
-  if (mode < 0) return fail(MGLMA_ERR_INVALID, "coarse_apply: op must be D, D^dag or Q");
+  const int mode = op == MGLMA_OP_D ? 0 : op == MGLMA_OP_DDAG ? 3 : op == MGLMA_OP_Q ? 2
+                 : op == MGLMA_OP_SCHUR ? 0 : op == MGLMA_OP_SCHUR_Q ? 2 : -1;
+  if (mode < 0) return fail(MGLMA_ERR_INVALID, "coarse_apply: op must be D, D^dag, Q, SCHUR or SCHUR_Q");
+  const bool schur = op == MGLMA_OP_SCHUR || op == MGLMA_OP_SCHUR_Q;
   if (compute != MGLMA_FP64 && compute != MGLMA_FP32)
     return fail(MGLMA_ERR_INVALID, "coarse_apply: compute must be FP64 or FP32");
   if (nrhs <= 0) return nrhs == 0 ? MGLMA_OK : fail(MGLMA_ERR_INVALID, "coarse_apply: nrhs < 0");
@@ -401,7 +405,10 @@ mglma_status mglma_coarse_apply(mglma_ctx ctx, mglma_coarse Cc, mglma_op op, int
   MG_CHECK(dalloc(ctx, &Y, n * cb, s));
   fl.add(Y);
   MG_CHECK(coarse_from_canonical(ctx, si.dev, n, X, compute, s));
-  MG_CHECK(coarse_apply(ctx, Cc, X, Y, nrhs, compute, mode, s));
+  if (schur)
+    MG_CHECK(coarse_schur_full(ctx, Cc, X, Y, nrhs, compute, mode, s));
+  else
+    MG_CHECK(coarse_apply(ctx, Cc, X, Y, nrhs, compute, mode, s));
   MG_CHECK(coarse_tc_check(Cc, s));
   MG_CHECK(coarse_to_canonical(ctx, Y, compute, n, so.dev, s));
   MG_CHECK(stage_out_finish(out, n * sizeof(double2), s, so));

@@ -170,10 +170,39 @@ __device__ __forceinline__ void tmem_ld<64>(uint32_t taddr, uint32_t* v) {
 //     unit's accumulator (two TMEM buffers, alternating by unit), commits the
 //     stage back to warp 2 and, after slot 8, the accumulator to the epilogue
 //   warps 0-1: read the accumulator (rows = TMEM lanes), release it, store Y
+// One launch of the stencil: which sites, which slots, which operands.
+//   par < 0: every site y, fields indexed by y;  par = 0 / 1: the sites of
+//     that parity (x0 + x1 + x2 + x3 mod 2), fields of half the sites indexed
+//     by y >> 1 (every extent even, so y and y + 1 differ in parity) -- the
+//     hop slots then read a field of the other parity, the self slot one of
+//     the same parity (even-odd preconditioning)
+//   slots d_lo .. d_hi of the nine (0..8 all, 0..7 the hops, 8 the self block)
+//   A: operator image (nine slots per site); Aself: a one-slot-per-site image
+//     that replaces slot 8 (NULL: slot 8 of A)
+//   XB / XBself: B images for the hop slots / the self slot
+//   Y = sign * (the sum), gamma5hat on rows by mode bit 1 as before
+struct TcRun {
+  const uint8_t* A;
+  const uint8_t* Aself;
+  const uint8_t* XB;
+  const uint8_t* XBself;
+  float2* Y;
+  int d_lo, d_hi;
+  int par;
+  float sign;
+};
+
+// site of parity `par` with half-lattice index u (needs an even extent L3)
+__device__ __forceinline__ int64_t parity_site(const LatIdx& q, int64_t u, int par) {
+  const int64_t y0 = 2 * u;
+  int xc[4];
+  site_coords(q, y0, xc);
+  return y0 + ((par ^ (xc[0] + xc[1] + xc[2] + xc[3])) & 1);
+}
+
 template <int NT>
 __global__ void __launch_bounds__(TC_THREADS, 2)
-    coarse_tc_kernel(const uint8_t* __restrict__ Aimg, const uint8_t* __restrict__ XB, float2* __restrict__ Y,
-                     LatIdx q, int n2, int nrhs, int mode, int nstages, int* __restrict__ err) {
+    coarse_tc_kernel(TcRun run, LatIdx q, int n2, int nrhs, int mode, int nstages, int* __restrict__ err) {
   constexpr int N = 2 * NT;
   constexpr uint32_t TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -192,8 +221,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   __shared__ int abort_flag;
   volatile int* abrt = &abort_flag;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int64_t V1 = q.V;
+  const int64_t nunits = run.par < 0 ? q.V : q.V / 2;  // sites this launch computes (and field length)
   const int ntiles = (nrhs + NT - 1) / NT;
+  const int nslots = run.d_hi - run.d_lo + 1;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -227,18 +257,30 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     uint32_t it = 0;
     if (lane == 0) {
       bool ok = true;
-      for (int64_t y = blockIdx.x; y < V1 && ok; y += gridDim.x) {
+      for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const int64_t y = run.par < 0 ? u : parity_site(q, u, run.par);
         int xx[4];
         site_coords(q, y, xx);
-        int64_t nb[9];
-#pragma unroll
-        for (int d = 0; d < 4; ++d) {
-          nb[d] = nbr_fwd(q, y, xx, d);
-          nb[4 + d] = nbr_bwd(q, y, xx, d);
-        }
-        nb[8] = y;
+        // row of the B image slot d reads: the neighbour (full or half-lattice
+        // index), or this unit for the self slot (constant-index cases only,
+        // so nothing lands in local memory)
+        auto row_of = [&](int d) -> int64_t {
+          int64_t z;
+          switch (d) {
+            case 0: z = nbr_fwd(q, y, xx, 0); break;
+            case 1: z = nbr_fwd(q, y, xx, 1); break;
+            case 2: z = nbr_fwd(q, y, xx, 2); break;
+            case 3: z = nbr_fwd(q, y, xx, 3); break;
+            case 4: z = nbr_bwd(q, y, xx, 0); break;
+            case 5: z = nbr_bwd(q, y, xx, 1); break;
+            case 6: z = nbr_bwd(q, y, xx, 2); break;
+            case 7: z = nbr_bwd(q, y, xx, 3); break;
+            default: return u;
+          }
+          return run.par >= 0 ? (z >> 1) : z;
+        };
         for (int t = 0; t < ntiles && ok; ++t) {
-          for (int d = 0; d < 9; ++d, ++it) {
+          for (int d = run.d_lo; d <= run.d_hi; ++d, ++it) {
             const int st = (int)(it % S);
             const uint32_t ph = (it / S) & 1u;
             if (!mbar_wait(smem_u32(empty + st), ph ^ 1u, abrt)) {
@@ -250,8 +292,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             const uint32_t dst = smem_u32(sm + (size_t)st * stage_bytes);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(stage_bytes)
                          : "memory");
-            const uint8_t* srcA = Aimg + ((size_t)y * 9 + d) * a_slot;
-            const uint8_t* srcB = XB + ((size_t)t * V1 + nb[d]) * b_slot;
+            const uint8_t* srcA =
+                (d == 8 && run.Aself) ? run.Aself + (size_t)y * a_slot : run.A + ((size_t)y * 9 + d) * a_slot;
+            const uint8_t* srcB = (d == 8 ? run.XBself : run.XB) + ((size_t)t * nunits + row_of(d)) * b_slot;
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                 "l"(srcA), "r"(a_slot), "r"(bar)
@@ -278,7 +321,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       const uint32_t lboA = (uint32_t)G * 128, lboB = (uint32_t)(N / 8) * 128;
       uint32_t it = 0, u = 0;
       bool ok = true;
-      for (int64_t y = blockIdx.x; y < V1 && ok; y += gridDim.x) {
+      for (int64_t y = blockIdx.x; y < nunits && ok; y += gridDim.x) {
         for (int t = 0; t < ntiles && ok; ++t, ++u) {
           const uint32_t b = u & 1u, aph = (u >> 1) & 1u;
           if (!mbar_wait(smem_u32(acce + b), aph ^ 1u, abrt)) {
@@ -288,7 +331,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t dcol = tmem + b * N;
-          for (int d = 0; d < 9; ++d, ++it) {
+          for (int d = 0; d < nslots; ++d, ++it) {
             const int st = (int)(it % S);
             const uint32_t ph = (it / S) & 1u;
             if (!mbar_wait(smem_u32(full + st), ph, abrt)) {
@@ -325,9 +368,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     // ------------------------------------------------------------ epilogue
     uint32_t u = 0;
     const int i = warp * 32 + lane;
-    const float sg = ((mode & 2) && i >= n2 / 2) ? -1.f : 1.f;
+    const float sg = ((mode & 2) && i >= n2 / 2) ? -run.sign : run.sign;
     bool ok = true;
-    for (int64_t y = blockIdx.x; y < V1 && ok; y += gridDim.x) {
+    for (int64_t y = blockIdx.x; y < nunits && ok; y += gridDim.x) {
       for (int t = 0; t < ntiles; ++t, ++u) {
         const uint32_t b = u & 1u, aph = (u >> 1) & 1u;
         // every lane waits; the warp proceeds only if all saw the phase
@@ -349,7 +392,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 #pragma unroll
           for (int r = 0; r < NT; ++r)
             if (r0 + r < nrhs)
-              Y[((size_t)(r0 + r) * V1 + y) * n2 + i] =
+              run.Y[((size_t)(r0 + r) * nunits + y) * n2 + i] =
                   make_float2(sg * __uint_as_float(v[r]), sg * __uint_as_float(v[NT + r]));
         }
       }
@@ -361,9 +404,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 }
 
 // operator image for the kernel: per site [c][g][8 rows][8 bf16] with
-// k = 8c + kk = (d * 2 + part) * n2 + j and row i = 8g + ri
-__global__ void a_image_kernel(const double2* __restrict__ A64, uint16_t* __restrict__ img, int64_t V1, int n2) {
-  const size_t per = (size_t)18 * n2 * n2;
+// k = 8c + kk = (d * 2 + part) * n2 + j and row i = 8g + ri, from nslots
+// blocks per site of A64 ([site][slot][col j][row i])
+__global__ void a_image_kernel(const double2* __restrict__ A64, uint16_t* __restrict__ img, int64_t V1, int n2,
+                               int nslots) {
+  const size_t per = (size_t)2 * nslots * n2 * n2;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= per * V1) return;
   const int64_t y = (int64_t)(t / per);
@@ -372,7 +417,7 @@ __global__ void a_image_kernel(const double2* __restrict__ A64, uint16_t* __rest
   const int kk = (int)(e % 8), ri = (int)((e / 8) % 8), g = (int)((e / 64) % G), c = (int)(e / (64 * (size_t)G));
   const int i = 8 * g + ri, k = 8 * c + kk;
   const int d = k / (2 * n2), part = (k / n2) % 2, j = k % n2;
-  const double2 a = A64[(((size_t)y * 9 + d) * n2 + j) * n2 + i];
+  const double2 a = A64[(((size_t)y * nslots + d) * n2 + j) * n2 + i];
   img[t] = bf16_bits((float)(part ? a.y : a.x));
 }
 
@@ -403,7 +448,7 @@ mglma_status coarse_tc_image(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s) {
   MG_CUDA(cudaMalloc(&C->tc_err, sizeof(int)));
   MG_CUDA(cudaMemsetAsync(C->tc_err, 0, sizeof(int), s));
   ProfScope ps(ctx, K_SETUP, s);
-  a_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C->A64, C->Aimg, C->geo.V1, C->n2);
+  a_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C->A64, C->Aimg, C->geo.V1, C->n2, 9);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }
@@ -427,10 +472,85 @@ static mglma_status launch_tc(mglma_ctx ctx, const mglma_coarse_s* C, const floa
   // two resident CTAs per SM: while one waits for its MMAs to release a
   // stage, the other's copies and MMAs proceed
   const unsigned grid = (unsigned)std::min<int64_t>(V1, 2 * (int64_t)ctx->sm_count);
-  coarse_tc_kernel<NT><<<grid, TC_THREADS, smem, s>>>((const uint8_t*)C->Aimg, (const uint8_t*)xb, Y,
-                                                      make_latidx(C->geo.Lb), n2, nrhs, mode, tc_stages(n2, NT), err);
+  TcRun run;
+  run.A = (const uint8_t*)C->Aimg;
+  run.Aself = nullptr;
+  run.XB = run.XBself = (const uint8_t*)xb;
+  run.Y = Y;
+  run.d_lo = 0;
+  run.d_hi = 8;
+  run.par = -1;
+  run.sign = 1.f;
+  coarse_tc_kernel<NT><<<grid, TC_THREADS, smem, s>>>(run, make_latidx(C->geo.Lb), n2, nrhs, mode,
+                                                      tc_stages(n2, NT), err);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
+}
+
+mglma_status coarse_tc_image_blocks(mglma_ctx ctx, const double2* A64, int64_t V1, int n2, int nslots,
+                                    uint16_t** img, cudaStream_t s) {
+  const size_t n = (size_t)2 * nslots * n2 * n2 * V1;
+  MG_CUDA(cudaMalloc(img, n * sizeof(uint16_t)));
+  ProfScope ps(ctx, K_SETUP, s);
+  a_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A64, *img, V1, n2, nslots);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+// B image bytes of one half-lattice field (RHS rounded up to the widest tile)
+size_t coarse_tc_half_image_bytes(const mglma_coarse_s* C, int nrhs) {
+  return (size_t)((nrhs + 31) / 32 * 32) * (C->geo.V1 / 2) * C->n2 * 8;
+}
+
+template <int NT>
+static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
+                                 float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
+                                 float sign, void* scratch, cudaStream_t s) {
+  const int n2 = C->n2;
+  const int64_t Vh = C->geo.V1 / 2;
+  const size_t half = coarse_tc_half_image_bytes(C, nrhs);
+  uint8_t* xb_hop = (uint8_t*)scratch;
+  uint8_t* xb_self = xb_hop + half;
+  const size_t groups = (size_t)((nrhs + NT - 1) / NT) * Vh * (n2 / 8) * NT;
+  // images of the inputs the slots read (gamma5hat on the inputs by mode bit 0)
+  if (d_lo < 8)
+    x_image_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, s>>>(Xhop, (uint4*)xb_hop, Vh, n2, nrhs, NT, mode);
+  if (d_hi == 8)
+    x_image_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, s>>>(Xself, (uint4*)xb_self, Vh, n2, nrhs, NT, mode);
+  MG_LAUNCH_CHECK();
+  const size_t smem = tc_smem(n2, NT);
+  static size_t attr = 0;
+  if (smem > attr) {
+    MG_CUDA(cudaFuncSetAttribute(coarse_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  const unsigned grid = (unsigned)std::min<int64_t>(Vh, 2 * (int64_t)ctx->sm_count);
+  TcRun run;
+  run.A = (const uint8_t*)C->Aimg;
+  run.Aself = (const uint8_t*)Aself;
+  run.XB = xb_hop;
+  run.XBself = xb_self;
+  run.Y = Y;
+  run.d_lo = d_lo;
+  run.d_hi = d_hi;
+  run.par = par;
+  run.sign = sign;
+  coarse_tc_kernel<NT><<<grid, TC_THREADS, smem, s>>>(run, make_latidx(C->geo.Lb), n2, nrhs, mode & 2,
+                                                      tc_stages(n2, NT), C->tc_err);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status coarse_tc_eo_launch(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
+                                 float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
+                                 float sign, void* scratch, cudaStream_t s) {
+  if (!C->Aimg || !coarse_tc_supported(C->n2)) return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: no tensor image");
+  if (par < 0 || par > 1 || d_lo < 0 || d_hi > 8 || d_lo > d_hi)
+    return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: bad launch");
+  const int nt = tuned(ctx, TUNE_COARSE_NT, nrhs, C->geo.V1, coarse_tc_default_nt(nrhs));
+  if (nt == 32) return launch_tc_eo<32>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s);
+  if (nt == 16) return launch_tc_eo<16>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s);
+  return launch_tc_eo<8>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s);
 }
 
 mglma_status coarse_tc_check(mglma_coarse_s* C, cudaStream_t s) {
@@ -451,7 +571,7 @@ mglma_status coarse_apply_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float
                              void* scratch, size_t scratch_bytes, cudaStream_t s) {
   if (!C->Aimg || !coarse_tc_supported(C->n2)) return fail(MGLMA_ERR_INVALID, "coarse_apply_tc: no tensor image");
   int* err = C->tc_err;
-  const int nt = tuned(ctx, TUNE_COARSE_NT, nrhs, coarse_tc_default_nt(nrhs));
+  const int nt = tuned(ctx, TUNE_COARSE_NT, nrhs, C->geo.V1, coarse_tc_default_nt(nrhs));
   const size_t need = coarse_tc_scratch_bytes(C, nrhs);
   void* xb = scratch;
   void* own = nullptr;

@@ -279,16 +279,10 @@ constexpr int dslash_min_ctas() {
   return sizeof(R) == 8 ? 3 : (NR == 1 ? (RW == 1 ? 6 : 5) : (NR == 2 ? 4 : 3));
 }
 
-// RED (FP32, one RHS per thread, one RHS tile per CTA only) also reduces, per
-// CTA, |t|^2 and <t, in> = sum conj(t) in over the CTA's 128 sites of t = op(in)
-// into part[(rhs * nblk + block) * 3 + {0, 1, 2}] (|t|^2, Re, Im): FP32 over
-// each warp's 32 sites, FP64 from there on, summed over the blocks in a fixed
-// order by dot_finish_kernel.
-template <typename R, int NR, bool DAG, int RW, bool RED = false>
+template <typename R, int NR, bool DAG, int RW>
 __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kernel(const void* __restrict__ in, void* __restrict__ out,
                                                      const void* __restrict__ U, const void* __restrict__ C,
-                                                     DslashArgs a, double* __restrict__ part = nullptr) {
-  static_assert(!RED || (NR == 1 && RW == 1 && sizeof(R) == 4), "fused reduction: FP32 tile 1,1 only");
+                                                     DslashArgs a) {
   constexpr int SW = 128 / RW;  // sites per CTA
   const int64_t V = a.q.V;
   // RHS tile groups run fastest in launch order, so the CTAs that share a
@@ -296,14 +290,9 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
   const int ntile = (a.nrhs + NR - 1) / NR;
   int64_t site;
   int r0;
-  bool valid = true;  // with RED every thread reaches the block reduction
   if constexpr (RW == 1) {
     site = (int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x;
-    if (site >= V) {
-      if constexpr (!RED) return;
-      valid = false;
-      site = V - 1;
-    }
+    if (site >= V) return;
     r0 = (blockIdx.x % ntile) * NR;
   } else {
     const int ngrp = (ntile + RW - 1) / RW;
@@ -364,47 +353,187 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
   }
 #pragma unroll
   for (int r = 0; r < NR; ++r)
-    if (r0 + r < a.nrhs && valid) {
+    if (r0 + r < a.nrhs) {
       if (a.g5out) {
 #pragma unroll
         for (int k = 6; k < 12; ++k) acc[r][k] = -acc[r][k];
       }
       IO<R>::store(out, V, r0 + r, site, acc[r]);
     }
-  if constexpr (RED) {
-    float nn = 0.f, dr = 0.f, di = 0.f;
-    if (valid) {
-      Cx<R> sv[12];
-      IO<R>::load(in, V, r0, site, sv);
+}
+
+// ------------------------------------------------------------ staged-tile FP32 stencil (many RHS)
+// A CTA covers DT = 32 consecutive sites and NRT right-hand sides: warp w
+// computes RHS r0 + w on the 32 sites (lane = site), so every spinor load of a
+// warp is one coalesced 512-byte row.  Everything that depends on the site
+// but not on the RHS is staged once per CTA in shared memory: the eight
+// links a site's hops use -- U_mu(x) for the forward hops and U_mu(x-mu)^dag
+// for the backward hops, third row rebuilt, already multiplied by the hop
+// factor -1/2 (times t_bc where the hop crosses the time boundary) -- and the
+// two clover blocks.  The per-RHS work is then projection, one 3x3 product
+// per half spinor and reconstruction.  Scaling a link by +-1/2 is exact and
+// commutes with every rounding, and the terms are summed in the same order
+// as dslash_kernel, so both kernels give the same bits.
+constexpr int kDT = 32;  // sites per CTA of the staged kernel
+
+struct StagedTile {
+  float2 U[8][9][kDT];  // hop slot (0..3 forward, 4..7 backward), entry (row*3 + col), site
+  float4 C[2][9][kDT];  // clover chirality block, packed float4, site
+};
+
+// hop slot MU (forward: U_MU(x)) or 4 + MU (backward: U_MU(x - MU)^dag) of site
+// `site` (coordinates x) into the tile, times -1/2 (and t_bc across the time
+// boundary)
+template <int MU, bool FWD>
+__device__ __forceinline__ void stage_link(StagedTile& st, int ls, const float4* __restrict__ U, const DslashArgs& a,
+                                           int64_t site, const int x[4]) {
+  const int64_t ls_site = FWD ? site : nbr_bwd(a.q, site, x, MU);
+  const bool crossing = MU == 0 && (FWD ? x[0] == a.q.L[0] - 1 : x[0] == 0);
+  const float f = -0.5f * (crossing ? (float)a.bc : 1.f);
+  M3<float> m;
+  Link<float>::load(U, a.q.V, MU, ls_site, m);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const Cx<float> e = FWD ? m.e[i][j] : conj(m.e[j][i]);
+      st.U[FWD ? MU : 4 + MU][i * 3 + j][ls] = make_float2(f * e.re, f * e.im);
+    }
+}
+
+// acc += (1 + s gamma_mu) W psi(nb) with the staged, pre-scaled link W of hop
+// slot MU (forward) or 4 + MU (backward)
+template <int MU, bool FWD>
+__device__ __forceinline__ void staged_hop(const StagedTile& st, int ls, const float4* __restrict__ in, int64_t V,
+                                           int r, int64_t nb, float sg, Cx<float> acc[12]) {
+  constexpr int slot = FWD ? MU : 4 + MU;
+  Cx<float> psi[12];
+  IO<float>::load(in, V, r, nb, psi);
+  M3<float> Um;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    const float2 v = st.U[slot][e][ls];
+    Um.e[e / 3][e % 3] = cx(v.x, v.y);
+  }
+  Cx<float> h0[3], h1[3], g0[3], g1[3];
+  project<float>(MU, sg, psi, h0, h1);
+  mat_vec<float>(Um, h0, g0);
+  mat_vec<float>(Um, h1, g1);
+  reconstruct_add<float>(MU, sg, g0, g1, acc);
+}
+
+// RED: per warp (one RHS, 32 sites) |t|^2 and <t, in> in FP32, written as FP64
+// partials part[((rhs * ntiles) + tile) * 3 + {0, 1, 2}] (ntiles = ceil(V / 32))
+// resident warps per SM the register allocation must allow: 24 (80
+// registers a thread), 20 with the reduction epilogue (which holds the
+// result and the input spinor at once)
+template <int NRT, bool RED>
+constexpr int staged_min_ctas() {
+  return (RED ? 20 : 24) / NRT > 0 ? (RED ? 20 : 24) / NRT : 1;
+}
+
+template <int NRT, bool DAG, bool RED = false>
+__global__ void __launch_bounds__(NRT * 32, staged_min_ctas<NRT, RED>()) dslash_staged_kernel(const float4* __restrict__ in, float4* __restrict__ out,
+                                                                 const float4* __restrict__ U, const float4* __restrict__ C,
+                                                                 DslashArgs a, double* __restrict__ part = nullptr) {
+  __shared__ StagedTile st;
+  const int64_t V = a.q.V;
+  const int ngrp = (a.nrhs + NRT - 1) / NRT;
+  const int64_t tile = blockIdx.x / ngrp;
+  const int r0 = (int)(blockIdx.x % ngrp) * NRT;
+  const int64_t base = tile * kDT;
+  // ---- stage links (one (slot, site) per job) and clover blocks
+  for (int job = threadIdx.x; job < 8 * kDT; job += blockDim.x) {
+    const int l = job / kDT, ls = job % kDT;  // l is uniform across a warp
+    const int64_t site = base + ls;
+    if (site >= V) continue;
+    int x[4];
+    site_coords(a.q, site, x);
+    switch (l) {
+      case 0: stage_link<0, true>(st, ls, U, a, site, x); break;
+      case 1: stage_link<1, true>(st, ls, U, a, site, x); break;
+      case 2: stage_link<2, true>(st, ls, U, a, site, x); break;
+      case 3: stage_link<3, true>(st, ls, U, a, site, x); break;
+      case 4: stage_link<0, false>(st, ls, U, a, site, x); break;
+      case 5: stage_link<1, false>(st, ls, U, a, site, x); break;
+      case 6: stage_link<2, false>(st, ls, U, a, site, x); break;
+      default: stage_link<3, false>(st, ls, U, a, site, x); break;
+    }
+  }
+  for (int job = threadIdx.x; job < 18 * kDT; job += blockDim.x) {
+    const int k = job / kDT, ls = job % kDT;
+    const int64_t site = base + ls;
+    if (site < V) st.C[k / 9][k % 9][ls] = __ldg(C + (size_t)k * V + site);
+  }
+  __syncthreads();
+  const int w = threadIdx.x / 32, ls = threadIdx.x % 32;
+  const int r = r0 + w;
+  const int64_t site = base + ls;
+  const bool valid = site < V;
+  if (r >= a.nrhs) return;  // no barrier follows
+  float nn = 0.f, dr = 0.f, di = 0.f;
+  if (valid) {
+    int x[4];
+    site_coords(a.q, site, x);
+    const float sF = DAG ? 1.f : -1.f;  // forward hop carries (1 + sF gamma)
+    const float sB = -sF;
+    Cx<float> acc[12];
+    {
+      Cx<float> psi[12];
+      IO<float>::load(in, V, r, site, psi);
+#pragma unroll
+      for (int chi = 0; chi < 2; ++chi) {
+        float c[36];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+          const float4 v = st.C[chi][j][ls];
+          c[4 * j] = v.x;
+          c[4 * j + 1] = v.y;
+          c[4 * j + 2] = v.z;
+          c[4 * j + 3] = v.w;
+        }
+        clover_apply6<float>(c, psi + 6 * chi, acc + 6 * chi);
+      }
+    }
+    // hop order of dslash_kernel: mu = 0..3, forward then backward
+    staged_hop<0, true>(st, ls, in, V, r, nbr_fwd(a.q, site, x, 0), sF, acc);
+    staged_hop<0, false>(st, ls, in, V, r, nbr_bwd(a.q, site, x, 0), sB, acc);
+    staged_hop<1, true>(st, ls, in, V, r, nbr_fwd(a.q, site, x, 1), sF, acc);
+    staged_hop<1, false>(st, ls, in, V, r, nbr_bwd(a.q, site, x, 1), sB, acc);
+    staged_hop<2, true>(st, ls, in, V, r, nbr_fwd(a.q, site, x, 2), sF, acc);
+    staged_hop<2, false>(st, ls, in, V, r, nbr_bwd(a.q, site, x, 2), sB, acc);
+    staged_hop<3, true>(st, ls, in, V, r, nbr_fwd(a.q, site, x, 3), sF, acc);
+    staged_hop<3, false>(st, ls, in, V, r, nbr_bwd(a.q, site, x, 3), sB, acc);
+    if (a.g5out) {
+#pragma unroll
+      for (int k = 6; k < 12; ++k) acc[k] = -acc[k];
+    }
+    IO<float>::store(out, V, r, site, acc);
+    if constexpr (RED) {
+      Cx<float> sv[12];
+      IO<float>::load(in, V, r, site, sv);
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        const Cx<R> t = acc[0][k];
+        const Cx<float> t = acc[k];
         nn += t.re * t.re + t.im * t.im;
         dr += t.re * sv[k].re + t.im * sv[k].im;
         di += t.re * sv[k].im - t.im * sv[k].re;
       }
     }
-    // FP32 within a warp (32 sites), FP64 from the warp partials on: the
-    // FP64 pipe of GB300 is too narrow for a per-thread FP64 tree
+  }
+  if constexpr (RED) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       nn += __shfl_down_sync(0xffffffffu, nn, o);
       dr += __shfl_down_sync(0xffffffffu, dr, o);
       di += __shfl_down_sync(0xffffffffu, di, o);
     }
-    __shared__ float wsum[4][3];
-    const int w = threadIdx.x / 32;
-    if (threadIdx.x % 32 == 0) {
-      wsum[w][0] = nn;
-      wsum[w][1] = dr;
-      wsum[w][2] = di;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-      const int64_t nblk = (V + 127) / 128;
-      const int c = threadIdx.x;
-      part[((size_t)r0 * nblk + blockIdx.x / ntile) * 3 + c] =
-          (((double)wsum[0][c] + (double)wsum[1][c]) + (double)wsum[2][c]) + (double)wsum[3][c];
+    if (ls == 0) {
+      const int64_t ntiles = (V + kDT - 1) / kDT;
+      double* p = part + ((size_t)r * ntiles + tile) * 3;
+      p[0] = (double)nn;
+      p[1] = (double)dr;
+      p[2] = (double)di;
     }
   }
 }
@@ -779,13 +908,38 @@ static void launch_dslash(const Spinor& in, Spinor& out, const void* U, const vo
 }
 
 // FP32 tile shape (RHS per thread NR, RHS tiles per CTA RW) encoded as
-// NR + 16 (RW - 1); the autotuner (tune.cu) may replace the default below
-// for an RHS count on a context.  Measured on GB300 (64x32^3, 1-16 RHS),
-// one RHS per thread and one RHS tile per CTA was fastest at every count.
-int dslash32_default_tile(int) { return dslash32_tile_code(1, 1); }
+// NR + 16 (RW - 1), or 64 + NRT for the staged-tile kernel; the autotuner
+// (tune.cu) may replace the default below for an RHS count on a context.
+// One RHS: one site per thread (the links are read once anyway); from 4
+// RHS on, the staged-tile kernel shares each site's links and clover among
+// the RHS of a CTA.
+int dslash32_default_tile(int nrhs) { return nrhs >= 4 ? 64 + 8 : dslash32_tile_code(1, 1); }
+
+template <int NRT, bool RED>
+static void launch_staged(const Spinor& in, Spinor& out, const void* U, const void* C, const DslashArgs& a,
+                          bool dagger, cudaStream_t s, double* part = nullptr) {
+  const int64_t ntiles = (in.V + kDT - 1) / kDT;
+  const unsigned ctas = (unsigned)(ntiles * ((in.nrhs + NRT - 1) / NRT));
+  const float4* x = (const float4*)in.p;
+  float4* y = (float4*)out.p;
+  if (dagger)
+    dslash_staged_kernel<NRT, true, RED><<<ctas, NRT * 32, 0, s>>>(x, y, (const float4*)U, (const float4*)C, a, part);
+  else
+    dslash_staged_kernel<NRT, false, RED><<<ctas, NRT * 32, 0, s>>>(x, y, (const float4*)U, (const float4*)C, a, part);
+}
 
 static void launch_dslash32(int code, const Spinor& in, Spinor& out, const void* U, const void* C,
                             const DslashArgs& a, bool dagger, cudaStream_t s) {
+  if (dslash32_tile_staged(code)) {
+    const int nrt = dslash32_tile_nrt(code);
+    if (nrt == 4)
+      launch_staged<4, false>(in, out, U, C, a, dagger, s);
+    else if (nrt == 8)
+      launch_staged<8, false>(in, out, U, C, a, dagger, s);
+    else
+      launch_staged<16, false>(in, out, U, C, a, dagger, s);
+    return;
+  }
   int nr = dslash32_tile_nr(code), rw = dslash32_tile_rw(code);
   if (in.nrhs < nr) nr = in.nrhs >= 2 ? 2 : 1;
   if (nr == 4)
@@ -820,14 +974,14 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
     launch_dslash<double, 1, 1>(in, out, G->U64, G->C64, a, dagger, s);
   } else {
     ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(in.V, in.nrhs, false), flops);
-    launch_dslash32(tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, dslash32_default_tile(in.nrhs)), in, out, G->U32, G->C32,
+    launch_dslash32(tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, G->g.V, dslash32_default_tile(in.nrhs)), in, out, G->U32, G->C32,
                     a, dagger, s);
   }
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }
 
-size_t dslash_dot_part_doubles(int64_t V, int nrhs) { return (size_t)3 * nrhs * (size_t)((V + 127) / 128); }
+size_t dslash_dot_part_doubles(int64_t V, int nrhs) { return (size_t)3 * nrhs * (size_t)((V + kDT - 1) / kDT); }
 
 mglma_status dslash_dot(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, double* part,
                         double* nrm, double2* dot, cudaStream_t s) {
@@ -840,11 +994,12 @@ mglma_status dslash_dot(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in,
   a.bc = (double)G->g.t_bc;
   a.nrhs = in.nrhs;
   a.g5out = 0;
-  const int64_t nblk = (in.V + 127) / 128;
+  const int64_t nblk = (in.V + kDT - 1) / kDT;
   {
+    // the staged-tile kernel with its per-warp reduction epilogue, RHS tiles
+    // of 4 (the epilogue fits 96 registers there without spilling)
     ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(in.V, in.nrhs, false), dslash_flops(in.V, in.nrhs));
-    dslash_kernel<float, 1, false, 1, true><<<(unsigned)(nblk * in.nrhs), 128, 0, s>>>(in.p, out.p, G->U32, G->C32,
-                                                                                       a, part);
+    launch_staged<4, true>(in, out, G->U32, G->C32, a, false, s, part);
   }
   MG_LAUNCH_CHECK();
   {

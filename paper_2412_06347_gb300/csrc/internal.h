@@ -78,6 +78,7 @@ struct KernelStat {
 }  // namespace mglma
 
 #include <map>
+#include <tuple>
 
 struct mglma_ctx_s {
   int device = 0;
@@ -89,8 +90,10 @@ struct mglma_ctx_s {
     int count_cap = 0;
   };
   std::map<cudaStream_t, RedScratch> red;
-  // autotuned tile choices: key = kernel * 1024 + RHS bucket -> (choice, ms)
-  std::map<int, std::pair<int, double>> tune;
+  // autotuned tile choices: (kernel, RHS bucket, lattice volume) -> (choice,
+  // ms); volume 0 applies to every lattice (mglma_autotune_set)
+  std::map<std::tuple<int, int, int64_t>, std::pair<int, double>> tune;
+  std::string tune_cache;  // file the table is saved to after automatic tuning ("" = none)
   cudaStream_t stream = nullptr;  // default stream of the context
   cudaMemPool_t pool = nullptr;
   int sm_count = 0;
@@ -133,18 +136,30 @@ inline int rhs_bucket(int n) {
   while (b < n && b < 64) b *= 2;
   return b;
 }
-inline int tuned(const mglma_ctx_s* ctx, int kernel, int nrhs, int dflt) {
-  auto it = ctx->tune.find(kernel * 1024 + rhs_bucket(nrhs));
+// the tuned choice for this lattice volume, else the one set for every
+// lattice, else dflt
+inline int tuned(const mglma_ctx_s* ctx, int kernel, int nrhs, int64_t volume, int dflt) {
+  auto it = ctx->tune.find(std::make_tuple(kernel, rhs_bucket(nrhs), volume));
+  if (it == ctx->tune.end()) it = ctx->tune.find(std::make_tuple(kernel, rhs_bucket(nrhs), (int64_t)0));
   return it == ctx->tune.end() ? dflt : it->second.first;
 }
+inline bool has_tuned(const mglma_ctx_s* ctx, int kernel, int nrhs, int64_t volume) {
+  return ctx->tune.count(std::make_tuple(kernel, rhs_bucket(nrhs), volume)) > 0;
+}
 // FP32 stencil tile codes: NR RHS per thread (1, 2, 4) and RW RHS tiles per
-// CTA (1, 2, 4), code = NR + 16 (RW - 1); codes 1, 2, 4 are RW = 1
+// CTA (1, 2, 4), code = NR + 16 (RW - 1); codes 1, 2, 4 are RW = 1.  Codes
+// 64 + NRT (NRT = 4, 8, 16) select the staged-tile kernel: 32 sites x NRT
+// RHS per CTA with links and clover staged in shared memory.
 inline int dslash32_tile_code(int nr, int rw) { return nr + 16 * (rw - 1); }
 inline int dslash32_tile_nr(int code) { return code & 15; }
 inline int dslash32_tile_rw(int code) { return 1 + (code >> 4); }
+inline bool dslash32_tile_staged(int code) { return code == 68 || code == 72 || code == 80; }
+inline int dslash32_tile_nrt(int code) { return code - 64; }
 inline bool dslash32_tile_valid(int code) {
+  if (dslash32_tile_staged(code)) return true;
   const int nr = dslash32_tile_nr(code), rw = dslash32_tile_rw(code);
-  return code > 0 && (nr == 1 || nr == 2 || nr == 4) && (rw == 1 || rw == 2 || rw == 4) && (nr < 4 || rw == 1);
+  return code > 0 && code < 64 && (nr == 1 || nr == 2 || nr == 4) && (rw == 1 || rw == 2 || rw == 4) &&
+         (nr < 4 || rw == 1);
 }
 int dslash32_default_tile(int nrhs);
 
@@ -186,6 +201,9 @@ struct ProfScope {
   ProfScope(mglma_ctx c, int k, cudaStream_t st, double bytes_ = 0, double flops_ = 0);
   ~ProfScope();
 };
+
+// tile shapes of this (lattice, RHS bucket) tuned unless already known (tune.cu)
+mglma_status autotune_for_batch(mglma_ctx ctx, mglma_gauge_s* G, struct ::mglma_coarse_s* C, int nrhs);
 
 // ---------------------------------------------------------------- memory
 mglma_status dalloc(mglma_ctx ctx, void** p, size_t bytes, cudaStream_t s);
@@ -237,8 +255,8 @@ mglma_status dslash(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor&
                     bool gamma5_out, cudaStream_t s);
 // FP32 t = D in with, per RHS, nrm = |t|^2 and dot = <t, in> = sum conj(t) in
 // reduced in the same pass (FP32 per warp of 32 sites, then FP64 partials per
-// 128-site block in `part`, at least dslash_dot_part_doubles(V, nrhs)
-// doubles, summed in a fixed order).
+// 32-site tile in `part`, at least dslash_dot_part_doubles(V, nrhs) doubles,
+// summed in a fixed order).
 mglma_status dslash_dot(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, double* part, double* nrm,
                         double2* dot, cudaStream_t s);
 size_t dslash_dot_part_doubles(int64_t V, int nrhs);

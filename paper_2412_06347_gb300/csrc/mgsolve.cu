@@ -342,12 +342,17 @@ static mglma_status minres_init(MinresWork& w, const mglma_coarse_s* C, const Ve
   return coarse_g5_scale(w.ctx, b, v0, w.st(MR_CF + 4), C->n2, w.s);
 }
 
+// eo: the vectors hold the even sites only and the operator is g5hat S_ee
+// (even-odd preconditioning, coarse_eo.cu), else all sites and g5hat D1
 static mglma_status minres_iter(MinresWork& w, const mglma_coarse_s* C, Vec& x, int n, int k, double tol,
-                                void* scr, size_t scr_bytes) {
+                                void* scr, size_t scr_bytes, bool eo = false) {
   const int a = k % 3, b = (k + 1) % 3, c = (k + 2) % 3;
   Vec v = w.view(w.Vp, a, n), vo = w.view(w.Vp, c, n), z = w.view(w.Vp, b, n);
   Vec wn = w.view(w.Wp, a, n), w1 = w.view(w.Wp, c, n), w2 = w.view(w.Wp, b, n);
-  MG_CHECK(coarse_apply(w.ctx, C, v.p, z.p, n, MGLMA_FP32, CMODE_Q, w.s, scr, scr_bytes));
+  if (eo)
+    MG_CHECK(coarse_schur_apply(w.ctx, C, v.p, z.p, n, MGLMA_FP32, CMODE_Q, scr, scr_bytes, w.s));
+  else
+    MG_CHECK(coarse_apply(w.ctx, C, v.p, z.p, n, MGLMA_FP32, CMODE_Q, w.s, scr, scr_bytes));
   MG_CHECK(cdot(w.ctx, v, z, w.sc.z, w.s));
   MG_CHECK(lanczos_norm(w.ctx, w.sc.z, w.st(MR_BETA), w.sc.active, v, vo, z, w.st(MR_BN2), w.s));
   {
@@ -366,10 +371,12 @@ static mglma_status read_mask(const int* dev, int n, std::vector<int>& h, cudaSt
 }
 
 // Coarse solve of the preconditioner with a persistent workspace: MINRES on
-// Qhat (default) or GCR(m) on Dhat.  One cycle (m GCR iterations = one
-// restart; 12 MINRES iterations) is captured as a CUDA graph and replayed,
-// with one host poll of the convergence mask per cycle.  With profiling on,
-// a separately captured copy records event brackets around every launch.
+// Qhat (default), MINRES on g5hat S_ee of the even-odd preconditioned
+// operator (the odd sites follow by back-substitution), or GCR(m) on Dhat.
+// One cycle (m GCR iterations = one restart; 12 MINRES iterations) is
+// captured as a CUDA graph and replayed, with one host poll of the
+// convergence mask per cycle.  With profiling on, a separately captured copy
+// records event brackets around every launch.
 struct CoarseSolver {
   mglma_ctx ctx = nullptr;
   cudaStream_t s = nullptr;
@@ -381,6 +388,7 @@ struct CoarseSolver {
   MinresWork mw;
   void* scr = nullptr;  // tensor-core apply work space (B images of X)
   size_t scr_bytes = 0;
+  Vec be, xe;  // even-odd: the prepared source and the solution on the even sites
   struct Graphs {
     cudaGraphExec_t init = nullptr, cycle = nullptr;
     int n = -1;
@@ -393,6 +401,8 @@ struct CoarseSolver {
   ~CoarseSolver() {
     reset();
     if (scr) dfree(ctx, scr, s);
+    if (be.p) dfree(ctx, be.p, s);
+    if (xe.p) dfree(ctx, xe.p, s);
   }
   // destroys one graph set (both execs, its event brackets) and marks it empty
   static void drop(Graphs& G) {
@@ -411,7 +421,8 @@ struct CoarseSolver {
   void reset() {
     for (auto& G : g) drop(G);
   }
-  bool minres() const { return method == MGLMA_COARSE_MINRES; }
+  bool eo() const { return method == MGLMA_COARSE_MINRES_EO; }
+  bool minres() const { return method == MGLMA_COARSE_MINRES || eo(); }
   int cycle_len() const { return minres() ? 12 : m; }
   int capacity() const { return minres() ? mw.cap : w.cap; }
   const int* active() const { return minres() ? mw.sc.active : w.sc.active; }
@@ -420,9 +431,27 @@ struct CoarseSolver {
       return coarse_apply(ctx, C, in.p, out.p, in.nrhs, MGLMA_FP32, CMODE_D, s, scr, scr_bytes);
     };
   }
-  mglma_status init(const Vec& b, Vec& x) { return minres() ? minres_init(mw, C, b, x) : gcr_init(w, b, x); }
+  mglma_status init(const Vec& b, Vec& x) {
+    if (eo()) {  // b_e' = b_e - D_eo D_oo^-1 b_o, MINRES for x_e
+      Vec bn = be, xn = xe;
+      bn.nrhs = xn.nrhs = b.nrhs;
+      MG_CHECK(coarse_eo_prepare(ctx, C, b.p, bn.p, b.nrhs, MGLMA_FP32, scr, scr_bytes, s));
+      return minres_init(mw, C, bn, xn);
+    }
+    return minres() ? minres_init(mw, C, b, x) : gcr_init(w, b, x);
+  }
   mglma_status iter(const OpFn& A, Vec& x, int n, int k, double tol) {
+    if (eo()) {
+      Vec xn = xe;
+      xn.nrhs = n;
+      return minres_iter(mw, C, xn, n, k, tol, scr, scr_bytes, true);
+    }
     return minres() ? minres_iter(mw, C, x, n, k, tol, scr, scr_bytes) : gcr_iter(w, A, nullptr, x, n, k, tol * tol);
+  }
+  // even-odd: x_o = D_oo^-1 (b_o - D_oe x_e), x = (x_e, x_o)
+  mglma_status finish(const Vec& b, Vec& x) {
+    if (!eo()) return MGLMA_OK;
+    return coarse_eo_reconstruct(ctx, C, b.p, xe.p, x.p, b.nrhs, MGLMA_FP32, scr, scr_bytes, s);
   }
   // captures the init and cycle graphs of n RHS into G; on any failure G is
   // left empty (no half-built set survives to be launched)
@@ -470,12 +499,23 @@ struct CoarseSolver {
     const int n = b.nrhs;
     if (!capacity()) {
       const int c = std::max(n, cap_hint);
-      if (minres())
+      if (eo()) {
+        MG_CHECK(coarse_eo_setup(ctx, const_cast<mglma_coarse_s*>(C), s));
+        be = b;
+        be.nrhs = c;
+        be.n = b.n / 2;  // the even sites
+        xe = be;
+        be.p = xe.p = nullptr;
+        MG_CHECK(dalloc(ctx, &be.p, be.bytes(), s));
+        MG_CHECK(dalloc(ctx, &xe.p, xe.bytes(), s));
+        MG_CHECK(mw.setup(ctx, s, be, c));
+      } else if (minres()) {
         MG_CHECK(mw.setup(ctx, s, b, c));
-      else
+      } else {
         MG_CHECK(w.setup(ctx, s, b, c, m));
+      }
       if (C->Aimg) {
-        scr_bytes = coarse_tc_scratch_bytes(C, c);
+        scr_bytes = std::max(coarse_tc_scratch_bytes(C, c), eo() ? coarse_eo_scratch_bytes(C, c) : (size_t)0);
         MG_CHECK(dalloc(ctx, &scr, scr_bytes, s));
       }
     }
@@ -501,7 +541,7 @@ struct CoarseSolver {
       }
       *iters += (long long)c * L;
       warmed = true;
-      return MGLMA_OK;
+      return finish(b, x);
     }
     if (b.p != gb || x.p != gx || tol != gtol) {
       reset();
@@ -526,7 +566,7 @@ struct CoarseSolver {
       }
     }
     *iters += (long long)c * L;
-    return MGLMA_OK;
+    return finish(b, x);
   }
 };
 

@@ -251,6 +251,7 @@ void mglma_solve_params_default(mglma_solve_params* p, int method) {
   p->check_every = method == MGLMA_SOLVER_CGNE ? 20 : 1;
   p->max_batch = 0;
   p->coarse_solver = MGLMA_COARSE_MINRES;
+  p->autotune = method == MGLMA_SOLVER_MG ? 1 : 0;
 }
 
 mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, const mglma_solve_params* prm,
@@ -271,7 +272,8 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
                                           !(prm->inner_tol > 0) || !(prm->coarse_tol > 0) ||
                                           prm->coarse_max_iter < 1 ||
                                           (prm->coarse_solver != MGLMA_COARSE_GCR &&
-                                           prm->coarse_solver != MGLMA_COARSE_MINRES))))
+                                           prm->coarse_solver != MGLMA_COARSE_MINRES &&
+                                           prm->coarse_solver != MGLMA_COARSE_MINRES_EO))))
     return fail(MGLMA_ERR_INVALID, "solve_batch: bad parameters");
   int total = 0;
   for (int g = 0; g < ngroups; ++g) {
@@ -311,6 +313,7 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
     fl.add(X.p);
     MG_CHECK(pack_spinor(ctx, sb.dev + (size_t)off * V * 24, B, s));
     MG_CUDA(cudaMemsetAsync(X.p, 0, X.bytes(), s));
+    if (prm->method == MGLMA_SOLVER_MG && prm->autotune) MG_CHECK(autotune_for_batch(ctx, G, C, n));
     std::vector<RhsStat> rs;
     mglma_status st;
     if (prm->method == MGLMA_SOLVER_CGNE) {

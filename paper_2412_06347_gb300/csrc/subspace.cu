@@ -622,6 +622,67 @@ static double transfer_bytes(const mglma_subspace_s* S, int prec, int nrhs) {
   return V * n2 * 6.0 * cb + N * (V * 12.0 * cf + V1 * n2 * cf) + (S->phi16 && prec != MGLMA_FP64 ? V1 * n2 * 4.0 : 0.0);
 }
 
+// ------------------------------------------------------------ coarse gamma5 gamma_k (level 1)
+// out[((y b0 + t) n2 + i) n2 + j] = sum over the sites x of B_y on the block's
+// local time slice t of phi_i(x)^dag gamma5 gamma_k phi_j(x).  In the chiral
+// basis gamma5 gamma_k = [[0, -i sigma_k], [-i sigma_k, 0]] couples the two
+// chiralities only, so blocks with alpha_i = alpha_j vanish; phi_i keeps the
+// two spins of its chirality (q = spin * 3 + colour within them).
+template <typename B>
+__global__ void gamma_level1_kernel(const void* base, const float* scale, BlockGeo g, int nv, int k,
+                                    double2* __restrict__ out) {
+  const int64_t y = blockIdx.x / g.b[0];
+  const int t = (int)(blockIdx.x % g.b[0]);
+  const int n2 = 2 * nv;
+  const int per_t = g.nB / g.b[0];  // site-in-block index: local time slowest
+  // -i sigma_k as (re, im) of m00, m01, m10, m11
+  double m[4][2];
+  if (k == 1) {
+    const double v[4][2] = {{0, 0}, {0, -1}, {0, -1}, {0, 0}};
+    for (int a = 0; a < 4; ++a) m[a][0] = v[a][0], m[a][1] = v[a][1];
+  } else if (k == 2) {
+    const double v[4][2] = {{0, 0}, {-1, 0}, {1, 0}, {0, 0}};
+    for (int a = 0; a < 4; ++a) m[a][0] = v[a][0], m[a][1] = v[a][1];
+  } else {
+    const double v[4][2] = {{0, -1}, {0, 0}, {0, 0}, {0, 1}};
+    for (int a = 0; a < 4; ++a) m[a][0] = v[a][0], m[a][1] = v[a][1];
+  }
+  for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+    const int i = e / n2, j = e % n2;
+    Cx<double> acc = cx(0.0, 0.0);
+    if (i / nv != j / nv) {
+      for (int kk = t * per_t; kk < (t + 1) * per_t; ++kk) {
+        Cx<double> pi[6], pj[6];
+        BIO<B>::template load<double>(base, scale, (size_t)y * n2 + i, g.nB, kk, pi);
+        BIO<B>::template load<double>(base, scale, (size_t)y * n2 + j, g.nB, kk, pj);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const Cx<double> u = pj[c], l = pj[3 + c];
+          const Cx<double> w0 = cx(m[0][0], m[0][1]) * u + cx(m[1][0], m[1][1]) * l;
+          const Cx<double> w1 = cx(m[2][0], m[2][1]) * u + cx(m[3][0], m[3][1]) * l;
+          cfma_conj(acc, pi[c], w0);
+          cfma_conj(acc, pi[3 + c], w1);
+        }
+      }
+    }
+    out[((size_t)blockIdx.x * n2 + i) * n2 + j] = make_double2(acc.re, acc.im);
+  }
+}
+
+mglma_status coarse_gamma_level1(mglma_ctx ctx, const mglma_subspace_s* S, int k, double2* out, cudaStream_t s) {
+  const BlockGeo& g = S->geo;
+  const unsigned blocks = (unsigned)(g.V1 * g.b[0]);
+  ProfScope ps(ctx, K_SETUP, s);
+  if (S->phi64)
+    gamma_level1_kernel<double><<<blocks, 256, 0, s>>>(S->phi64, nullptr, g, S->nv, k, out);
+  else if (S->phi16)
+    gamma_level1_kernel<__half><<<blocks, 256, 0, s>>>(S->phi16, S->scale16, g, S->nv, k, out);
+  else
+    gamma_level1_kernel<float><<<blocks, 256, 0, s>>>(S->phi32, nullptr, g, S->nv, k, out);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
 mglma_status restrict_fine(mglma_ctx ctx, const mglma_subspace_s* S, const Spinor& in, void* out_coarse,
                            cudaStream_t s) {
   ProfScope ps(ctx, K_RESTRICT, s, transfer_bytes(S, in.prec, in.nrhs), 8.0 * S->geo.V * 12.0 * S->nv * in.nrhs);

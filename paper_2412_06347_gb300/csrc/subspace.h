@@ -44,6 +44,11 @@ struct mglma_coarse_s {
   // geo.V1 = V_l; sub is the level-1 basis of the chain)
   int level = 1;
   const mglma_coarse_s* parent = nullptr;
+  // even-odd preconditioning (coarse_eo.cu), built on first use: inverses of
+  // the self blocks D_yy (FP64, layout of one slot of A64) and their BF16
+  // tensor-core image (one slot per site)
+  double2* Sinv64 = nullptr;
+  uint16_t* Sinv_img = nullptr;
 };
 
 namespace mglma {
@@ -81,6 +86,41 @@ constexpr int CMODE_D = 0, CMODE_Q = 2, CMODE_DDAG = 3;
 // scratch (optional): work space of the tensor-core path, see coarse_apply_tc
 mglma_status coarse_apply(mglma_ctx ctx, const mglma_coarse_s* Cc, const void* X, void* Y, int nrhs, int prec,
                           int mode, cudaStream_t s, void* scratch = nullptr, size_t scratch_bytes = 0);
+// ---- even-odd (Schur) preconditioning of the coarse operator (coarse_eo.cu)
+// Needs every coarse extent even (then every hop joins opposite parities).
+// Half-lattice fields: [rhs][V1 / 2][n2], site y of a parity at index y >> 1.
+mglma_status coarse_eo_setup(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s);
+// Y_e = S_ee X_e (mode bit 1: gamma5hat S_ee, the Hermitian form) with
+// S_ee = D_ee - D_eo D_oo^-1 D_oe; FP32 fields use the tensor cores when the
+// operator has its BF16 image, FP64 fields the FP64 operator
+mglma_status coarse_schur_apply(mglma_ctx ctx, const mglma_coarse_s* C, const void* Xe, void* Ye, int nrhs, int prec,
+                                int mode, void* scratch, size_t scratch_bytes, cudaStream_t s);
+// b_e' = b_e - D_eo D_oo^-1 b_o from a full field b; x (full) from x_e and b:
+// x_o = D_oo^-1 (b_o - D_oe x_e)
+mglma_status coarse_eo_prepare(mglma_ctx ctx, const mglma_coarse_s* C, const void* b, void* be, int nrhs, int prec,
+                               void* scratch, size_t scratch_bytes, cudaStream_t s);
+mglma_status coarse_eo_reconstruct(mglma_ctx ctx, const mglma_coarse_s* C, const void* b, const void* xe, void* x,
+                                   int nrhs, int prec, void* scratch, size_t scratch_bytes, cudaStream_t s);
+// Y (full field) = S_ee X on the even sites, zero on the odd ones (the C ABI's
+// MGLMA_OP_SCHUR / _Q); forms the even-odd set-up on first use
+mglma_status coarse_schur_full(mglma_ctx ctx, mglma_coarse_s* C, const void* X, void* Y, int nrhs, int prec,
+                               int mode, cudaStream_t s);
+// scratch the FP32 (tensor-core) even-odd calls need for nrhs RHS
+size_t coarse_eo_scratch_bytes(const mglma_coarse_s* C, int nrhs);
+// one tensor-core launch on half-lattice fields (coarse_tc.cu): Y = sign *
+// sum over slots d_lo..d_hi, hop slots reading Xhop, the self slot reading
+// Xself (with the self-block image Aself when given), for the sites of
+// parity par; mode bit 0 applies gamma5hat to both inputs, bit 1 to Y
+mglma_status coarse_tc_eo_launch(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
+                                 float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
+                                 float sign, void* scratch, cudaStream_t s);
+size_t coarse_tc_half_image_bytes(const mglma_coarse_s* C, int nrhs);
+mglma_status coarse_tc_image_blocks(mglma_ctx ctx, const double2* A64, int64_t V1, int n2, int nslots,
+                                    uint16_t** img, cudaStream_t s);
+
+// Gam_k on level 1 (Eq. coarse:gamma with an open time index): out[y][t][i][j],
+// t < b[0] the block's local time slice, FP64
+mglma_status coarse_gamma_level1(mglma_ctx ctx, const mglma_subspace_s* S, int k, double2* out, cudaStream_t s);
 // the copy the FP32 solvers read (FP32, BF16 tensor-core image or BF16 plain)
 // from the FP64 master A64
 mglma_status coarse_store_copies(mglma_ctx ctx, mglma_coarse_s* Cc, int store, cudaStream_t s);

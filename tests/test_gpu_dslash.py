@@ -82,25 +82,56 @@ def test_dirac_fp32_parity(m, ctx, L, nrhs):
     m.mglma_gauge_free(g)
 
 
-TILES = [(1, 1), (2, 1), (4, 1), (1, 2), (1, 4), (2, 2), (2, 4)]
+TILES = [(1, 1), (2, 1), (4, 1), (1, 2), (1, 4), (2, 2), (2, 4), ("staged", 4), ("staged", 8), ("staged", 16)]
+
+
+def tile_code(m, nr, rw):
+    return m.dslash32_staged_code(rw) if nr == "staged" else m.dslash32_tile_code(nr, rw)
 
 
 @pytest.mark.parametrize("nr,rw", TILES)
 def test_dirac_fp32_tile_shapes(m, ctx, nr, rw):
-    """Every FP32 tile shape (RHS per thread x RHS tiles per CTA) against the
-    oracle, with RHS counts that leave partial tiles and partial tile groups
-    and a volume (6x3x5x2 = 180) that is not a multiple of any CTA's sites."""
+    """Every FP32 tile shape (RHS per thread x RHS tiles per CTA, and the
+    staged-tile kernel's 32 sites x NRT RHS) against the oracle, with RHS
+    counts that leave partial tiles and partial tile groups and a volume
+    (6x3x5x2 = 180) that is not a multiple of any CTA's sites."""
     kappa, csw = 0.125, 1.7
     L = (6, 3, 5, 2)
     U, g = load(m, ctx, L, 0.2, 1002, kappa, csw)
     c = m.Context(0)
-    for nrhs in (1, 5, 11):
-        m.mglma_autotune_set(c, 0, nrhs, m.dslash32_tile_code(nr, rw))
+    for nrhs in (1, 5, 11, 17):
+        m.mglma_autotune_set(c, 0, nrhs, tile_code(m, nr, rw))
         psi = synthetic.random_spinors(L, nrhs, 60 + nrhs)
         for op in (0, 1, 2, 3):
             out = np.zeros_like(psi)
             m.mglma_dirac_apply(c, g, op, nrhs, psi, out, m.MGLMA_FP32)
             assert rel_per_rhs(out, oracle_op(U, psi, kappa, csw, op)).max() < 2e-6, (nrhs, op)
+    c.close()
+    m.mglma_gauge_free(g)
+
+
+@pytest.mark.parametrize("L,t_bc", [((6, 3, 5, 2), -1), ((4, 4, 4, 8), 1), ((2, 8, 2, 16), -1)])
+def test_staged_kernel_equals_thread_per_site_bitwise(m, ctx, L, t_bc):
+    """The staged-tile kernel pre-scales the staged links by -1/2 (times
+    t_bc across the time boundary), which is exact, and sums the terms in the
+    order of the one-site-per-thread kernel: both give identical bits for D,
+    D^dag, Q and D^dag D."""
+    kappa, csw = 0.1266, 1.9
+    U = synthetic.gauge_links(L, 0.2, 1005)
+    g = m.mglma_gauge_load(ctx, L, U, kappa, csw, t_bc=t_bc)
+    c = m.Context(0)
+    nrhs = 9
+    psi = synthetic.random_spinors(L, nrhs, 70)
+    for op in (0, 1, 2, 3):
+        outs = []
+        for code in (m.dslash32_tile_code(1, 1), m.dslash32_staged_code(4), m.dslash32_staged_code(8),
+                     m.dslash32_staged_code(16)):
+            m.mglma_autotune_set(c, 0, nrhs, code)
+            o = np.zeros_like(psi)
+            m.mglma_dirac_apply(c, g, op, nrhs, psi, o, m.MGLMA_FP32)
+            outs.append(o)
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0]), op
     c.close()
     m.mglma_gauge_free(g)
 

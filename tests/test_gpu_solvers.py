@@ -105,7 +105,8 @@ def test_autotune_table_and_cache(m, ctx, c1, tmp_path):
     m.mglma_autotune(ctx, c1["g"], c1["C"], 3)
     nr, ms = m.mglma_autotune_get(ctx, 0, 3)
     nt, ms2 = m.mglma_autotune_get(ctx, 1, 3)
-    assert nr in [m.dslash32_tile_code(a, b) for a in (1, 2, 4) for b in (1, 2, 4) if a < 4 or b == 1]
+    assert nr in [m.dslash32_tile_code(a, b) for a in (1, 2, 4) for b in (1, 2, 4) if a < 4 or b == 1] + \
+        [m.dslash32_staged_code(t) for t in (4, 8, 16)]
     assert ms > 0 and nt in (8, 16, 32) and ms2 > 0
     f = tmp_path / "tune.txt"
     m.mglma_autotune_save(ctx, f)
