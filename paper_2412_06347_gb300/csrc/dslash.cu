@@ -279,10 +279,16 @@ constexpr int dslash_min_ctas() {
   return sizeof(R) == 8 ? 3 : (NR == 1 ? (RW == 1 ? 6 : 5) : (NR == 2 ? 4 : 3));
 }
 
-template <typename R, int NR, bool DAG, int RW>
+// RED (FP32, one RHS per thread, one RHS tile per CTA only) also reduces, per
+// CTA, |t|^2 and <t, in> = sum conj(t) in over the CTA's 128 sites of t = op(in)
+// into part[(rhs * nblk + block) * 3 + {0, 1, 2}] (|t|^2, Re, Im): FP32 over
+// each warp's 32 sites, FP64 from there on, summed over the blocks in a fixed
+// order by dot_finish_kernel.
+template <typename R, int NR, bool DAG, int RW, bool RED = false>
 __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kernel(const void* __restrict__ in, void* __restrict__ out,
                                                      const void* __restrict__ U, const void* __restrict__ C,
-                                                     DslashArgs a) {
+                                                     DslashArgs a, double* __restrict__ part = nullptr) {
+  static_assert(!RED || (NR == 1 && RW == 1 && sizeof(R) == 4), "fused reduction: FP32 tile 1,1 only");
   constexpr int SW = 128 / RW;  // sites per CTA
   const int64_t V = a.q.V;
   // RHS tile groups run fastest in launch order, so the CTAs that share a
@@ -290,9 +296,14 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
   const int ntile = (a.nrhs + NR - 1) / NR;
   int64_t site;
   int r0;
+  bool valid = true;  // with RED every thread reaches the block reduction
   if constexpr (RW == 1) {
     site = (int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x;
-    if (site >= V) return;
+    if (site >= V) {
+      if constexpr (!RED) return;
+      valid = false;
+      site = V - 1;
+    }
     r0 = (blockIdx.x % ntile) * NR;
   } else {
     const int ngrp = (ntile + RW - 1) / RW;
@@ -353,13 +364,49 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
   }
 #pragma unroll
   for (int r = 0; r < NR; ++r)
-    if (r0 + r < a.nrhs) {
+    if (r0 + r < a.nrhs && valid) {
       if (a.g5out) {
 #pragma unroll
         for (int k = 6; k < 12; ++k) acc[r][k] = -acc[r][k];
       }
       IO<R>::store(out, V, r0 + r, site, acc[r]);
     }
+  if constexpr (RED) {
+    float nn = 0.f, dr = 0.f, di = 0.f;
+    if (valid) {
+      Cx<R> sv[12];
+      IO<R>::load(in, V, r0, site, sv);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const Cx<R> t = acc[0][k];
+        nn += t.re * t.re + t.im * t.im;
+        dr += t.re * sv[k].re + t.im * sv[k].im;
+        di += t.re * sv[k].im - t.im * sv[k].re;
+      }
+    }
+    // FP32 within a warp (32 sites), FP64 from the warp partials on: the
+    // FP64 pipe of GB300 is too narrow for a per-thread FP64 tree
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nn += __shfl_down_sync(0xffffffffu, nn, o);
+      dr += __shfl_down_sync(0xffffffffu, dr, o);
+      di += __shfl_down_sync(0xffffffffu, di, o);
+    }
+    __shared__ float wsum[4][3];
+    const int w = threadIdx.x / 32;
+    if (threadIdx.x % 32 == 0) {
+      wsum[w][0] = nn;
+      wsum[w][1] = dr;
+      wsum[w][2] = di;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      const int64_t nblk = (V + 127) / 128;
+      const int c = threadIdx.x;
+      part[((size_t)r0 * nblk + blockIdx.x / ntile) * 3 + c] =
+          (((double)wsum[0][c] + (double)wsum[1][c]) + (double)wsum[2][c]) + (double)wsum[3][c];
+    }
+  }
 }
 
 // ------------------------------------------------------------ staged-tile FP32 stencil (many RHS)
@@ -910,10 +957,12 @@ static void launch_dslash(const Spinor& in, Spinor& out, const void* U, const vo
 // FP32 tile shape (RHS per thread NR, RHS tiles per CTA RW) encoded as
 // NR + 16 (RW - 1), or 64 + NRT for the staged-tile kernel; the autotuner
 // (tune.cu) may replace the default below for an RHS count on a context.
-// One RHS: one site per thread (the links are read once anyway); from 4
-// RHS on, the staged-tile kernel shares each site's links and clover among
-// the RHS of a CTA.
-int dslash32_default_tile(int nrhs) { return nrhs >= 4 ? 64 + 8 : dslash32_tile_code(1, 1); }
+// Measured on GB300 (64x32^3, 1-16 RHS): one RHS per thread and one RHS tile
+// per CTA was fastest at every count (16 RHS: 2.93 ms, staged tiles of 4, 8,
+// 16 RHS 3.45, 3.36, 3.49 ms -- the staged kernel issues as many
+// instructions per site and RHS, its shared-memory loads replacing the
+// rebuilt third link row).
+int dslash32_default_tile(int) { return dslash32_tile_code(1, 1); }
 
 template <int NRT, bool RED>
 static void launch_staged(const Spinor& in, Spinor& out, const void* U, const void* C, const DslashArgs& a,
@@ -981,6 +1030,7 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
   return MGLMA_OK;
 }
 
+// room for the finer of the two partial-sum grids (32-site tiles)
 size_t dslash_dot_part_doubles(int64_t V, int nrhs) { return (size_t)3 * nrhs * (size_t)((V + kDT - 1) / kDT); }
 
 mglma_status dslash_dot(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, double* part,
@@ -994,12 +1044,18 @@ mglma_status dslash_dot(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in,
   a.bc = (double)G->g.t_bc;
   a.nrhs = in.nrhs;
   a.g5out = 0;
-  const int64_t nblk = (in.V + kDT - 1) / kDT;
+  // the kernel of the tuned tile shape: the staged-tile kernel (per-warp
+  // partials of 32-site tiles, RHS tiles of 4, whose epilogue fits 96
+  // registers) or one site per thread (partials of 128-site blocks)
+  const bool staged = dslash32_tile_staged(tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, G->g.V, dslash32_default_tile(in.nrhs)));
+  const int64_t nblk = staged ? (in.V + kDT - 1) / kDT : (in.V + 127) / 128;
   {
-    // the staged-tile kernel with its per-warp reduction epilogue, RHS tiles
-    // of 4 (the epilogue fits 96 registers there without spilling)
     ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(in.V, in.nrhs, false), dslash_flops(in.V, in.nrhs));
-    launch_staged<4, true>(in, out, G->U32, G->C32, a, false, s, part);
+    if (staged)
+      launch_staged<4, true>(in, out, G->U32, G->C32, a, false, s, part);
+    else
+      dslash_kernel<float, 1, false, 1, true><<<(unsigned)(nblk * in.nrhs), 128, 0, s>>>(in.p, out.p, G->U32,
+                                                                                         G->C32, a, part);
   }
   MG_LAUNCH_CHECK();
   {
