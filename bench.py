@@ -538,7 +538,7 @@ def main():
     ap.add_argument("--serve-hbm", type=float, default=0.9, help="c5: share of free HBM the serving slots take")
     ap.add_argument("--group", type=int, default=0, help="sources per step (default: the workload's)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--coarse-solver", default="minres", choices=sorted(COARSE_SOLVERS),
+    ap.add_argument("--coarse-solver", default="minres_eo", choices=sorted(COARSE_SOLVERS),
                     help="coarse solver inside the preconditioner")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-solver sample")
     ap.add_argument("--micro", default="", choices=["", "dslash32", "dslash64", "coarse", "transfer", "contract"],

@@ -240,7 +240,9 @@ mglma_status mglma_coarse_build(mglma_ctx ctx, mglma_gauge g, mglma_subspace s, 
 void mglma_coarse_free(mglma_coarse c);
 /* Frees the FP64 copy of D1 when a low-precision copy exists (store BF16 or
  * FP32), e.g. to keep large lattices resident for serving; FP64 coarse
- * applications, export and the propagator pieces are refused afterwards. */
+ * applications, export and the propagator pieces are refused afterwards.
+ * When every coarse extent is even and the BF16 tensor-core copy exists, the
+ * even-odd self-block inverses are formed first and their BF16 image kept. */
 mglma_status mglma_coarse_release_fp64(mglma_coarse c);
 mglma_status mglma_coarse_info(mglma_coarse c, int* nv, int Lb[4], int64_t* coarse_volume);
 /* Exports the FP64 stencil as complex128 [9][V1][2nv][2nv]. */
@@ -390,9 +392,12 @@ typedef enum {
                                  odd sites by back-substitution (the paper's
                                  coarse solves use the even-odd preconditioned
                                  coarse operator, Sec. "Comparison of the
-                                 cost"); every coarse extent must be even and
-                                 the FP64 coarse operator held (the self-block
-                                 inverses are formed from it on first use) */
+                                 cost"); the default.  On a coarse grid with an
+                                 odd extent it runs as MGLMA_COARSE_MINRES.  The
+                                 self-block inverses are formed from the FP64
+                                 operator on first use (or by
+                                 mglma_coarse_release_fp64, before it frees the
+                                 FP64 copies) */
 } mglma_coarse_solver;
 
 typedef struct {
@@ -427,7 +432,7 @@ typedef struct {
 
 /* Fills *p with the library defaults for `method`: tol 1e-10; MG: gcr_m 4,
  * nu 7, inner_tol 3e-6, coarse_tol 0.02, coarse_max_iter 108 (whole cycles
- * of 12 MINRES iterations), coarse_solver MINRES, check_every 1, max_batch 0,
+ * of 12 MINRES iterations), coarse_solver MINRES_EO, check_every 1, max_batch 0,
  * autotune 1; CGNE: max_iter 100000, check_every 20, autotune 0. */
 void mglma_solve_params_default(mglma_solve_params* p, int method);
 

@@ -345,9 +345,16 @@ mglma_status mglma_coarse_release_fp64(mglma_coarse Cc) {
   if (!Cc->A32 && !Cc->A16 && !Cc->Aimg)
     return fail(MGLMA_ERR_INVALID, "coarse_release_fp64: the FP64 operator is the only copy");
   if (Cc->ctx) MG_CUDA(cudaSetDevice(Cc->ctx->device));
+  // the even-odd set-up needs the FP64 operator: form it now when the coarse
+  // grid allows it, keeping only its low-precision image
+  bool even = Cc->Aimg != nullptr;
+  for (int m = 0; m < 4; ++m) even = even && Cc->geo.Lb[m] % 2 == 0;
+  if (even && Cc->ctx) MG_CHECK(coarse_eo_setup(Cc->ctx, Cc, Cc->ctx->stream));
   MG_CUDA(cudaDeviceSynchronize());
   cudaFree(Cc->A64);
   Cc->A64 = nullptr;
+  cudaFree(Cc->Sinv64);
+  Cc->Sinv64 = nullptr;
   return MGLMA_OK;
 }
 

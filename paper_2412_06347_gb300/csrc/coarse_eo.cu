@@ -199,7 +199,7 @@ __global__ void eo_g5_kernel(T* y, int n2, size_t n) {
 static unsigned nblk(size_t n) { return (unsigned)((n + 255) / 256); }
 
 mglma_status coarse_eo_setup(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s) {
-  if (C->Sinv64) return MGLMA_OK;
+  if (C->Sinv64 || (C->Sinv_img && !C->A64)) return MGLMA_OK;  // formed (FP64 copy kept, or released)
   for (int m = 0; m < 4; ++m)
     if (C->geo.Lb[m] % 2)
       return fail(MGLMA_ERR_INVALID, "even-odd: every extent of the coarse grid must be even");
@@ -298,7 +298,9 @@ static mglma_status schur_composed(mglma_ctx ctx, const mglma_coarse_s* C, const
 
 mglma_status coarse_schur_apply(mglma_ctx ctx, const mglma_coarse_s* C, const void* Xe, void* Ye, int nrhs, int prec,
                                 int mode, void* scratch, size_t scratch_bytes, cudaStream_t s) {
-  if (!C->Sinv64) return fail(MGLMA_ERR_INVALID, "schur apply: even-odd set-up missing");
+  if (!C->Sinv64 && !C->Sinv_img) return fail(MGLMA_ERR_INVALID, "schur apply: even-odd set-up missing");
+  if (!C->Sinv64 && (prec == MGLMA_FP64 || !C->Aimg))
+    return fail(MGLMA_ERR_INVALID, "schur apply: the FP64 self-block inverses were released");
   if (nrhs == 0) return MGLMA_OK;
   const double V1 = (double)C->geo.V1, n2 = C->n2, N = nrhs;
   ProfScope ps(ctx, K_COARSE, s, V1 * (9.0 * n2 * n2 * 4.0 + 2.0 * N * n2 * 8.0),

@@ -421,7 +421,13 @@ struct CoarseSolver {
   void reset() {
     for (auto& G : g) drop(G);
   }
-  bool eo() const { return method == MGLMA_COARSE_MINRES_EO; }
+  // even-odd needs every coarse extent even; elsewhere it runs as MINRES on Q1
+  bool eo() const {
+    if (method != MGLMA_COARSE_MINRES_EO) return false;
+    for (int m = 0; m < 4; ++m)
+      if (C->geo.Lb[m] % 2) return false;
+    return true;
+  }
   bool minres() const { return method == MGLMA_COARSE_MINRES || eo(); }
   int cycle_len() const { return minres() ? 12 : m; }
   int capacity() const { return minres() ? mw.cap : w.cap; }

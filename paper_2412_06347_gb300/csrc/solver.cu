@@ -250,7 +250,7 @@ void mglma_solve_params_default(mglma_solve_params* p, int method) {
   p->coarse_max_iter = 108;
   p->check_every = method == MGLMA_SOLVER_CGNE ? 20 : 1;
   p->max_batch = 0;
-  p->coarse_solver = MGLMA_COARSE_MINRES;
+  p->coarse_solver = MGLMA_COARSE_MINRES_EO;
   p->autotune = method == MGLMA_SOLVER_MG ? 1 : 0;
 }
 
