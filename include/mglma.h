@@ -241,8 +241,9 @@ void mglma_coarse_free(mglma_coarse c);
 /* Frees the FP64 copy of D1 when a low-precision copy exists (store BF16 or
  * FP32), e.g. to keep large lattices resident for serving; FP64 coarse
  * applications, export and the propagator pieces are refused afterwards.
- * When every coarse extent is even and the BF16 tensor-core copy exists, the
- * even-odd self-block inverses are formed first and their BF16 image kept. */
+ * When every coarse extent is even, the even-odd self-block inverses are
+ * formed first (kept as their BF16 tensor-core image when the operator has
+ * one, else in FP64). */
 mglma_status mglma_coarse_release_fp64(mglma_coarse c);
 mglma_status mglma_coarse_info(mglma_coarse c, int* nv, int Lb[4], int64_t* coarse_volume);
 /* Exports the FP64 stencil as complex128 [9][V1][2nv][2nv]. */
@@ -393,11 +394,12 @@ typedef enum {
                                  coarse solves use the even-odd preconditioned
                                  coarse operator, Sec. "Comparison of the
                                  cost"); the default.  On a coarse grid with an
-                                 odd extent it runs as MGLMA_COARSE_MINRES.  The
-                                 self-block inverses are formed from the FP64
-                                 operator on first use (or by
-                                 mglma_coarse_release_fp64, before it frees the
-                                 FP64 copies) */
+                                 odd extent, or when the set-up cannot be formed
+                                 (FP64 operator released before it was), it runs
+                                 as MGLMA_COARSE_MINRES.  The self-block inverses
+                                 are formed from the FP64 operator on first use
+                                 (or by mglma_coarse_release_fp64, before it
+                                 frees the FP64 operator) */
 } mglma_coarse_solver;
 
 typedef struct {
@@ -418,6 +420,14 @@ typedef struct {
                            bucket) tunes the stencil and coarse tile shapes
                            (mglma_autotune) before it runs; 0 = use the table as
                            it stands (defaults where empty) */
+  int graph;            /* MG: 1 = every FGCR iteration after the first runs as one
+                           CUDA graph -- fine stencil, restriction, the coarse
+                           MINRES loop as a device-side conditional node that
+                           stops when every RHS converged or the cycle cap is
+                           reached, prolongation, MR smoothing, orthogonalisation
+                           and update -- with one host read of the convergence
+                           mask per iteration (not while mglma_profile is on);
+                           0 = launches issued from the host */
 } mglma_solve_params;
 
 typedef struct {
@@ -433,7 +443,8 @@ typedef struct {
 /* Fills *p with the library defaults for `method`: tol 1e-10; MG: gcr_m 4,
  * nu 7, inner_tol 3e-6, coarse_tol 0.02, coarse_max_iter 108 (whole cycles
  * of 12 MINRES iterations), coarse_solver MINRES_EO, check_every 1, max_batch 0,
- * autotune 1; CGNE: max_iter 100000, check_every 20, autotune 0. */
+ * autotune 1, graph 1; CGNE: max_iter 100000, check_every 20, autotune 0,
+ * graph 0. */
 void mglma_solve_params_default(mglma_solve_params* p, int method);
 
 /* Solves D x = b (x = S b, the propagator of Sec. 2 applied to b) for

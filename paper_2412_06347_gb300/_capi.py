@@ -99,7 +99,7 @@ class mglma_solve_params(C.Structure):
     _fields_ = [("method", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("gcr_m", C.c_int),
                 ("nu", C.c_int), ("inner_tol", C.c_double), ("coarse_tol", C.c_double),
                 ("coarse_max_iter", C.c_int), ("check_every", C.c_int), ("max_batch", C.c_int),
-                ("coarse_solver", C.c_int), ("autotune", C.c_int)]
+                ("coarse_solver", C.c_int), ("autotune", C.c_int), ("graph", C.c_int)]
 
 
 class mglma_solve_stats(C.Structure):

@@ -346,15 +346,17 @@ mglma_status mglma_coarse_release_fp64(mglma_coarse Cc) {
     return fail(MGLMA_ERR_INVALID, "coarse_release_fp64: the FP64 operator is the only copy");
   if (Cc->ctx) MG_CUDA(cudaSetDevice(Cc->ctx->device));
   // the even-odd set-up needs the FP64 operator: form it now when the coarse
-  // grid allows it, keeping only its low-precision image
-  bool even = Cc->Aimg != nullptr;
+  // grid allows it; with the tensor-core image only its BF16 image is kept
+  bool even = true;
   for (int m = 0; m < 4; ++m) even = even && Cc->geo.Lb[m] % 2 == 0;
   if (even && Cc->ctx) MG_CHECK(coarse_eo_setup(Cc->ctx, Cc, Cc->ctx->stream));
   MG_CUDA(cudaDeviceSynchronize());
   cudaFree(Cc->A64);
   Cc->A64 = nullptr;
-  cudaFree(Cc->Sinv64);
-  Cc->Sinv64 = nullptr;
+  if (Cc->Sinv_img) {
+    cudaFree(Cc->Sinv64);
+    Cc->Sinv64 = nullptr;
+  }
   return MGLMA_OK;
 }
 

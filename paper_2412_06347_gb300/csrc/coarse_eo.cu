@@ -199,7 +199,7 @@ __global__ void eo_g5_kernel(T* y, int n2, size_t n) {
 static unsigned nblk(size_t n) { return (unsigned)((n + 255) / 256); }
 
 mglma_status coarse_eo_setup(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s) {
-  if (C->Sinv64 || (C->Sinv_img && !C->A64)) return MGLMA_OK;  // formed (FP64 copy kept, or released)
+  if (C->Sinv64 || C->Sinv_img) return MGLMA_OK;  // formed
   for (int m = 0; m < 4; ++m)
     if (C->geo.Lb[m] % 2)
       return fail(MGLMA_ERR_INVALID, "even-odd: every extent of the coarse grid must be even");

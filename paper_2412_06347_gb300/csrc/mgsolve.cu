@@ -174,15 +174,72 @@ static mglma_status read_active(GcrWork& w, int n, std::vector<int>& h) {
 // mask on the host every that many iterations and stops when all converged.
 // tol_scale (nullable, host, n entries): RHS r stops at |r| <= tol *
 // tol_scale[r] * |b_r| instead of tol * |b_r|.
+// Graphs of whole FGCR iterations, one per direction slot k, captured on
+// first use; valid while the workspace, the iterate and the operators keep
+// their buffers (one defect-correction solve).
+struct IterGraphs {
+  std::vector<cudaGraphExec_t> ex;
+  std::function<mglma_status(bool)> set_capturing;  // preconditioner: record its coarse loop on the device
+  std::function<bool()> ready;                       // the operators were used once uncaptured
+  ~IterGraphs() {
+    for (auto e : ex)
+      if (e) cudaGraphExecDestroy(e);
+  }
+};
+
+static mglma_status gcr_run(GcrWork& w, const OpFn& A, const OpFn* M, const Vec& b, Vec& x, int max_iter, double tol,
+                            int poll_every, GcrResult& res, const std::vector<double>* tol_scale,
+                            IterGraphs* graphs);
+
 static mglma_status gcr(mglma_ctx ctx, cudaStream_t s, const OpFn& A, const OpFn* M, const Vec& b, Vec& x, int m,
                         int max_iter, double tol, int poll_every, GcrResult& res,
                         const std::vector<double>* tol_scale = nullptr) {
+  res = GcrResult();
+  res.per_rhs.assign(b.nrhs, 0);
+  if (b.nrhs == 0) return MGLMA_OK;
+  GcrWork w;
+  MG_CHECK(w.setup(ctx, s, b, b.nrhs, m));
+  return gcr_run(w, A, M, b, x, max_iter, tol, poll_every, res, tol_scale, nullptr);
+}
+
+// one FGCR iteration of slot k as a graph (captured on first use)
+static mglma_status gcr_iter_graphed(GcrWork& w, const OpFn& A, const OpFn* M, Vec& x, int n, int k, double tol2,
+                                     IterGraphs& G) {
+  if ((int)G.ex.size() < w.m) G.ex.assign(w.m, nullptr);
+  if (!G.ex[k]) {
+    MG_CHECK(G.set_capturing(true));
+    MG_CUDA(cudaStreamBeginCapture(w.s, cudaStreamCaptureModeThreadLocal));
+    mglma_status st = gcr_iter(w, A, M, x, n, k, tol2);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(w.s, &g);
+    G.set_capturing(false);
+    if (st != MGLMA_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return st != MGLMA_OK ? st : fail(MGLMA_ERR_CUDA, std::string("FGCR iteration capture: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MGLMA_ERR_CUDA, std::string("FGCR iteration instantiate: ") + cudaGetErrorString(ei));
+    }
+    G.ex[k] = ex;
+  }
+  MG_CUDA(cudaGraphLaunch(G.ex[k], w.s));
+  return MGLMA_OK;
+}
+
+static mglma_status gcr_run(GcrWork& w, const OpFn& A, const OpFn* M, const Vec& b, Vec& x, int max_iter, double tol,
+                            int poll_every, GcrResult& res, const std::vector<double>* tol_scale,
+                            IterGraphs* graphs) {
   const int n = b.nrhs;
+  const int m = w.m;
+  cudaStream_t s = w.s;
   res = GcrResult();
   res.per_rhs.assign(n, 0);
   if (n == 0) return MGLMA_OK;
-  GcrWork w;
-  MG_CHECK(w.setup(ctx, s, b, n, m));
   MG_CHECK(gcr_init(w, b, x));
   if (tol_scale) {
     // the mask compares |r|^2 with tol^2 |b|^2: scale the stored |b|^2
@@ -197,7 +254,10 @@ static mglma_status gcr(mglma_ctx ctx, cudaStream_t s, const OpFn& A, const OpFn
   if (poll_every == 1) MG_CHECK(read_active(w, n, prev));
   int it = 0;
   while (it < max_iter) {
-    MG_CHECK(gcr_iter(w, A, M, x, n, it % m, tol * tol));
+    if (graphs && graphs->ready())
+      MG_CHECK(gcr_iter_graphed(w, A, M, x, n, it % m, tol * tol, *graphs));
+    else
+      MG_CHECK(gcr_iter(w, A, M, x, n, it % m, tol * tol));
     ++it;
     if (poll_every > 0 && (it % poll_every == 0 || it == max_iter)) {
       MG_CHECK(read_active(w, n, hact));
@@ -370,6 +430,20 @@ static mglma_status read_mask(const int* dev, int n, std::vector<int>& h, cudaSt
   return MGLMA_OK;
 }
 
+// Body-end kernel of the captured coarse loop (a conditional WHILE node): one
+// more cycle ran; the loop goes on while some RHS is still active and fewer
+// than max_cycles cycles ran in this solve, so it always ends.  total counts
+// the cycles of every solve (iteration statistics).
+__global__ void coarse_loop_cond_kernel(const int* __restrict__ active, int n, int* cycles, long long* total,
+                                        int max_cycles, cudaGraphConditionalHandle h) {
+  int any = 0;
+  for (int r = 0; r < n; ++r) any |= active[r];
+  const int c = *cycles + 1;
+  *cycles = c;
+  *total += 1;
+  cudaGraphSetConditional(h, (any && c < max_cycles) ? 1u : 0u);
+}
+
 // Coarse solve of the preconditioner with a persistent workspace: MINRES on
 // Qhat (default), MINRES on g5hat S_ee of the even-odd preconditioned
 // operator (the odd sites follow by back-substitution), or GCR(m) on Dhat.
@@ -389,6 +463,12 @@ struct CoarseSolver {
   void* scr = nullptr;  // tensor-core apply work space (B images of X)
   size_t scr_bytes = 0;
   Vec be, xe;  // even-odd: the prepared source and the solution on the even sites
+  // captured form (inside a graph of a whole FGCR iteration): the loop body is
+  // captured on `side`; d_loop[0] counts the cycles of the current solve,
+  // d_total (long long) all cycles since the last read
+  cudaStream_t side = nullptr;
+  int* d_loop = nullptr;
+  long long* d_total = nullptr;
   struct Graphs {
     cudaGraphExec_t init = nullptr, cycle = nullptr;
     int n = -1;
@@ -403,6 +483,88 @@ struct CoarseSolver {
     if (scr) dfree(ctx, scr, s);
     if (be.p) dfree(ctx, be.p, s);
     if (xe.p) dfree(ctx, xe.p, s);
+    if (d_loop) dfree(ctx, d_loop, s);
+    if (d_total) dfree(ctx, d_total, s);
+    if (side) {
+      cudaStreamSynchronize(side);
+      cudaStreamDestroy(side);
+    }
+  }
+  // streams of this solver and of its workspaces (the captured loop body is
+  // recorded on the side stream)
+  void use_stream(cudaStream_t st) {
+    s = st;
+    w.s = st;
+    mw.s = st;
+    mw.sc.s = st;
+    w.sc.s = st;
+  }
+  // prepares the captured form: side stream, its reduction scratch, counters
+  mglma_status capture_ready() {
+    if (side) return MGLMA_OK;
+    MG_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    MG_CHECK(red_scratch_ready(ctx, side));
+    MG_CHECK(dalloc(ctx, (void**)&d_loop, sizeof(int), s));
+    MG_CHECK(dalloc(ctx, (void**)&d_total, sizeof(long long), s));
+    MG_CUDA(cudaMemsetAsync(d_total, 0, sizeof(long long), s));
+    MG_CUDA(cudaStreamSynchronize(side));
+    MG_CUDA(cudaStreamSynchronize(s));
+    return MGLMA_OK;
+  }
+  // cycles run by captured solves since the last call, times the cycle length
+  mglma_status take_captured_iters(long long* iters) {
+    if (!d_total) return MGLMA_OK;
+    long long h = 0;
+    MG_CUDA(cudaMemcpyAsync(&h, d_total, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaMemsetAsync(d_total, 0, sizeof(long long), s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    *iters += h * cycle_len();
+    return MGLMA_OK;
+  }
+  // e1 = D1^-1 b1 recorded into the graph being captured on s: init, then a
+  // conditional WHILE node running whole cycles until every RHS converged or
+  // ceil(max_iter / cycle) cycles ran, then (even-odd) the back-substitution
+  mglma_status solve_captured(const Vec& b, Vec& x, double tol, int max_iter) {
+    CoarseLevelScope level(ctx);
+    const int n = b.nrhs;
+    const int L = cycle_len();
+    const int max_cycles = (max_iter + L - 1) / L;
+    MG_CHECK(init(b, x));
+    MG_CUDA(cudaMemsetAsync(d_loop, 0, sizeof(int), s));
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    MG_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &ed, &nd));
+    if (cst != cudaStreamCaptureStatusActive) return fail(MGLMA_ERR_INVALID, "coarse solve: not inside a capture");
+    cudaGraphConditionalHandle h;
+    MG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    MG_CUDA(cudaGraphAddNode(&node, g, deps, ed, nd, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    MG_CUDA(cudaStreamBeginCaptureToGraph(side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const cudaStream_t main = s;
+    use_stream(side);
+    OpFn A = op();
+    mglma_status st = MGLMA_OK;
+    for (int k = 0; k < L && st == MGLMA_OK; ++k) st = iter(A, x, n, k, tol);
+    if (st == MGLMA_OK) {
+      coarse_loop_cond_kernel<<<1, 1, 0, side>>>(active(), n, d_loop, d_total, max_cycles, h);
+      if (cudaGetLastError() != cudaSuccess) st = fail(MGLMA_ERR_CUDA, "coarse loop: condition launch failed");
+    }
+    use_stream(main);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(side, &out);
+    MG_CHECK(st);
+    if (e != cudaSuccess) return fail(MGLMA_ERR_CUDA, std::string("coarse loop capture: ") + cudaGetErrorString(e));
+    MG_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return finish(b, x);
   }
   // destroys one graph set (both execs, its event brackets) and marks it empty
   static void drop(Graphs& G) {
@@ -421,12 +583,13 @@ struct CoarseSolver {
   void reset() {
     for (auto& G : g) drop(G);
   }
-  // even-odd needs every coarse extent even; elsewhere it runs as MINRES on Q1
+  // even-odd needs every coarse extent even and its set-up formed or formable
+  // (the FP64 operator held); elsewhere it runs as MINRES on Q1
   bool eo() const {
     if (method != MGLMA_COARSE_MINRES_EO) return false;
     for (int m = 0; m < 4; ++m)
       if (C->geo.Lb[m] % 2) return false;
-    return true;
+    return C->Sinv64 || (C->Sinv_img && C->Aimg) || C->A64;
   }
   bool minres() const { return method == MGLMA_COARSE_MINRES || eo(); }
   int cycle_len() const { return minres() ? 12 : m; }
@@ -600,6 +763,7 @@ struct TwoLevel {
   Scalars sc;
   CoarseSolver cs;
   bool ready = false;
+  bool capturing = false;  // recording into a graph: the coarse loop runs on the device
   ~TwoLevel() {
     dfree(ctx, b1.p, s);
     dfree(ctx, e1.p, s);
@@ -643,7 +807,10 @@ struct TwoLevel {
     b1n.nrhs = e1n.nrhs = svn.nrhs = tvn.nrhs = n;
     Spinor rs = as_spinor(r, V), zs = as_spinor(z, V);
     MG_CHECK(restrict_fine(ctx, S, rs, b1n.p, s));
-    MG_CHECK(cs.solve(b1n, e1n, p->coarse_tol, p->coarse_max_iter, &coarse_iters));
+    if (capturing)
+      MG_CHECK(cs.solve_captured(b1n, e1n, p->coarse_tol, p->coarse_max_iter));
+    else
+      MG_CHECK(cs.solve(b1n, e1n, p->coarse_tol, p->coarse_max_iter, &coarse_iters));
     MG_CHECK(prolong_coarse(ctx, S, e1n.p, zs, false, s));
     if (p->nu > 0) {
       // s = r - D z ; nu MR steps on D e = s, accumulated into z
@@ -711,6 +878,21 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
   OpFn Kf = [&](const Vec& in, Vec& o) { return K(in, o); };
   const int tb = 64, nb = (n + tb - 1) / tb;
   int total_inner = 0;
+  // FGCR workspace kept over the defect-correction cycles; with p.graph each
+  // FGCR iteration after the first runs as one captured graph (the coarse
+  // loop as a device-side conditional node), unless per-launch profiling is on
+  GcrWork gw;
+  {
+    Vec like = as_vec(r32);
+    MG_CHECK(gw.setup(ctx, s, like, n, p.gcr_m));
+  }
+  IterGraphs graphs;
+  const bool use_graphs = p.graph && !ctx->profile;
+  graphs.set_capturing = [&](bool on) -> mglma_status {
+    K.capturing = on;
+    return on ? K.cs.capture_ready() : MGLMA_OK;
+  };
+  graphs.ready = [&]() { return K.ready && K.cs.warmed; };
   for (int cycle = 0;; ++cycle) {
     MG_CHECK(norm2(ctx, vr, rr, s));
     MG_CHECK(read_doubles(rr, hrr, n, s));
@@ -736,7 +918,8 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
     std::vector<double> scale(n, 1.0);
     for (int i = 0; i < n; ++i) scale[i] = final_cycle_scale(p, out[i].residual);
     GcrResult gr;
-    MG_CHECK(gcr(ctx, s, A, &Kf, v32, e, p.gcr_m, p.max_iter - total_inner, p.inner_tol, 1, gr, &scale));
+    MG_CHECK(gcr_run(gw, A, &Kf, v32, e, p.max_iter - total_inner, p.inner_tol, 1, gr, &scale,
+                     use_graphs ? &graphs : nullptr));
     total_inner += gr.iterations;
     for (int i = 0; i < n; ++i) {
       out[i].iterations += gr.per_rhs[i];
@@ -748,6 +931,7 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
     MG_CHECK(copy_vec(ctx, vb, vr, s));
     MG_CHECK(axpby(ctx, nullptr, CM1, vw, nullptr, C1, vr, s));
   }
+  MG_CHECK(K.cs.take_captured_iters(&K.coarse_iters));
   for (int i = 0; i < n; ++i) out[i].coarse_iterations = K.coarse_iters;
   return coarse_tc_check(const_cast<mglma_coarse_s*>(C), s);
 }

@@ -233,6 +233,7 @@ MgParams mglma::mg_params(const mglma_solve_params& p) {
   mp.coarse_tol = p.coarse_tol;
   mp.coarse_max_iter = p.coarse_max_iter;
   mp.coarse_solver = p.coarse_solver;
+  mp.graph = p.graph;
   return mp;
 }
 
@@ -252,6 +253,7 @@ void mglma_solve_params_default(mglma_solve_params* p, int method) {
   p->max_batch = 0;
   p->coarse_solver = MGLMA_COARSE_MINRES_EO;
   p->autotune = method == MGLMA_SOLVER_MG ? 1 : 0;
+  p->graph = method == MGLMA_SOLVER_MG ? 1 : 0;
 }
 
 mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, const mglma_solve_params* prm,

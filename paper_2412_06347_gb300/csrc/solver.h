@@ -74,6 +74,7 @@ struct MgParams {
   double coarse_tol = 0.02;
   int coarse_max_iter = 108;
   int coarse_solver = MGLMA_COARSE_MINRES;
+  int graph = 1;  // FGCR iterations as captured graphs
 };
 
 // the MG fields of the public parameter block
