@@ -72,9 +72,10 @@ typedef enum {
   MGLMA_OP_DDAG = 1,     /* D^dag = g5 D g5   */
   MGLMA_OP_Q = 2,        /* Q = gamma5 D (Sec. 2) */
   MGLMA_OP_DDAGD = 3,    /* D^dag D           */
-  MGLMA_OP_SCHUR = 4,    /* coarse only: S_ee = D_ee - D_eo D_oo^-1 D_oe, the
-                            even-odd preconditioned operator on the even sites */
-  MGLMA_OP_SCHUR_Q = 5   /* coarse only: g5hat S_ee (Hermitian) */
+  MGLMA_OP_SCHUR = 4,    /* S = A_ee - H_eo A_oo^-1 H_oe, the even-odd
+                            preconditioned operator on the even sites
+                            (x0 + x1 + x2 + x3 even); coarse: D_ee - D_eo D_oo^-1 D_oe */
+  MGLMA_OP_SCHUR_Q = 5   /* gamma5 S (coarse: g5hat S_ee), Hermitian */
 } mglma_op;
 
 typedef struct {
@@ -136,7 +137,11 @@ mglma_status mglma_gauge_info(mglma_gauge g, int L[4], int64_t* volume);
 /* Applies op to nrhs canonical spinors: out = op(in).  compute selects the
  * arithmetic: MGLMA_FP64 (FP64 links and clover) or MGLMA_FP32 (FP32
  * reconstruct-12 links, FP32 clover, inputs rounded to FP32).  The definition
- * of D is the one stated at the top of this header (Sec. 2: Q = gamma5 D). */
+ * of D is the one stated at the top of this header (Sec. 2: Q = gamma5 D).
+ * MGLMA_OP_SCHUR / _SCHUR_Q (FP64 only, every extent even): the even-odd
+ * operator S (or gamma5 S) reads the even sites of in and writes the even
+ * sites of out, zero on the odd ones; the first call on a gauge field forms
+ * the inverse clover blocks (two Hermitian 6x6 per site, FP64). */
 mglma_status mglma_dirac_apply(mglma_ctx ctx, mglma_gauge g, mglma_op op, int nrhs, const double* in, double* out,
                                mglma_prec compute, void* cuda_stream);
 
@@ -374,10 +379,17 @@ mglma_status mglma_gamma5_gamma(mglma_ctx ctx, const mglma_lattice* lat, int k, 
 
 /* ---------------------------------------------------------------- solves (Sec. 2, Sec. 5) */
 typedef enum {
-  MGLMA_SOLVER_CGNE = 0, /* FP64 CG on D^dag D x = D^dag b: the plain method */
-  MGLMA_SOLVER_MG = 1    /* FP64 defect correction around FP32 flexible GCR
-                            preconditioned by the coarse-grid correction
-                            T0 D1^-1 R0 plus MR smoothing */
+  MGLMA_SOLVER_CGNE = 0,    /* FP64 CG on D^dag D x = D^dag b: the plain method */
+  MGLMA_SOLVER_MG = 1,      /* FP64 defect correction around FP32 flexible GCR
+                               preconditioned by the coarse-grid correction
+                               T0 D1^-1 R0 plus MR smoothing */
+  MGLMA_SOLVER_CGNE_EO = 2  /* the plain method on the even-odd preconditioned
+                               operator: FP64 CG on S^dag S x_e = S^dag b_e' with
+                               S = A_ee - H_eo A_oo^-1 H_oe (A the clover term,
+                               H the hops), b_e' = b_e - H_eo A_oo^-1 b_o, then
+                               x_o = A_oo^-1 (b_o - H_oe x_e) and FP64 defect
+                               correction on the true residual of D; every
+                               lattice extent must be even */
 } mglma_solver;
 
 /* Solver of the coarse system inside the MG preconditioner. */

@@ -11,7 +11,7 @@ from . import build as _build
 MGLMA_FP64, MGLMA_FP32, MGLMA_BF16, MGLMA_FP16 = 0, 1, 2, 3
 MGLMA_OP_D, MGLMA_OP_DDAG, MGLMA_OP_Q, MGLMA_OP_DDAGD, MGLMA_OP_SCHUR, MGLMA_OP_SCHUR_Q = 0, 1, 2, 3, 4, 5
 MGLMA_COARSE_GCR, MGLMA_COARSE_MINRES, MGLMA_COARSE_MINRES_EO = 0, 1, 2
-MGLMA_SOLVER_CGNE, MGLMA_SOLVER_MG = 0, 1
+MGLMA_SOLVER_CGNE, MGLMA_SOLVER_MG, MGLMA_SOLVER_CGNE_EO = 0, 1, 2
 MGLMA_SOURCE_Z2, MGLMA_SOURCE_Z4, MGLMA_SOURCE_POINT = 0, 1, 2
 _STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "NOT_CONVERGED", 6: "NUMERIC",
            7: "TIMEOUT", 8: "REJECTED"}

@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "internal.h"
+#include "solver.h"
 
 namespace mglma {
 
@@ -384,6 +385,7 @@ void mglma_gauge_free(mglma_gauge G) {
   cudaFree(G->U32);
   cudaFree(G->C64);
   cudaFree(G->C32);
+  cudaFree(G->Cinv64);
   delete G;
 }
 
@@ -401,9 +403,12 @@ mglma_status mglma_dirac_apply(mglma_ctx ctx, mglma_gauge G, mglma_op op, int nr
   if (!G->ready) return fail(MGLMA_ERR_INVALID, "mglma_dirac_apply: gauge field incomplete");
   MG_CHECK(check_gauge_device(ctx, G, "mglma_dirac_apply"));
   if (nrhs < 0) return fail(MGLMA_ERR_INVALID, "mglma_dirac_apply: nrhs < 0");
-  if (op < MGLMA_OP_D || op > MGLMA_OP_DDAGD) return fail(MGLMA_ERR_INVALID, "mglma_dirac_apply: bad op");
+  if (op < MGLMA_OP_D || op > MGLMA_OP_SCHUR_Q) return fail(MGLMA_ERR_INVALID, "mglma_dirac_apply: bad op");
   if (compute != MGLMA_FP64 && compute != MGLMA_FP32)
     return fail(MGLMA_ERR_INVALID, "mglma_dirac_apply: compute must be FP64 or FP32");
+  const bool schur = op == MGLMA_OP_SCHUR || op == MGLMA_OP_SCHUR_Q;
+  if (schur && compute != MGLMA_FP64)
+    return fail(MGLMA_ERR_INVALID, "mglma_dirac_apply: the even-odd operators are FP64 only");
   if (nrhs == 0) return MGLMA_OK;
   MG_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = pick_stream(ctx, cuda_stream);
@@ -411,6 +416,10 @@ mglma_status mglma_dirac_apply(mglma_ctx ctx, mglma_gauge G, mglma_op op, int nr
   Staged sin, sout;
   MG_CHECK(stage_in(ctx, in, bytes, s, sin));
   MG_CHECK(stage_out_alloc(ctx, out, bytes, s, sout));
+  if (schur) {
+    MG_CHECK(dirac_schur64(ctx, G, nrhs, sin.dev, sout.dev, op == MGLMA_OP_SCHUR_Q, s));
+    return stage_out_finish(out, bytes, s, sout);
+  }
   Spinor a, b;
   a.prec = b.prec = compute;
   a.nrhs = b.nrhs = nrhs;

@@ -121,6 +121,7 @@ struct mglma_gauge_s {
   float4* U32 = nullptr;   // [4][3][V]
   double2* C64 = nullptr;  // [2][18][V]
   float4* C32 = nullptr;   // [2][9][V]
+  double2* Cinv64 = nullptr;  // [2][18][V] inverse clover blocks (even-odd, formed on first use)
   int slabs_loaded = 0;   // time slices received
   std::vector<char> slab_seen;
   bool ready = false;

@@ -243,13 +243,13 @@ void mglma_solve_params_default(mglma_solve_params* p, int method) {
   if (!p) return;
   p->method = method;
   p->tol = 1e-10;
-  p->max_iter = method == MGLMA_SOLVER_CGNE ? 100000 : 4000;
+  p->max_iter = method == MGLMA_SOLVER_MG ? 4000 : 100000;
   p->gcr_m = 4;
   p->nu = 7;
   p->inner_tol = 3e-6;
   p->coarse_tol = 0.02;
   p->coarse_max_iter = 108;
-  p->check_every = method == MGLMA_SOLVER_CGNE ? 20 : 1;
+  p->check_every = method == MGLMA_SOLVER_MG ? 1 : 20;
   p->max_batch = 0;
   p->coarse_solver = MGLMA_COARSE_MINRES_EO;
   p->autotune = method == MGLMA_SOLVER_MG ? 1 : 0;
@@ -262,8 +262,11 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
   if (!ctx || !G || !prm || !group_nrhs || !b || !x) return fail(MGLMA_ERR_INVALID, "solve_batch: NULL argument");
   if (!G->ready) return fail(MGLMA_ERR_INVALID, "solve_batch: gauge field incomplete");
   MG_CHECK(check_gauge_device(ctx, G, "solve_batch"));
-  if (prm->method != MGLMA_SOLVER_CGNE && prm->method != MGLMA_SOLVER_MG)
+  if (prm->method != MGLMA_SOLVER_CGNE && prm->method != MGLMA_SOLVER_MG && prm->method != MGLMA_SOLVER_CGNE_EO)
     return fail(MGLMA_ERR_INVALID, "solve_batch: unknown method");
+  if (prm->method == MGLMA_SOLVER_CGNE_EO)
+    for (int m = 0; m < 4; ++m)
+      if (G->g.L[m] % 2) return fail(MGLMA_ERR_INVALID, "solve_batch: even-odd needs every lattice extent even");
   if ((prm->method == MGLMA_SOLVER_MG || x_coarse) && !C)
     return fail(MGLMA_ERR_INVALID, "solve_batch: the MG method and the pieces need a coarse operator");
   if (C && C->sub->gauge != G) return fail(MGLMA_ERR_INVALID, "solve_batch: coarse operator of another gauge field");
@@ -297,7 +300,7 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
   int cap = prm->max_batch > 0 ? prm->max_batch : 64;
   if (prm->max_batch <= 0) {
     const size_t room = device_room(ctx, s);
-    const size_t per_site = prm->method == MGLMA_SOLVER_CGNE ? 6 * 192 : 4 * 192 + (size_t)(6 + 2 * prm->gcr_m) * 96;
+    const size_t per_site = prm->method != MGLMA_SOLVER_MG ? 6 * 192 : 4 * 192 + (size_t)(6 + 2 * prm->gcr_m) * 96;
     const size_t per_rhs = per_site * (size_t)V;
     cap = (int)std::max<size_t>(1, std::min<size_t>(64, (size_t)(0.7 * (double)room) / per_rhs));
   }
@@ -318,12 +321,12 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
     if (prm->method == MGLMA_SOLVER_MG && prm->autotune) MG_CHECK(autotune_for_batch(ctx, G, C, n));
     std::vector<RhsStat> rs;
     mglma_status st;
-    if (prm->method == MGLMA_SOLVER_CGNE) {
+    if (prm->method != MGLMA_SOLVER_MG) {
       SolveControl ctl;
       ctl.tol = prm->tol;
       ctl.max_iter = prm->max_iter;
       ctl.check_every = prm->check_every;
-      st = cgne64(ctx, G, B, X, ctl, rs, s);
+      st = prm->method == MGLMA_SOLVER_CGNE ? cgne64(ctx, G, B, X, ctl, rs, s) : cgne_eo64(ctx, G, B, X, ctl, rs, s);
     } else {
       const MgParams mp = mg_params(*prm);
       st = mg_solve(ctx, G, C, B, X, mp, rs, s);

@@ -87,5 +87,13 @@ mglma_status coarse_solve64(mglma_ctx ctx, const mglma_coarse_s* C, const void* 
 
 mglma_status cgne64(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& b, Spinor& x, const SolveControl& ctl,
                     std::vector<RhsStat>& out, cudaStream_t s);
+// even-odd (evenodd.cu): FP64 CGNE on the Schur complement S = A_ee - H_eo
+// A_oo^-1 H_oe with reconstruction and FP64 defect correction on D
+mglma_status cgne_eo64(mglma_ctx ctx, mglma_gauge_s* G, const Spinor& b, Spinor& x, const SolveControl& ctl,
+                       std::vector<RhsStat>& out, cudaStream_t s);
+// out = S in (g5: gamma5 S in) on the even sites of canonical device fields,
+// zero on the odd sites (FP64)
+mglma_status dirac_schur64(mglma_ctx ctx, mglma_gauge_s* G, int nrhs, const double* in_dev, double* out_dev, bool g5,
+                           cudaStream_t s);
 
 }  // namespace mglma
