@@ -405,10 +405,11 @@ typedef enum {
                                  odd sites by back-substitution (the paper's
                                  coarse solves use the even-odd preconditioned
                                  coarse operator, Sec. "Comparison of the
-                                 cost"); the default.  On a coarse grid with an
-                                 odd extent, or when the set-up cannot be formed
-                                 (FP64 operator released before it was), it runs
-                                 as MGLMA_COARSE_MINRES.  The self-block inverses
+                                 cost"); the default.  It runs on the BF16
+                                 tensor-core operator; without one, on a coarse
+                                 grid with an odd extent, or when the set-up
+                                 cannot be formed (FP64 operator released before
+                                 it was), it runs as MGLMA_COARSE_MINRES.  The self-block inverses
                                  are formed from the FP64 operator on first use
                                  (or by mglma_coarse_release_fp64, before it
                                  frees the FP64 operator) */

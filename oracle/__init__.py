@@ -20,19 +20,28 @@ without blocking, fusion or reordering beyond what the definition states:
                    Eq. mg_basis with Gram-Schmidt, the restrictor R0 (Eq.
                    res_mg), prolongator T0 (Eq. pro_mg), and the coarse
                    operator D1 = R0 D T0 as a nine-slot stencil (Sec. 4,
-                   Fig. A).
-* ``solvers``   -- CG on the normal equations, dense solves, and the
+                   Fig. A); the inner-level transfers R_l / T_l with
+                   sqrt(V_{l+1} / V_l), the recursive D_{l+1} = R_l D_l T_l
+                   and the multilevel pieces (Sec. "Multigrid
+                   decompositions").
+* ``solvers``   -- CG on the normal equations, dense solves, the
                    propagator pieces S1 = T Q1^-1 R gamma5 and S0 = S - S1
-                   (Sec. 2, App. chirality).
+                   (Sec. 2, App. chirality), the FP64 residual evaluated in
+                   time slabs, and the even-odd (Schur) decomposition of a
+                   dense operator.
 * ``contract``  -- the time-slice contraction of the stochastic estimator
                    (Sec. 5, Eq. C_stoch2), the correlator from a dense
-                   propagator (Eq. tmr) and the translation average (Eq.
-                   timetrans).
+                   propagator (Eq. tmr), the translation average (Eq.
+                   timetrans), and the exact estimator on a coarse level
+                   with its coarse gamma5 gamma_k matrices (Eq. G_LL:exact,
+                   Eq. coarse:gamma).
 
 Parity pins (tests/test_oracle_*.py) tie each part to facts that do not come
 from this package: the free-field momentum-space spectrum, an abelian
 constant-field clover, gamma5-hermiticity, gauge covariance, QR factorisation,
-brute-force dense matrices, dense LU inverses, and the eigenvalue alignment of
-App. spectra.  No function here is "parity unpinned".
+brute-force dense matrices, dense LU inverses, the eigenvalue alignment of
+App. spectra, the Krylov-space minimiser that CG reaches, the block-LU
+determinant identity, and fine-lattice definitions evaluated densely.  No
+function here is "parity unpinned".
 """
 from . import lattice, dirac, multigrid, solvers, contract  # noqa: F401

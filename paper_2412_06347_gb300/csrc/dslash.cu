@@ -171,41 +171,20 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
 // A CTA covers DT = 32 consecutive sites and NRT right-hand sides: warp w
 // computes RHS r0 + w on the 32 sites (lane = site), so every spinor load of a
 // warp is one coalesced 512-byte row.  Everything that depends on the site
-// but not on the RHS is staged once per CTA in shared memory, already in the
-// form the paired FP32 instructions of sm_100+ (fma.rn.f32x2) take: the eight
+// but not on the RHS is staged once per CTA in shared memory: the eight
 // links a site's hops use -- U_mu(x) for the forward hops and U_mu(x-mu)^dag
-// for the backward hops, third row rebuilt, multiplied by the hop factor
-// -1/2 (times t_bc where the hop crosses the time boundary) -- as
-// (w.re, w.re, -w.im, w.im) per entry w, and the two clover blocks as (d, d)
-// per diagonal and (a.re, a.re, -a.im, a.im) per upper entry a.  A complex
-// multiply-add acc += w b is then two paired FMAs,
-//     acc = (w.re, w.re) (b.re, b.im) + acc ;  acc = (-w.im, w.im) (b.im, b.re) + acc,
-// whose components round exactly like the scalar sequence of cfma (and
-// cfma_conj with the second pair negated).  Scaling a link by +-1/2 is exact
-// and commutes with every rounding, and the terms are summed in the order of
-// dslash_kernel, so both kernels give the same bits.
+// for the backward hops, third row rebuilt, already multiplied by the hop
+// factor -1/2 (times t_bc where the hop crosses the time boundary) -- and the
+// two clover blocks.  The per-RHS work is then projection, one 3x3 product
+// per half spinor and reconstruction.  Scaling a link by +-1/2 is exact and
+// commutes with every rounding, and the terms are summed in the same order
+// as dslash_kernel, so both kernels give the same bits.
 constexpr int kDT = 32;  // sites per CTA of the staged kernel
 
 struct StagedTile {
-  float4 U[8][9][kDT];   // hop slot (0..3 forward, 4..7 backward), entry row*3 + col, site
-  float2 Cd[2][6][kDT];  // clover block, diagonal entry, site: (d, d)
-  float4 Co[2][15][kDT]; // clover block, upper entry (row-major i < j), site
+  float2 U[8][9][kDT];  // hop slot (0..3 forward, 4..7 backward), entry (row*3 + col), site
+  float4 C[2][9][kDT];  // clover chirality block, packed float4, site
 };
-
-__device__ __forceinline__ float2 f2(Cx<float> z) { return make_float2(z.re, z.im); }
-__device__ __forceinline__ float2 f2swap(Cx<float> z) { return make_float2(z.im, z.re); }
-__device__ __forceinline__ Cx<float> cxf(float2 v) { return cx(v.x, v.y); }
-
-// acc += w b with w staged as (w.re, w.re, -w.im, w.im); bv = (b.re, b.im), bs = (b.im, b.re)
-__device__ __forceinline__ float2 cfma_f2(float2 acc, float4 w, float2 bv, float2 bs) {
-  acc = __ffma2_rn(make_float2(w.x, w.y), bv, acc);
-  return __ffma2_rn(make_float2(w.z, w.w), bs, acc);
-}
-// acc += conj(w) b
-__device__ __forceinline__ float2 cfma_conj_f2(float2 acc, float4 w, float2 bv, float2 bs) {
-  acc = __ffma2_rn(make_float2(w.x, w.y), bv, acc);
-  return __ffma2_rn(make_float2(-w.z, -w.w), bs, acc);
-}
 
 // hop slot MU (forward: U_MU(x)) or 4 + MU (backward: U_MU(x - MU)^dag) of site
 // `site` (coordinates x) into the tile, times -1/2 (and t_bc across the time
@@ -223,34 +202,8 @@ __device__ __forceinline__ void stage_link(StagedTile& st, int ls, const float4*
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const Cx<float> e = FWD ? m.e[i][j] : conj(m.e[j][i]);
-      const float re = f * e.re, im = f * e.im;
-      st.U[FWD ? MU : 4 + MU][i * 3 + j][ls] = make_float4(re, re, -im, im);
+      st.U[FWD ? MU : 4 + MU][i * 3 + j][ls] = make_float2(f * e.re, f * e.im);
     }
-}
-
-// clover block chi of one site: out[i] = d_i in[i] + sum_{j != i} A_ij in[j] in
-// the order of clover_apply6 (A_ij = a for i < j, conj(a_ji) for i > j)
-__device__ __forceinline__ void clover_staged(const StagedTile& st, int chi, int ls, const Cx<float>* in,
-                                              Cx<float>* out) {
-  float2 v[6], w[6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    v[j] = f2(in[j]);
-    w[j] = f2swap(in[j]);
-  }
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    float2 s = __fmul2_rn(st.Cd[chi][i][ls], v[i]);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      if (j == i) continue;
-      if (i < j)
-        s = cfma_f2(s, st.Co[chi][offdiag_slot(i, j)][ls], v[j], w[j]);
-      else
-        s = cfma_conj_f2(s, st.Co[chi][offdiag_slot(j, i)][ls], v[j], w[j]);
-    }
-    out[i] = cxf(s);
-  }
 }
 
 // acc += (1 + s gamma_mu) W psi(nb) with the staged, pre-scaled link W of hop
@@ -261,31 +214,21 @@ __device__ __forceinline__ void staged_hop(const StagedTile& st, int ls, const f
   constexpr int slot = FWD ? MU : 4 + MU;
   Cx<float> psi[12];
   IO<float>::load(in, V, r, nb, psi);
+  M3<float> Um;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    const float2 v = st.U[slot][e][ls];
+    Um.e[e / 3][e % 3] = cx(v.x, v.y);
+  }
   Cx<float> h0[3], h1[3], g0[3], g1[3];
   project<float>(MU, sg, psi, h0, h1);
-  float2 hv0[3], hs0[3], hv1[3], hs1[3];
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    hv0[b] = f2(h0[b]);
-    hs0[b] = f2swap(h0[b]);
-    hv1[b] = f2(h1[b]);
-    hs1[b] = f2swap(h1[b]);
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const float4 w = st.U[slot][a * 3 + b][ls];
-      s0 = cfma_f2(s0, w, hv0[b], hs0[b]);
-      s1 = cfma_f2(s1, w, hv1[b], hs1[b]);
-    }
-    g0[a] = cxf(s0);
-    g1[a] = cxf(s1);
-  }
+  mat_vec<float>(Um, h0, g0);
+  mat_vec<float>(Um, h1, g1);
   reconstruct_add<float>(MU, sg, g0, g1, acc);
 }
 
+// RED: per warp (one RHS, 32 sites) |t|^2 and <t, in> in FP32, written as FP64
+// partials part[((rhs * ntiles) + tile) * 3 + {0, 1, 2}] (ntiles = ceil(V / 32))
 // resident warps per SM the register allocation must allow: 24 (80
 // registers a thread), 20 with the reduction epilogue (which holds the
 // result and the input spinor at once)
@@ -294,20 +237,17 @@ constexpr int staged_min_ctas() {
   return (RED ? 20 : 24) / NRT > 0 ? (RED ? 20 : 24) / NRT : 1;
 }
 
-// RED: per warp (one RHS, 32 sites) |t|^2 and <t, in> in FP32, written as FP64
-// partials part[((rhs * ntiles) + tile) * 3 + {0, 1, 2}] (ntiles = ceil(V / 32))
 template <int NRT, bool DAG, bool RED = false>
-__global__ void __launch_bounds__(NRT * 32, staged_min_ctas<NRT, RED>())
-    dslash_staged_kernel(const float4* __restrict__ in, float4* __restrict__ out, const float4* __restrict__ U,
-                         const float4* __restrict__ C, DslashArgs a, double* __restrict__ part = nullptr) {
-  extern __shared__ __align__(16) unsigned char smraw_staged[];
-  StagedTile& st = *reinterpret_cast<StagedTile*>(smraw_staged);
+__global__ void __launch_bounds__(NRT * 32, staged_min_ctas<NRT, RED>()) dslash_staged_kernel(const float4* __restrict__ in, float4* __restrict__ out,
+                                                                 const float4* __restrict__ U, const float4* __restrict__ C,
+                                                                 DslashArgs a, double* __restrict__ part = nullptr) {
+  __shared__ StagedTile st;
   const int64_t V = a.q.V;
   const int ngrp = (a.nrhs + NRT - 1) / NRT;
   const int64_t tile = blockIdx.x / ngrp;
   const int r0 = (int)(blockIdx.x % ngrp) * NRT;
   const int64_t base = tile * kDT;
-  // ---- stage links (one (slot, site) per job) and clover blocks (one (site, chi) per job)
+  // ---- stage links (one (slot, site) per job) and clover blocks
   for (int job = threadIdx.x; job < 8 * kDT; job += blockDim.x) {
     const int l = job / kDT, ls = job % kDT;  // l is uniform across a warp
     const int64_t site = base + ls;
@@ -325,19 +265,10 @@ __global__ void __launch_bounds__(NRT * 32, staged_min_ctas<NRT, RED>())
       default: stage_link<3, false>(st, ls, U, a, site, x); break;
     }
   }
-  for (int job = threadIdx.x; job < 2 * kDT; job += blockDim.x) {
-    const int chi = job / kDT, ls = job % kDT;
+  for (int job = threadIdx.x; job < 18 * kDT; job += blockDim.x) {
+    const int k = job / kDT, ls = job % kDT;
     const int64_t site = base + ls;
-    if (site >= V) continue;
-    float c[36];
-    Clover<float>::load(C, V, chi, site, c);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) st.Cd[chi][i][ls] = make_float2(c[i], c[i]);
-#pragma unroll
-    for (int k = 0; k < 15; ++k) {
-      const float re = c[6 + 2 * k], im = c[7 + 2 * k];
-      st.Co[chi][k][ls] = make_float4(re, re, -im, im);
-    }
+    if (site < V) st.C[k / 9][k % 9][ls] = __ldg(C + (size_t)k * V + site);
   }
   __syncthreads();
   const int w = threadIdx.x / 32, ls = threadIdx.x % 32;
@@ -355,8 +286,19 @@ __global__ void __launch_bounds__(NRT * 32, staged_min_ctas<NRT, RED>())
     {
       Cx<float> psi[12];
       IO<float>::load(in, V, r, site, psi);
-      clover_staged(st, 0, ls, psi, acc);
-      clover_staged(st, 1, ls, psi + 6, acc + 6);
+#pragma unroll
+      for (int chi = 0; chi < 2; ++chi) {
+        float c[36];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+          const float4 v = st.C[chi][j][ls];
+          c[4 * j] = v.x;
+          c[4 * j + 1] = v.y;
+          c[4 * j + 2] = v.z;
+          c[4 * j + 3] = v.w;
+        }
+        clover_apply6<float>(c, psi + 6 * chi, acc + 6 * chi);
+      }
     }
     // hop order of dslash_kernel: mu = 0..3, forward then backward
     staged_hop<0, true>(st, ls, in, V, r, nbr_fwd(a.q, site, x, 0), sF, acc);
@@ -777,18 +719,11 @@ static void launch_dslash(const Spinor& in, Spinor& out, const void* U, const vo
 // per CTA was fastest at every count (16 RHS: 2.93 ms, staged tiles of 4, 8,
 // 16 RHS 3.45, 3.36, 3.49 ms -- the staged kernel issues as many
 // instructions per site and RHS, its shared-memory loads replacing the
-// rebuilt third link row).
+// rebuilt third link row; staging the operands pre-broadcast for paired FP32
+// FMAs cut the instructions by a fifth but doubled the shared-memory bytes
+// per site and RHS, and at 3.63 ms was slower still: this stencil is bound
+// by the L1 / shared-memory bandwidth and latency of its operand loads).
 int dslash32_default_tile(int) { return dslash32_tile_code(1, 1); }
-
-template <int NRT, bool DAG, bool RED>
-static void staged_smem_attr() {
-  static bool done = false;  // the tile exceeds the 48 KB of static shared memory
-  if (!done) {
-    cudaFuncSetAttribute(dslash_staged_kernel<NRT, DAG, RED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(StagedTile));
-    done = true;
-  }
-}
 
 template <int NRT, bool RED>
 static void launch_staged(const Spinor& in, Spinor& out, const void* U, const void* C, const DslashArgs& a,
@@ -797,16 +732,10 @@ static void launch_staged(const Spinor& in, Spinor& out, const void* U, const vo
   const unsigned ctas = (unsigned)(ntiles * ((in.nrhs + NRT - 1) / NRT));
   const float4* x = (const float4*)in.p;
   float4* y = (float4*)out.p;
-  const size_t smem = sizeof(StagedTile);
-  if (dagger) {
-    staged_smem_attr<NRT, true, RED>();
-    dslash_staged_kernel<NRT, true, RED><<<ctas, NRT * 32, smem, s>>>(x, y, (const float4*)U, (const float4*)C, a,
-                                                                       part);
-  } else {
-    staged_smem_attr<NRT, false, RED>();
-    dslash_staged_kernel<NRT, false, RED><<<ctas, NRT * 32, smem, s>>>(x, y, (const float4*)U, (const float4*)C, a,
-                                                                        part);
-  }
+  if (dagger)
+    dslash_staged_kernel<NRT, true, RED><<<ctas, NRT * 32, 0, s>>>(x, y, (const float4*)U, (const float4*)C, a, part);
+  else
+    dslash_staged_kernel<NRT, false, RED><<<ctas, NRT * 32, 0, s>>>(x, y, (const float4*)U, (const float4*)C, a, part);
 }
 
 static void launch_dslash32(int code, const Spinor& in, Spinor& out, const void* U, const void* C,

@@ -583,13 +583,15 @@ struct CoarseSolver {
   void reset() {
     for (auto& G : g) drop(G);
   }
-  // even-odd needs every coarse extent even and its set-up formed or formable
-  // (the FP64 operator held); elsewhere it runs as MINRES on Q1
+  // even-odd runs on the tensor-core operator (whose parity-restricted
+  // launches need no work memory beyond the solver's scratch, so they can be
+  // recorded in graphs) with every coarse extent even and its set-up formed or
+  // formable (the FP64 operator held); elsewhere it runs as MINRES on Q1
   bool eo() const {
-    if (method != MGLMA_COARSE_MINRES_EO) return false;
+    if (method != MGLMA_COARSE_MINRES_EO || !C->Aimg) return false;
     for (int m = 0; m < 4; ++m)
       if (C->geo.Lb[m] % 2) return false;
-    return C->Sinv64 || (C->Sinv_img && C->Aimg) || C->A64;
+    return C->Sinv_img || C->A64;
   }
   bool minres() const { return method == MGLMA_COARSE_MINRES || eo(); }
   int cycle_len() const { return minres() ? 12 : m; }
