@@ -498,8 +498,13 @@ def run_micro(args, w):
         if args.micro == "coarse":
             X = torch.randn(n, V1, 2 * nv, dtype=torch.complex128, device="cuda")
             Y = torch.empty_like(X)
+            op = {"full": m.MGLMA_OP_D, "schur": m.MGLMA_OP_SCHUR_Q}[args.coarse_op]
+            m.mglma_profile(ctx, False, True)
+            m.mglma_coarse_apply(ctx, C, n, X, Y, m.MGLMA_FP32, op=op, stream=stream)  # even-odd set-up
+            torch.cuda.synchronize()
+            m.mglma_profile(ctx, True, True)
             for _ in range(reps):
-                m.mglma_coarse_apply(ctx, C, n, X, Y, m.MGLMA_FP32, stream=stream)
+                m.mglma_coarse_apply(ctx, C, n, X, Y, m.MGLMA_FP32, op=op, stream=stream)
             kinds = ["coarse"]
         else:
             f = torch.randn(n, V, 12, dtype=torch.complex128, device="cuda")
@@ -541,9 +546,13 @@ def main():
     ap.add_argument("--coarse-solver", default="minres_eo", choices=sorted(COARSE_SOLVERS),
                     help="coarse solver inside the preconditioner")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-solver sample")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the solve's kernels one by one instead of as captured CUDA graphs")
     ap.add_argument("--micro", default="", choices=["", "dslash32", "dslash64", "coarse", "transfer", "contract"],
                     help="time one kernel class on the workload lattice instead of the solve")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch in --micro mode")
+    ap.add_argument("--coarse-op", default="full", choices=["full", "schur"],
+                    help="--micro coarse: the full coarse operator or g5hat S_ee (three tensor-core launches)")
     ap.add_argument("--tile", default="", help="FP32 stencil tile NR,RW (RHS per thread, RHS tiles per CTA) or sNRT "
                                                 "(staged-tile kernel, 32 sites x NRT RHS per CTA, NRT 4, 8, 16); "
                                                 "default: the library's choice")
@@ -599,6 +608,8 @@ def main():
                                   n_cg=w["n_cg"], cg_prec=m.MGLMA_FP32)
     C = m.mglma_coarse_build(ctx, g, sub, prec[w["coarse_store"]])
     prm = m.mglma_solve_params_default(m.MGLMA_SOLVER_MG, coarse_solver=COARSE_SOLVERS[args.coarse_solver])
+    if args.no_graph:
+        prm.graph = 0
     stream = torch.cuda.Stream(device=dev)
     set_tile(m, ctx, args, G)
 
@@ -633,8 +644,10 @@ def main():
     all_stats = []
     torch.cuda.synchronize()
     t_start.record(stream)
+    torch.cuda.nvtx.range_push("timed")
     for i in range(args.warmup, nsteps):
         all_stats += step(i, dev_b[i % ngroups], dev_x)
+    torch.cuda.nvtx.range_pop()
     t_end.record(stream)
     torch.cuda.synchronize()
     ms = t_start.elapsed_time(t_end)
@@ -787,6 +800,7 @@ def main():
                        "kappa": w["kappa"], "csw": w["csw"], "block": "x".join(map(str, w["block"])),
                        "Nv": w["nv"], "basis": w["sub_store"], "coarse_operator": w["coarse_store"],
                        "coarse_solver": args.coarse_solver,
+                       "launch": "one by one" if args.no_graph else "CUDA graph per FGCR iteration",
                        "setup": f"{w['n_smooth']} MR + {w['n_cg']} CG relaxation steps",
                        "rhs_per_step": G, "global_batch": G * world, "tol": 1e-10,
                        "l2": "inputs larger than L2 (each source 0.4 GB)", "parallelism": f"replicas x{world}",

@@ -313,10 +313,14 @@ mglma_status coarse_schur_apply(mglma_ctx ctx, const mglma_coarse_s* C, const vo
   float2* To = reinterpret_cast<float2*>(img + 2 * coarse_tc_half_image_bytes(C, nrhs));
   float2* Uo = To + half;
   const float2* X = (const float2*)Xe;
-  // T_o = D_oe X_e ; U_o = -D_oo^-1 T_o ; Y_e = D_eo U_o + D_ee X_e (g5hat by mode bit 1)
+  // T_o = D_oe X_e ; U_o = -D_oo^-1 T_o ; Y_e = D_eo U_o + D_ee X_e (g5hat by
+  // mode bit 1).  The image of X_e the first launch writes (first half image)
+  // serves the third as its self input; the third writes the image of U_o
+  // over that of T_o (second half image), which the second launch has read.
+  const size_t hb = coarse_tc_half_image_bytes(C, nrhs);
   MG_CHECK(coarse_tc_eo_launch(ctx, C, X, nullptr, To, nrhs, 0, 1, 0, 7, nullptr, 1.f, img, s));
   MG_CHECK(coarse_tc_eo_launch(ctx, C, nullptr, To, Uo, nrhs, 0, 1, 8, 8, C->Sinv_img, -1.f, img, s));
-  return coarse_tc_eo_launch(ctx, C, Uo, X, (float2*)Ye, nrhs, mode & 2, 0, 0, 8, nullptr, 1.f, img, s);
+  return coarse_tc_eo_launch(ctx, C, Uo, X, (float2*)Ye, nrhs, mode & 2, 0, 0, 8, nullptr, 1.f, img + hb, s, img);
 }
 
 mglma_status coarse_eo_prepare(mglma_ctx ctx, const mglma_coarse_s* C, const void* b, void* be, int nrhs, int prec,

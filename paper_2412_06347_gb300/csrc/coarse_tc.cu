@@ -505,17 +505,17 @@ size_t coarse_tc_half_image_bytes(const mglma_coarse_s* C, int nrhs) {
 template <int NT>
 static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
-                                 float sign, void* scratch, cudaStream_t s) {
+                                 float sign, void* scratch, cudaStream_t s, const void* self_image) {
   const int n2 = C->n2;
   const int64_t Vh = C->geo.V1 / 2;
   const size_t half = coarse_tc_half_image_bytes(C, nrhs);
   uint8_t* xb_hop = (uint8_t*)scratch;
-  uint8_t* xb_self = xb_hop + half;
+  uint8_t* xb_self = self_image ? (uint8_t*)self_image : xb_hop + half;
   const size_t groups = (size_t)((nrhs + NT - 1) / NT) * Vh * (n2 / 8) * NT;
   // images of the inputs the slots read (gamma5hat on the inputs by mode bit 0)
   if (d_lo < 8)
     x_image_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, s>>>(Xhop, (uint4*)xb_hop, Vh, n2, nrhs, NT, mode);
-  if (d_hi == 8)
+  if (d_hi == 8 && !self_image)
     x_image_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, s>>>(Xself, (uint4*)xb_self, Vh, n2, nrhs, NT, mode);
   MG_LAUNCH_CHECK();
   const size_t smem = tc_smem(n2, NT);
@@ -543,14 +543,16 @@ static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const f
 
 mglma_status coarse_tc_eo_launch(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
-                                 float sign, void* scratch, cudaStream_t s) {
+                                 float sign, void* scratch, cudaStream_t s, const void* self_image) {
   if (!C->Aimg || !coarse_tc_supported(C->n2)) return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: no tensor image");
   if (par < 0 || par > 1 || d_lo < 0 || d_hi > 8 || d_lo > d_hi)
     return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: bad launch");
   const int nt = tuned(ctx, TUNE_COARSE_NT, nrhs, C->geo.V1, coarse_tc_default_nt(nrhs));
-  if (nt == 32) return launch_tc_eo<32>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s);
-  if (nt == 16) return launch_tc_eo<16>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s);
-  return launch_tc_eo<8>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s);
+  if (nt == 32)
+    return launch_tc_eo<32>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image);
+  if (nt == 16)
+    return launch_tc_eo<16>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image);
+  return launch_tc_eo<8>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image);
 }
 
 mglma_status coarse_tc_check(mglma_coarse_s* C, cudaStream_t s) {

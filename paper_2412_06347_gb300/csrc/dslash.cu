@@ -42,11 +42,28 @@ constexpr int dslash_min_ctas() {
 // into part[(rhs * nblk + block) * 3 + {0, 1, 2}] (|t|^2, Re, Im): FP32 over
 // each warp's 32 sites, FP64 from there on, summed over the blocks in a fixed
 // order by dot_finish_kernel.
-template <typename R, int NR, bool DAG, int RW, bool RED = false>
+//
+// MRF (with RED) makes the kernel one fused minimal-residual smoothing step:
+// with in = t_k and u = op(t_k), per site and RHS
+//   out = t_{k+1} = t_k - alpha u,  s <- s_{k+1} = s_k - alpha t_k,
+//   z <- z + alpha s_k,
+// alpha = mr.alpha[rhs], and the block partials of |t_{k+1}|^2 and
+// <t_{k+1}, s_{k+1}> in place of those of |t|^2 and <t, in>.  Since
+// t_{k+1} = op(s_{k+1}) in exact arithmetic, the next step needs no separate
+// vector update and its memory traffic runs under the stencil's.
+struct MrArgs {
+  float4* s = nullptr;
+  float4* z = nullptr;
+  const double2* alpha = nullptr;
+};
+
+template <typename R, int NR, bool DAG, int RW, bool RED = false, bool MRF = false>
 __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kernel(const void* __restrict__ in, void* __restrict__ out,
                                                      const void* __restrict__ U, const void* __restrict__ C,
-                                                     DslashArgs a, double* __restrict__ part = nullptr) {
+                                                     DslashArgs a, double* __restrict__ part = nullptr,
+                                                     MrArgs mr = MrArgs()) {
   static_assert(!RED || (NR == 1 && RW == 1 && sizeof(R) == 4), "fused reduction: FP32 tile 1,1 only");
+  static_assert(!MRF || RED, "the fused MR step reduces its dots");
   constexpr int SW = 128 / RW;  // sites per CTA
   const int64_t V = a.q.V;
   // RHS tile groups run fastest in launch order, so the CTAs that share a
@@ -120,28 +137,65 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
         }
     }
   }
-#pragma unroll
-  for (int r = 0; r < NR; ++r)
-    if (r0 + r < a.nrhs && valid) {
-      if (a.g5out) {
-#pragma unroll
-        for (int k = 6; k < 12; ++k) acc[r][k] = -acc[r][k];
-      }
-      IO<R>::store(out, V, r0 + r, site, acc[r]);
-    }
-  if constexpr (RED) {
-    float nn = 0.f, dr = 0.f, di = 0.f;
+  float nn = 0.f, dr = 0.f, di = 0.f;  // RED: this thread's |t|^2 and <t, s>
+  if constexpr (MRF) {
     if (valid) {
-      Cx<R> sv[12];
-      IO<R>::load(in, V, r0, site, sv);
+      const double2 al = mr.alpha[r0];
+      const Cx<float> alpha = cx((float)al.x, (float)al.y);
+      const size_t off = (size_t)r0 * 6 * V + site;
+      const float4* tp = reinterpret_cast<const float4*>(in) + off;
+      float4* op = reinterpret_cast<float4*>(out) + off;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        const Cx<R> t = acc[0][k];
-        nn += t.re * t.re + t.im * t.im;
-        dr += t.re * sv[k].re + t.im * sv[k].im;
-        di += t.re * sv[k].im - t.im * sv[k].re;
+      for (int j = 0; j < 6; ++j) {
+        const float4 tv = __ldg(tp + j * V), sv = mr.s[off + j * V], zv = mr.z[off + j * V];
+        const Cx<float> t[2] = {cx(tv.x, tv.y), cx(tv.z, tv.w)}, sk[2] = {cx(sv.x, sv.y), cx(sv.z, sv.w)},
+                        zk[2] = {cx(zv.x, zv.y), cx(zv.z, zv.w)};
+        Cx<float> tn[2], sn[2], zn[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          tn[h] = t[h] - alpha * acc[0][2 * j + h];
+          sn[h] = sk[h] - alpha * t[h];
+          zn[h] = zk[h] + alpha * sk[h];
+          nn += tn[h].re * tn[h].re + tn[h].im * tn[h].im;
+          dr += tn[h].re * sn[h].re + tn[h].im * sn[h].im;
+          di += tn[h].re * sn[h].im - tn[h].im * sn[h].re;
+        }
+        op[j * V] = make_float4(tn[0].re, tn[0].im, tn[1].re, tn[1].im);
+        mr.s[off + j * V] = make_float4(sn[0].re, sn[0].im, sn[1].re, sn[1].im);
+        mr.z[off + j * V] = make_float4(zn[0].re, zn[0].im, zn[1].re, zn[1].im);
       }
     }
+  } else {
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r0 + r < a.nrhs && valid) {
+        if (a.g5out) {
+#pragma unroll
+          for (int k = 6; k < 12; ++k) acc[r][k] = -acc[r][k];
+        }
+        if (a.bsub) {
+          Cx<R> bv[12];
+          IO<R>::load(a.bsub, V, r0 + r, site, bv);
+#pragma unroll
+          for (int k = 0; k < 12; ++k) acc[r][k] = bv[k] - acc[r][k];
+        }
+        IO<R>::store(out, V, r0 + r, site, acc[r]);
+      }
+    if constexpr (RED) {
+      if (valid) {
+        Cx<R> sv[12];
+        IO<R>::load(in, V, r0, site, sv);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const Cx<R> t = acc[0][k];
+          nn += t.re * t.re + t.im * t.im;
+          dr += t.re * sv[k].re + t.im * sv[k].im;
+          di += t.re * sv[k].im - t.im * sv[k].re;
+        }
+      }
+    }
+  }
+  if constexpr (RED) {
     // FP32 within a warp (32 sites), FP64 from the warp partials on: the
     // FP64 pipe of GB300 is too narrow for a per-thread FP64 tree
 #pragma unroll
@@ -791,6 +845,29 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
   return MGLMA_OK;
 }
 
+mglma_status dslash_resid(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, const Spinor& b, Spinor& out,
+                          cudaStream_t s) {
+  if (in.prec != MGLMA_FP32 || out.prec != MGLMA_FP32 || b.prec != MGLMA_FP32 || in.V != G->g.V ||
+      out.V != G->g.V || b.V != G->g.V || in.nrhs != out.nrhs || b.nrhs != out.nrhs)
+    return fail(MGLMA_ERR_INVALID, "dslash_resid: FP32 fields of the gauge field's volume needed");
+  if (in.p == out.p || b.p == out.p) return fail(MGLMA_ERR_INVALID, "dslash_resid: out must differ from in and b");
+  if (in.nrhs == 0) return MGLMA_OK;
+  DslashArgs a;
+  a.q = make_latidx(G->g.L);
+  a.bc = (double)G->g.t_bc;
+  a.nrhs = in.nrhs;
+  a.g5out = 0;
+  a.bsub = b.p;
+  ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(in.V, in.nrhs, false) + 96.0 * (double)in.V * in.nrhs,
+               dslash_flops(in.V, in.nrhs) + 24.0 * (double)in.V * in.nrhs);
+  // the staged-tile kernel has no room for the epilogue's extra operand
+  int code = tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, G->g.V, dslash32_default_tile(in.nrhs));
+  if (dslash32_tile_staged(code)) code = dslash32_tile_code(1, 1);
+  launch_dslash32(code, in, out, G->U32, G->C32, a, false, s);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
 // room for the finer of the two partial-sum grids (32-site tiles)
 size_t dslash_dot_part_doubles(int64_t V, int nrhs) { return (size_t)3 * nrhs * (size_t)((V + kDT - 1) / kDT); }
 
@@ -822,6 +899,47 @@ mglma_status dslash_dot(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in,
   {
     ProfScope ps(ctx, K_REDUCE, s, (double)dslash_dot_part_doubles(in.V, in.nrhs) * 8.0);
     dot_finish_kernel<<<in.nrhs, 256, 0, s>>>(part, nblk, nrm, dot);
+  }
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+bool dslash_mr_fused(mglma_ctx ctx, const mglma_gauge_s* G, int nrhs) {
+  return !dslash32_tile_staged(tuned(ctx, TUNE_DSLASH32_NR, nrhs, G->g.V, dslash32_default_tile(nrhs)));
+}
+
+mglma_status dslash_mr_step(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& t, Spinor& tn, Spinor& sk,
+                            Spinor& z, const double2* alpha, double* part, double* nrm, double2* dot,
+                            cudaStream_t s) {
+  const Spinor* f[4] = {&t, &tn, &sk, &z};
+  for (const Spinor* v : f)
+    if (v->prec != MGLMA_FP32 || v->V != G->g.V || v->nrhs != t.nrhs)
+      return fail(MGLMA_ERR_INVALID, "dslash_mr_step: FP32 fields of the gauge field's volume needed");
+  for (int i = 0; i < 4; ++i)
+    for (int j = i + 1; j < 4; ++j)
+      if (f[i]->p == f[j]->p) return fail(MGLMA_ERR_INVALID, "dslash_mr_step: the four fields must differ");
+  if (t.nrhs == 0) return MGLMA_OK;
+  DslashArgs a;
+  a.q = make_latidx(G->g.L);
+  a.bc = (double)G->g.t_bc;
+  a.nrhs = t.nrhs;
+  a.g5out = 0;
+  MrArgs mr;
+  mr.s = (float4*)sk.p;
+  mr.z = (float4*)z.p;
+  mr.alpha = alpha;
+  const int64_t nblk = (t.V + 127) / 128;
+  {
+    // the stencil's bytes plus s and z read and written once
+    ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(t.V, t.nrhs, false) + 4.0 * 96.0 * (double)t.V * t.nrhs,
+                 dslash_flops(t.V, t.nrhs) + 432.0 * (double)t.V * t.nrhs);
+    dslash_kernel<float, 1, false, 1, true, true><<<(unsigned)(nblk * t.nrhs), 128, 0, s>>>(t.p, tn.p, G->U32, G->C32,
+                                                                                            a, part, mr);
+  }
+  MG_LAUNCH_CHECK();
+  {
+    ProfScope ps(ctx, K_REDUCE, s, (double)dslash_dot_part_doubles(t.V, t.nrhs) * 8.0);
+    dot_finish_kernel<<<t.nrhs, 256, 0, s>>>(part, nblk, nrm, dot);
   }
   MG_LAUNCH_CHECK();
   return MGLMA_OK;

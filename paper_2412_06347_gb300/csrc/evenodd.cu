@@ -36,7 +36,11 @@ __device__ __forceinline__ int64_t eo_site(const LatIdx& q, int64_t u, int par) 
 
 // inverse of each packed Hermitian 6x6 clover block (one thread per (site,
 // chirality)): Gauss-Jordan with partial pivoting in FP64; the inverse of a
-// Hermitian matrix is Hermitian and is packed the same way
+// Hermitian matrix is Hermitian and is packed the same way.  Every loop is
+// unrolled and every index static (row and column exchanges are predicated
+// swaps), so the 6x6 matrix stays in registers: a version that indexed a
+// local array by the pivot row gave wrong inverses when built with -O3 on
+// sm_103a (exact in a debug build and on the host).
 __global__ void clover_inverse_kernel(const double2* __restrict__ C, double2* __restrict__ Ci, int64_t V,
                                       int* __restrict__ singular) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -46,18 +50,24 @@ __global__ void clover_inverse_kernel(const double2* __restrict__ C, double2* __
   double c[36];
   Clover<double>::load(C, V, chi, site, c);
   Cx<double> M[6][6];
+#pragma unroll
   for (int i = 0; i < 6; ++i) M[i][i] = cx(c[i], 0.0);
+#pragma unroll
   for (int i = 0; i < 6; ++i)
+#pragma unroll
     for (int j = i + 1; j < 6; ++j) {
       const int k = 6 + 2 * offdiag_slot(i, j);
       M[i][j] = cx(c[k], c[k + 1]);
       M[j][i] = cx(c[k], -c[k + 1]);
     }
   int perm[6];
+  bool ok = true;
+#pragma unroll
   for (int k = 0; k < 6; ++k) {
     int p = k;
-    double best = -1;
-    for (int r = k; r < 6; ++r) {
+    double best = M[k][k].re * M[k][k].re + M[k][k].im * M[k][k].im;
+#pragma unroll
+    for (int r = k + 1; r < 6; ++r) {
       const double m = M[r][k].re * M[r][k].re + M[r][k].im * M[r][k].im;
       if (m > best) {
         best = m;
@@ -65,44 +75,61 @@ __global__ void clover_inverse_kernel(const double2* __restrict__ C, double2* __
       }
     }
     perm[k] = p;
-    if (!(best > 0)) {
-      atomicExch(singular, 1);
-      return;
-    }
-    if (p != k)
-      for (int j = 0; j < 6; ++j) {
-        const Cx<double> tmp = M[k][j];
-        M[k][j] = M[p][j];
-        M[p][j] = tmp;
-      }
+    ok = ok && best > 0;
+    if (!(best > 0)) best = 1;  // singular: finish with harmless numbers, report below
+#pragma unroll
+    for (int r = k + 1; r < 6; ++r)
+      if (r == p)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const Cx<double> tmp = M[k][j];
+          M[k][j] = M[r][j];
+          M[r][j] = tmp;
+        }
     const double m = M[k][k].re * M[k][k].re + M[k][k].im * M[k][k].im;
-    const Cx<double> d = cx(M[k][k].re / m, -M[k][k].im / m);
+    const Cx<double> d = m > 0 ? cx(M[k][k].re / m, -M[k][k].im / m) : cx(0.0, 0.0);
+#pragma unroll
     for (int j = 0; j < 6; ++j)
       if (j != k) M[k][j] = M[k][j] * d;
+#pragma unroll
     for (int r = 0; r < 6; ++r) {
       if (r == k) continue;
       const Cx<double> f = M[r][k];
+#pragma unroll
       for (int j = 0; j < 6; ++j)
         if (j != k) M[r][j] = M[r][j] - f * M[k][j];
       M[r][k] = -(f * d);
     }
     M[k][k] = d;
   }
+  // undo the row exchanges as column exchanges, last first
+#pragma unroll
   for (int k = 5; k >= 0; --k)
-    if (perm[k] != k)
-      for (int r = 0; r < 6; ++r) {
-        const Cx<double> tmp = M[r][k];
-        M[r][k] = M[r][perm[k]];
-        M[r][perm[k]] = tmp;
-      }
+#pragma unroll
+    for (int c2 = k + 1; c2 < 6; ++c2)
+      if (perm[k] == c2)
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          const Cx<double> tmp = M[r][k];
+          M[r][k] = M[r][c2];
+          M[r][c2] = tmp;
+        }
+  if (!ok) {
+    atomicExch(singular, 1);
+    return;
+  }
   double pk[36];
+#pragma unroll
   for (int i = 0; i < 6; ++i) pk[i] = M[i][i].re;
+#pragma unroll
   for (int i = 0; i < 6; ++i)
+#pragma unroll
     for (int j = i + 1; j < 6; ++j) {
       const int k = 6 + 2 * offdiag_slot(i, j);
       pk[k] = M[i][j].re;
       pk[k + 1] = M[i][j].im;
     }
+#pragma unroll
   for (int j = 0; j < 18; ++j) Ci[((size_t)chi * 18 + j) * V + site] = make_double2(pk[2 * j], pk[2 * j + 1]);
 }
 

@@ -254,6 +254,19 @@ mglma_status convert_spinor(mglma_ctx, const Spinor& src, Spinor& dst, cudaStrea
 // fine operator application: out = op(in), op in {D, D^dag, gamma5 D, gamma5 D^dag}
 mglma_status dslash(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, bool dagger,
                     bool gamma5_out, cudaStream_t s);
+// One fused MR smoothing step (FP32, the (1,1) stencil tile): with u = D t,
+// tn = t - alpha u, sk <- sk - alpha t, z <- z + alpha sk (alpha per RHS, the
+// previous step's), and per RHS nrm = |tn|^2, dot = <tn, sk_new>, reduced as
+// in dslash_dot.  The four fields must differ.  dslash_mr_fused says whether
+// the tuned stencil tile for nrhs RHS has this form (else the step runs as
+// dslash_dot plus a vector update).
+bool dslash_mr_fused(mglma_ctx, const mglma_gauge_s* G, int nrhs);
+mglma_status dslash_mr_step(mglma_ctx, const mglma_gauge_s* G, const Spinor& t, Spinor& tn, Spinor& sk, Spinor& z,
+                            const double2* alpha, double* part, double* nrm, double2* dot, cudaStream_t s);
+// out = b - D in (FP32; the residual of the preconditioner's coarse correction
+// formed in the stencil's epilogue); out must not alias in or b
+mglma_status dslash_resid(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, const Spinor& b, Spinor& out,
+                          cudaStream_t s);
 // FP32 t = D in with, per RHS, nrm = |t|^2 and dot = <t, in> = sum conj(t) in
 // reduced in the same pass (FP32 per warp of 32 sites, then FP64 partials per
 // 32-site tile in `part`, at least dslash_dot_part_doubles(V, nrhs) doubles,

@@ -760,7 +760,7 @@ struct TwoLevel {
   const MgParams* p;
   long long coarse_iters = 0;
   int cap = 0;  // RHS the scratch is sized for (0: the first call's count)
-  Vec b1, e1, sv, tv;
+  Vec b1, e1, sv, tv, tv2;
   double* part = nullptr;  // per-block partial sums of the fused MR reductions
   Scalars sc;
   CoarseSolver cs;
@@ -771,6 +771,7 @@ struct TwoLevel {
     dfree(ctx, e1.p, s);
     dfree(ctx, sv.p, s);
     dfree(ctx, tv.p, s);
+    dfree(ctx, tv2.p, s);
     dfree(ctx, part, s);
   }
   mglma_status setup(const Vec& r) {
@@ -785,8 +786,10 @@ struct TwoLevel {
     sv.nrhs = n;
     tv = sv;
     sv.p = tv.p = nullptr;
+    tv2 = sv;
     MG_CHECK(dalloc(ctx, &sv.p, sv.bytes(), s));
     MG_CHECK(dalloc(ctx, &tv.p, tv.bytes(), s));
+    if (p->nu > 1 && dslash_mr_fused(ctx, G, n)) MG_CHECK(dalloc(ctx, &tv2.p, tv2.bytes(), s));
     MG_CHECK(dalloc(ctx, (void**)&part, dslash_dot_part_doubles(C->sub->geo.V, n) * sizeof(double), s));
     MG_CHECK(sc.alloc(ctx, n, 1, 1, s));
     cs.ctx = ctx;
@@ -805,8 +808,8 @@ struct TwoLevel {
     const int n = r.nrhs;
     const mglma_subspace_s* S = C->sub;
     const int64_t V = S->geo.V;
-    Vec b1n = b1, e1n = e1, svn = sv, tvn = tv;
-    b1n.nrhs = e1n.nrhs = svn.nrhs = tvn.nrhs = n;
+    Vec b1n = b1, e1n = e1, svn = sv, tvn = tv, tv2n = tv2;
+    b1n.nrhs = e1n.nrhs = svn.nrhs = tvn.nrhs = tv2n.nrhs = n;
     Spinor rs = as_spinor(r, V), zs = as_spinor(z, V);
     MG_CHECK(restrict_fine(ctx, S, rs, b1n.p, s));
     if (capturing)
@@ -815,16 +818,33 @@ struct TwoLevel {
       MG_CHECK(cs.solve(b1n, e1n, p->coarse_tol, p->coarse_max_iter, &coarse_iters));
     MG_CHECK(prolong_coarse(ctx, S, e1n.p, zs, false, s));
     if (p->nu > 0) {
-      // s = r - D z ; nu MR steps on D e = s, accumulated into z
+      // s = r - D z (in the stencil's epilogue) ; nu MR steps on D e = s,
+      // accumulated into z (the last one leaves s as it is)
       Spinor ss = as_spinor(svn, V), ts = as_spinor(tvn, V);
-      MG_CHECK(dslash(ctx, G, zs, ts, false, false, s));
-      MG_CHECK(copy_vec(ctx, r, svn, s));
-      MG_CHECK(axpby(ctx, nullptr, CM1, tvn, nullptr, C1, svn, s));
-      for (int k = 0; k < p->nu; ++k) {
-        // t = D s with |D s|^2 and <D s, s> reduced in the same pass
+      MG_CHECK(dslash_resid(ctx, G, zs, rs, ss, s));
+      if (tv2.p && dslash_mr_fused(ctx, G, n)) {
+        // t_0 = D s_0 ; then each step's vector update rides on the next
+        // step's stencil, t_{k+1} = t_k - alpha_k D t_k (dslash_mr_step)
+        Spinor t2s = as_spinor(tv2n, V);
+        Spinor *tc = &ts, *tn = &t2s;
         MG_CHECK(dslash_dot(ctx, G, ss, ts, part, sc.d, sc.z, s));
         MG_CHECK(mr_alpha(ctx, sc.z, sc.d, sc.z, n, s));
-        MG_CHECK(axpy2(ctx, sc.z, svn, z, tvn, svn, s));
+        for (int k = 1; k < p->nu; ++k) {
+          MG_CHECK(dslash_mr_step(ctx, G, *tc, *tn, ss, zs, sc.z, part, sc.d, sc.z, s));
+          MG_CHECK(mr_alpha(ctx, sc.z, sc.d, sc.z, n, s));
+          std::swap(tc, tn);
+        }
+        MG_CHECK(caxpy(ctx, sc.z, svn, z, s));
+      } else {
+        for (int k = 0; k < p->nu; ++k) {
+          // t = D s with |D s|^2 and <D s, s> reduced in the same pass
+          MG_CHECK(dslash_dot(ctx, G, ss, ts, part, sc.d, sc.z, s));
+          MG_CHECK(mr_alpha(ctx, sc.z, sc.d, sc.z, n, s));
+          if (k + 1 < p->nu)
+            MG_CHECK(axpy2(ctx, sc.z, svn, z, tvn, svn, s));
+          else
+            MG_CHECK(caxpy(ctx, sc.z, svn, z, s));
+        }
       }
     }
     return MGLMA_OK;
@@ -1049,7 +1069,7 @@ struct Engine {
   // device bytes one slot needs (FP64 b, x, r -- r also holds D x while the
   // residual is formed; FP32 r, e, FGCR directions and images, preconditioner
   // scratch)
-  static size_t slot_bytes(int64_t V, int m) { return (size_t)V * (3 * 192 + (size_t)(5 + 2 * m) * 96); }
+  static size_t slot_bytes(int64_t V, int m) { return (size_t)V * (3 * 192 + (size_t)(6 + 2 * m) * 96); }
   // one canonical spinor that host requests pass through, allocated on the
   // first host request (device requests need none)
   static size_t fixed_bytes(int64_t) { return 0; }

@@ -255,6 +255,7 @@ struct DslashArgs {
   double bc;
   int nrhs;
   int g5out;
+  const void* bsub = nullptr;  // dslash_kernel: when set, out = bsub - op(in) (same layout as out)
 };
 
 }  // namespace mglma

@@ -110,10 +110,14 @@ size_t coarse_eo_scratch_bytes(const mglma_coarse_s* C, int nrhs);
 // one tensor-core launch on half-lattice fields (coarse_tc.cu): Y = sign *
 // sum over slots d_lo..d_hi, hop slots reading Xhop, the self slot reading
 // Xself (with the self-block image Aself when given), for the sites of
-// parity par; mode bit 0 applies gamma5hat to both inputs, bit 1 to Y
+// parity par; mode bit 0 applies gamma5hat to both inputs, bit 1 to Y.  The
+// B images go to scratch (hop input) and scratch + one half image (self
+// input); self_image (nullable) is an image of the self input an earlier
+// launch with the same RHS count and mode bit 0 left, used instead of writing
+// one
 mglma_status coarse_tc_eo_launch(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
-                                 float sign, void* scratch, cudaStream_t s);
+                                 float sign, void* scratch, cudaStream_t s, const void* self_image = nullptr);
 size_t coarse_tc_half_image_bytes(const mglma_coarse_s* C, int nrhs);
 mglma_status coarse_tc_image_blocks(mglma_ctx ctx, const double2* A64, int64_t V1, int n2, int nslots,
                                     uint16_t** img, cudaStream_t s);
