@@ -454,7 +454,7 @@ typedef struct {
 } mglma_solve_stats;
 
 /* Fills *p with the library defaults for `method`: tol 1e-10; MG: gcr_m 4,
- * nu 7, inner_tol 3e-6, coarse_tol 0.02, coarse_max_iter 108 (whole cycles
+ * nu 7, inner_tol 3e-6, coarse_tol 0.02, coarse_max_iter 48 (whole cycles
  * of 12 MINRES iterations), coarse_solver MINRES_EO, check_every 1, max_batch 0,
  * autotune 1, graph 1; CGNE: max_iter 100000, check_every 20, autotune 0,
  * graph 0. */

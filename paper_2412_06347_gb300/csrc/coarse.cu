@@ -365,6 +365,7 @@ void mglma_coarse_free(mglma_coarse Cc) {
   if (Cc->ctx) cudaSetDevice(Cc->ctx->device);
   cudaFree(Cc->Sinv64);
   cudaFree(Cc->Sinv_img);
+  cudaFree(Cc->Ahat_img);
   cudaFree(Cc->A64);
   cudaFree(Cc->A32);
   cudaFree(Cc->A16);

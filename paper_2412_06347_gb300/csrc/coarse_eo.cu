@@ -13,12 +13,13 @@
 // on it as on g5hat D.  Half-lattice fields hold the sites of one parity, site
 // y at index y >> 1.
 //
-// The FP32 path (BF16 operator on the tensor cores) applies S_ee in three
+// The FP32 path (BF16 operator on the tensor cores) applies S_ee in two
 // launches of the stencil kernel restricted to one parity:
-//     T_o  = D_oe X_e                       (odd sites, hop slots)
-//     U_o  = -D_oo^-1 T_o                   (odd sites, self slot, inverse image)
+//     U_o  = -(D_oo^-1 D_oe) X_e            (odd sites, the eight hop slots
+//                                             premultiplied by the inverse
+//                                             self block in FP64 at set-up)
 //     Y_e  = D_eo U_o + D_ee X_e            (even sites, all nine slots)
-// which streams 8 + 1 + 9 slot blocks per pair of sites -- the bytes of one
+// which streams 8 + 9 slot blocks per pair of sites -- about the bytes of one
 // full application -- on vectors of half the length.  The FP64 path composes
 // full FP64 applications (used for the exact checks through the C ABI).
 #include <algorithm>
@@ -122,6 +123,37 @@ __global__ void self_inverse_kernel(const double2* __restrict__ A, double2* __re
   }
 }
 
+// Ahat[u][d] = Sinv(y) A[y][d] for the odd site y of half-lattice index u and
+// the hop slots d = 0..7 (FP64, [u][8][col j][row i]); one CTA per (u, d),
+// both factors staged in shared memory
+__global__ void ahat_kernel(const double2* __restrict__ A64, const double2* __restrict__ Sinv,
+                            double2* __restrict__ Ahat, LatIdx q, int n2) {
+  extern __shared__ double2 sh[];
+  double2* S = sh;            // [col l][row i]
+  double2* A = sh + n2 * n2;  // [col j][row l]
+  const int64_t u = blockIdx.x / 8;
+  const int d = (int)(blockIdx.x % 8);
+  int xc[4];
+  site_coords(q, 2 * u, xc);
+  const int64_t y = 2 * u + ((1 ^ (xc[0] + xc[1] + xc[2] + xc[3])) & 1);
+  const int nn = n2 * n2;
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    S[e] = Sinv[(size_t)y * nn + e];
+    A[e] = A64[((size_t)y * 9 + d) * nn + e];
+  }
+  __syncthreads();
+  double2* O = Ahat + ((size_t)u * 8 + d) * nn;
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    const int j = e / n2, i = e % n2;
+    Cx<double> acc = cx(0.0, 0.0);
+    for (int l = 0; l < n2; ++l) {
+      const double2 a = S[l * n2 + i], b = A[j * n2 + l];
+      cfma(acc, cx(a.x, a.y), cx(b.x, b.y));
+    }
+    O[e] = make_double2(acc.re, acc.im);
+  }
+}
+
 // half-lattice field of parity par <-> full field (the other parity of a
 // full output is set to zero)
 template <typename T>
@@ -217,7 +249,23 @@ mglma_status coarse_eo_setup(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s) {
     self_inverse_kernel<<<(unsigned)C->geo.V1, 256, smem, s>>>(C->A64, C->Sinv64, n2, sing);
   }
   MG_LAUNCH_CHECK();
-  if (C->Aimg) MG_CHECK(coarse_tc_image_blocks(ctx, C->Sinv64, C->geo.V1, n2, 1, &C->Sinv_img, s));
+  if (C->Aimg) {
+    MG_CHECK(coarse_tc_image_blocks(ctx, C->Sinv64, C->geo.V1, n2, 1, &C->Sinv_img, s));
+    // D_oo^-1 D_oe in FP64, rounded to BF16 once in its image
+    const int64_t Vh = C->geo.V1 / 2;
+    double2* ahat = nullptr;
+    MG_CHECK(dalloc(ctx, (void**)&ahat, (size_t)Vh * 8 * n2 * n2 * sizeof(double2), s));
+    const int smem2 = 2 * smem;
+    MG_CUDA(cudaFuncSetAttribute(ahat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+    {
+      ProfScope ps(ctx, K_SETUP, s);
+      ahat_kernel<<<(unsigned)(Vh * 8), 256, smem2, s>>>(C->A64, C->Sinv64, ahat, make_latidx(C->geo.Lb), n2);
+    }
+    MG_LAUNCH_CHECK();
+    const mglma_status st = coarse_tc_image_blocks(ctx, ahat, Vh, n2, 8, &C->Ahat_img, s);
+    dfree(ctx, ahat, s);
+    MG_CHECK(st);
+  }
   int h = 0;
   MG_CUDA(cudaMemcpyAsync(&h, sing, sizeof(int), cudaMemcpyDeviceToHost, s));
   dfree(ctx, sing, s);
@@ -313,13 +361,19 @@ mglma_status coarse_schur_apply(mglma_ctx ctx, const mglma_coarse_s* C, const vo
   float2* To = reinterpret_cast<float2*>(img + 2 * coarse_tc_half_image_bytes(C, nrhs));
   float2* Uo = To + half;
   const float2* X = (const float2*)Xe;
-  // T_o = D_oe X_e ; U_o = -D_oo^-1 T_o ; Y_e = D_eo U_o + D_ee X_e (g5hat by
-  // mode bit 1).  The image of X_e the first launch writes (first half image)
-  // serves the third as its self input; the third writes the image of U_o
-  // over that of T_o (second half image), which the second launch has read.
+  // U_o = -D_oo^-1 D_oe X_e (one launch on the D_oo^-1 D_oe image, else
+  // T_o = D_oe X_e and U_o = -D_oo^-1 T_o) ; Y_e = D_eo U_o + D_ee X_e
+  // (g5hat by mode bit 1).  The image of X_e the first launch writes (first
+  // half image) serves the last as its self input; the last writes the image
+  // of U_o into the second half image.
   const size_t hb = coarse_tc_half_image_bytes(C, nrhs);
-  MG_CHECK(coarse_tc_eo_launch(ctx, C, X, nullptr, To, nrhs, 0, 1, 0, 7, nullptr, 1.f, img, s));
-  MG_CHECK(coarse_tc_eo_launch(ctx, C, nullptr, To, Uo, nrhs, 0, 1, 8, 8, C->Sinv_img, -1.f, img, s));
+  if (C->Ahat_img) {
+    MG_CHECK(coarse_tc_eo_launch(ctx, C, X, nullptr, Uo, nrhs, 0, 1, 0, 7, nullptr, -1.f, img, s, nullptr,
+                                 C->Ahat_img));
+  } else {
+    MG_CHECK(coarse_tc_eo_launch(ctx, C, X, nullptr, To, nrhs, 0, 1, 0, 7, nullptr, 1.f, img, s));
+    MG_CHECK(coarse_tc_eo_launch(ctx, C, nullptr, To, Uo, nrhs, 0, 1, 8, 8, C->Sinv_img, -1.f, img, s));
+  }
   return coarse_tc_eo_launch(ctx, C, Uo, X, (float2*)Ye, nrhs, mode & 2, 0, 0, 8, nullptr, 1.f, img + hb, s, img);
 }
 

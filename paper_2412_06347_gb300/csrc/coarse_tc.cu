@@ -28,6 +28,7 @@
 // for its copies in flight, the MMA thread for its MMAs, TMEM is freed and
 // the kernel returns; the host reports MGLMA_ERR_TIMEOUT.
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -184,6 +185,7 @@ __device__ __forceinline__ void tmem_ld<64>(uint32_t taddr, uint32_t* v) {
 struct TcRun {
   const uint8_t* A;
   const uint8_t* Aself;
+  int a_unit;  // 1: A holds eight hop slots per unit u ([u][8]), else nine per site ([y][9])
   const uint8_t* XB;
   const uint8_t* XBself;
   float2* Y;
@@ -292,8 +294,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             const uint32_t dst = smem_u32(sm + (size_t)st * stage_bytes);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(stage_bytes)
                          : "memory");
-            const uint8_t* srcA =
-                (d == 8 && run.Aself) ? run.Aself + (size_t)y * a_slot : run.A + ((size_t)y * 9 + d) * a_slot;
+            const uint8_t* srcA = (d == 8 && run.Aself) ? run.Aself + (size_t)y * a_slot
+                                  : run.a_unit          ? run.A + ((size_t)u * 8 + d) * a_slot
+                                                        : run.A + ((size_t)y * 9 + d) * a_slot;
             const uint8_t* srcB = (d == 8 ? run.XBself : run.XB) + ((size_t)t * nunits + row_of(d)) * b_slot;
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -453,6 +456,20 @@ mglma_status coarse_tc_image(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s) {
   return MGLMA_OK;
 }
 
+// The dynamic shared memory granted to coarse_tc_kernel<NT>: one record per
+// instantiation shared by every launcher, raised only (a second record could
+// lower the grant below what the first believes it holds).
+template <int NT>
+static mglma_status tc_grant_smem(size_t smem) {
+  static std::mutex mu;
+  static size_t granted = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (smem <= granted) return MGLMA_OK;
+  MG_CUDA(cudaFuncSetAttribute(coarse_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  granted = smem;
+  return MGLMA_OK;
+}
+
 template <int NT>
 static mglma_status launch_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float2* X, float2* Y, int nrhs, int mode,
                               void* xb, int* err, cudaStream_t s) {
@@ -464,17 +481,14 @@ static mglma_status launch_tc(mglma_ctx ctx, const mglma_coarse_s* C, const floa
     MG_LAUNCH_CHECK();
   }
   const size_t smem = tc_smem(n2, NT);
-  static size_t attr = 0;  // largest dynamic shared memory granted so far
-  if (smem > attr) {
-    MG_CUDA(cudaFuncSetAttribute(coarse_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  MG_CHECK(tc_grant_smem<NT>(smem));
   // two resident CTAs per SM: while one waits for its MMAs to release a
   // stage, the other's copies and MMAs proceed
   const unsigned grid = (unsigned)std::min<int64_t>(V1, 2 * (int64_t)ctx->sm_count);
   TcRun run;
   run.A = (const uint8_t*)C->Aimg;
   run.Aself = nullptr;
+  run.a_unit = 0;
   run.XB = run.XBself = (const uint8_t*)xb;
   run.Y = Y;
   run.d_lo = 0;
@@ -505,7 +519,8 @@ size_t coarse_tc_half_image_bytes(const mglma_coarse_s* C, int nrhs) {
 template <int NT>
 static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
-                                 float sign, void* scratch, cudaStream_t s, const void* self_image) {
+                                 float sign, void* scratch, cudaStream_t s, const void* self_image,
+                                 const uint16_t* Ahop) {
   const int n2 = C->n2;
   const int64_t Vh = C->geo.V1 / 2;
   const size_t half = coarse_tc_half_image_bytes(C, nrhs);
@@ -519,15 +534,12 @@ static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const f
     x_image_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, s>>>(Xself, (uint4*)xb_self, Vh, n2, nrhs, NT, mode);
   MG_LAUNCH_CHECK();
   const size_t smem = tc_smem(n2, NT);
-  static size_t attr = 0;
-  if (smem > attr) {
-    MG_CUDA(cudaFuncSetAttribute(coarse_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  MG_CHECK(tc_grant_smem<NT>(smem));
   const unsigned grid = (unsigned)std::min<int64_t>(Vh, 2 * (int64_t)ctx->sm_count);
   TcRun run;
-  run.A = (const uint8_t*)C->Aimg;
+  run.A = Ahop ? (const uint8_t*)Ahop : (const uint8_t*)C->Aimg;
   run.Aself = (const uint8_t*)Aself;
+  run.a_unit = Ahop ? 1 : 0;
   run.XB = xb_hop;
   run.XBself = xb_self;
   run.Y = Y;
@@ -543,16 +555,21 @@ static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const f
 
 mglma_status coarse_tc_eo_launch(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
-                                 float sign, void* scratch, cudaStream_t s, const void* self_image) {
+                                 float sign, void* scratch, cudaStream_t s, const void* self_image,
+                                 const uint16_t* Ahop) {
   if (!C->Aimg || !coarse_tc_supported(C->n2)) return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: no tensor image");
   if (par < 0 || par > 1 || d_lo < 0 || d_hi > 8 || d_lo > d_hi)
     return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: bad launch");
+  if (Ahop && d_hi > 7) return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: the eight-slot image has no self slot");
   const int nt = tuned(ctx, TUNE_COARSE_NT, nrhs, C->geo.V1, coarse_tc_default_nt(nrhs));
   if (nt == 32)
-    return launch_tc_eo<32>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image);
+    return launch_tc_eo<32>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image,
+                            Ahop);
   if (nt == 16)
-    return launch_tc_eo<16>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image);
-  return launch_tc_eo<8>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image);
+    return launch_tc_eo<16>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image,
+                            Ahop);
+  return launch_tc_eo<8>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image,
+                         Ahop);
 }
 
 mglma_status coarse_tc_check(mglma_coarse_s* C, cudaStream_t s) {

@@ -35,12 +35,26 @@ namespace mglma {
 void set_error(const std::string& msg);
 mglma_status fail(mglma_status st, const std::string& msg);
 
+// "file.cu:line" of a check, for error messages
+inline std::string src_line(const char* file, int line) {
+  const char* b = file;
+  for (const char* p = file; *p; ++p)
+    if (*p == '/') b = p + 1;
+  return std::string(b) + ":" + std::to_string(line);
+}
+
+// A failed runtime call is reported with its text and source line; the
+// runtime's last-error slot is cleared so that a handled failure is not
+// reported again by a later launch check.
 #define MG_CUDA(call)                                                              \
   do {                                                                             \
     cudaError_t e_ = (call);                                                       \
-    if (e_ != cudaSuccess)                                                         \
-      return ::mglma::fail(MGLMA_ERR_CUDA, std::string(#call) + ": " +             \
-                                               cudaGetErrorString(e_));            \
+    if (e_ != cudaSuccess) {                                                       \
+      (void)cudaGetLastError();                                                    \
+      return ::mglma::fail(MGLMA_ERR_CUDA, std::string(#call) + " (" +             \
+                                               ::mglma::src_line(__FILE__, __LINE__) + \
+                                               "): " + cudaGetErrorString(e_));    \
+    }                                                                              \
   } while (0)
 
 #define MG_CHECK(expr)                                                             \

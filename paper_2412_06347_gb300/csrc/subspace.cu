@@ -25,6 +25,7 @@
 //   FP32 : float4  [V1][2Nv][3][|B|]          (2 complex per float4)
 //   FP16 : uint2   [V1][2Nv][3][|B|] (2 complex as 4 halves) with one FP32
 //          scale per (y, j): value = half * scale
+#include <algorithm>
 #include <cmath>
 
 #include "cplx.cuh"
@@ -566,6 +567,201 @@ __global__ void basis_export_kernel(const double2* __restrict__ p64, double2* __
   for (int q = 0; q < 6; ++q) o[6 * alpha + q] = p64[(yj * 6 + q) * nB + k];
 }
 
+// ------------------------------------------------------------ R0 / T0 at many RHS (FP32 fields)
+// One CTA per (block, tile of 16 RHS), so the block's basis is read once for
+// all of them.  R0: the basis and the spinors of a chunk of the block's sites
+// are staged in shared memory (FP32, rows padded so that the staging stores
+// of consecutive sites fall in different banks); each thread owns a 4 dof x
+// 4 RHS tile of the outputs over a share of the chunk's sites (split K), and
+// the shares are summed in a fixed order at the end.  T0: each thread owns
+// one site, one chirality and four RHS (6 x 4 complex accumulators) and runs
+// over the Nv dofs of that chirality.  The FP16 basis's per-(block, dof)
+// scale multiplies the R0 result and the T0 coefficients instead of every
+// basis element.  Needs Nv % 4 == 0.
+constexpr int T16_KC = 16;     // sites per staged chunk (R0)
+constexpr int T16_MAXT = 384;  // R0 threads per CTA (at most)
+
+// the six components of phi_{y j}(k) without the FP16 scale
+template <typename B>
+__device__ __forceinline__ void basis_raw(const void* base, size_t yj, int nB, int k, Cx<float> o[6]);
+template <>
+__device__ __forceinline__ void basis_raw<__half>(const void* base, size_t yj, int nB, int k, Cx<float> o[6]) {
+  const uint2* p = reinterpret_cast<const uint2*>(base) + yj * 3 * nB + k;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    uint2 v = __ldg(p + q * nB);
+    const float2 fa = __half22float2(*reinterpret_cast<__half2*>(&v.x));
+    const float2 fb = __half22float2(*reinterpret_cast<__half2*>(&v.y));
+    o[2 * q] = cx(fa.x, fa.y);
+    o[2 * q + 1] = cx(fb.x, fb.y);
+  }
+}
+template <>
+__device__ __forceinline__ void basis_raw<float>(const void* base, size_t yj, int nB, int k, Cx<float> o[6]) {
+  BIO<float>::template load<float>(base, nullptr, yj, nB, k, o);
+}
+template <typename B>
+__device__ __forceinline__ float basis_scale(const float* scale, size_t yj) {
+  return sizeof(B) == 2 ? __ldg(scale + yj) : 1.f;
+}
+
+// staged rows, in float4: phi [kk][q][h][jg] + 1 pad, psi [kk][c][h][rg] + 1 pad
+__host__ __device__ constexpr int t16_phi_row(int n2) { return 3 * n2 + 1; }
+constexpr int T16_PSI_ROW = 12 * 2 * 4 + 1;
+
+template <typename B>
+__global__ void __launch_bounds__(T16_MAXT) restrict16_kernel(const float4* __restrict__ fine, int nrhs,
+                                                              const void* __restrict__ basis,
+                                                              const float* __restrict__ scale, BlockGeo g, int nv,
+                                                              float2* __restrict__ out) {
+  extern __shared__ float4 sm16[];
+  const int n2 = 2 * nv, ng = n2 / 4;  // dof groups of four
+  const int prow = t16_phi_row(n2);
+  // phi row kk: float4 ((q * 2 + h) * ng + jg) = (phi_{4jg+2h}, phi_{4jg+2h+1}) at site kk
+  // psi row kk: float4 ((c * 2 + h) * 4 + rg) = (psi_{4rg+2h}, psi_{4rg+2h+1}) at site kk
+  float4* sphi = sm16;
+  float4* spsi = sm16 + T16_KC * prow;
+  __shared__ int64_t site_of[T16_KC];
+  const int ntile = (nrhs + 15) / 16;
+  const int64_t y = blockIdx.x / ntile;
+  const int r0 = (int)(blockIdx.x % ntile) * 16;
+  const int ntt = 4 * ng;  // output tiles (dof group, RHS group)
+  const int KS = blockDim.x / ntt;
+  const int tid = threadIdx.x;
+  const int tt = tid % ntt, ks = tid / ntt;
+  const int jg = tt % ng, rg = tt / ng;
+  const int al = (4 * jg) / nv;
+  Cx<float> acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = cx(0.f, 0.f);
+  for (int k0 = 0; k0 < g.nB; k0 += T16_KC) {
+    const int ck = min(T16_KC, g.nB - k0);
+    __syncthreads();  // the previous chunk is consumed
+    if (tid < ck) site_of[tid] = block_site(g, y, k0 + tid);
+    for (int idx = tid; idx < n2 * ck; idx += blockDim.x) {
+      const int kk = idx % ck, j = idx / ck;
+      Cx<float> ph[6];
+      basis_raw<B>(basis, (size_t)y * n2 + j, g.nB, k0 + kk, ph);
+      float2* dst = reinterpret_cast<float2*>(sphi + (size_t)kk * prow);
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        dst[((q * 2 + (j % 4) / 2) * ng + j / 4) * 2 + (j % 2)] = make_float2(ph[q].re, ph[q].im);
+    }
+    __syncthreads();  // site_of is ready
+    for (int idx = tid; idx < 16 * 6 * ck; idx += blockDim.x) {
+      const int kk = idx % ck, c = (idx / ck) % 6, r = idx / (ck * 6);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r0 + r < nrhs) v = __ldg(fine + ((size_t)(r0 + r) * 6 + c) * g.V + site_of[kk]);
+      float2* dst = reinterpret_cast<float2*>(spsi + (size_t)kk * T16_PSI_ROW);
+      dst[(((2 * c) * 2 + (r % 4) / 2) * 4 + r / 4) * 2 + (r % 2)] = make_float2(v.x, v.y);
+      dst[(((2 * c + 1) * 2 + (r % 4) / 2) * 4 + r / 4) * 2 + (r % 2)] = make_float2(v.z, v.w);
+    }
+    __syncthreads();
+    if (ks < KS) {
+      for (int kk = ks; kk < ck; kk += KS) {
+        const float4* prw = sphi + (size_t)kk * prow;
+        const float4* srw = spsi + (size_t)kk * T16_PSI_ROW;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const float4 pa = prw[(q * 2 + 0) * ng + jg], pb = prw[(q * 2 + 1) * ng + jg];
+          const float4 sa = srw[((6 * al + q) * 2 + 0) * 4 + rg], sb = srw[((6 * al + q) * 2 + 1) * 4 + rg];
+          const Cx<float> ph[4] = {cx(pa.x, pa.y), cx(pa.z, pa.w), cx(pb.x, pb.y), cx(pb.z, pb.w)};
+          const Cx<float> ps[4] = {cx(sa.x, sa.y), cx(sa.z, sa.w), cx(sb.x, sb.y), cx(sb.z, sb.w)};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cfma_conj(acc[a][b], ph[a], ps[b]);
+        }
+      }
+    }
+  }
+  // sum the K shares in a fixed order
+  __syncthreads();
+  float2* red = reinterpret_cast<float2*>(sm16);  // [ks][tt][16]
+  if (ks < KS)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) red[((size_t)ks * ntt + tt) * 16 + a * 4 + b] = make_float2(acc[a][b].re, acc[a][b].im);
+  __syncthreads();
+  for (int o = tid; o < n2 * 16; o += blockDim.x) {
+    const int j = o % n2, r = o / n2;
+    if (r0 + r >= nrhs) continue;
+    const int t2 = (r / 4) * ng + j / 4, e = (j % 4) * 4 + r % 4;
+    float sx = 0.f, sy = 0.f;
+    for (int k = 0; k < KS; ++k) {
+      const float2 v = red[((size_t)k * ntt + t2) * 16 + e];
+      sx += v.x;
+      sy += v.y;
+    }
+    const float sc = basis_scale<B>(scale, (size_t)y * n2 + j);
+    out[((size_t)(r0 + r) * g.V1 + y) * n2 + j] = make_float2(sc * sx, sc * sy);
+  }
+}
+
+template <typename B>
+__global__ void __launch_bounds__(256) prolong16_kernel(const float2* __restrict__ coarse, int nrhs,
+                                                        const void* __restrict__ basis,
+                                                        const float* __restrict__ scale, BlockGeo g, int nv,
+                                                        float4* __restrict__ fine, int accumulate) {
+  __shared__ float4 cs[64 * 2 * 4];  // [j][h][rg] = scale_j (c_{4rg+2h}, c_{4rg+2h+1}), n2 <= 64
+  const int n2 = 2 * nv;
+  const int ntile = (nrhs + 15) / 16;
+  const int64_t y = blockIdx.x / ntile;
+  const int r0 = (int)(blockIdx.x % ntile) * 16;
+  for (int idx = threadIdx.x; idx < n2 * 16; idx += blockDim.x) {
+    const int j = idx % n2, r = idx / n2;
+    const float sc = basis_scale<B>(scale, (size_t)y * n2 + j);
+    float2 v = r0 + r < nrhs ? coarse[((size_t)(r0 + r) * g.V1 + y) * n2 + j] : make_float2(0.f, 0.f);
+    v.x *= sc;
+    v.y *= sc;
+    reinterpret_cast<float2*>(cs)[((j * 2 + (r % 4) / 2) * 4 + r / 4) * 2 + (r % 2)] = v;
+  }
+  __syncthreads();
+  // work items (site k fastest, then chirality, then RHS group of four)
+  for (int w = threadIdx.x; w < g.nB * 8; w += blockDim.x) {
+    const int k = w % g.nB, al = (w / g.nB) % 2, rg = w / (2 * g.nB);
+    if (r0 + 4 * rg >= nrhs) continue;
+    Cx<float> acc[6][4];
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[q][b] = cx(0.f, 0.f);
+    for (int jj = 0; jj < nv; ++jj) {
+      const int j = al * nv + jj;
+      Cx<float> ph[6];
+      basis_raw<B>(basis, (size_t)y * n2 + j, g.nB, k, ph);
+      const float4 ca = cs[(j * 2 + 0) * 4 + rg], cb = cs[(j * 2 + 1) * 4 + rg];
+      const Cx<float> cv[4] = {cx(ca.x, ca.y), cx(ca.z, ca.w), cx(cb.x, cb.y), cx(cb.z, cb.w)};
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) cfma(acc[q][b], cv[b], ph[q]);
+    }
+    const int64_t site = block_site(g, y, k);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = r0 + 4 * rg + b;
+      if (r >= nrhs) break;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float4* p = fine + ((size_t)r * 6 + 3 * al + c) * g.V + site;
+        float4 v = make_float4(acc[2 * c][b].re, acc[2 * c][b].im, acc[2 * c + 1][b].re, acc[2 * c + 1][b].im);
+        if (accumulate) {
+          const float4 o = *p;
+          v.x += o.x;
+          v.y += o.y;
+          v.z += o.z;
+          v.w += o.w;
+        }
+        *p = v;
+      }
+    }
+  }
+}
+
 // ============================================================ host side
 static int subspace_smem_restrict(int nrt, int rbytes) { return nrt * 12 * RP_CHUNK * 2 * rbytes; }
 
@@ -683,6 +879,12 @@ mglma_status coarse_gamma_level1(mglma_ctx ctx, const mglma_subspace_s* S, int k
   return MGLMA_OK;
 }
 
+// the many-RHS R0 / T0 kernels: FP32 fields, at least 8 RHS, Nv % 4 == 0 and
+// 2 Nv <= 64, FP32 or FP16 basis
+static bool use_t16(const mglma_subspace_s* S, int nrhs) {
+  return nrhs >= 8 && S->nv % 4 == 0 && 2 * S->nv <= 64 && (S->phi16 || S->phi32);
+}
+
 mglma_status restrict_fine(mglma_ctx ctx, const mglma_subspace_s* S, const Spinor& in, void* out_coarse,
                            cudaStream_t s) {
   ProfScope ps(ctx, K_RESTRICT, s, transfer_bytes(S, in.prec, in.nrhs), 8.0 * S->geo.V * 12.0 * S->nv * in.nrhs);
@@ -691,6 +893,32 @@ mglma_status restrict_fine(mglma_ctx ctx, const mglma_subspace_s* S, const Spino
     if (!S->lean) return fail(MGLMA_ERR_INVALID, "restrict: FP64 needs a subspace stored in FP64");
     if (S->phi16) return launch_restrict<double, __half, 2>(S, in.p, in.nrhs, S->phi16, out_coarse, s);
     return launch_restrict<double, float, 2>(S, in.p, in.nrhs, S->phi32, out_coarse, s);
+  }
+  if (use_t16(S, in.nrhs)) {
+    const BlockGeo g = S->geo;
+    const int n2 = 2 * S->nv, ntt = n2;
+    const int threads = (T16_MAXT / ntt) * ntt;
+    const size_t stage = (size_t)T16_KC * (t16_phi_row(n2) + T16_PSI_ROW) * sizeof(float4);
+    const size_t smem = std::max(stage, (size_t)threads * 16 * sizeof(float2));
+    const unsigned grid = (unsigned)(g.V1 * ((in.nrhs + 15) / 16));
+    static size_t attr16 = 0, attr32 = 0;
+    if (S->phi16) {
+      if (smem > attr16) {
+        MG_CUDA(cudaFuncSetAttribute(restrict16_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr16 = smem;
+      }
+      restrict16_kernel<__half><<<grid, threads, smem, s>>>((const float4*)in.p, in.nrhs, S->phi16, S->scale16, g,
+                                                            S->nv, (float2*)out_coarse);
+    } else {
+      if (smem > attr32) {
+        MG_CUDA(cudaFuncSetAttribute(restrict16_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr32 = smem;
+      }
+      restrict16_kernel<float><<<grid, threads, smem, s>>>((const float4*)in.p, in.nrhs, S->phi32, nullptr, g, S->nv,
+                                                           (float2*)out_coarse);
+    }
+    MG_LAUNCH_CHECK();
+    return MGLMA_OK;
   }
   if (S->phi16) return launch_restrict<float, __half, 4>(S, in.p, in.nrhs, S->phi16, out_coarse, s);
   return launch_restrict<float, float, 4>(S, in.p, in.nrhs, S->phi32, out_coarse, s);
@@ -704,6 +932,18 @@ mglma_status prolong_coarse(mglma_ctx ctx, const mglma_subspace_s* S, const void
     if (!S->lean) return fail(MGLMA_ERR_INVALID, "prolong: FP64 needs a subspace stored in FP64");
     if (S->phi16) return launch_prolong<double, __half, 2>(S, in_coarse, out.nrhs, S->phi16, out.p, accumulate, s);
     return launch_prolong<double, float, 2>(S, in_coarse, out.nrhs, S->phi32, out.p, accumulate, s);
+  }
+  if (use_t16(S, out.nrhs)) {
+    const BlockGeo g = S->geo;
+    const unsigned grid = (unsigned)(g.V1 * ((out.nrhs + 15) / 16));
+    if (S->phi16)
+      prolong16_kernel<__half><<<grid, 256, 0, s>>>((const float2*)in_coarse, out.nrhs, S->phi16, S->scale16, g, S->nv,
+                                                    (float4*)out.p, accumulate ? 1 : 0);
+    else
+      prolong16_kernel<float><<<grid, 256, 0, s>>>((const float2*)in_coarse, out.nrhs, S->phi32, nullptr, g, S->nv,
+                                                   (float4*)out.p, accumulate ? 1 : 0);
+    MG_LAUNCH_CHECK();
+    return MGLMA_OK;
   }
   if (S->phi16) return launch_prolong<float, __half, 4>(S, in_coarse, out.nrhs, S->phi16, out.p, accumulate, s);
   return launch_prolong<float, float, 4>(S, in_coarse, out.nrhs, S->phi32, out.p, accumulate, s);

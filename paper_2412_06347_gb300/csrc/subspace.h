@@ -49,6 +49,10 @@ struct mglma_coarse_s {
   // tensor-core image (one slot per site)
   double2* Sinv64 = nullptr;
   uint16_t* Sinv_img = nullptr;
+  // D_oo^-1 D_oe: per odd site (half-lattice index u) the eight hop slots
+  // multiplied by the inverse self block, as a BF16 tensor-core image
+  // ([u][8 slots]); with it S_ee takes two tensor-core launches
+  uint16_t* Ahat_img = nullptr;
 };
 
 namespace mglma {
@@ -114,10 +118,12 @@ size_t coarse_eo_scratch_bytes(const mglma_coarse_s* C, int nrhs);
 // B images go to scratch (hop input) and scratch + one half image (self
 // input); self_image (nullable) is an image of the self input an earlier
 // launch with the same RHS count and mode bit 0 left, used instead of writing
-// one
+// one; Ahop (nullable) replaces the hop slots with an eight-slot image
+// indexed by the half-lattice index of the output site
 mglma_status coarse_tc_eo_launch(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
-                                 float sign, void* scratch, cudaStream_t s, const void* self_image = nullptr);
+                                 float sign, void* scratch, cudaStream_t s, const void* self_image = nullptr,
+                                 const uint16_t* Ahop = nullptr);
 size_t coarse_tc_half_image_bytes(const mglma_coarse_s* C, int nrhs);
 mglma_status coarse_tc_image_blocks(mglma_ctx ctx, const double2* A64, int64_t V1, int n2, int nslots,
                                     uint16_t** img, cudaStream_t s);

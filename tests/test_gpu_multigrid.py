@@ -104,22 +104,26 @@ def test_coarse_operator_and_apply(m, ctx, setup):
         m.mglma_coarse_free(C)
 
 
-def test_low_precision_transfers(m, ctx):
-    L, b, nv = (8, 4, 4, 8), (4, 4, 4, 4), 6
+@pytest.mark.parametrize("nv,nrhs", [(6, 5), (8, 17)])
+def test_low_precision_transfers(m, ctx, nv, nrhs):
+    """FP32 R0 / T0 against the oracle on the same basis; (8, 17) runs the
+    many-RHS kernels (tiles of 16 RHS, a one-RHS remainder tile), (6, 5) the
+    few-RHS ones."""
+    L, b = (8, 4, 4, 8), (4, 4, 4, 4)
     U = synthetic.gauge_links(L, 0.2, 31)
     g = m.mglma_gauge_load(ctx, L, U, 0.125, 1.7)
     phi = MG.subspace(U, synthetic.gaussian_start_vectors(L, nv, 32), 0.125, 1.7, b, 2)
-    psi = synthetic.random_spinors(L, 5, 33)
+    psi = synthetic.random_spinors(L, nrhs, 33)
     ref = MG.restrict(phi, psi, L, b)
-    c = synthetic.random_coarse(phi.shape[0], 2 * nv, 5, 34)
+    c = synthetic.random_coarse(phi.shape[0], 2 * nv, nrhs, 34)
     pref = MG.prolong(phi, c, L, b)
     for store, tol in ((m.MGLMA_FP32, 2e-6), (m.MGLMA_FP16, 2e-3)):
         sub = m.mglma_subspace_build(ctx, g, b, nv, 2, 32, store)
         out = np.zeros_like(ref)
-        m.mglma_restrict(ctx, sub, 5, psi, out, m.MGLMA_FP32)
+        m.mglma_restrict(ctx, sub, nrhs, psi, out, m.MGLMA_FP32)
         assert rel_per_rhs(out, ref).max() < tol
         f = np.zeros_like(psi)
-        m.mglma_prolong(ctx, sub, 5, c, f, m.MGLMA_FP32)
+        m.mglma_prolong(ctx, sub, nrhs, c, f, m.MGLMA_FP32)
         assert rel_per_rhs(f, pref).max() < tol
         m.mglma_subspace_free(sub)
     m.mglma_gauge_free(g)
