@@ -16,6 +16,7 @@
 // coalesced; neighbours are found arithmetically (no halo, no tables); links
 // are stored reconstruct-12 in FP32 with the third row rebuilt in registers.
 #include <mutex>
+#include <type_traits>
 #include <string>
 
 #include "internal.h"
@@ -52,12 +53,13 @@ constexpr int dslash_min_ctas() {
 // t_{k+1} = op(s_{k+1}) in exact arithmetic, the next step needs no separate
 // vector update and its memory traffic runs under the stencil's.
 struct MrArgs {
-  float4* s = nullptr;
+  void* s = nullptr;  // storage of in / out (FP32 or BF16)
   float4* z = nullptr;
   const double2* alpha = nullptr;
 };
 
-template <typename R, int NR, bool DAG, int RW, bool RED = false, bool MRF = false>
+template <typename R, int NR, bool DAG, int RW, bool RED = false, bool MRF = false, typename SI = R,
+          typename SO = R>
 __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kernel(const void* __restrict__ in, void* __restrict__ out,
                                                      const void* __restrict__ U, const void* __restrict__ C,
                                                      DslashArgs a, double* __restrict__ part = nullptr,
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         if (r0 + r < a.nrhs) {
-          IO<R>::load(in, V, r0 + r, site, psi);
+          SIO<SI>::load(in, V, r0 + r, site, psi);
           clover_apply6<R>(c, psi + 6 * chi, acc[r] + 6 * chi);
         }
       }
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
 #pragma unroll
       for (int r = 0; r < NR; ++r)
         if (r0 + r < a.nrhs) {
-          IO<R>::load(in, V, r0 + r, nf, psi);
+          SIO<SI>::load(in, V, r0 + r, nf, psi);
           hop_add<R, true>(mu, sF, f, Um, psi, acc[r]);
         }
     }
@@ -132,22 +134,59 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
 #pragma unroll
       for (int r = 0; r < NR; ++r)
         if (r0 + r < a.nrhs) {
-          IO<R>::load(in, V, r0 + r, nb, psi);
+          SIO<SI>::load(in, V, r0 + r, nb, psi);
           hop_add<R, false>(mu, sB, f, Um, psi, acc[r]);
         }
     }
   }
   float nn = 0.f, dr = 0.f, di = 0.f;  // RED: this thread's |t|^2 and <t, s>
-  if constexpr (MRF) {
+  constexpr bool BF = std::is_same<SO, SpinBf16>::value;
+  if constexpr (MRF && BF) {
+    // t, s in BF16 ([rhs][3][V] uint4 of four complex), z in FP32; the dots
+    // are taken on the values as stored
+    if (valid) {
+      const double2 al = mr.alpha[r0];
+      const Cx<float> alpha = cx((float)al.x, (float)al.y);
+      const size_t offb = (size_t)r0 * 3 * V + site, offz = (size_t)r0 * 6 * V + site;
+      const uint4* tp = reinterpret_cast<const uint4*>(in) + offb;
+      uint4* op = reinterpret_cast<uint4*>(out) + offb;
+      uint4* sp = reinterpret_cast<uint4*>(mr.s) + offb;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const uint4 tv = __ldg(tp + j * V), sv = sp[j * V];
+        const float4 z0 = mr.z[offz + 2 * j * V], z1 = mr.z[offz + (2 * j + 1) * V];
+        const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w}, sw[4] = {sv.x, sv.y, sv.z, sv.w};
+        const Cx<float> zk[4] = {cx(z0.x, z0.y), cx(z0.z, z0.w), cx(z1.x, z1.y), cx(z1.z, z1.w)};
+        uint32_t tno[4], sno[4];
+        Cx<float> zn[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const Cx<float> t = bf16_unpack(tw[h]), sk = bf16_unpack(sw[h]);
+          tno[h] = bf16_pack(t - alpha * acc[0][4 * j + h]);
+          sno[h] = bf16_pack(sk - alpha * t);
+          zn[h] = zk[h] + alpha * sk;
+          const Cx<float> tr = bf16_unpack(tno[h]), sr = bf16_unpack(sno[h]);
+          nn += tr.re * tr.re + tr.im * tr.im;
+          dr += tr.re * sr.re + tr.im * sr.im;
+          di += tr.re * sr.im - tr.im * sr.re;
+        }
+        op[j * V] = make_uint4(tno[0], tno[1], tno[2], tno[3]);
+        sp[j * V] = make_uint4(sno[0], sno[1], sno[2], sno[3]);
+        mr.z[offz + 2 * j * V] = make_float4(zn[0].re, zn[0].im, zn[1].re, zn[1].im);
+        mr.z[offz + (2 * j + 1) * V] = make_float4(zn[2].re, zn[2].im, zn[3].re, zn[3].im);
+      }
+    }
+  } else if constexpr (MRF) {
     if (valid) {
       const double2 al = mr.alpha[r0];
       const Cx<float> alpha = cx((float)al.x, (float)al.y);
       const size_t off = (size_t)r0 * 6 * V + site;
       const float4* tp = reinterpret_cast<const float4*>(in) + off;
       float4* op = reinterpret_cast<float4*>(out) + off;
+      float4* msp = reinterpret_cast<float4*>(mr.s);
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        const float4 tv = __ldg(tp + j * V), sv = mr.s[off + j * V], zv = mr.z[off + j * V];
+        const float4 tv = __ldg(tp + j * V), sv = msp[off + j * V], zv = mr.z[off + j * V];
         const Cx<float> t[2] = {cx(tv.x, tv.y), cx(tv.z, tv.w)}, sk[2] = {cx(sv.x, sv.y), cx(sv.z, sv.w)},
                         zk[2] = {cx(zv.x, zv.y), cx(zv.z, zv.w)};
         Cx<float> tn[2], sn[2], zn[2];
@@ -161,7 +200,7 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
           di += tn[h].re * sn[h].im - tn[h].im * sn[h].re;
         }
         op[j * V] = make_float4(tn[0].re, tn[0].im, tn[1].re, tn[1].im);
-        mr.s[off + j * V] = make_float4(sn[0].re, sn[0].im, sn[1].re, sn[1].im);
+        msp[off + j * V] = make_float4(sn[0].re, sn[0].im, sn[1].re, sn[1].im);
         mr.z[off + j * V] = make_float4(zn[0].re, zn[0].im, zn[1].re, zn[1].im);
       }
     }
@@ -179,12 +218,17 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
 #pragma unroll
           for (int k = 0; k < 12; ++k) acc[r][k] = bv[k] - acc[r][k];
         }
-        IO<R>::store(out, V, r0 + r, site, acc[r]);
+        if constexpr (BF) {
+          // the dots below see the values as stored
+#pragma unroll
+          for (int k = 0; k < 12; ++k) acc[r][k] = bf16_unpack(bf16_pack(acc[r][k]));
+        }
+        SIO<SO>::store(out, V, r0 + r, site, acc[r]);
       }
     if constexpr (RED) {
       if (valid) {
         Cx<R> sv[12];
-        IO<R>::load(in, V, r0, site, sv);
+        SIO<SI>::load(in, V, r0, site, sv);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           const Cx<R> t = acc[0][k];
@@ -754,16 +798,16 @@ static double dslash_bytes(int64_t V, int nrhs, bool fp64) {
 }
 static double dslash_flops(int64_t V, int nrhs) { return 1896.0 * (double)V * nrhs; }
 
-template <typename R, int NR, int RW>
+template <typename R, int NR, int RW, typename SO = R>
 static void launch_dslash(const Spinor& in, Spinor& out, const void* U, const void* C, const DslashArgs& a,
                           bool dagger, cudaStream_t s) {
   constexpr int SW = 128 / RW;
   const int ntile = (in.nrhs + NR - 1) / NR;
   const size_t ctas = (size_t)((in.V + SW - 1) / SW) * ((ntile + RW - 1) / RW);
   if (dagger)
-    dslash_kernel<R, NR, true, RW><<<(unsigned)ctas, 128, 0, s>>>(in.p, out.p, U, C, a);
+    dslash_kernel<R, NR, true, RW, false, false, R, SO><<<(unsigned)ctas, 128, 0, s>>>(in.p, out.p, U, C, a);
   else
-    dslash_kernel<R, NR, false, RW><<<(unsigned)ctas, 128, 0, s>>>(in.p, out.p, U, C, a);
+    dslash_kernel<R, NR, false, RW, false, false, R, SO><<<(unsigned)ctas, 128, 0, s>>>(in.p, out.p, U, C, a);
 }
 
 // FP32 tile shape (RHS per thread NR, RHS tiles per CTA RW) encoded as
@@ -847,9 +891,9 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
 
 mglma_status dslash_resid(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, const Spinor& b, Spinor& out,
                           cudaStream_t s) {
-  if (in.prec != MGLMA_FP32 || out.prec != MGLMA_FP32 || b.prec != MGLMA_FP32 || in.V != G->g.V ||
-      out.V != G->g.V || b.V != G->g.V || in.nrhs != out.nrhs || b.nrhs != out.nrhs)
-    return fail(MGLMA_ERR_INVALID, "dslash_resid: FP32 fields of the gauge field's volume needed");
+  if (in.prec != MGLMA_FP32 || (out.prec != MGLMA_FP32 && out.prec != MGLMA_BF16) || b.prec != MGLMA_FP32 ||
+      in.V != G->g.V || out.V != G->g.V || b.V != G->g.V || in.nrhs != out.nrhs || b.nrhs != out.nrhs)
+    return fail(MGLMA_ERR_INVALID, "dslash_resid: FP32 in and b (FP32 or BF16 out) of the gauge field's volume needed");
   if (in.p == out.p || b.p == out.p) return fail(MGLMA_ERR_INVALID, "dslash_resid: out must differ from in and b");
   if (in.nrhs == 0) return MGLMA_OK;
   DslashArgs a;
@@ -858,12 +902,18 @@ mglma_status dslash_resid(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& i
   a.nrhs = in.nrhs;
   a.g5out = 0;
   a.bsub = b.p;
-  ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(in.V, in.nrhs, false) + 96.0 * (double)in.V * in.nrhs,
+  const bool bf = out.prec == MGLMA_BF16;
+  ProfScope ps(ctx, K_DSLASH32, s,
+               dslash_bytes(in.V, in.nrhs, false) + (bf ? 96.0 - 48.0 : 96.0) * (double)in.V * in.nrhs,
                dslash_flops(in.V, in.nrhs) + 24.0 * (double)in.V * in.nrhs);
-  // the staged-tile kernel has no room for the epilogue's extra operand
-  int code = tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, G->g.V, dslash32_default_tile(in.nrhs));
-  if (dslash32_tile_staged(code)) code = dslash32_tile_code(1, 1);
-  launch_dslash32(code, in, out, G->U32, G->C32, a, false, s);
+  if (bf) {
+    launch_dslash<float, 1, 1, SpinBf16>(in, out, G->U32, G->C32, a, false, s);
+  } else {
+    // the staged-tile kernel has no room for the epilogue's extra operand
+    int code = tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, G->g.V, dslash32_default_tile(in.nrhs));
+    if (dslash32_tile_staged(code)) code = dslash32_tile_code(1, 1);
+    launch_dslash32(code, in, out, G->U32, G->C32, a, false, s);
+  }
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }
@@ -873,8 +923,10 @@ size_t dslash_dot_part_doubles(int64_t V, int nrhs) { return (size_t)3 * nrhs * 
 
 mglma_status dslash_dot(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, double* part,
                         double* nrm, double2* dot, cudaStream_t s) {
-  if (in.prec != MGLMA_FP32 || out.prec != MGLMA_FP32 || in.V != G->g.V || out.V != G->g.V || in.nrhs != out.nrhs)
-    return fail(MGLMA_ERR_INVALID, "dslash_dot: FP32 fields of the gauge field's volume needed");
+  const bool bf = in.prec == MGLMA_BF16;
+  if ((in.prec != MGLMA_FP32 && !bf) || out.prec != in.prec || in.V != G->g.V || out.V != G->g.V ||
+      in.nrhs != out.nrhs)
+    return fail(MGLMA_ERR_INVALID, "dslash_dot: FP32 or BF16 fields of the gauge field's volume needed");
   if (in.p == out.p) return fail(MGLMA_ERR_INVALID, "dslash_dot: in and out must differ");
   if (in.nrhs == 0) return MGLMA_OK;
   DslashArgs a;
@@ -885,12 +937,17 @@ mglma_status dslash_dot(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in,
   // the kernel of the tuned tile shape: the staged-tile kernel (per-warp
   // partials of 32-site tiles, RHS tiles of 4, whose epilogue fits 96
   // registers) or one site per thread (partials of 128-site blocks)
-  const bool staged = dslash32_tile_staged(tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, G->g.V, dslash32_default_tile(in.nrhs)));
+  const bool staged =
+      !bf && dslash32_tile_staged(tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, G->g.V, dslash32_default_tile(in.nrhs)));
   const int64_t nblk = staged ? (in.V + kDT - 1) / kDT : (in.V + 127) / 128;
   {
-    ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(in.V, in.nrhs, false), dslash_flops(in.V, in.nrhs));
+    ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(in.V, in.nrhs, false) - (bf ? 96.0 * (double)in.V * in.nrhs : 0.0),
+                 dslash_flops(in.V, in.nrhs));
     if (staged)
       launch_staged<4, true>(in, out, G->U32, G->C32, a, false, s, part);
+    else if (bf)
+      dslash_kernel<float, 1, false, 1, true, false, SpinBf16, SpinBf16>
+          <<<(unsigned)(nblk * in.nrhs), 128, 0, s>>>(in.p, out.p, G->U32, G->C32, a, part);
     else
       dslash_kernel<float, 1, false, 1, true><<<(unsigned)(nblk * in.nrhs), 128, 0, s>>>(in.p, out.p, G->U32,
                                                                                          G->C32, a, part);
@@ -912,9 +969,11 @@ mglma_status dslash_mr_step(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor&
                             Spinor& z, const double2* alpha, double* part, double* nrm, double2* dot,
                             cudaStream_t s) {
   const Spinor* f[4] = {&t, &tn, &sk, &z};
+  const bool bf = t.prec == MGLMA_BF16;
   for (const Spinor* v : f)
-    if (v->prec != MGLMA_FP32 || v->V != G->g.V || v->nrhs != t.nrhs)
-      return fail(MGLMA_ERR_INVALID, "dslash_mr_step: FP32 fields of the gauge field's volume needed");
+    if (v->V != G->g.V || v->nrhs != t.nrhs ||
+        v->prec != (v == &z ? MGLMA_FP32 : (bf ? MGLMA_BF16 : MGLMA_FP32)))
+      return fail(MGLMA_ERR_INVALID, "dslash_mr_step: t, tn, sk FP32 or BF16 and z FP32, of the gauge field's volume");
   for (int i = 0; i < 4; ++i)
     for (int j = i + 1; j < 4; ++j)
       if (f[i]->p == f[j]->p) return fail(MGLMA_ERR_INVALID, "dslash_mr_step: the four fields must differ");
@@ -925,22 +984,61 @@ mglma_status dslash_mr_step(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor&
   a.nrhs = t.nrhs;
   a.g5out = 0;
   MrArgs mr;
-  mr.s = (float4*)sk.p;
+  mr.s = sk.p;
   mr.z = (float4*)z.p;
   mr.alpha = alpha;
   const int64_t nblk = (t.V + 127) / 128;
   {
-    // the stencil's bytes plus s and z read and written once
-    ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(t.V, t.nrhs, false) + 4.0 * 96.0 * (double)t.V * t.nrhs,
+    // the stencil's bytes (t in, tn out) plus s read and written and z read
+    // and written once
+    const double sb = bf ? 48.0 : 96.0;
+    ProfScope ps(ctx, K_DSLASH32, s, 480.0 * (double)t.V + (4.0 * sb + 2.0 * 96.0) * (double)t.V * t.nrhs,
                  dslash_flops(t.V, t.nrhs) + 432.0 * (double)t.V * t.nrhs);
-    dslash_kernel<float, 1, false, 1, true, true><<<(unsigned)(nblk * t.nrhs), 128, 0, s>>>(t.p, tn.p, G->U32, G->C32,
-                                                                                            a, part, mr);
+    if (bf)
+      dslash_kernel<float, 1, false, 1, true, true, SpinBf16, SpinBf16>
+          <<<(unsigned)(nblk * t.nrhs), 128, 0, s>>>(t.p, tn.p, G->U32, G->C32, a, part, mr);
+    else
+      dslash_kernel<float, 1, false, 1, true, true><<<(unsigned)(nblk * t.nrhs), 128, 0, s>>>(t.p, tn.p, G->U32,
+                                                                                              G->C32, a, part, mr);
   }
   MG_LAUNCH_CHECK();
   {
     ProfScope ps(ctx, K_REDUCE, s, (double)dslash_dot_part_doubles(t.V, t.nrhs) * 8.0);
     dot_finish_kernel<<<t.nrhs, 256, 0, s>>>(part, nblk, nrm, dot);
   }
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+// z += alpha s for FP32 z and BF16 s (the last MR step); one thread per site
+// and group of four components
+__global__ void mr_zupdate_kernel(float4* __restrict__ z, const uint4* __restrict__ sb,
+                                  const double2* __restrict__ alpha, int64_t V) {
+  const int r = blockIdx.y;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)3 * V) return;
+  const int j = (int)(e / V);
+  const int64_t site = (int64_t)(e % V);
+  const double2 al = alpha[r];
+  const Cx<float> a = cx((float)al.x, (float)al.y);
+  const uint4 sv = sb[((size_t)r * 3 + j) * V + site];
+  float4* z0 = z + ((size_t)r * 6 + 2 * j) * V + site;
+  float4* z1 = z0 + V;
+  const float4 u0 = *z0, u1 = *z1;
+  const Cx<float> s0 = bf16_unpack(sv.x), s1 = bf16_unpack(sv.y), s2 = bf16_unpack(sv.z), s3 = bf16_unpack(sv.w);
+  const Cx<float> w0 = cx(u0.x, u0.y) + a * s0, w1 = cx(u0.z, u0.w) + a * s1;
+  const Cx<float> w2 = cx(u1.x, u1.y) + a * s2, w3 = cx(u1.z, u1.w) + a * s3;
+  *z0 = make_float4(w0.re, w0.im, w1.re, w1.im);
+  *z1 = make_float4(w2.re, w2.im, w3.re, w3.im);
+}
+
+mglma_status mr_zupdate(mglma_ctx ctx, const double2* alpha, const Spinor& sk, Spinor& z, cudaStream_t s) {
+  if (sk.prec != MGLMA_BF16 || z.prec != MGLMA_FP32 || sk.V != z.V || sk.nrhs != z.nrhs)
+    return fail(MGLMA_ERR_INVALID, "mr_zupdate: BF16 s and FP32 z of one shape needed");
+  if (z.nrhs == 0) return MGLMA_OK;
+  ProfScope ps(ctx, K_BLAS, s, (48.0 + 2.0 * 96.0) * (double)z.V * z.nrhs);
+  const dim3 g((unsigned)((3 * z.V + 255) / 256), (unsigned)z.nrhs, 1);
+  mr_zupdate_kernel<<<g, 256, 0, s>>>((float4*)z.p, (const uint4*)sk.p, alpha, z.V);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }

@@ -250,11 +250,11 @@ cudaStream_t pick_stream(mglma_ctx ctx, void* s);
 // Internal spinor batch (see layout at top).
 struct Spinor {
   void* p = nullptr;
-  int prec = MGLMA_FP32;  // MGLMA_FP64 or MGLMA_FP32
+  int prec = MGLMA_FP32;  // MGLMA_FP64 or MGLMA_FP32; MGLMA_BF16 for the MR smoother's fields
   int nrhs = 0;
   int64_t V = 0;
   size_t rhs_reals() const { return (size_t)24 * V; }
-  size_t bytes() const { return rhs_reals() * nrhs * (prec == MGLMA_FP64 ? 8 : 4); }
+  size_t bytes() const { return rhs_reals() * nrhs * (prec == MGLMA_FP64 ? 8 : prec == MGLMA_BF16 ? 2 : 4); }
 };
 
 // conversions canonical complex128 (device) <-> internal
@@ -268,13 +268,16 @@ mglma_status convert_spinor(mglma_ctx, const Spinor& src, Spinor& dst, cudaStrea
 // fine operator application: out = op(in), op in {D, D^dag, gamma5 D, gamma5 D^dag}
 mglma_status dslash(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, bool dagger,
                     bool gamma5_out, cudaStream_t s);
-// One fused MR smoothing step (FP32, the (1,1) stencil tile): with u = D t,
+// One fused MR smoothing step (the (1,1) stencil tile; t, tn, sk FP32 or all
+// BF16, z FP32): with u = D t,
 // tn = t - alpha u, sk <- sk - alpha t, z <- z + alpha sk (alpha per RHS, the
 // previous step's), and per RHS nrm = |tn|^2, dot = <tn, sk_new>, reduced as
 // in dslash_dot.  The four fields must differ.  dslash_mr_fused says whether
 // the tuned stencil tile for nrhs RHS has this form (else the step runs as
 // dslash_dot plus a vector update).
 bool dslash_mr_fused(mglma_ctx, const mglma_gauge_s* G, int nrhs);
+// z += alpha s (per-RHS alpha) for BF16 s and FP32 z: the last MR step
+mglma_status mr_zupdate(mglma_ctx, const double2* alpha, const Spinor& sk, Spinor& z, cudaStream_t s);
 mglma_status dslash_mr_step(mglma_ctx, const mglma_gauge_s* G, const Spinor& t, Spinor& tn, Spinor& sk, Spinor& z,
                             const double2* alpha, double* part, double* nrm, double2* dot, cudaStream_t s);
 // out = b - D in (FP32; the residual of the preconditioner's coarse correction
@@ -303,7 +306,7 @@ struct Vec {
   int prec = MGLMA_FP32;
   int nrhs = 0;
   size_t n = 0;  // reals per RHS (multiple of 4)
-  size_t bytes() const { return n * (size_t)nrhs * (prec == MGLMA_FP64 ? 8 : 4); }
+  size_t bytes() const { return n * (size_t)nrhs * (prec == MGLMA_FP64 ? 8 : prec == MGLMA_BF16 ? 2 : 4); }
 };
 inline Vec as_vec(const Spinor& s) {
   Vec v;

@@ -8,6 +8,8 @@
 // lower half s e_mu^dag h (u, l: spins {0,1}, {2,3}), so each hop moves one
 // two-spin half spinor through the link.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "cplx.cuh"
 #include "internal.h"
 #include "lattice.cuh"
@@ -50,6 +52,65 @@ struct IO<double> {
     double2* p = reinterpret_cast<double2*>(base) + (size_t)rhs * 12 * V + site;
 #pragma unroll
     for (int j = 0; j < 12; ++j) p[j * V] = make_double2(s[j].re, s[j].im);
+  }
+};
+
+// ------------------------------------------------------------ spinor storage
+// Storage of a spinor field, computed on in FP32 or FP64: float ([rhs][6][V]
+// float4), double ([rhs][12][V] double2) or SpinBf16 ([rhs][3][V] uint4, each
+// holding four complex components as (re, im) BF16 pairs, re in the low half)
+struct SpinBf16 {};
+
+__device__ __forceinline__ Cx<float> bf16_unpack(uint32_t u) {
+  return cx(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+__device__ __forceinline__ uint32_t bf16_pack(Cx<float> a) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a.re, a.im);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+template <typename S>
+struct SIO;
+template <>
+struct SIO<float> {
+  using R = float;
+  __device__ __forceinline__ static void load(const void* b, int64_t V, int rhs, int64_t site, Cx<float> s[12]) {
+    IO<float>::load(b, V, rhs, site, s);
+  }
+  __device__ __forceinline__ static void store(void* b, int64_t V, int rhs, int64_t site, const Cx<float> s[12]) {
+    IO<float>::store(b, V, rhs, site, s);
+  }
+};
+template <>
+struct SIO<double> {
+  using R = double;
+  __device__ __forceinline__ static void load(const void* b, int64_t V, int rhs, int64_t site, Cx<double> s[12]) {
+    IO<double>::load(b, V, rhs, site, s);
+  }
+  __device__ __forceinline__ static void store(void* b, int64_t V, int rhs, int64_t site, const Cx<double> s[12]) {
+    IO<double>::store(b, V, rhs, site, s);
+  }
+};
+template <>
+struct SIO<SpinBf16> {
+  using R = float;
+  __device__ __forceinline__ static void load(const void* b, int64_t V, int rhs, int64_t site, Cx<float> s[12]) {
+    const uint4* p = reinterpret_cast<const uint4*>(b) + (size_t)rhs * 3 * V + site;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const uint4 v = __ldg(p + j * V);
+      s[4 * j] = bf16_unpack(v.x);
+      s[4 * j + 1] = bf16_unpack(v.y);
+      s[4 * j + 2] = bf16_unpack(v.z);
+      s[4 * j + 3] = bf16_unpack(v.w);
+    }
+  }
+  __device__ __forceinline__ static void store(void* b, int64_t V, int rhs, int64_t site, const Cx<float> s[12]) {
+    uint4* p = reinterpret_cast<uint4*>(b) + (size_t)rhs * 3 * V + site;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      p[j * V] = make_uint4(bf16_pack(s[4 * j]), bf16_pack(s[4 * j + 1]), bf16_pack(s[4 * j + 2]),
+                            bf16_pack(s[4 * j + 3]));
   }
 };
 
