@@ -64,7 +64,9 @@ C5 = dict(shapes=[(128, 64, 64, 64), (96, 48, 48, 48), (64, 32, 32, 32)], eps=0.
 # RHS count, from ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
 # capture divided by the captured lattice's volume; traffic grows with the
 # volume).  The capture and its command are summarised under profiles/.
-NCU_TRAFFIC_PER_SITE = {("dslash32", 16): 3431.0}  # 32x16^3, 16 RHS, plain and fused stencil 2 : 7
+# 32x16^3, 16 RHS, one FGCR iteration's mix of the class: fused residual,
+# fused dots, six fused MR steps (BF16 smoother fields), one plain stencil
+NCU_TRAFFIC_PER_SITE = {("dslash32", 16): 5244.9}
 
 
 def peaks():
