@@ -27,6 +27,7 @@
 //          scale per (y, j): value = half * scale
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "cplx.cuh"
 #include "internal.h"
@@ -569,45 +570,63 @@ __global__ void basis_export_kernel(const double2* __restrict__ p64, double2* __
 
 // ------------------------------------------------------------ R0 / T0 at many RHS (FP32 fields)
 // One CTA per (block, tile of 16 RHS), so the block's basis is read once for
-// all of them.  R0: the basis and the spinors of a chunk of the block's sites
-// are staged in shared memory (FP32, rows padded so that the staging stores
-// of consecutive sites fall in different banks); each thread owns a 4 dof x
-// 4 RHS tile of the outputs over a share of the chunk's sites (split K), and
-// the shares are summed in a fixed order at the end.  T0: each thread owns
-// one site, one chirality and four RHS (6 x 4 complex accumulators) and runs
-// over the Nv dofs of that chirality.  The FP16 basis's per-(block, dof)
-// scale multiplies the R0 result and the T0 coefficients instead of every
-// basis element.  Needs Nv % 4 == 0.
-constexpr int T16_KC = 16;     // sites per staged chunk (R0)
+// all of them.  Both kernels walk the block's sites in chunks staged in
+// shared memory by cp.async into two buffers: the next chunk is in flight
+// while the current one is consumed.  The FP16 basis is staged as it is
+// stored (converted at use) and its per-(block, dof) scale multiplies the R0
+// result and the T0 coefficients instead of every element.  Rows are padded
+// so that the consumers' loads of consecutive sites fall in different banks.
+//   R0: each thread owns a 4 dof x 4 RHS tile of the outputs over a share of
+//       each chunk's sites (split K); the shares are summed in a fixed order.
+//   T0: each thread owns one site of the chunk, one chirality and four RHS
+//       (6 x 4 complex accumulators) and runs over that chirality's Nv dofs.
+// Needs Nv % 4 == 0 and 2 Nv <= 64.
+constexpr int T16_KC = 16;     // sites per chunk (R0)
 constexpr int T16_MAXT = 384;  // R0 threads per CTA (at most)
+constexpr int T16_TKC = 32;    // sites per chunk (T0)
 
-// the six components of phi_{y j}(k) without the FP16 scale
+__device__ __forceinline__ uint32_t t16_smem(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+template <int BYTES>
+__device__ __forceinline__ void t16_cp(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(t16_smem(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void t16_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void t16_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// one complex basis element as staged: FP16 pair (4 B) or FP32 pair (8 B)
 template <typename B>
-__device__ __forceinline__ void basis_raw(const void* base, size_t yj, int nB, int k, Cx<float> o[6]);
+struct T16El;
 template <>
-__device__ __forceinline__ void basis_raw<__half>(const void* base, size_t yj, int nB, int k, Cx<float> o[6]) {
-  const uint2* p = reinterpret_cast<const uint2*>(base) + yj * 3 * nB + k;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    uint2 v = __ldg(p + q * nB);
-    const float2 fa = __half22float2(*reinterpret_cast<__half2*>(&v.x));
-    const float2 fb = __half22float2(*reinterpret_cast<__half2*>(&v.y));
-    o[2 * q] = cx(fa.x, fa.y);
-    o[2 * q + 1] = cx(fb.x, fb.y);
+struct T16El<__half> {
+  static constexpr int bytes = 4;
+  __device__ __forceinline__ static Cx<float> get(const void* p) {
+    uint32_t u = *reinterpret_cast<const uint32_t*>(p);
+    const float2 f = __half22float2(*reinterpret_cast<__half2*>(&u));
+    return cx(f.x, f.y);
   }
-}
+};
 template <>
-__device__ __forceinline__ void basis_raw<float>(const void* base, size_t yj, int nB, int k, Cx<float> o[6]) {
-  BIO<float>::template load<float>(base, nullptr, yj, nB, k, o);
-}
+struct T16El<float> {
+  static constexpr int bytes = 8;
+  __device__ __forceinline__ static Cx<float> get(const void* p) {
+    const float2 f = *reinterpret_cast<const float2*>(p);
+    return cx(f.x, f.y);
+  }
+};
 template <typename B>
 __device__ __forceinline__ float basis_scale(const float* scale, size_t yj) {
   return sizeof(B) == 2 ? __ldg(scale + yj) : 1.f;
 }
 
-// staged rows, in float4: phi [kk][q][h][jg] + 1 pad, psi [kk][c][h][rg] + 1 pad
-__host__ __device__ constexpr int t16_phi_row(int n2) { return 3 * n2 + 1; }
-constexpr int T16_PSI_ROW = 12 * 2 * 4 + 1;
+// bytes of one staged R0 chunk row (site kk): phi [q][jg][a] elements, then
+// psi [c][h][rg] float4, each padded by 16 B
+template <typename B>
+__host__ __device__ constexpr int r16_phi_row(int n2) { return 6 * n2 * T16El<B>::bytes + 16; }
+constexpr int R16_PSI_ROW = 12 * 2 * 4 * 16 + 16;
+template <typename B>
+__host__ __device__ constexpr size_t r16_buf(int n2) { return (size_t)T16_KC * (r16_phi_row<B>(n2) + R16_PSI_ROW); }
 
 template <typename B>
 __global__ void __launch_bounds__(T16_MAXT) restrict16_kernel(const float4* __restrict__ fine, int nrhs,
@@ -615,13 +634,12 @@ __global__ void __launch_bounds__(T16_MAXT) restrict16_kernel(const float4* __re
                                                               const float* __restrict__ scale, BlockGeo g, int nv,
                                                               float2* __restrict__ out) {
   extern __shared__ float4 sm16[];
-  const int n2 = 2 * nv, ng = n2 / 4;  // dof groups of four
-  const int prow = t16_phi_row(n2);
-  // phi row kk: float4 ((q * 2 + h) * ng + jg) = (phi_{4jg+2h}, phi_{4jg+2h+1}) at site kk
-  // psi row kk: float4 ((c * 2 + h) * 4 + rg) = (psi_{4rg+2h}, psi_{4rg+2h+1}) at site kk
-  float4* sphi = sm16;
-  float4* spsi = sm16 + T16_KC * prow;
-  __shared__ int64_t site_of[T16_KC];
+  constexpr int EB = T16El<B>::bytes;
+  const int n2 = 2 * nv, ng = n2 / 4;
+  const int prow = r16_phi_row<B>(n2);
+  const size_t buf = r16_buf<B>(n2);
+  uint8_t* base = reinterpret_cast<uint8_t*>(sm16);
+  int64_t* site_of = reinterpret_cast<int64_t*>(base + 2 * buf);  // [nB]
   const int ntile = (nrhs + 15) / 16;
   const int64_t y = blockIdx.x / ntile;
   const int r0 = (int)(blockIdx.x % ntile) * 16;
@@ -631,48 +649,66 @@ __global__ void __launch_bounds__(T16_MAXT) restrict16_kernel(const float4* __re
   const int tt = tid % ntt, ks = tid / ntt;
   const int jg = tt % ng, rg = tt / ng;
   const int al = (4 * jg) / nv;
+  for (int k = tid; k < g.nB; k += blockDim.x) site_of[k] = block_site(g, y, k);
+  __syncthreads();
+  const size_t esz = sizeof(B) == 2 ? 8 : 16;  // stored bytes of two complex components
+  // stage chunk k0 into buffer b (cp.async; RHS beyond nrhs read as zero)
+  auto stage = [&](int k0, int b) {
+    const int ck = min(T16_KC, g.nB - k0);
+    uint8_t* bb = base + (size_t)b * buf;
+    for (int idx = tid; idx < n2 * 3 * ck; idx += blockDim.x) {
+      const int kk = idx % ck, c = (idx / ck) % 3, j = idx / (ck * 3);
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(basis) + (((size_t)y * n2 + j) * 3 + c) * g.nB * esz +
+                           (size_t)(k0 + kk) * esz;
+      uint8_t* row = bb + (size_t)kk * (prow + R16_PSI_ROW);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        t16_cp<EB>(row + (((2 * c + h) * ng + j / 4) * 4 + j % 4) * EB, src + h * EB);
+    }
+    for (int idx = tid; idx < 16 * 6 * ck; idx += blockDim.x) {
+      const int kk = idx % ck, c = (idx / ck) % 6, r = idx / (ck * 6);
+      uint8_t* row = bb + (size_t)kk * (prow + R16_PSI_ROW) + prow;
+      float2* d0 = reinterpret_cast<float2*>(row + (((2 * c) * 2 + (r % 4) / 2) * 4 + r / 4) * 16 + (r % 2) * 8);
+      float2* d1 = reinterpret_cast<float2*>(row + (((2 * c + 1) * 2 + (r % 4) / 2) * 4 + r / 4) * 16 + (r % 2) * 8);
+      if (r0 + r < nrhs) {
+        const float4* src = fine + ((size_t)(r0 + r) * 6 + c) * g.V + site_of[k0 + kk];
+        t16_cp<8>(d0, src);
+        t16_cp<8>(d1, reinterpret_cast<const uint8_t*>(src) + 8);
+      } else {
+        *d0 = make_float2(0.f, 0.f);
+        *d1 = make_float2(0.f, 0.f);
+      }
+    }
+    t16_commit();
+  };
   Cx<float> acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = cx(0.f, 0.f);
-  for (int k0 = 0; k0 < g.nB; k0 += T16_KC) {
+  stage(0, 0);
+  int b = 0;
+  for (int k0 = 0; k0 < g.nB; k0 += T16_KC, b ^= 1) {
     const int ck = min(T16_KC, g.nB - k0);
-    __syncthreads();  // the previous chunk is consumed
-    if (tid < ck) site_of[tid] = block_site(g, y, k0 + tid);
-    for (int idx = tid; idx < n2 * ck; idx += blockDim.x) {
-      const int kk = idx % ck, j = idx / ck;
-      Cx<float> ph[6];
-      basis_raw<B>(basis, (size_t)y * n2 + j, g.nB, k0 + kk, ph);
-      float2* dst = reinterpret_cast<float2*>(sphi + (size_t)kk * prow);
-#pragma unroll
-      for (int q = 0; q < 6; ++q)
-        dst[((q * 2 + (j % 4) / 2) * ng + j / 4) * 2 + (j % 2)] = make_float2(ph[q].re, ph[q].im);
-    }
-    __syncthreads();  // site_of is ready
-    for (int idx = tid; idx < 16 * 6 * ck; idx += blockDim.x) {
-      const int kk = idx % ck, c = (idx / ck) % 6, r = idx / (ck * 6);
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r0 + r < nrhs) v = __ldg(fine + ((size_t)(r0 + r) * 6 + c) * g.V + site_of[kk]);
-      float2* dst = reinterpret_cast<float2*>(spsi + (size_t)kk * T16_PSI_ROW);
-      dst[(((2 * c) * 2 + (r % 4) / 2) * 4 + r / 4) * 2 + (r % 2)] = make_float2(v.x, v.y);
-      dst[(((2 * c + 1) * 2 + (r % 4) / 2) * 4 + r / 4) * 2 + (r % 2)] = make_float2(v.z, v.w);
-    }
-    __syncthreads();
+    t16_wait();
+    __syncthreads();  // chunk k0 landed in buffer b; buffer b ^ 1 is free
+    if (k0 + T16_KC < g.nB) stage(k0 + T16_KC, b ^ 1);
+    const uint8_t* bb = base + (size_t)b * buf;
     if (ks < KS) {
       for (int kk = ks; kk < ck; kk += KS) {
-        const float4* prw = sphi + (size_t)kk * prow;
-        const float4* srw = spsi + (size_t)kk * T16_PSI_ROW;
+        const uint8_t* prw = bb + (size_t)kk * (prow + R16_PSI_ROW);
+        const float4* srw = reinterpret_cast<const float4*>(prw + prow);
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-          const float4 pa = prw[(q * 2 + 0) * ng + jg], pb = prw[(q * 2 + 1) * ng + jg];
+          const uint8_t* pe = prw + ((q * ng + jg) * 4) * EB;
+          const Cx<float> ph[4] = {T16El<B>::get(pe), T16El<B>::get(pe + EB), T16El<B>::get(pe + 2 * EB),
+                                   T16El<B>::get(pe + 3 * EB)};
           const float4 sa = srw[((6 * al + q) * 2 + 0) * 4 + rg], sb = srw[((6 * al + q) * 2 + 1) * 4 + rg];
-          const Cx<float> ph[4] = {cx(pa.x, pa.y), cx(pa.z, pa.w), cx(pb.x, pb.y), cx(pb.z, pb.w)};
           const Cx<float> ps[4] = {cx(sa.x, sa.y), cx(sa.z, sa.w), cx(sb.x, sb.y), cx(sb.z, sb.w)};
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) cfma_conj(acc[a][b], ph[a], ps[b]);
+            for (int c2 = 0; c2 < 4; ++c2) cfma_conj(acc[a][c2], ph[a], ps[c2]);
         }
       }
     }
@@ -684,7 +720,8 @@ __global__ void __launch_bounds__(T16_MAXT) restrict16_kernel(const float4* __re
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) red[((size_t)ks * ntt + tt) * 16 + a * 4 + b] = make_float2(acc[a][b].re, acc[a][b].im);
+      for (int c2 = 0; c2 < 4; ++c2)
+        red[((size_t)ks * ntt + tt) * 16 + a * 4 + c2] = make_float2(acc[a][c2].re, acc[a][c2].im);
   __syncthreads();
   for (int o = tid; o < n2 * 16; o += blockDim.x) {
     const int j = o % n2, r = o / n2;
@@ -701,17 +738,42 @@ __global__ void __launch_bounds__(T16_MAXT) restrict16_kernel(const float4* __re
   }
 }
 
+// bytes of one staged T0 chunk row (site kk): the basis [j][q] elements, padded
+// by two elements (consecutive sites' rows two banks apart for FP16, four for
+// FP32; rows stay aligned for the 8- or 16-byte copies)
+template <typename B>
+__host__ __device__ constexpr int p16_row(int n2) { return 6 * n2 * T16El<B>::bytes + 2 * T16El<B>::bytes; }
+
 template <typename B>
 __global__ void __launch_bounds__(256) prolong16_kernel(const float2* __restrict__ coarse, int nrhs,
                                                         const void* __restrict__ basis,
                                                         const float* __restrict__ scale, BlockGeo g, int nv,
                                                         float4* __restrict__ fine, int accumulate) {
+  extern __shared__ float4 sm16[];
+  constexpr int EB = T16El<B>::bytes;
   __shared__ float4 cs[64 * 2 * 4];  // [j][h][rg] = scale_j (c_{4rg+2h}, c_{4rg+2h+1}), n2 <= 64
   const int n2 = 2 * nv;
+  const int prow = p16_row<B>(n2);
+  const size_t buf = (size_t)T16_TKC * prow;
+  uint8_t* base = reinterpret_cast<uint8_t*>(sm16);
   const int ntile = (nrhs + 15) / 16;
   const int64_t y = blockIdx.x / ntile;
   const int r0 = (int)(blockIdx.x % ntile) * 16;
-  for (int idx = threadIdx.x; idx < n2 * 16; idx += blockDim.x) {
+  const int tid = threadIdx.x;
+  const size_t esz = sizeof(B) == 2 ? 8 : 16;
+  auto stage = [&](int k0, int b) {
+    const int ck = min(T16_TKC, g.nB - k0);
+    uint8_t* bb = base + (size_t)b * buf;
+    for (int idx = tid; idx < n2 * 3 * ck; idx += blockDim.x) {
+      const int kk = idx % ck, c = (idx / ck) % 3, j = idx / (ck * 3);
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(basis) + (((size_t)y * n2 + j) * 3 + c) * g.nB * esz +
+                           (size_t)(k0 + kk) * esz;
+      t16_cp<2 * EB>(bb + (size_t)kk * prow + (j * 6 + 2 * c) * EB, src);
+    }
+    t16_commit();
+  };
+  stage(0, 0);
+  for (int idx = tid; idx < n2 * 16; idx += blockDim.x) {
     const int j = idx % n2, r = idx / n2;
     const float sc = basis_scale<B>(scale, (size_t)y * n2 + j);
     float2 v = r0 + r < nrhs ? coarse[((size_t)(r0 + r) * g.V1 + y) * n2 + j] : make_float2(0.f, 0.f);
@@ -719,36 +781,43 @@ __global__ void __launch_bounds__(256) prolong16_kernel(const float2* __restrict
     v.y *= sc;
     reinterpret_cast<float2*>(cs)[((j * 2 + (r % 4) / 2) * 4 + r / 4) * 2 + (r % 2)] = v;
   }
-  __syncthreads();
-  // work items (site k fastest, then chirality, then RHS group of four)
-  for (int w = threadIdx.x; w < g.nB * 8; w += blockDim.x) {
-    const int k = w % g.nB, al = (w / g.nB) % 2, rg = w / (2 * g.nB);
-    if (r0 + 4 * rg >= nrhs) continue;
+  // work item of a chunk: (site kk fastest, chirality, RHS group of four)
+  const int kk = tid % T16_TKC, al = (tid / T16_TKC) % 2, rg = tid / (2 * T16_TKC);
+  int b = 0;
+  for (int k0 = 0; k0 < g.nB; k0 += T16_TKC, b ^= 1) {
+    const int ck = min(T16_TKC, g.nB - k0);
+    t16_wait();
+    __syncthreads();  // chunk k0 landed in buffer b (and cs is ready); buffer b ^ 1 is free
+    if (k0 + T16_TKC < g.nB) stage(k0 + T16_TKC, b ^ 1);
+    if (kk >= ck || r0 + 4 * rg >= nrhs) continue;
+    const uint8_t* row = base + (size_t)b * buf + (size_t)kk * prow;
     Cx<float> acc[6][4];
 #pragma unroll
     for (int q = 0; q < 6; ++q)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[q][b] = cx(0.f, 0.f);
+      for (int c2 = 0; c2 < 4; ++c2) acc[q][c2] = cx(0.f, 0.f);
     for (int jj = 0; jj < nv; ++jj) {
       const int j = al * nv + jj;
+      const uint8_t* pe = row + (size_t)j * 6 * EB;
       Cx<float> ph[6];
-      basis_raw<B>(basis, (size_t)y * n2 + j, g.nB, k, ph);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) ph[q] = T16El<B>::get(pe + q * EB);
       const float4 ca = cs[(j * 2 + 0) * 4 + rg], cb = cs[(j * 2 + 1) * 4 + rg];
       const Cx<float> cv[4] = {cx(ca.x, ca.y), cx(ca.z, ca.w), cx(cb.x, cb.y), cx(cb.z, cb.w)};
 #pragma unroll
       for (int q = 0; q < 6; ++q)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) cfma(acc[q][b], cv[b], ph[q]);
+        for (int c2 = 0; c2 < 4; ++c2) cfma(acc[q][c2], cv[c2], ph[q]);
     }
-    const int64_t site = block_site(g, y, k);
+    const int64_t site = block_site(g, y, k0 + kk);
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int r = r0 + 4 * rg + b;
+    for (int c2 = 0; c2 < 4; ++c2) {
+      const int r = r0 + 4 * rg + c2;
       if (r >= nrhs) break;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         float4* p = fine + ((size_t)r * 6 + 3 * al + c) * g.V + site;
-        float4 v = make_float4(acc[2 * c][b].re, acc[2 * c][b].im, acc[2 * c + 1][b].re, acc[2 * c + 1][b].im);
+        float4 v = make_float4(acc[2 * c][c2].re, acc[2 * c][c2].im, acc[2 * c + 1][c2].re, acc[2 * c + 1][c2].im);
         if (accumulate) {
           const float4 o = *p;
           v.x += o.x;
@@ -760,6 +829,7 @@ __global__ void __launch_bounds__(256) prolong16_kernel(const float2* __restrict
       }
     }
   }
+  t16_wait();
 }
 
 // ============================================================ host side
@@ -879,6 +949,45 @@ mglma_status coarse_gamma_level1(mglma_ctx ctx, const mglma_subspace_s* S, int k
   return MGLMA_OK;
 }
 
+template <typename B>
+static mglma_status launch_r16(const void* basis, const float* scale, const BlockGeo& g, int nv, const Spinor& in,
+                               int threads, unsigned grid, void* out, cudaStream_t s) {
+  const int n2 = 2 * nv;
+  const size_t smem = std::max(2 * r16_buf<B>(n2) + (size_t)g.nB * sizeof(int64_t),
+                               (size_t)threads * 16 * sizeof(float2));
+  static std::mutex mu;
+  static size_t granted = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem > granted) {
+      MG_CUDA(cudaFuncSetAttribute(restrict16_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      granted = smem;
+    }
+  }
+  restrict16_kernel<B><<<grid, threads, smem, s>>>((const float4*)in.p, in.nrhs, basis, scale, g, nv, (float2*)out);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+template <typename B>
+static mglma_status launch_p16(const void* basis, const float* scale, const BlockGeo& g, int nv, const void* coarse,
+                               Spinor& out, bool accumulate, unsigned grid, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)T16_TKC * p16_row<B>(2 * nv);
+  static std::mutex mu;
+  static size_t granted = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem > granted) {
+      MG_CUDA(cudaFuncSetAttribute(prolong16_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      granted = smem;
+    }
+  }
+  prolong16_kernel<B><<<grid, 256, smem, s>>>((const float2*)coarse, out.nrhs, basis, scale, g, nv, (float4*)out.p,
+                                              accumulate ? 1 : 0);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
 // the many-RHS R0 / T0 kernels: FP32 fields, at least 8 RHS, Nv % 4 == 0 and
 // 2 Nv <= 64, FP32 or FP16 basis
 static bool use_t16(const mglma_subspace_s* S, int nrhs) {
@@ -898,27 +1007,10 @@ mglma_status restrict_fine(mglma_ctx ctx, const mglma_subspace_s* S, const Spino
     const BlockGeo g = S->geo;
     const int n2 = 2 * S->nv, ntt = n2;
     const int threads = (T16_MAXT / ntt) * ntt;
-    const size_t stage = (size_t)T16_KC * (t16_phi_row(n2) + T16_PSI_ROW) * sizeof(float4);
-    const size_t smem = std::max(stage, (size_t)threads * 16 * sizeof(float2));
     const unsigned grid = (unsigned)(g.V1 * ((in.nrhs + 15) / 16));
-    static size_t attr16 = 0, attr32 = 0;
-    if (S->phi16) {
-      if (smem > attr16) {
-        MG_CUDA(cudaFuncSetAttribute(restrict16_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr16 = smem;
-      }
-      restrict16_kernel<__half><<<grid, threads, smem, s>>>((const float4*)in.p, in.nrhs, S->phi16, S->scale16, g,
-                                                            S->nv, (float2*)out_coarse);
-    } else {
-      if (smem > attr32) {
-        MG_CUDA(cudaFuncSetAttribute(restrict16_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr32 = smem;
-      }
-      restrict16_kernel<float><<<grid, threads, smem, s>>>((const float4*)in.p, in.nrhs, S->phi32, nullptr, g, S->nv,
-                                                           (float2*)out_coarse);
-    }
-    MG_LAUNCH_CHECK();
-    return MGLMA_OK;
+    if (S->phi16)
+      return launch_r16<__half>(S->phi16, S->scale16, g, S->nv, in, threads, grid, out_coarse, s);
+    return launch_r16<float>(S->phi32, nullptr, g, S->nv, in, threads, grid, out_coarse, s);
   }
   if (S->phi16) return launch_restrict<float, __half, 4>(S, in.p, in.nrhs, S->phi16, out_coarse, s);
   return launch_restrict<float, float, 4>(S, in.p, in.nrhs, S->phi32, out_coarse, s);
@@ -937,13 +1029,8 @@ mglma_status prolong_coarse(mglma_ctx ctx, const mglma_subspace_s* S, const void
     const BlockGeo g = S->geo;
     const unsigned grid = (unsigned)(g.V1 * ((out.nrhs + 15) / 16));
     if (S->phi16)
-      prolong16_kernel<__half><<<grid, 256, 0, s>>>((const float2*)in_coarse, out.nrhs, S->phi16, S->scale16, g, S->nv,
-                                                    (float4*)out.p, accumulate ? 1 : 0);
-    else
-      prolong16_kernel<float><<<grid, 256, 0, s>>>((const float2*)in_coarse, out.nrhs, S->phi32, nullptr, g, S->nv,
-                                                   (float4*)out.p, accumulate ? 1 : 0);
-    MG_LAUNCH_CHECK();
-    return MGLMA_OK;
+      return launch_p16<__half>(S->phi16, S->scale16, g, S->nv, in_coarse, out, accumulate, grid, s);
+    return launch_p16<float>(S->phi32, nullptr, g, S->nv, in_coarse, out, accumulate, grid, s);
   }
   if (S->phi16) return launch_prolong<float, __half, 4>(S, in_coarse, out.nrhs, S->phi16, out.p, accumulate, s);
   return launch_prolong<float, float, 4>(S, in_coarse, out.nrhs, S->phi32, out.p, accumulate, s);
