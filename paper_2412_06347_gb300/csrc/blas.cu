@@ -316,6 +316,47 @@ __global__ void __launch_bounds__(RT) axpy2_norm_kernel(const typename Pair<R>::
   finish<0>(part, count, 1, nb, nrhs, nullptr, out1);
 }
 
+// y_r -= sum_{j<k} c[j][r] x_j,r (and yb from x0b with the same
+// coefficients), as multi_axpy, with out1 = |y_new|^2 and out2 = <y_new, w>
+// = sum conj(y_new) w per RHS reduced in the same pass (GCR: the
+// orthogonalised image, its norm and its overlap with the residual)
+template <typename R>
+__global__ void __launch_bounds__(RT) multi_axpy_nd_kernel(const typename Pair<R>::T* __restrict__ x0,
+                                                           typename Pair<R>::T* __restrict__ y,
+                                                           const typename Pair<R>::T* __restrict__ x0b,
+                                                           typename Pair<R>::T* __restrict__ yb, size_t jstride, int k,
+                                                           const double2* __restrict__ c,
+                                                           const typename Pair<R>::T* __restrict__ w, size_t m,
+                                                           double2* __restrict__ part, unsigned* __restrict__ count,
+                                                           double2* out2, double* out1) {
+  __shared__ double2 cs[64];
+  const int r = blockIdx.y, nrhs = gridDim.y, nb = gridDim.x;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    const double2 v = c[(size_t)j * nrhs + r];
+    cs[j] = make_double2(-v.x, -v.y);
+  }
+  __syncthreads();
+  const size_t off = (size_t)r * m;
+  const double2 one = make_double2(1, 0);
+  RAcc<R> acc;
+  for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < m; i += (size_t)nb * RT) {
+    auto v = y[off + i];
+    for (int j = 0; j < k; ++j) v = lc(x0[j * jstride + off + i], v, cs[j], one);
+    y[off + i] = v;
+    if (yb) {
+      auto vb = yb[off + i];
+      for (int j = 0; j < k; ++j) vb = lc(x0b[j * jstride + off + i], vb, cs[j], one);
+      yb[off + i] = vb;
+    }
+    acc.add_nd(v, w[off + i]);
+  }
+  double2 v = block_sum2<RT>(make_double2(acc.norm(), 0));
+  if (threadIdx.x == 0) part[(size_t)r * nb + blockIdx.x] = v;
+  v = block_sum2<RT>(acc.dot());
+  if (threadIdx.x == 0) part[((size_t)nrhs + r) * nb + blockIdx.x] = v;
+  finish<2>(part, count, 1, nb, nrhs, out2, out1);
+}
+
 // ------------------------------------------------------------- MINRES (real scalars)
 __device__ __forceinline__ float4 rlc3(float4 x, float4 y, float4 z, double a, double b, double c) {
   const float fa = (float)a, fb = (float)b, fc = (float)c;
@@ -582,6 +623,25 @@ mglma_status norm2(mglma_ctx ctx, const Vec& x, double* out, cudaStream_t s) {
 mglma_status norm2_cdot(mglma_ctx ctx, const Vec& x, const Vec& y, double* nrm, double2* dot, cudaStream_t s) {
   if (x.prec != y.prec || x.n != y.n || x.nrhs != y.nrhs) return fail(MGLMA_ERR_INVALID, "norm2_cdot: mismatch");
   return reduce_impl<2>(ctx, x, 0, 1, &y, dot, nrm, s);
+}
+
+mglma_status multi_axpy_nd(mglma_ctx ctx, const Vec& x0, size_t jstride_reals, int k, Vec& y, const double2* c,
+                           const Vec* x0b, Vec* yb, const Vec& w, double* nrm, double2* dot, cudaStream_t s) {
+  if (k < 1 || k > 64) return fail(MGLMA_ERR_INVALID, "multi_axpy_nd: 1 to 64 directions");
+  if (y.prec != MGLMA_FP32 || w.prec != y.prec || w.n != y.n || w.nrhs != y.nrhs)
+    return fail(MGLMA_ERR_INVALID, "multi_axpy_nd: FP32 fields of one shape needed");
+  ProfScope ps(ctx, K_BLAS, s, (k + 3.0) * y.bytes() + (yb ? (k + 2.0) * y.bytes() : 0.0));
+  const size_t m = pairs(y);
+  const int nb = reduce_blocks(m);
+  double2* part = nullptr;
+  unsigned* count = nullptr;
+  MG_CHECK(red_scratch(ctx, s, (size_t)nb * y.nrhs * 2, y.nrhs, &part, &count));
+  dim3 g(nb, y.nrhs, 1);
+  multi_axpy_nd_kernel<float><<<g, RT, 0, s>>>((const float4*)x0.p, (float4*)y.p,
+                                               x0b ? (const float4*)x0b->p : nullptr, yb ? (float4*)yb->p : nullptr,
+                                               jstride_reals / 4, k, c, (const float4*)w.p, m, part, count, dot, nrm);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
 }
 
 mglma_status axpy2_norm(mglma_ctx ctx, const double2* a, const Vec& p, Vec& x, const Vec& w, Vec& r, double* rr,

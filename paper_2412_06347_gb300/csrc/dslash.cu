@@ -58,12 +58,26 @@ struct MrArgs {
   const double2* alpha = nullptr;
 };
 
+// GD makes the plain FP32 stencil (one RHS per thread, one RHS tile per CTA)
+// the GCR direction image W_k = D Z_k with its dots in the epilogue: for
+// k = 0, |W|^2 and <W, r>; for k = 1..3, <W_j, W> for j < k (W_j at W0 + j
+// wslot float4) -- per RHS and 128-site block into part[(rhs nblk + blk) 6 +
+// v], summed by gd_finish_kernel
+struct GdArgs {
+  const float4* W0 = nullptr;
+  size_t wslot = 0;
+  int k = 0;
+  const float4* r = nullptr;
+  double* part = nullptr;
+};
+
 template <typename R, int NR, bool DAG, int RW, bool RED = false, bool MRF = false, typename SI = R,
-          typename SO = R>
+          typename SO = R, bool GD = false>
 __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kernel(const void* __restrict__ in, void* __restrict__ out,
                                                      const void* __restrict__ U, const void* __restrict__ C,
                                                      DslashArgs a, double* __restrict__ part = nullptr,
-                                                     MrArgs mr = MrArgs()) {
+                                                     MrArgs mr = MrArgs(), GdArgs gd = GdArgs()) {
+  static_assert(!GD || (!RED && NR == 1 && RW == 1 && sizeof(R) == 4), "GCR dots: plain FP32 tile 1,1 only");
   static_assert(!RED || (NR == 1 && RW == 1 && sizeof(R) == 4), "fused reduction: FP32 tile 1,1 only");
   static_assert(!MRF || RED, "the fused MR step reduces its dots");
   constexpr int SW = 128 / RW;  // sites per CTA
@@ -77,7 +91,7 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
   if constexpr (RW == 1) {
     site = (int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x;
     if (site >= V) {
-      if constexpr (!RED) return;
+      if constexpr (!RED && !GD) return;
       valid = false;
       site = V - 1;
     }
@@ -261,6 +275,50 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
       const int c = threadIdx.x;
       part[((size_t)r0 * nblk + blockIdx.x / ntile) * 3 + c] =
           (((double)wsum[0][c] + (double)wsum[1][c]) + (double)wsum[2][c]) + (double)wsum[3][c];
+    }
+  }
+  if constexpr (GD) {
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+      const size_t off = (size_t)r0 * 6 * V + site;
+      if (gd.k == 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const float4 q = __ldg(gd.r + off + c * V);
+          const Cx<float> w0 = acc[0][2 * c], w1 = acc[0][2 * c + 1];
+          v[0] += w0.re * w0.re + w0.im * w0.im + w1.re * w1.re + w1.im * w1.im;
+          v[1] += w0.re * q.x + w0.im * q.y + w1.re * q.z + w1.im * q.w;
+          v[2] += w0.re * q.y - w0.im * q.x + w1.re * q.w - w1.im * q.z;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (j >= gd.k) break;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            const float4 q = __ldg(gd.W0 + j * gd.wslot + off + c * V);
+            const Cx<float> w0 = acc[0][2 * c], w1 = acc[0][2 * c + 1];
+            v[2 * j] += q.x * w0.re + q.y * w0.im + q.z * w1.re + q.w * w1.im;
+            v[2 * j + 1] += q.x * w0.im - q.y * w0.re + q.z * w1.im - q.w * w1.re;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int e = 0; e < 6; ++e) v[e] += __shfl_down_sync(0xffffffffu, v[e], o);
+    __shared__ float gsum[4][6];
+    const int w = threadIdx.x / 32;
+    if (threadIdx.x % 32 == 0)
+#pragma unroll
+      for (int e = 0; e < 6; ++e) gsum[w][e] = v[e];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      const int64_t nblk = (V + 127) / 128;
+      const int e = threadIdx.x;
+      gd.part[((size_t)r0 * nblk + blockIdx.x / ntile) * 6 + e] =
+          (((double)gsum[0][e] + (double)gsum[1][e]) + (double)gsum[2][e]) + (double)gsum[3][e];
     }
   }
 }
@@ -469,6 +527,38 @@ __global__ void __launch_bounds__(256) dot_finish_kernel(const double* __restric
   if (threadIdx.x == 0) {
     nrm[r] = sh[0][0];
     dot[r] = make_double2(sh[1][0], sh[2][0]);
+  }
+}
+
+// the GD partials of RHS r (one CTA each) in a fixed order: k = 0 -> nw[r] =
+// |W|^2, num[r] = <W, r>; k > 0 -> dots[j n + r] = <W_j, W> for j < k
+__global__ void __launch_bounds__(256) gd_finish_kernel(const double* __restrict__ part, int64_t nblk, int k, int n,
+                                                        double* __restrict__ nw, double2* __restrict__ num,
+                                                        double2* __restrict__ dots) {
+  const int r = blockIdx.x;
+  double a[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t i = threadIdx.x; i < nblk; i += 256) {
+    const double* p = part + ((size_t)r * nblk + i) * 6;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) a[e] += p[e];
+  }
+  __shared__ double sh[6][256];
+#pragma unroll
+  for (int e = 0; e < 6; ++e) sh[e][threadIdx.x] = a[e];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+#pragma unroll
+      for (int e = 0; e < 6; ++e) sh[e][threadIdx.x] += sh[e][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (k == 0) {
+      nw[r] = sh[0][0];
+      num[r] = make_double2(sh[1][0], sh[2][0]);
+    } else {
+      for (int j = 0; j < k; ++j) dots[(size_t)j * n + r] = make_double2(sh[2 * j][0], sh[2 * j + 1][0]);
+    }
   }
 }
 
@@ -956,6 +1046,44 @@ mglma_status dslash_dot(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in,
   {
     ProfScope ps(ctx, K_REDUCE, s, (double)dslash_dot_part_doubles(in.V, in.nrhs) * 8.0);
     dot_finish_kernel<<<in.nrhs, 256, 0, s>>>(part, nblk, nrm, dot);
+  }
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+size_t dslash_gcr_part_doubles(int64_t V, int nrhs) { return (size_t)6 * nrhs * (size_t)((V + 127) / 128); }
+
+mglma_status dslash_gcr(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, int k,
+                        const void* W0, size_t wslot_reals, const void* r, double* part, double* nw, double2* num,
+                        double2* dots, cudaStream_t s) {
+  if (in.prec != MGLMA_FP32 || out.prec != MGLMA_FP32 || in.V != G->g.V || out.V != G->g.V || in.nrhs != out.nrhs)
+    return fail(MGLMA_ERR_INVALID, "dslash_gcr: FP32 fields of the gauge field's volume needed");
+  if (k < 0 || k > 3) return fail(MGLMA_ERR_INVALID, "dslash_gcr: 0 to 3 earlier directions");
+  if (in.p == out.p) return fail(MGLMA_ERR_INVALID, "dslash_gcr: in and out must differ");
+  if (in.nrhs == 0) return MGLMA_OK;
+  DslashArgs a;
+  a.q = make_latidx(G->g.L);
+  a.bc = (double)G->g.t_bc;
+  a.nrhs = in.nrhs;
+  a.g5out = 0;
+  GdArgs gd;
+  gd.W0 = (const float4*)W0;
+  gd.wslot = wslot_reals / 4;
+  gd.k = k;
+  gd.r = (const float4*)r;
+  gd.part = part;
+  const int64_t nblk = (in.V + 127) / 128;
+  {
+    // the stencil's bytes plus r (k = 0) or the k earlier images read once
+    ProfScope ps(ctx, K_DSLASH32, s, dslash_bytes(in.V, in.nrhs, false) + 96.0 * (k ? k : 1) * (double)in.V * in.nrhs,
+                 dslash_flops(in.V, in.nrhs) + 48.0 * (k ? k : 1) * (double)in.V * in.nrhs);
+    dslash_kernel<float, 1, false, 1, false, false, float, float, true>
+        <<<(unsigned)(nblk * in.nrhs), 128, 0, s>>>(in.p, out.p, G->U32, G->C32, a, nullptr, MrArgs(), gd);
+  }
+  MG_LAUNCH_CHECK();
+  {
+    ProfScope ps(ctx, K_REDUCE, s, (double)dslash_gcr_part_doubles(in.V, in.nrhs) * 8.0);
+    gd_finish_kernel<<<in.nrhs, 256, 0, s>>>(part, nblk, k, in.nrhs, nw, num, dots);
   }
   MG_LAUNCH_CHECK();
   return MGLMA_OK;

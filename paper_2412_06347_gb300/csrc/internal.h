@@ -276,6 +276,14 @@ mglma_status dslash(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor&
 // the tuned stencil tile for nrhs RHS has this form (else the step runs as
 // dslash_dot plus a vector update).
 bool dslash_mr_fused(mglma_ctx, const mglma_gauge_s* G, int nrhs);
+// FGCR direction image out = D in (FP32, the (1,1) tile) with its dots in the
+// same pass: k = 0 -> nw[r] = |out|^2, num[r] = <out, res>; k = 1..3 ->
+// dots[j n + r] = <W_j, out> for the earlier images W_j = W0 + j wslot reals;
+// part: dslash_gcr_part_doubles(V, nrhs) doubles of scratch
+size_t dslash_gcr_part_doubles(int64_t V, int nrhs);
+mglma_status dslash_gcr(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, Spinor& out, int k, const void* W0,
+                        size_t wslot_reals, const void* res, double* part, double* nw, double2* num, double2* dots,
+                        cudaStream_t s);
 // z += alpha s (per-RHS alpha) for BF16 s and FP32 z: the last MR step
 mglma_status mr_zupdate(mglma_ctx, const double2* alpha, const Spinor& sk, Spinor& z, cudaStream_t s);
 mglma_status dslash_mr_step(mglma_ctx, const mglma_gauge_s* G, const Spinor& t, Spinor& tn, Spinor& sk, Spinor& z,
@@ -324,6 +332,10 @@ mglma_status axpby(mglma_ctx, const double2* a, double2 a_def, const Vec& x, con
 mglma_status caxpy(mglma_ctx, const double2* a, const Vec& x, Vec& y, cudaStream_t s, double sign = 1.0);
 // x += a p ; r -= a w
 mglma_status axpy2(mglma_ctx, const double2* a, const Vec& p, Vec& x, const Vec& w, Vec& r, cudaStream_t s);
+// multi_axpy on FP32 fields with nrm = |y_new|^2 and dot = <y_new, w> per RHS
+// in the same pass
+mglma_status multi_axpy_nd(mglma_ctx, const Vec& x0, size_t jstride_reals, int k, Vec& y, const double2* c,
+                           const Vec* x0b, Vec* yb, const Vec& w, double* nrm, double2* dot, cudaStream_t s);
 // y -= sum_{j<k} c[j*nrhs + r] x_j  where x_j starts jstride reals after x_{j-1}
 // (x0b, yb optional: a second set updated with the same coefficients)
 mglma_status multi_axpy(mglma_ctx, const Vec& x0, size_t jstride_reals, int k, Vec& y, const double2* c,

@@ -67,10 +67,17 @@ struct GcrResult {
 // directions Z and their images W (direction j of RHS r at j*cap + r), the
 // residual, and the per-RHS scalars.  Reused across solves so CUDA graphs
 // that captured its kernels stay valid.
+// The operator with the FGCR dots of direction slot k taken in its own pass
+// (dslash_gcr): out = A in; k = 0 -> nw = |out|^2, num = <out, r>; k > 0 ->
+// dots[j n + r] = <W_j, out>, j < k
+using AdFn = std::function<mglma_status(const Vec& in, Vec& out, int k, const Vec& W0, size_t wslot_reals,
+                                        const Vec& r, double* nw, double2* num, double2* dots)>;
+
 struct GcrWork {
   mglma_ctx ctx = nullptr;
   cudaStream_t s = nullptr;
   int cap = 0, m = 0;
+  const AdFn* Ad = nullptr;  // when set, used for slots k <= 3 instead of A plus separate dots
   Vec proto;  // precision and reals per RHS
   void *Zp = nullptr, *Wp = nullptr, *rp = nullptr;
   Scalars sc;
@@ -138,6 +145,18 @@ static mglma_status gcr_iter(GcrWork& w, const OpFn& A, const OpFn* M, Vec& x, i
   } else {
     MG_CHECK(copy_vec(ctx, r, Zk, s));
   }
+  if (w.Ad && k <= 3) {
+    // the image with its dots in one pass; the orthogonalisation returns the
+    // new image's norm and overlap with r in its own pass
+    MG_CHECK((*w.Ad)(Zk, Wk, k, W0, w.stride(), r, nw + (size_t)k * n, num, dots));
+    if (k > 0) {
+      {
+        ProfScope ps(ctx, K_SCALAR, s);
+        gcr_coef_kernel<<<(k * n + 63) / 64, 64, 0, s>>>(dots, nw, coef, k, n);
+      }
+      MG_CHECK(multi_axpy_nd(ctx, W0, w.stride(), k, Wk, coef, &Z0, &Zk, r, nw + (size_t)k * n, num, s));
+    }
+  } else {
   MG_CHECK(A(Zk, Wk));
   if (k > 0) {
     // dots and coefficients are stored [j][n] (dense in n) for j < k
@@ -149,6 +168,7 @@ static mglma_status gcr_iter(GcrWork& w, const OpFn& A, const OpFn* M, Vec& x, i
     MG_CHECK(multi_axpy(ctx, W0, w.stride(), k, Wk, coef, s, &Z0, &Zk));
   }
   MG_CHECK(norm2_cdot(ctx, Wk, r, nw + (size_t)k * n, num, s));
+  }
   {
     ProfScope ps(ctx, K_SCALAR, s);
     gcr_alpha_kernel<<<nb, tb, 0, s>>>(num, nw + (size_t)k * n, w.sc.active, a, n);
@@ -913,6 +933,15 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
     Vec like = as_vec(r32);
     MG_CHECK(gw.setup(ctx, s, like, n, p.gcr_m));
   }
+  double* gpart = nullptr;
+  MG_CHECK(dalloc(ctx, (void**)&gpart, dslash_gcr_part_doubles(V, n) * sizeof(double), s));
+  fl.add(gpart);
+  const AdFn Ad = [&](const Vec& in, Vec& o, int k, const Vec& W0, size_t wslot, const Vec& res, double* nw,
+                      double2* num, double2* dots) {
+    Spinor a = as_spinor(in, V), bo = as_spinor(o, V);
+    return dslash_gcr(ctx, G, a, bo, k, W0.p, wslot, res.p, gpart, nw, num, dots, s);
+  };
+  gw.Ad = &Ad;
   IterGraphs graphs;
   const bool use_graphs = p.graph && !ctx->profile;
   graphs.set_capturing = [&](bool on) -> mglma_status {
@@ -1065,6 +1094,7 @@ struct Engine {
   Spinor b64, x64, r64, r32, e32;
   double* dsc = nullptr;  // per slot: |r|^2 [cap], |r| [cap], 1/|r| [cap]
   double* stage = nullptr;  // one canonical spinor: host requests pass through it
+  double* gpart = nullptr;  // partials of the FGCR image's dots
   GcrWork gw;
   TwoLevel K;
   std::vector<Slot> slots;
@@ -1108,6 +1138,8 @@ struct Engine {
     MG_CHECK(dalloc(ctx, (void**)&dsc, sizeof(double) * 3 * cap, s));
     fl->add(dsc);
     MG_CHECK(gw.setup(ctx, s, as_vec(r32), cap, p.gcr_m));
+    MG_CHECK(dalloc(ctx, (void**)&gpart, dslash_gcr_part_doubles(V, cap) * sizeof(double), s));
+    fl->add(gpart);
     K.ctx = ctx;
     K.s = s;
     K.G = G;
@@ -1198,8 +1230,17 @@ struct Engine {
       return dslash(ctx, G, a, bo, false, false, s);
     };
     OpFn M = [&](const Vec& in, Vec& o) { return K(in, o); };
+    const AdFn Ad = [&](const Vec& in, Vec& o, int k, const Vec& W0, size_t wslot, const Vec& res, double* nw,
+                        double2* num, double2* dots) {
+      Spinor a = as_spinor(in, V), bo = as_spinor(o, V);
+      return dslash_gcr(ctx, G, a, bo, k, W0.p, wslot, res.p, gpart, nw, num, dots, s);
+    };
+    gw.Ad = &Ad;
     Vec x = vsub(as_vec(e32), 0, hi);
-    for (int k = 0; k < gw.m; ++k) MG_CHECK(gcr_iter(gw, A, &M, x, hi, k, p.inner_tol * p.inner_tol));
+    mglma_status st = MGLMA_OK;
+    for (int k = 0; k < gw.m && st == MGLMA_OK; ++k) st = gcr_iter(gw, A, &M, x, hi, k, p.inner_tol * p.inner_tol);
+    gw.Ad = nullptr;
+    MG_CHECK(st);
     std::vector<int> act;
     MG_CHECK(read_active(gw, hi, act));
     for (int i = 0; i < hi; ++i) {
