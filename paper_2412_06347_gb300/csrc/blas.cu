@@ -316,6 +316,28 @@ __global__ void __launch_bounds__(RT) axpy2_norm_kernel(const typename Pair<R>::
   finish<0>(part, count, 1, nb, nrhs, nullptr, out1);
 }
 
+// r -= a w ; out1 = |r|^2 (GCR residual update when the iterate is formed later)
+template <typename R>
+__global__ void __launch_bounds__(RT) axpy_norm_kernel(const typename Pair<R>::T* w, typename Pair<R>::T* res,
+                                                       const double2* __restrict__ a, size_t m,
+                                                       double2* __restrict__ part, unsigned* __restrict__ count,
+                                                       double* out1) {
+  const int r = blockIdx.y, nrhs = gridDim.y, nb = gridDim.x;
+  const double2 ar = a[r];
+  const double2 na = make_double2(-ar.x, -ar.y);
+  const double2 one = make_double2(1, 0);
+  const size_t off = (size_t)r * m;
+  RAcc<R> acc;
+  for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < m; i += (size_t)nb * RT) {
+    const auto nr = lc(w[off + i], res[off + i], na, one);
+    res[off + i] = nr;
+    acc.add_n(nr);
+  }
+  const double2 v = block_sum2<RT>(make_double2(acc.norm(), 0));
+  if (threadIdx.x == 0) part[(size_t)r * nb + blockIdx.x] = v;
+  finish<0>(part, count, 1, nb, nrhs, nullptr, out1);
+}
+
 // y_r -= sum_{j<k} c[j][r] x_j,r (and yb from x0b with the same
 // coefficients), as multi_axpy, with out1 = |y_new|^2 and out2 = <y_new, w>
 // = sum conj(y_new) w per RHS reduced in the same pass (GCR: the
@@ -640,6 +662,21 @@ mglma_status multi_axpy_nd(mglma_ctx ctx, const Vec& x0, size_t jstride_reals, i
   multi_axpy_nd_kernel<float><<<g, RT, 0, s>>>((const float4*)x0.p, (float4*)y.p,
                                                x0b ? (const float4*)x0b->p : nullptr, yb ? (float4*)yb->p : nullptr,
                                                jstride_reals / 4, k, c, (const float4*)w.p, m, part, count, dot, nrm);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status axpy_norm(mglma_ctx ctx, const double2* a, const Vec& w, Vec& r, double* rr, cudaStream_t s) {
+  if (w.prec != MGLMA_FP32 || r.prec != w.prec || w.n != r.n || w.nrhs != r.nrhs)
+    return fail(MGLMA_ERR_INVALID, "axpy_norm: FP32 fields of one shape needed");
+  ProfScope ps(ctx, K_BLAS, s, 3.0 * r.bytes());
+  const size_t m = pairs(r);
+  const int nb = reduce_blocks(m);
+  double2* part = nullptr;
+  unsigned* count = nullptr;
+  MG_CHECK(red_scratch(ctx, s, (size_t)nb * r.nrhs, r.nrhs, &part, &count));
+  dim3 g(nb, r.nrhs, 1);
+  axpy_norm_kernel<float><<<g, RT, 0, s>>>((const float4*)w.p, (float4*)r.p, a, m, part, count, rr);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }

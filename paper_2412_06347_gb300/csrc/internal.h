@@ -332,6 +332,8 @@ mglma_status axpby(mglma_ctx, const double2* a, double2 a_def, const Vec& x, con
 mglma_status caxpy(mglma_ctx, const double2* a, const Vec& x, Vec& y, cudaStream_t s, double sign = 1.0);
 // x += a p ; r -= a w
 mglma_status axpy2(mglma_ctx, const double2* a, const Vec& p, Vec& x, const Vec& w, Vec& r, cudaStream_t s);
+// r -= a w with rr = |r|^2 per RHS (FP32)
+mglma_status axpy_norm(mglma_ctx, const double2* a, const Vec& w, Vec& r, double* rr, cudaStream_t s);
 // multi_axpy on FP32 fields with nrm = |y_new|^2 and dot = <y_new, w> per RHS
 // in the same pass
 mglma_status multi_axpy_nd(mglma_ctx, const Vec& x0, size_t jstride_reals, int k, Vec& y, const double2* c,

@@ -23,6 +23,7 @@
 #include <memory>
 #include <thread>
 
+#include "cplx.cuh"
 #include "internal.h"
 #include "solver.h"
 #include "subspace.h"
@@ -41,6 +42,32 @@ __global__ void gcr_alpha_kernel(const double2* num, const double* nwk, const in
   if (r >= n) return;
   const double d = nwk[r];
   a[r] = (active[r] && d > 0) ? make_double2(num[r].x / d, num[r].y / d) : make_double2(0, 0);
+}
+
+// Deferred FGCR iterate of slots 0..K: Z'_k = Z_k - sum_{j<k} c_kj Z'_j (c_kj =
+// cz[(k m + j) n' + r] with n' = n) gives Z' = Z T, T unit upper triangular,
+// and x += sum_k alpha_k Z'_k = sum_i beta_i Z_i with beta = T alpha; writes
+// -beta_i into out[i n + r] (multi_axpy subtracts)
+__global__ void gcr_beta_kernel(const double2* __restrict__ cz, const double2* __restrict__ az, int K, int m, int n,
+                                double2* __restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  Cx<double> T[4][4];
+  for (int k = 0; k <= K; ++k) {
+    for (int i = 0; i <= K; ++i) T[i][k] = cx(i == k ? 1.0 : 0.0, 0.0);
+    for (int j = 0; j < k; ++j) {
+      const double2 c = cz[((size_t)k * m + j) * n + r];
+      for (int i = 0; i <= j; ++i) T[i][k] = T[i][k] - cx(c.x, c.y) * T[i][j];
+    }
+  }
+  for (int i = 0; i <= K; ++i) {
+    Cx<double> b = cx(0.0, 0.0);
+    for (int k = i; k <= K; ++k) {
+      const double2 a = az[(size_t)k * n + r];
+      b = b + T[i][k] * cx(a.x, a.y);
+    }
+    out[(size_t)i * n + r] = make_double2(-b.re, -b.im);
+  }
 }
 
 __global__ void gcr_mask_kernel(const double* rr, const double* bb, double tol2, int* active, int n) {
@@ -81,11 +108,19 @@ struct GcrWork {
   Vec proto;  // precision and reals per RHS
   void *Zp = nullptr, *Wp = nullptr, *rp = nullptr;
   Scalars sc;
+  // deferred iterate (with Ad and m <= 4): the directions Z_k stay as the
+  // preconditioner returned them; cz[k][j][n] holds the orthogonalisation
+  // coefficients of slot k, az[k][n] its step, and the end of a restart
+  // cycle adds sum_i beta_i Z_i to x (beta = T alpha, Z' = Z T)
+  double2 *cz = nullptr, *az = nullptr;
+  bool defer() const { return Ad && m <= 4; }
   ~GcrWork() {
     if (ctx) {
       dfree(ctx, Zp, s);
       dfree(ctx, Wp, s);
       dfree(ctx, rp, s);
+      dfree(ctx, cz, s);
+      dfree(ctx, az, s);
     }
   }
   mglma_status setup(mglma_ctx c, cudaStream_t st, const Vec& like, int capacity, int mm) {
@@ -99,6 +134,8 @@ struct GcrWork {
     MG_CHECK(dalloc(ctx, &Wp, proto.bytes() * m, s));
     MG_CHECK(dalloc(ctx, &rp, proto.bytes(), s));
     MG_CHECK(sc.alloc(ctx, cap, m + 2, 2 * m + 2, s));
+    MG_CHECK(dalloc(ctx, (void**)&cz, sizeof(double2) * (size_t)m * m * cap, s));
+    MG_CHECK(dalloc(ctx, (void**)&az, sizeof(double2) * (size_t)m * cap, s));
     return red_scratch_ready(ctx, s);
   }
   size_t stride() const { return (size_t)cap * proto.n; }  // reals between directions
@@ -123,6 +160,18 @@ static mglma_status gcr_init(GcrWork& w, const Vec& b, Vec& x) {
   gcr_mask_kernel<<<(n + 63) / 64, 64, 0, w.s>>>(bb, bb, 0.0, w.sc.active, n);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
+}
+
+// x += sum_{i<=K} beta_i Z_i: the deferred iterate of slots 0..K (see GcrWork)
+static mglma_status gcr_flush(GcrWork& w, Vec& x, int n, int K) {
+  double2* nb = w.sc.z;  // the dots of slot K are used up: -beta [i][n]
+  {
+    ProfScope ps(w.ctx, K_SCALAR, w.s);
+    gcr_beta_kernel<<<(n + 63) / 64, 64, 0, w.s>>>(w.cz, w.az, K, w.m, n, nb);
+    MG_LAUNCH_CHECK();
+  }
+  Vec Z0 = w.view(w.Zp, 0, n);
+  return multi_axpy(w.ctx, Z0, w.stride(), K + 1, x, nb, w.s);
 }
 
 // iteration with direction slot k (no host interaction)
@@ -150,11 +199,15 @@ static mglma_status gcr_iter(GcrWork& w, const OpFn& A, const OpFn* M, Vec& x, i
     // new image's norm and overlap with r in its own pass
     MG_CHECK((*w.Ad)(Zk, Wk, k, W0, w.stride(), r, nw + (size_t)k * n, num, dots));
     if (k > 0) {
+      double2* ck = w.defer() ? w.cz + (size_t)k * w.m * n : coef;
       {
         ProfScope ps(ctx, K_SCALAR, s);
-        gcr_coef_kernel<<<(k * n + 63) / 64, 64, 0, s>>>(dots, nw, coef, k, n);
+        gcr_coef_kernel<<<(k * n + 63) / 64, 64, 0, s>>>(dots, nw, ck, k, n);
       }
-      MG_CHECK(multi_axpy_nd(ctx, W0, w.stride(), k, Wk, coef, &Z0, &Zk, r, nw + (size_t)k * n, num, s));
+      if (w.defer())
+        MG_CHECK(multi_axpy_nd(ctx, W0, w.stride(), k, Wk, ck, nullptr, nullptr, r, nw + (size_t)k * n, num, s));
+      else
+        MG_CHECK(multi_axpy_nd(ctx, W0, w.stride(), k, Wk, ck, &Z0, &Zk, r, nw + (size_t)k * n, num, s));
     }
   } else {
   MG_CHECK(A(Zk, Wk));
@@ -169,16 +222,21 @@ static mglma_status gcr_iter(GcrWork& w, const OpFn& A, const OpFn* M, Vec& x, i
   }
   MG_CHECK(norm2_cdot(ctx, Wk, r, nw + (size_t)k * n, num, s));
   }
+  double2* ak = w.defer() ? w.az + (size_t)k * n : a;
   {
     ProfScope ps(ctx, K_SCALAR, s);
-    gcr_alpha_kernel<<<nb, tb, 0, s>>>(num, nw + (size_t)k * n, w.sc.active, a, n);
+    gcr_alpha_kernel<<<nb, tb, 0, s>>>(num, nw + (size_t)k * n, w.sc.active, ak, n);
   }
-  MG_CHECK(axpy2_norm(ctx, a, Zk, x, Wk, r, rr, s));
+  if (w.defer())
+    MG_CHECK(axpy_norm(ctx, ak, Wk, r, rr, s));
+  else
+    MG_CHECK(axpy2_norm(ctx, a, Zk, x, Wk, r, rr, s));
   {
     ProfScope ps(ctx, K_SCALAR, s);
     gcr_mask_kernel<<<nb, tb, 0, s>>>(rr, bb, tol2, w.sc.active, n);
   }
   MG_LAUNCH_CHECK();
+  if (w.defer() && k == w.m - 1) MG_CHECK(gcr_flush(w, x, n, k));
   return MGLMA_OK;
 }
 
@@ -290,6 +348,8 @@ static mglma_status gcr_run(GcrWork& w, const OpFn& A, const OpFn* M, const Vec&
       if (!any) break;
     }
   }
+  // the deferred iterate of a cycle cut short
+  if (w.defer() && it > 0 && (it - 1) % m != m - 1) MG_CHECK(gcr_flush(w, x, n, (it - 1) % m));
   res.iterations = it;
   if (poll_every != 1)
     for (int i = 0; i < n; ++i) res.per_rhs[i] = it;
