@@ -371,6 +371,8 @@ void mglma_coarse_free(mglma_coarse Cc) {
   cudaFree(Cc->A16);
   cudaFree(Cc->Aimg);
   cudaFree(Cc->tc_err);
+  cudaFree(Cc->tc_dpart);
+  cudaFree(Cc->tc_dcount);
   delete Cc;
 }
 

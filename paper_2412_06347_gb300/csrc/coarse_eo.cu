@@ -344,8 +344,15 @@ static mglma_status schur_composed(mglma_ctx ctx, const mglma_coarse_s* C, const
   return MGLMA_OK;
 }
 
+bool coarse_schur_dot_ok(mglma_ctx ctx, const mglma_coarse_s* C, int nrhs, int prec) {
+  return prec == MGLMA_FP32 && C->Aimg && C->Sinv_img && C->tc_dpart && nrhs >= 1 &&
+         nrhs <= tuned(ctx, TUNE_COARSE_NT, nrhs, C->geo.V1, coarse_tc_default_nt(nrhs));
+}
+
 mglma_status coarse_schur_apply(mglma_ctx ctx, const mglma_coarse_s* C, const void* Xe, void* Ye, int nrhs, int prec,
-                                int mode, void* scratch, size_t scratch_bytes, cudaStream_t s) {
+                                int mode, void* scratch, size_t scratch_bytes, cudaStream_t s, double2* dot_out) {
+  if (dot_out && !coarse_schur_dot_ok(ctx, C, nrhs, prec))
+    return fail(MGLMA_ERR_INVALID, "schur apply: the fused dot needs the tensor-core path and one RHS tile");
   if (!C->Sinv64 && !C->Sinv_img) return fail(MGLMA_ERR_INVALID, "schur apply: even-odd set-up missing");
   if (!C->Sinv64 && (prec == MGLMA_FP64 || !C->Aimg))
     return fail(MGLMA_ERR_INVALID, "schur apply: the FP64 self-block inverses were released");
@@ -374,7 +381,8 @@ mglma_status coarse_schur_apply(mglma_ctx ctx, const mglma_coarse_s* C, const vo
     MG_CHECK(coarse_tc_eo_launch(ctx, C, X, nullptr, To, nrhs, 0, 1, 0, 7, nullptr, 1.f, img, s));
     MG_CHECK(coarse_tc_eo_launch(ctx, C, nullptr, To, Uo, nrhs, 0, 1, 8, 8, C->Sinv_img, -1.f, img, s));
   }
-  return coarse_tc_eo_launch(ctx, C, Uo, X, (float2*)Ye, nrhs, mode & 2, 0, 0, 8, nullptr, 1.f, img + hb, s, img);
+  return coarse_tc_eo_launch(ctx, C, Uo, X, (float2*)Ye, nrhs, mode & 2, 0, 0, 8, nullptr, 1.f, img + hb, s, img,
+                             nullptr, dot_out ? X : nullptr, dot_out);
 }
 
 mglma_status coarse_eo_prepare(mglma_ctx ctx, const mglma_coarse_s* C, const void* b, void* be, int nrhs, int prec,

@@ -185,6 +185,13 @@ __device__ __forceinline__ void tmem_ld<64>(uint32_t taddr, uint32_t* v) {
 struct TcRun {
   const uint8_t* A;
   const uint8_t* Aself;
+  // optional dot in the epilogue (one RHS tile only): dout[r] = <dotX_r, Y_r>
+  // = sum conj(dotX) Y over this launch's units, per-CTA partials in dpart
+  // ([CTA][nrhs]) summed in a fixed order by the last CTA (ticket dcount)
+  const float2* dotX;
+  double2* dpart;
+  unsigned* dcount;
+  double2* dout;
   int a_unit;  // 1: A holds eight hop slots per unit u ([u][8]), else nine per site ([y][9])
   const uint8_t* XB;
   const uint8_t* XBself;
@@ -253,6 +260,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     abort_flag = 1;
     atomicExch(err, code);
   };
+
+  float dre[NT], dim[NT];  // epilogue: this thread's share of the optional dot
+#pragma unroll
+  for (int r = 0; r < NT; ++r) dre[r] = dim[r] = 0.f;
 
   if (warp == 2) {
     // ------------------------------------------------------------ copies
@@ -376,6 +387,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     for (int64_t y = blockIdx.x; y < nunits && ok; y += gridDim.x) {
       for (int t = 0; t < ntiles; ++t, ++u) {
         const uint32_t b = u & 1u, aph = (u >> 1) & 1u;
+        // the dot's operand is fetched before the wait, so its latency
+        // overlaps the MMAs of this unit
+        float2 xq[NT];
+        if (run.dotX) {
+#pragma unroll
+          for (int r = 0; r < NT; ++r)
+            xq[r] = (i < n2 && t * NT + r < nrhs)
+                        ? __ldg(run.dotX + ((size_t)(t * NT + r) * nunits + y) * n2 + i)
+                        : make_float2(0.f, 0.f);
+        }
         // every lane waits; the warp proceeds only if all saw the phase
         const bool mine = mbar_wait(smem_u32(accf + b), aph, abrt);
         if (!__all_sync(0xffffffffu, mine)) {
@@ -394,9 +415,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
           const int r0 = t * NT;
 #pragma unroll
           for (int r = 0; r < NT; ++r)
-            if (r0 + r < nrhs)
-              run.Y[((size_t)(r0 + r) * nunits + y) * n2 + i] =
-                  make_float2(sg * __uint_as_float(v[r]), sg * __uint_as_float(v[NT + r]));
+            if (r0 + r < nrhs) {
+              const size_t e = ((size_t)(r0 + r) * nunits + y) * n2 + i;
+              const float yr = sg * __uint_as_float(v[r]), yi = sg * __uint_as_float(v[NT + r]);
+              run.Y[e] = make_float2(yr, yi);
+              if (run.dotX) {
+                dre[r] += xq[r].x * yr + xq[r].y * yi;
+                dim[r] += xq[r].x * yi - xq[r].y * yr;
+              }
+            }
         }
       }
     }
@@ -404,6 +431,60 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  if (run.dotX) {
+    // the pipeline is drained: the stage buffers hold the reduction
+#pragma unroll
+    for (int r = 0; r < NT; ++r)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dre[r] += __shfl_down_sync(0xffffffffu, dre[r], o);
+        dim[r] += __shfl_down_sync(0xffffffffu, dim[r], o);
+      }
+    float* red = reinterpret_cast<float*>(sm);  // [warp][2 NT]
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < NT; ++r) {
+        red[warp * 2 * NT + r] = dre[r];
+        red[warp * 2 * NT + NT + r] = dim[r];
+      }
+    __syncthreads();
+    if (tid < nrhs && tid < NT) {
+      double a = 0, c = 0;
+      for (int w2 = 0; w2 < TC_THREADS / 32; ++w2) {
+        a += (double)red[w2 * 2 * NT + tid];
+        c += (double)red[w2 * 2 * NT + NT + tid];
+      }
+      run.dpart[(size_t)blockIdx.x * nrhs + tid] = make_double2(a, c);
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (tid == 0) last = atomicAdd(run.dcount, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+      // all threads: RHS r = tid / GL summed by GL consecutive lanes, each over
+      // a fixed stride of the CTA partials, then a fixed shuffle tree
+      __threadfence();
+      constexpr int GL = TC_THREADS / NT;
+      const int r = tid / GL, l = tid % GL;
+      double a = 0, c = 0;
+      if (r < nrhs) {
+#pragma unroll 4
+        for (unsigned b2 = l; b2 < gridDim.x; b2 += GL) {
+          const double2 q = __ldcg(run.dpart + (size_t)b2 * nrhs + r);
+          a += q.x;
+          c += q.y;
+        }
+      }
+#pragma unroll
+      for (int o = GL / 2; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o, GL);
+        c += __shfl_down_sync(0xffffffffu, c, o, GL);
+      }
+      if (l == 0 && r < nrhs) run.dout[r] = make_double2(a, c);
+      if (tid == 0) *run.dcount = 0;
+    }
+  }
 }
 
 // operator image for the kernel: per site [c][g][8 rows][8 bf16] with
@@ -450,6 +531,10 @@ mglma_status coarse_tc_image(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s) {
   MG_CUDA(cudaMalloc(&C->Aimg, n * sizeof(uint16_t)));
   MG_CUDA(cudaMalloc(&C->tc_err, sizeof(int)));
   MG_CUDA(cudaMemsetAsync(C->tc_err, 0, sizeof(int), s));
+  // epilogue-dot partials: at most two CTAs per SM, one RHS tile of <= 32
+  MG_CUDA(cudaMalloc(&C->tc_dpart, sizeof(double2) * 2 * (size_t)ctx->sm_count * 32));
+  MG_CUDA(cudaMalloc(&C->tc_dcount, sizeof(unsigned)));
+  MG_CUDA(cudaMemsetAsync(C->tc_dcount, 0, sizeof(unsigned), s));
   ProfScope ps(ctx, K_SETUP, s);
   a_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C->A64, C->Aimg, C->geo.V1, C->n2, 9);
   MG_LAUNCH_CHECK();
@@ -489,6 +574,10 @@ static mglma_status launch_tc(mglma_ctx ctx, const mglma_coarse_s* C, const floa
   run.A = (const uint8_t*)C->Aimg;
   run.Aself = nullptr;
   run.a_unit = 0;
+  run.dotX = nullptr;
+  run.dpart = nullptr;
+  run.dcount = nullptr;
+  run.dout = nullptr;
   run.XB = run.XBself = (const uint8_t*)xb;
   run.Y = Y;
   run.d_lo = 0;
@@ -520,7 +609,7 @@ template <int NT>
 static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
                                  float sign, void* scratch, cudaStream_t s, const void* self_image,
-                                 const uint16_t* Ahop) {
+                                 const uint16_t* Ahop, const float2* dotX, double2* dot_out) {
   const int n2 = C->n2;
   const int64_t Vh = C->geo.V1 / 2;
   const size_t half = coarse_tc_half_image_bytes(C, nrhs);
@@ -540,6 +629,10 @@ static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const f
   run.A = Ahop ? (const uint8_t*)Ahop : (const uint8_t*)C->Aimg;
   run.Aself = (const uint8_t*)Aself;
   run.a_unit = Ahop ? 1 : 0;
+  run.dotX = dot_out && nrhs <= NT ? dotX : nullptr;
+  run.dpart = C->tc_dpart;
+  run.dcount = C->tc_dcount;
+  run.dout = dot_out;
   run.XB = xb_hop;
   run.XBself = xb_self;
   run.Y = Y;
@@ -556,20 +649,22 @@ static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const f
 mglma_status coarse_tc_eo_launch(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
                                  float sign, void* scratch, cudaStream_t s, const void* self_image,
-                                 const uint16_t* Ahop) {
+                                 const uint16_t* Ahop, const float2* dotX, double2* dot_out) {
   if (!C->Aimg || !coarse_tc_supported(C->n2)) return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: no tensor image");
+  if (dot_out && (!dotX || !C->tc_dpart || nrhs > tuned(ctx, TUNE_COARSE_NT, nrhs, C->geo.V1, coarse_tc_default_nt(nrhs))))
+    return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: the epilogue dot needs one RHS tile");
   if (par < 0 || par > 1 || d_lo < 0 || d_hi > 8 || d_lo > d_hi)
     return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: bad launch");
   if (Ahop && d_hi > 7) return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: the eight-slot image has no self slot");
   const int nt = tuned(ctx, TUNE_COARSE_NT, nrhs, C->geo.V1, coarse_tc_default_nt(nrhs));
   if (nt == 32)
     return launch_tc_eo<32>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image,
-                            Ahop);
+                            Ahop, dotX, dot_out);
   if (nt == 16)
     return launch_tc_eo<16>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image,
-                            Ahop);
+                            Ahop, dotX, dot_out);
   return launch_tc_eo<8>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image,
-                         Ahop);
+                         Ahop, dotX, dot_out);
 }
 
 mglma_status coarse_tc_check(mglma_coarse_s* C, cudaStream_t s) {

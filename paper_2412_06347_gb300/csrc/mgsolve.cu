@@ -489,11 +489,14 @@ static mglma_status minres_iter(MinresWork& w, const mglma_coarse_s* C, Vec& x, 
   const int a = k % 3, b = (k + 1) % 3, c = (k + 2) % 3;
   Vec v = w.view(w.Vp, a, n), vo = w.view(w.Vp, c, n), z = w.view(w.Vp, b, n);
   Vec wn = w.view(w.Wp, a, n), w1 = w.view(w.Wp, c, n), w2 = w.view(w.Wp, b, n);
+  // alpha = <v, Qhat v>: in the last tensor-core launch's epilogue when it can
+  const bool fused_dot = eo && coarse_schur_dot_ok(w.ctx, C, n, MGLMA_FP32);
   if (eo)
-    MG_CHECK(coarse_schur_apply(w.ctx, C, v.p, z.p, n, MGLMA_FP32, CMODE_Q, scr, scr_bytes, w.s));
+    MG_CHECK(coarse_schur_apply(w.ctx, C, v.p, z.p, n, MGLMA_FP32, CMODE_Q, scr, scr_bytes, w.s,
+                                fused_dot ? w.sc.z : nullptr));
   else
     MG_CHECK(coarse_apply(w.ctx, C, v.p, z.p, n, MGLMA_FP32, CMODE_Q, w.s, scr, scr_bytes));
-  MG_CHECK(cdot(w.ctx, v, z, w.sc.z, w.s));
+  if (!fused_dot) MG_CHECK(cdot(w.ctx, v, z, w.sc.z, w.s));
   MG_CHECK(lanczos_norm(w.ctx, w.sc.z, w.st(MR_BETA), w.sc.active, v, vo, z, w.st(MR_BN2), w.s));
   {
     ProfScope ps(w.ctx, K_SCALAR, w.s);

@@ -38,6 +38,8 @@ struct mglma_coarse_s {
   __nv_bfloat162* A16 = nullptr; // same layout, BF16 (re, im)
   uint16_t* Aimg = nullptr;      // BF16 tensor-core image, see coarse_tc.cu
   int* tc_err = nullptr;         // device error flag of the tensor-core kernel
+  double2* tc_dpart = nullptr;   // per-CTA partials of the epilogue dot ([CTA][RHS])
+  unsigned* tc_dcount = nullptr; // its ticket
   // level of the hierarchy: 1 for D1 = R0 D T0 (geo: fine lattice -> block
   // grid); l >= 2 for D_l = R_{l-1} D_{l-1} T_{l-1}, built by aggregation
   // from `parent` (geo: level l-1 grid -> level l grid, geo.V = V_{l-1},
@@ -97,8 +99,12 @@ mglma_status coarse_eo_setup(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s);
 // Y_e = S_ee X_e (mode bit 1: gamma5hat S_ee, the Hermitian form) with
 // S_ee = D_ee - D_eo D_oo^-1 D_oe; FP32 fields use the tensor cores when the
 // operator has its BF16 image, FP64 fields the FP64 operator
+// whether coarse_schur_apply can return <X_r, Y_r> per RHS (dot_out) from
+// its last launch: FP32 on the tensor cores, one RHS tile
+bool coarse_schur_dot_ok(mglma_ctx ctx, const mglma_coarse_s* C, int nrhs, int prec);
 mglma_status coarse_schur_apply(mglma_ctx ctx, const mglma_coarse_s* C, const void* Xe, void* Ye, int nrhs, int prec,
-                                int mode, void* scratch, size_t scratch_bytes, cudaStream_t s);
+                                int mode, void* scratch, size_t scratch_bytes, cudaStream_t s,
+                                double2* dot_out = nullptr);
 // b_e' = b_e - D_eo D_oo^-1 b_o from a full field b; x (full) from x_e and b:
 // x_o = D_oo^-1 (b_o - D_oe x_e)
 mglma_status coarse_eo_prepare(mglma_ctx ctx, const mglma_coarse_s* C, const void* b, void* be, int nrhs, int prec,
@@ -119,11 +125,13 @@ size_t coarse_eo_scratch_bytes(const mglma_coarse_s* C, int nrhs);
 // input); self_image (nullable) is an image of the self input an earlier
 // launch with the same RHS count and mode bit 0 left, used instead of writing
 // one; Ahop (nullable) replaces the hop slots with an eight-slot image
-// indexed by the half-lattice index of the output site
+// indexed by the half-lattice index of the output site; dot_out (nullable,
+// one RHS tile only) receives <dotX_r, Y_r> per RHS, taken in the epilogue
 mglma_status coarse_tc_eo_launch(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
                                  float sign, void* scratch, cudaStream_t s, const void* self_image = nullptr,
-                                 const uint16_t* Ahop = nullptr);
+                                 const uint16_t* Ahop = nullptr, const float2* dotX = nullptr,
+                                 double2* dot_out = nullptr);
 size_t coarse_tc_half_image_bytes(const mglma_coarse_s* C, int nrhs);
 mglma_status coarse_tc_image_blocks(mglma_ctx ctx, const double2* A64, int64_t V1, int n2, int nslots,
                                     uint16_t** img, cudaStream_t s);
