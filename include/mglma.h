@@ -226,7 +226,12 @@ mglma_status mglma_subspace_info(mglma_subspace s, int* nv, int Lb[4], int64_t* 
  * subspace exports its stored FP32 / FP16 copy (scale applied). */
 mglma_status mglma_subspace_export(mglma_subspace s, double* phi);
 /* R0 (Eq. res_mg): out[rhs][y][alpha nv + c] = sum_{x in B_y} phi^dag psi(x).
- * in: nrhs canonical spinors; out: nrhs canonical coarse fields. */
+ * in: nrhs canonical spinors; out: nrhs canonical coarse fields.  compute:
+ * MGLMA_FP64, MGLMA_FP32, or MGLMA_BF16 = the tensor-core path (tcgen05,
+ * FP32 fields rounded to BF16, BF16 image of the basis, FP32 accumulation;
+ * relative error of order 1e-3) for nv % 8 == 0, nv <= 32 and blocks of 64,
+ * 128, ... 512 sites; MGLMA_ERR_INVALID otherwise, MGLMA_ERR_TIMEOUT if a
+ * bounded wait of the kernel gave up. */
 mglma_status mglma_restrict(mglma_ctx ctx, mglma_subspace s, int nrhs, const double* in, double* out,
                             mglma_prec compute, void* cuda_stream);
 /* T0 (Eq. pro_mg): out(x) = sum_{alpha c} in[y(x)][alpha nv + c] phi(x). */

@@ -849,6 +849,7 @@ struct TwoLevel {
   CoarseSolver cs;
   bool ready = false;
   bool fused = false;      // fused MR steps on BF16 s, t
+  bool tc_r0 = false;      // R0 on the tensor cores (BF16 operands; the coarse solve is BF16 already)
   bool capturing = false;  // recording into a graph: the coarse loop runs on the device
   ~TwoLevel() {
     dfree(ctx, b1.p, s);
@@ -870,6 +871,7 @@ struct TwoLevel {
     // solve takes the rounded preconditioner; measured: same FGCR and coarse
     // iteration counts as FP32 at 64x32^3), FP32 otherwise
     fused = p->nu > 1 && dslash_mr_fused(ctx, G, n);
+    tc_r0 = n >= 8 && restrict_tc_supported(C->sub);
     sv = r;
     sv.nrhs = n;
     sv.p = nullptr;
@@ -899,7 +901,10 @@ struct TwoLevel {
     Vec b1n = b1, e1n = e1, svn = sv, tvn = tv, tv2n = tv2;
     b1n.nrhs = e1n.nrhs = svn.nrhs = tvn.nrhs = tv2n.nrhs = n;
     Spinor rs = as_spinor(r, V), zs = as_spinor(z, V);
-    MG_CHECK(restrict_fine(ctx, S, rs, b1n.p, s));
+    if (tc_r0)
+      MG_CHECK(restrict_tc(ctx, const_cast<mglma_subspace_s*>(S), rs, b1n.p, s));
+    else
+      MG_CHECK(restrict_fine(ctx, S, rs, b1n.p, s));
     if (capturing)
       MG_CHECK(cs.solve_captured(b1n, e1n, p->coarse_tol, p->coarse_max_iter));
     else
@@ -1052,6 +1057,7 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
   }
   MG_CHECK(K.cs.take_captured_iters(&K.coarse_iters));
   for (int i = 0; i < n; ++i) out[i].coarse_iterations = K.coarse_iters;
+  if (K.tc_r0) MG_CHECK(restrict_tc_check(C->sub, s));
   return coarse_tc_check(const_cast<mglma_coarse_s*>(C), s);
 }
 

@@ -1360,6 +1360,8 @@ void mglma_subspace_free(mglma_subspace S) {
   cudaFree(S->phi32);
   cudaFree(S->phi16);
   cudaFree(S->scale16);
+  cudaFree(S->rt_img);
+  cudaFree(S->rt_err);
   delete S;
 }
 
@@ -1406,8 +1408,13 @@ mglma_status mglma_subspace_export(mglma_subspace S, double* phi) {
 static mglma_status transfer(mglma_ctx ctx, mglma_subspace S, int nrhs, const double* in, double* out,
                              mglma_prec compute, void* stream, bool to_coarse) {
   if (!ctx || !S || !in || !out) return fail(MGLMA_ERR_INVALID, "restrict/prolong: NULL argument");
-  if (compute != MGLMA_FP64 && compute != MGLMA_FP32)
-    return fail(MGLMA_ERR_INVALID, "restrict/prolong: compute must be FP64 or FP32");
+  if (compute != MGLMA_FP64 && compute != MGLMA_FP32 && !(compute == MGLMA_BF16 && to_coarse))
+    return fail(MGLMA_ERR_INVALID, "restrict/prolong: compute must be FP64 or FP32 (or BF16 for restrict)");
+  if (compute == MGLMA_BF16 && !restrict_tc_supported(S))
+    return fail(MGLMA_ERR_INVALID, "restrict: the BF16 tensor-core path needs Nv % 8 == 0, Nv <= 32, 64 | |B| <= 512");
+  // BF16: the tensor-core R0 on FP32 fields
+  const bool tc = compute == MGLMA_BF16;
+  if (tc) compute = MGLMA_FP32;
   if (nrhs <= 0) return nrhs == 0 ? MGLMA_OK : fail(MGLMA_ERR_INVALID, "restrict/prolong: nrhs < 0");
   MG_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = pick_stream(ctx, stream);
@@ -1427,7 +1434,12 @@ static mglma_status transfer(mglma_ctx ctx, mglma_subspace S, int nrhs, const do
   fr.add(c);
   if (to_coarse) {
     MG_CHECK(pack_spinor(ctx, si.dev, f, s));
-    MG_CHECK(restrict_fine(ctx, S, f, c, s));
+    if (tc) {
+      MG_CHECK(restrict_tc(ctx, S, f, c, s));
+      MG_CHECK(restrict_tc_check(S, s));
+    } else {
+      MG_CHECK(restrict_fine(ctx, S, f, c, s));
+    }
     MG_CHECK(coarse_to_canonical(ctx, c, compute, (size_t)nrhs * V1 * n2, so.dev, s));
   } else {
     MG_CHECK(coarse_from_canonical(ctx, si.dev, (size_t)nrhs * V1 * n2, c, compute, s));

@@ -129,6 +129,34 @@ def test_low_precision_transfers(m, ctx, nv, nrhs):
     m.mglma_gauge_free(g)
 
 
+@pytest.mark.parametrize("nv,nrhs", [(8, 16), (8, 17), (24, 16)])
+def test_tensor_core_restrict(m, ctx, nv, nrhs):
+    """R0 on the tensor cores (BF16 operands, FP32 accumulation) against the
+    oracle on the same basis: 4^4 blocks (four 64-site segments per component
+    pair), one or two RHS tiles, FP32 and FP16 stored bases.  The bound is the
+    BF16 rounding of both operands (2^-9 each) summed over the block."""
+    L, b = (8, 4, 4, 8), (4, 4, 4, 4)
+    U = synthetic.gauge_links(L, 0.2, 31)
+    g = m.mglma_gauge_load(ctx, L, U, 0.125, 1.7)
+    phi = MG.subspace(U, synthetic.gaussian_start_vectors(L, nv, 32), 0.125, 1.7, b, 2)
+    psi = synthetic.random_spinors(L, nrhs, 35)
+    ref = MG.restrict(phi, psi, L, b)
+    for store in (m.MGLMA_FP32, m.MGLMA_FP16):
+        sub = m.mglma_subspace_build(ctx, g, b, nv, 2, 32, store)
+        out = np.zeros_like(ref)
+        m.mglma_restrict(ctx, sub, nrhs, psi, out, m.MGLMA_BF16)
+        err = rel_per_rhs(out, ref)
+        assert err.max() < 1e-2 and err.min() > 0, (store, err.max())
+        m.mglma_subspace_free(sub)
+    # Nv = 6 is not a multiple of 8: refused before any device work
+    sub = m.mglma_subspace_build(ctx, g, b, 6, 2, 32, m.MGLMA_FP32)
+    with pytest.raises(m.MglmaError) as e:
+        m.mglma_restrict(ctx, sub, 2, psi[:2], np.zeros((2, ref.shape[1], 12), ref.dtype), m.MGLMA_BF16)
+    assert e.value.status == 1
+    m.mglma_subspace_free(sub)
+    m.mglma_gauge_free(g)
+
+
 def test_subspace_load_exact_modes_and_rank_error(m, ctx):
     """Basis from caller-given vectors (exact low modes of Q, Sec. 3) and the
     rank check on linearly dependent vectors."""
