@@ -514,7 +514,8 @@ def run_micro(args, w):
             for _ in range(reps):
                 m.mglma_restrict(ctx, sub, n, f, c, m.MGLMA_BF16 if args.restrict == "bf16" else m.MGLMA_FP32,
                                  stream=stream)
-                m.mglma_prolong(ctx, sub, n, c, f, m.MGLMA_FP32, stream=stream)
+                m.mglma_prolong(ctx, sub, n, c, f, m.MGLMA_BF16 if args.restrict == "bf16" else m.MGLMA_FP32,
+                                stream=stream)
             kinds = ["restrict", "prolong"]
         r = {}
         for k in kinds:
@@ -555,7 +556,7 @@ def main():
                     help="time one kernel class on the workload lattice instead of the solve")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch in --micro mode")
     ap.add_argument("--restrict", default="fp32", choices=["fp32", "bf16"],
-                    help="--micro transfer: R0 on CUDA cores (FP32) or on the tensor cores (BF16 operands)")
+                    help="--micro transfer: R0 and T0 on CUDA cores (FP32) or on the tensor cores (BF16 operands)")
     ap.add_argument("--coarse-op", default="full", choices=["full", "schur"],
                     help="--micro coarse: the full coarse operator or g5hat S_ee (three tensor-core launches)")
     ap.add_argument("--tile", default="", help="FP32 stencil tile NR,RW (RHS per thread, RHS tiles per CTA) or sNRT "

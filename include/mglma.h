@@ -234,7 +234,13 @@ mglma_status mglma_subspace_export(mglma_subspace s, double* phi);
  * bounded wait of the kernel gave up. */
 mglma_status mglma_restrict(mglma_ctx ctx, mglma_subspace s, int nrhs, const double* in, double* out,
                             mglma_prec compute, void* cuda_stream);
-/* T0 (Eq. pro_mg): out(x) = sum_{alpha c} in[y(x)][alpha nv + c] phi(x). */
+/* T0 (Eq. pro_mg): out(x) = sum_{alpha c} in[y(x)][alpha nv + c] phi(x).
+ * in: nrhs canonical coarse fields; out: nrhs canonical spinors.  compute:
+ * MGLMA_FP64, MGLMA_FP32, or MGLMA_BF16 = the tensor-core path (coarse
+ * fields and the basis image in BF16, FP32 accumulation and output) for
+ * nv % 8 == 0, nv <= 32 and blocks of 128, 256, 384 or 512 sites;
+ * MGLMA_ERR_INVALID otherwise, MGLMA_ERR_TIMEOUT if a bounded wait of the
+ * kernel gave up. */
 mglma_status mglma_prolong(mglma_ctx ctx, mglma_subspace s, int nrhs, const double* in, double* out,
                            mglma_prec compute, void* cuda_stream);
 

@@ -850,6 +850,7 @@ struct TwoLevel {
   bool ready = false;
   bool fused = false;      // fused MR steps on BF16 s, t
   bool tc_r0 = false;      // R0 on the tensor cores (BF16 operands; the coarse solve is BF16 already)
+  bool tc_t0 = false;      // T0 on the tensor cores (BF16 operands)
   bool capturing = false;  // recording into a graph: the coarse loop runs on the device
   ~TwoLevel() {
     dfree(ctx, b1.p, s);
@@ -872,6 +873,7 @@ struct TwoLevel {
     // iteration counts as FP32 at 64x32^3), FP32 otherwise
     fused = p->nu > 1 && dslash_mr_fused(ctx, G, n);
     tc_r0 = n >= 8 && restrict_tc_supported(C->sub);
+    tc_t0 = n >= 8 && prolong_tc_supported(C->sub);
     sv = r;
     sv.nrhs = n;
     sv.p = nullptr;
@@ -909,7 +911,10 @@ struct TwoLevel {
       MG_CHECK(cs.solve_captured(b1n, e1n, p->coarse_tol, p->coarse_max_iter));
     else
       MG_CHECK(cs.solve(b1n, e1n, p->coarse_tol, p->coarse_max_iter, &coarse_iters));
-    MG_CHECK(prolong_coarse(ctx, S, e1n.p, zs, false, s));
+    if (tc_t0)
+      MG_CHECK(prolong_tc(ctx, const_cast<mglma_subspace_s*>(S), e1n.p, zs, s));
+    else
+      MG_CHECK(prolong_coarse(ctx, S, e1n.p, zs, false, s));
     if (p->nu > 0) {
       // s = r - D z (in the stencil's epilogue) ; nu MR steps on D e = s,
       // accumulated into z (the last one leaves s as it is)
@@ -1057,7 +1062,7 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
   }
   MG_CHECK(K.cs.take_captured_iters(&K.coarse_iters));
   for (int i = 0; i < n; ++i) out[i].coarse_iterations = K.coarse_iters;
-  if (K.tc_r0) MG_CHECK(restrict_tc_check(C->sub, s));
+  if (K.tc_r0 || K.tc_t0) MG_CHECK(restrict_tc_check(C->sub, s));
   return coarse_tc_check(const_cast<mglma_coarse_s*>(C), s);
 }
 

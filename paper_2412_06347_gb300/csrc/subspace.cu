@@ -1361,6 +1361,7 @@ void mglma_subspace_free(mglma_subspace S) {
   cudaFree(S->phi16);
   cudaFree(S->scale16);
   cudaFree(S->rt_img);
+  cudaFree(S->pt_img);
   cudaFree(S->rt_err);
   delete S;
 }
@@ -1408,11 +1409,13 @@ mglma_status mglma_subspace_export(mglma_subspace S, double* phi) {
 static mglma_status transfer(mglma_ctx ctx, mglma_subspace S, int nrhs, const double* in, double* out,
                              mglma_prec compute, void* stream, bool to_coarse) {
   if (!ctx || !S || !in || !out) return fail(MGLMA_ERR_INVALID, "restrict/prolong: NULL argument");
-  if (compute != MGLMA_FP64 && compute != MGLMA_FP32 && !(compute == MGLMA_BF16 && to_coarse))
-    return fail(MGLMA_ERR_INVALID, "restrict/prolong: compute must be FP64 or FP32 (or BF16 for restrict)");
-  if (compute == MGLMA_BF16 && !restrict_tc_supported(S))
+  if (compute != MGLMA_FP64 && compute != MGLMA_FP32 && compute != MGLMA_BF16)
+    return fail(MGLMA_ERR_INVALID, "restrict/prolong: compute must be FP64, FP32 or BF16");
+  if (compute == MGLMA_BF16 && to_coarse && !restrict_tc_supported(S))
     return fail(MGLMA_ERR_INVALID, "restrict: the BF16 tensor-core path needs Nv % 8 == 0, Nv <= 32, 64 | |B| <= 512");
-  // BF16: the tensor-core R0 on FP32 fields
+  if (compute == MGLMA_BF16 && !to_coarse && !prolong_tc_supported(S))
+    return fail(MGLMA_ERR_INVALID, "prolong: the BF16 tensor-core path needs Nv % 8 == 0, Nv <= 32, 128 | |B| <= 512");
+  // BF16: the tensor-core R0 / T0 on FP32 fields
   const bool tc = compute == MGLMA_BF16;
   if (tc) compute = MGLMA_FP32;
   if (nrhs <= 0) return nrhs == 0 ? MGLMA_OK : fail(MGLMA_ERR_INVALID, "restrict/prolong: nrhs < 0");
@@ -1443,7 +1446,12 @@ static mglma_status transfer(mglma_ctx ctx, mglma_subspace S, int nrhs, const do
     MG_CHECK(coarse_to_canonical(ctx, c, compute, (size_t)nrhs * V1 * n2, so.dev, s));
   } else {
     MG_CHECK(coarse_from_canonical(ctx, si.dev, (size_t)nrhs * V1 * n2, c, compute, s));
-    MG_CHECK(prolong_coarse(ctx, S, c, f, false, s));
+    if (tc) {
+      MG_CHECK(prolong_tc(ctx, S, c, f, s));
+      MG_CHECK(restrict_tc_check(S, s));
+    } else {
+      MG_CHECK(prolong_coarse(ctx, S, c, f, false, s));
+    }
     MG_CHECK(unpack_spinor(ctx, f, so.dev, s));
   }
   MG_CHECK(stage_out_finish(out, to_coarse ? cb : fb, s, so));

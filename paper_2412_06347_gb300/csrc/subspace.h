@@ -25,8 +25,9 @@ struct mglma_subspace_s {
   uint2* phi16 = nullptr;    // [V1][2Nv][3][nB], halves
   float* scale16 = nullptr;  // [V1][2Nv]
   bool lean = false;         // built without an FP64 copy (phi64 stays NULL)
-  uint16_t* rt_img = nullptr;  // cache: BF16 image of the basis for the tensor-core R0 (restrict_tc.cu), built on first use
-  int* rt_err = nullptr;       // its kernel's error flag
+  uint16_t* rt_img = nullptr;  // cache: BF16 image of the basis for the tensor-core R0 (transfer_tc.cu), built on first use
+  uint16_t* pt_img = nullptr;  // cache: BF16 image of the basis for the tensor-core T0, built on first use
+  int* rt_err = nullptr;       // the error flag of both tensor-core transfer kernels
 };
 
 struct mglma_coarse_s {
@@ -117,13 +118,18 @@ mglma_status coarse_eo_reconstruct(mglma_ctx ctx, const mglma_coarse_s* C, const
 // MGLMA_OP_SCHUR / _Q); forms the even-odd set-up on first use
 mglma_status coarse_schur_full(mglma_ctx ctx, mglma_coarse_s* C, const void* X, void* Y, int nrhs, int prec,
                                int mode, cudaStream_t s);
-// R0 on the tensor cores (restrict_tc.cu): FP32 fine fields in, FP32 coarse
+// R0 on the tensor cores (transfer_tc.cu): FP32 fine fields in, FP32 coarse
 // [rhs][V1][2Nv] out, BF16 operands (basis imaged on first use); needs
 // Nv % 8 == 0, Nv <= 32, 64 | |B| <= 512.  restrict_tc_check reports a
 // bounded wait that gave up.
 bool restrict_tc_supported(const mglma_subspace_s* S);
 mglma_status restrict_tc(mglma_ctx ctx, mglma_subspace_s* S, const Spinor& in, void* out, cudaStream_t s);
 mglma_status restrict_tc_check(const mglma_subspace_s* S, cudaStream_t s);
+// T0 on the tensor cores: FP32 coarse [rhs][V1][2Nv] in, FP32 fine fields
+// out (overwritten), BF16 operands; needs Nv % 8 == 0, Nv <= 32,
+// 128 | |B| <= 512.  Its timeouts are reported by restrict_tc_check too.
+bool prolong_tc_supported(const mglma_subspace_s* S);
+mglma_status prolong_tc(mglma_ctx ctx, mglma_subspace_s* S, const void* in_coarse, Spinor& out, cudaStream_t s);
 // scratch the FP32 (tensor-core) even-odd calls need for nrhs RHS
 size_t coarse_eo_scratch_bytes(const mglma_coarse_s* C, int nrhs);
 // one tensor-core launch on half-lattice fields (coarse_tc.cu): Y = sign *

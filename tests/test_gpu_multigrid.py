@@ -157,6 +157,40 @@ def test_tensor_core_restrict(m, ctx, nv, nrhs):
     m.mglma_gauge_free(g)
 
 
+@pytest.mark.parametrize("nv,nrhs,b", [(8, 16, (4, 4, 4, 4)), (8, 17, (4, 4, 4, 4)), (24, 16, (4, 4, 4, 4)),
+                                       (16, 33, (2, 4, 4, 4))])
+def test_tensor_core_prolong(m, ctx, nv, nrhs, b):
+    """T0 on the tensor cores (BF16 coarse fields and basis image, FP32
+    accumulation) against the oracle on the same basis: 256-site blocks (two
+    128-row tiles per component) and 128-site blocks, full and ragged RHS
+    tiles, FP32 and FP16 stored bases.  The bound is the BF16 rounding of both
+    operands summed over the 2 Nv coarse dofs."""
+    L = (8, 4, 4, 8)
+    U = synthetic.gauge_links(L, 0.2, 31)
+    g = m.mglma_gauge_load(ctx, L, U, 0.125, 1.7)
+    phi = MG.subspace(U, synthetic.gaussian_start_vectors(L, nv, 32), 0.125, 1.7, b, 2)
+    c = synthetic.random_coarse(phi.shape[0], 2 * nv, nrhs, 36)
+    ref = MG.prolong(phi, c, L, b)
+    for store in (m.MGLMA_FP32, m.MGLMA_FP16):
+        sub = m.mglma_subspace_build(ctx, g, b, nv, 2, 32, store)
+        f = np.full(ref.shape, 7.0 + 0j, ref.dtype)  # overwritten, not accumulated
+        m.mglma_prolong(ctx, sub, nrhs, c, f, m.MGLMA_BF16)
+        err = rel_per_rhs(f, ref)
+        assert err.max() < 1e-2 and err.min() > 0, (store, err.max())
+        m.mglma_subspace_free(sub)
+    # 64-site blocks fill no 128-row tile, Nv = 6 no K chunk: both refused
+    # before any device work
+    for bb, n in (((4, 4, 2, 2), 8), (b, 6)):
+        sub = m.mglma_subspace_build(ctx, g, bb, n, 2, 32, m.MGLMA_FP32)
+        nc = lat.volume(L) // int(np.prod(bb))
+        with pytest.raises(m.MglmaError) as e:
+            m.mglma_prolong(ctx, sub, 2, np.zeros((2, nc, 2 * n), complex), np.zeros((2,) + ref.shape[1:], ref.dtype),
+                            m.MGLMA_BF16)
+        assert e.value.status == 1
+        m.mglma_subspace_free(sub)
+    m.mglma_gauge_free(g)
+
+
 def test_subspace_load_exact_modes_and_rank_error(m, ctx):
     """Basis from caller-given vectors (exact low modes of Q, Sec. 3) and the
     rank check on linearly dependent vectors."""
