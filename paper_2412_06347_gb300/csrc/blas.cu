@@ -7,6 +7,7 @@
 // then FP64) in a fixed two-stage order, so results are bitwise reproducible
 // and independent of how RHS are grouped.
 #include "internal.h"
+#include "minres.cuh"
 
 
 namespace mglma {
@@ -148,7 +149,7 @@ constexpr int RT = 256;  // reduction threads per block
 // MODE 0: |x|^2 -> out1[r]; 1: <x_j, y> for j < k -> out2[j*n + r];
 // 2: |x|^2 -> out1[r] and <x, y> -> out2[r].
 template <int MODE>
-__device__ __forceinline__ void finish(double2* part, unsigned* count, int k, int nb, int nrhs, double2* out2,
+__device__ __forceinline__ bool finish(double2* part, unsigned* count, int k, int nb, int nrhs, double2* out2,
                                        double* out1) {
   __shared__ bool last;
   const int r = blockIdx.y;
@@ -156,7 +157,7 @@ __device__ __forceinline__ void finish(double2* part, unsigned* count, int k, in
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(count + r, 1u) == (unsigned)(nb - 1);
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   const int nslot = MODE == 2 ? 2 : k;
   for (int j = 0; j < nslot; ++j) {
@@ -178,6 +179,7 @@ __device__ __forceinline__ void finish(double2* part, unsigned* count, int k, in
     }
   }
   if (threadIdx.x == 0) count[r] = 0;
+  return true;
 }
 
 // FP32 data: products of one 16-byte load are summed in FP32, sixteen loads
@@ -403,15 +405,18 @@ __device__ __forceinline__ double2 rscale(double2 x, double a) { return make_dou
 
 // Lanczos step z -= a_r v + b_r u with a_r = Re dot[r], b_r = beta[r], and
 // out1[r] = |z_r|^2; RHS with active[r] == 0 are left alone (out1 = 0).
+// With st, the last block of each RHS then runs that RHS's MINRES scalar
+// step (minres.cuh; out1 must be its MR_BN2 slot).
 template <typename R>
 __global__ void __launch_bounds__(RT) lanczos_norm_kernel(const typename Pair<R>::T* __restrict__ v,
                                                           const typename Pair<R>::T* __restrict__ u,
                                                           typename Pair<R>::T* __restrict__ z,
                                                           const double2* __restrict__ dot,
                                                           const double* __restrict__ beta,
-                                                          const int* __restrict__ active, size_t m,
+                                                          const int* active, size_t m,
                                                           double2* __restrict__ part, unsigned* __restrict__ count,
-                                                          double* out1) {
+                                                          double* out1, double* st, double tol, int cap,
+                                                          int* act) {
   const int r = blockIdx.y, nrhs = gridDim.y, nb = gridDim.x;
   const bool on = active[r] != 0;
   const double a = on ? -dot[r].x : 0.0, b = on ? -beta[r] : 0.0;
@@ -426,7 +431,8 @@ __global__ void __launch_bounds__(RT) lanczos_norm_kernel(const typename Pair<R>
   }
   const double2 t = block_sum2<RT>(make_double2(acc.norm(), 0));
   if (threadIdx.x == 0) part[(size_t)r * nb + blockIdx.x] = t;
-  finish<0>(part, count, 1, nb, nrhs, nullptr, out1);
+  if (finish<0>(part, count, 1, nb, nrhs, nullptr, out1) && st && threadIdx.x == 0)
+    minres_scalar_step(st, dot, act, tol, cap, r);
 }
 
 // w_new = cf0 v + cf1 w1 + cf2 w2 ; x += cf3 w_new ; z *= cf4, for RHS with
@@ -703,7 +709,7 @@ mglma_status axpy2_norm(mglma_ctx ctx, const double2* a, const Vec& p, Vec& x, c
 }
 
 mglma_status lanczos_norm(mglma_ctx ctx, const double2* dot, const double* beta, const int* active, const Vec& v,
-                          const Vec& u, Vec& z, double* zz, cudaStream_t s) {
+                          const Vec& u, Vec& z, double* zz, cudaStream_t s, double* st, double tol, int cap) {
   if (v.prec != z.prec || u.prec != z.prec || v.n != z.n || u.n != z.n)
     return fail(MGLMA_ERR_INVALID, "lanczos_norm: mismatch");
   if (z.nrhs == 0) return MGLMA_OK;
@@ -716,10 +722,11 @@ mglma_status lanczos_norm(mglma_ctx ctx, const double2* dot, const double* beta,
   dim3 g(nb, z.nrhs, 1);
   if (z.prec == MGLMA_FP64)
     lanczos_norm_kernel<double><<<g, RT, 0, s>>>((const double2*)v.p, (const double2*)u.p, (double2*)z.p, dot, beta,
-                                                 active, m, part, count, zz);
+                                                 active, m, part, count, zz, st, tol, cap,
+                                                 const_cast<int*>(active));
   else
     lanczos_norm_kernel<float><<<g, RT, 0, s>>>((const float4*)v.p, (const float4*)u.p, (float4*)z.p, dot, beta,
-                                                active, m, part, count, zz);
+                                                active, m, part, count, zz, st, tol, cap, const_cast<int*>(active));
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }

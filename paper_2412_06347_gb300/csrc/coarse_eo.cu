@@ -350,9 +350,11 @@ bool coarse_schur_dot_ok(mglma_ctx ctx, const mglma_coarse_s* C, int nrhs, int p
 }
 
 mglma_status coarse_schur_apply(mglma_ctx ctx, const mglma_coarse_s* C, const void* Xe, void* Ye, int nrhs, int prec,
-                                int mode, void* scratch, size_t scratch_bytes, cudaStream_t s, double2* dot_out) {
+                                int mode, void* scratch, size_t scratch_bytes, cudaStream_t s, double2* dot_out,
+                                bool x_imaged) {
   if (dot_out && !coarse_schur_dot_ok(ctx, C, nrhs, prec))
     return fail(MGLMA_ERR_INVALID, "schur apply: the fused dot needs the tensor-core path and one RHS tile");
+  if (x_imaged && !dot_out) return fail(MGLMA_ERR_INVALID, "schur apply: a given X image goes with the fused dot");
   if (!C->Sinv64 && !C->Sinv_img) return fail(MGLMA_ERR_INVALID, "schur apply: even-odd set-up missing");
   if (!C->Sinv64 && (prec == MGLMA_FP64 || !C->Aimg))
     return fail(MGLMA_ERR_INVALID, "schur apply: the FP64 self-block inverses were released");
@@ -376,9 +378,10 @@ mglma_status coarse_schur_apply(mglma_ctx ctx, const mglma_coarse_s* C, const vo
   const size_t hb = coarse_tc_half_image_bytes(C, nrhs);
   if (C->Ahat_img) {
     MG_CHECK(coarse_tc_eo_launch(ctx, C, X, nullptr, Uo, nrhs, 0, 1, 0, 7, nullptr, -1.f, img, s, nullptr,
-                                 C->Ahat_img));
+                                 C->Ahat_img, nullptr, nullptr, x_imaged));
   } else {
-    MG_CHECK(coarse_tc_eo_launch(ctx, C, X, nullptr, To, nrhs, 0, 1, 0, 7, nullptr, 1.f, img, s));
+    MG_CHECK(coarse_tc_eo_launch(ctx, C, X, nullptr, To, nrhs, 0, 1, 0, 7, nullptr, 1.f, img, s, nullptr, nullptr,
+                                 nullptr, nullptr, x_imaged));
     MG_CHECK(coarse_tc_eo_launch(ctx, C, nullptr, To, Uo, nrhs, 0, 1, 8, 8, C->Sinv_img, -1.f, img, s));
   }
   return coarse_tc_eo_launch(ctx, C, Uo, X, (float2*)Ye, nrhs, mode & 2, 0, 0, 8, nullptr, 1.f, img + hb, s, img,

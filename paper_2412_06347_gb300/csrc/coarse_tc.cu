@@ -50,6 +50,24 @@ constexpr uint32_t TC_PAD = 2048;  // M = 128 rows read past the n2 real rows
 //   part 0: column r <- Re X_j,r, column NT + r <- Im X_j,r
 //   part 1: column r <- -Im X_j,r, column NT + r <- Re X_j,r
 // RHS beyond nrhs are zero; mode bit 0 applies gamma5hat (j >= nv negated).
+// the four 16-byte rows of dof group jo (8 dofs) for column ri of a tile,
+// dst = the image of one (tile, site)
+__device__ __forceinline__ void x_image_store(uint4* dst, int jo, int G, int NT, int ri, const float* re,
+                                              const float* im) {
+  uint32_t w[3][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    w[0][e] = (uint32_t)bf16_bits(re[2 * e]) | ((uint32_t)bf16_bits(re[2 * e + 1]) << 16);
+    w[1][e] = (uint32_t)bf16_bits(im[2 * e]) | ((uint32_t)bf16_bits(im[2 * e + 1]) << 16);
+    w[2][e] = (uint32_t)bf16_bits(-im[2 * e]) | ((uint32_t)bf16_bits(-im[2 * e + 1]) << 16);
+  }
+  const int N = 2 * NT;
+  dst[(size_t)jo * N + ri] = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
+  dst[(size_t)jo * N + NT + ri] = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+  dst[(size_t)(G + jo) * N + ri] = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
+  dst[(size_t)(G + jo) * N + NT + ri] = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
+}
+
 __global__ void x_image_kernel(const float2* __restrict__ X, uint4* __restrict__ XB, int64_t V1, int n2, int nrhs,
                                int NT, int mode) {
   // one thread per (tile t, site z, group jo of 8 dofs, RHS r of the tile):
@@ -64,10 +82,9 @@ __global__ void x_image_kernel(const float2* __restrict__ X, uint4* __restrict__
   const int64_t z = (int64_t)((u / ((size_t)NT * G)) % V1);
   const int t = (int)(u / ((size_t)NT * G * V1));
   const int rr = t * NT + ri;
-  uint32_t w[4][4] = {};  // rows: (part 0, Re col), (part 0, Im col), (part 1, Re col), (part 1, Im col)
+  float re[8] = {}, im[8] = {};
   if (rr < nrhs) {
     const float4* src = reinterpret_cast<const float4*>(X + ((size_t)rr * V1 + z) * n2 + jo * 8);
-    float re[8], im[8];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       const float4 q = __ldg(src + h);
@@ -82,19 +99,49 @@ __global__ void x_image_kernel(const float2* __restrict__ X, uint4* __restrict__
       re[e] *= sg;
       im[e] *= sg;
     }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      w[0][e] = (uint32_t)bf16_bits(re[2 * e]) | ((uint32_t)bf16_bits(re[2 * e + 1]) << 16);
-      w[1][e] = (uint32_t)bf16_bits(im[2 * e]) | ((uint32_t)bf16_bits(im[2 * e + 1]) << 16);
-      w[2][e] = (uint32_t)bf16_bits(-im[2 * e]) | ((uint32_t)bf16_bits(-im[2 * e + 1]) << 16);
-      w[3][e] = w[0][e];
-    }
   }
-  uint4* dst = XB + ((size_t)t * V1 + z) * rows;
-  dst[(size_t)jo * N + ri] = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
-  dst[(size_t)jo * N + NT + ri] = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
-  dst[(size_t)(G + jo) * N + ri] = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
-  dst[(size_t)(G + jo) * N + NT + ri] = make_uint4(w[3][0], w[3][1], w[3][2], w[3][3]);
+  x_image_store(XB + ((size_t)t * V1 + z) * rows, jo, G, NT, ri, re, im);
+}
+
+// The coarse MINRES update (w_new = cf0 v + cf1 w1 + cf2 w2, x += cf3 w_new,
+// z *= cf4 for RHS with cf5 != 0; cf_j[r] = cf[j stride + r]) on FP32
+// half-lattice fields, which also writes the B-operand image (tiles of NT,
+// no gamma5hat) of the scaled z -- the next iteration's Lanczos vector -- so
+// its operator application needs no image pass.  One thread per (site, group
+// of 8 dofs) of RHS blockIdx.y.
+__global__ void minres_update_image_kernel(const float4* __restrict__ v, const float4* __restrict__ w1,
+                                           const float4* __restrict__ w2, float4* __restrict__ wn,
+                                           float4* __restrict__ x, float4* __restrict__ z,
+                                           const double* __restrict__ cf, int stride, int64_t Vh, int n2, int NT,
+                                           uint4* __restrict__ XB) {
+  const int r = blockIdx.y;
+  if (cf[5 * (size_t)stride + r] == 0.0) return;
+  const float c0 = (float)cf[r], c1 = (float)cf[stride + r], c2 = (float)cf[2 * (size_t)stride + r],
+              c3 = (float)cf[3 * (size_t)stride + r], c4 = (float)cf[4 * (size_t)stride + r];
+  const int G = n2 / 8;
+  const size_t ng = (size_t)Vh * G, off = (size_t)r * Vh * (n2 / 2);
+  const size_t rows = (size_t)2 * G * 2 * NT;
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (size_t)gridDim.x * blockDim.x) {
+    float re[8], im[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const size_t i = off + 4 * g + q;
+      const float4 a = v[i], b = w1[i], c = w2[i];
+      const float4 w = make_float4(c0 * a.x + c1 * b.x + c2 * c.x, c0 * a.y + c1 * b.y + c2 * c.y,
+                                   c0 * a.z + c1 * b.z + c2 * c.z, c0 * a.w + c1 * b.w + c2 * c.w);
+      wn[i] = w;
+      const float4 xo = x[i];
+      x[i] = make_float4(xo.x + c3 * w.x, xo.y + c3 * w.y, xo.z + c3 * w.z, xo.w + c3 * w.w);
+      const float4 zo = z[i];
+      const float4 zn = make_float4(c4 * zo.x, c4 * zo.y, c4 * zo.z, c4 * zo.w);
+      z[i] = zn;
+      re[2 * q] = zn.x;
+      im[2 * q] = zn.y;
+      re[2 * q + 1] = zn.z;
+      im[2 * q + 1] = zn.w;
+    }
+    x_image_store(XB + ((size_t)(r / NT) * Vh + (int64_t)(g / G)) * rows, (int)(g % G), G, NT, r % NT, re, im);
+  }
 }
 
 // Warp-specialised persistent kernel: CTA b takes sites y = b, b + grid, ...
@@ -544,7 +591,7 @@ template <int NT>
 static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
                                  float sign, void* scratch, cudaStream_t s, const void* self_image,
-                                 const uint16_t* Ahop, const float2* dotX, double2* dot_out) {
+                                 const uint16_t* Ahop, const float2* dotX, double2* dot_out, bool hop_imaged) {
   const int n2 = C->n2;
   const int64_t Vh = C->geo.V1 / 2;
   const size_t half = coarse_tc_half_image_bytes(C, nrhs);
@@ -552,7 +599,7 @@ static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const f
   uint8_t* xb_self = self_image ? (uint8_t*)self_image : xb_hop + half;
   const size_t groups = (size_t)((nrhs + NT - 1) / NT) * Vh * (n2 / 8) * NT;
   // images of the inputs the slots read (gamma5hat on the inputs by mode bit 0)
-  if (d_lo < 8)
+  if (d_lo < 8 && !hop_imaged)
     x_image_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, s>>>(Xhop, (uint4*)xb_hop, Vh, n2, nrhs, NT, mode);
   if (d_hi == 8 && !self_image)
     x_image_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, s>>>(Xself, (uint4*)xb_self, Vh, n2, nrhs, NT, mode);
@@ -584,8 +631,9 @@ static mglma_status launch_tc_eo(mglma_ctx ctx, const mglma_coarse_s* C, const f
 mglma_status coarse_tc_eo_launch(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
                                  float sign, void* scratch, cudaStream_t s, const void* self_image,
-                                 const uint16_t* Ahop, const float2* dotX, double2* dot_out) {
+                                 const uint16_t* Ahop, const float2* dotX, double2* dot_out, bool hop_imaged) {
   if (!C->Aimg || !coarse_tc_supported(C->n2)) return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: no tensor image");
+  if (hop_imaged && (mode & 1)) return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: a given hop image carries no gamma5hat");
   if (dot_out && (!dotX || !C->tc_dpart || nrhs > tuned(ctx, TUNE_COARSE_NT, nrhs, C->geo.V1, coarse_tc_default_nt(nrhs))))
     return fail(MGLMA_ERR_INVALID, "coarse_tc_eo: the epilogue dot needs one RHS tile");
   if (par < 0 || par > 1 || d_lo < 0 || d_hi > 8 || d_lo > d_hi)
@@ -594,12 +642,12 @@ mglma_status coarse_tc_eo_launch(mglma_ctx ctx, const mglma_coarse_s* C, const f
   const int nt = tuned(ctx, TUNE_COARSE_NT, nrhs, C->geo.V1, coarse_tc_default_nt(nrhs));
   if (nt == 32)
     return launch_tc_eo<32>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image,
-                            Ahop, dotX, dot_out);
+                            Ahop, dotX, dot_out, hop_imaged);
   if (nt == 16)
     return launch_tc_eo<16>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image,
-                            Ahop, dotX, dot_out);
+                            Ahop, dotX, dot_out, hop_imaged);
   return launch_tc_eo<8>(ctx, C, Xhop, Xself, Y, nrhs, mode, par, d_lo, d_hi, Aself, sign, scratch, s, self_image,
-                         Ahop, dotX, dot_out);
+                         Ahop, dotX, dot_out, hop_imaged);
 }
 
 mglma_status coarse_tc_check(mglma_coarse_s* C, cudaStream_t s) {
@@ -615,6 +663,43 @@ mglma_status coarse_tc_check(mglma_coarse_s* C, cudaStream_t s) {
 }
 
 int coarse_tc_default_nt(int nrhs) { return nrhs <= 8 ? 8 : (nrhs <= 24 ? 16 : 32); }
+
+int coarse_tc_nt(mglma_ctx ctx, const mglma_coarse_s* C, int nrhs) {
+  return tuned(ctx, TUNE_COARSE_NT, nrhs, C->geo.V1, coarse_tc_default_nt(nrhs));
+}
+
+mglma_status coarse_x_image_half(mglma_ctx ctx, const mglma_coarse_s* C, const void* X, int nrhs, void* image,
+                                 cudaStream_t s) {
+  if (nrhs == 0) return MGLMA_OK;
+  const int n2 = C->n2, NT = coarse_tc_nt(ctx, C, nrhs);
+  const int64_t Vh = C->geo.V1 / 2;
+  const size_t groups = (size_t)((nrhs + NT - 1) / NT) * Vh * (n2 / 8) * NT;
+  ProfScope ps(ctx, K_COARSE, s);
+  x_image_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, s>>>((const float2*)X, (uint4*)image, Vh, n2, nrhs, NT,
+                                                                 0);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+mglma_status minres_update_image(mglma_ctx ctx, const mglma_coarse_s* C, const double* cf, int stride, const Vec& v,
+                                 const Vec& w1, const Vec& w2, Vec& wn, Vec& x, Vec& z, void* image, cudaStream_t s) {
+  const int n2 = C->n2;
+  const int64_t Vh = C->geo.V1 / 2;
+  if (x.prec != MGLMA_FP32 || n2 % 8 || x.n != (size_t)Vh * n2 * 2 || v.n != x.n || w1.n != x.n || w2.n != x.n ||
+      wn.n != x.n || z.n != x.n)
+    return fail(MGLMA_ERR_INVALID, "minres_update_image: FP32 half-lattice fields needed");
+  if (x.nrhs == 0) return MGLMA_OK;
+  const int NT = coarse_tc_nt(ctx, C, x.nrhs);
+  ProfScope ps(ctx, K_BLAS, s, 8.0 * x.bytes() + (double)x.nrhs * Vh * n2 * 8.0);
+  const size_t ng = (size_t)Vh * (n2 / 8);
+  const unsigned gx = (unsigned)std::min<size_t>((ng + 255) / 256, std::max(4, 8 * ctx->sm_count / x.nrhs + 1));
+  dim3 g(gx, x.nrhs, 1);
+  minres_update_image_kernel<<<g, 256, 0, s>>>((const float4*)v.p, (const float4*)w1.p, (const float4*)w2.p,
+                                               (float4*)wn.p, (float4*)x.p, (float4*)z.p, cf, stride, Vh, n2, NT,
+                                               (uint4*)image);
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
 
 mglma_status coarse_apply_tc(mglma_ctx ctx, const mglma_coarse_s* C, const float2* X, float2* Y, int nrhs, int mode,
                              void* scratch, size_t scratch_bytes, cudaStream_t s) {

@@ -362,8 +362,11 @@ mglma_status axpy2_norm(mglma_ctx, const double2* a, const Vec& p, Vec& x, const
                         cudaStream_t s);
 // MINRES: z -= Re(dot_r) v + beta_r u, zz[r] = |z_r|^2 (RHS with active[r] == 0
 // are left alone, zz = 0)
+// st (nullable): also runs the MINRES scalar step of each RHS (minres.cuh)
+// in the kernel's last block; zz must then be st's MR_BN2 slot
 mglma_status lanczos_norm(mglma_ctx, const double2* dot, const double* beta, const int* active, const Vec& v,
-                          const Vec& u, Vec& z, double* zz, cudaStream_t s);
+                          const Vec& u, Vec& z, double* zz, cudaStream_t s, double* st = nullptr, double tol = 0,
+                          int cap = 0);
 // MINRES: wn = c0 v + c1 w1 + c2 w2 ; x += c3 wn ; z *= c4 for RHS with c5 != 0,
 // c_j[r] = cf[j * stride + r] (real, device)
 mglma_status minres_update(mglma_ctx, const double* cf, int stride, const Vec& v, const Vec& w1, const Vec& w2,

@@ -25,6 +25,7 @@
 
 #include "cplx.cuh"
 #include "internal.h"
+#include "minres.cuh"
 #include "solver.h"
 #include "subspace.h"
 
@@ -372,19 +373,6 @@ static mglma_status gcr_run(GcrWork& w, const OpFn& A, const OpFn* M, const Vec&
 // stopping at |eta| <= tol beta_1.  Vectors rotate through three slots
 // (v_j, w_j in slot j mod 3), so a captured cycle is a multiple of three
 // iterations long.
-enum {
-  MR_BETA1 = 0,
-  MR_ETA,
-  MR_BETA,
-  MR_C2,
-  MR_S2,
-  MR_C1,
-  MR_S1,
-  MR_BN2,
-  MR_BB,
-  MR_CF,  // six update coefficients (minres_update), MR_CF + 4 also scales v_0
-  MR_COUNT = MR_CF + 6
-};
 
 __global__ void minres_init_kernel(double* st, int* active, int cap, int n) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -403,34 +391,7 @@ __global__ void minres_init_kernel(double* st, int* active, int cap, int n) {
 
 __global__ void minres_scalar_kernel(double* st, const double2* dot, int* active, double tol, int cap, int n) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  auto S = [&](int j) -> double& { return st[(size_t)j * cap + r]; };
-  S(MR_CF + 5) = 0;
-  if (!active[r]) return;
-  const double alpha = dot[r].x, beta = S(MR_BETA);
-  const double bn = sqrt(fmax(S(MR_BN2), 0.0));
-  const double eps = S(MR_S2) * beta, dp = S(MR_C2) * beta;
-  const double delta = S(MR_C1) * dp + S(MR_S1) * alpha;
-  const double gp = S(MR_C1) * alpha - S(MR_S1) * dp;
-  const double gamma = hypot(gp, bn);
-  if (!(gamma > 0) || !(gamma < INFINITY)) {  // breakdown: keep the iterate
-    active[r] = 0;
-    return;
-  }
-  const double c = gp / gamma, sn = bn / gamma;
-  S(MR_CF + 0) = 1.0 / gamma;
-  S(MR_CF + 1) = -delta / gamma;
-  S(MR_CF + 2) = -eps / gamma;
-  S(MR_CF + 3) = c * S(MR_ETA);
-  S(MR_CF + 4) = bn > 0 ? 1.0 / bn : 0.0;
-  S(MR_CF + 5) = 1;
-  S(MR_ETA) = -sn * S(MR_ETA);
-  S(MR_C2) = S(MR_C1);
-  S(MR_S2) = S(MR_S1);
-  S(MR_C1) = c;
-  S(MR_S1) = sn;
-  S(MR_BETA) = bn;
-  active[r] = (bn > 0 && fabs(S(MR_ETA)) > tol * S(MR_BETA1)) ? 1 : 0;
+  if (r < n) minres_scalar_step(st, dot, active, tol, cap, r);
 }
 
 struct MinresWork {
@@ -489,14 +450,22 @@ static mglma_status minres_iter(MinresWork& w, const mglma_coarse_s* C, Vec& x, 
   const int a = k % 3, b = (k + 1) % 3, c = (k + 2) % 3;
   Vec v = w.view(w.Vp, a, n), vo = w.view(w.Vp, c, n), z = w.view(w.Vp, b, n);
   Vec wn = w.view(w.Wp, a, n), w1 = w.view(w.Wp, c, n), w2 = w.view(w.Wp, b, n);
-  // alpha = <v, Qhat v>: in the last tensor-core launch's epilogue when it can
+  // alpha = <v, Qhat v>: in the last tensor-core launch's epilogue when it
+  // can; then the operator's input image of v was written by the previous
+  // update (or by the initialisation), the scalar step runs at the end of the
+  // Lanczos-norm kernel, and the update writes the image of the next v
   const bool fused_dot = eo && coarse_schur_dot_ok(w.ctx, C, n, MGLMA_FP32);
   if (eo)
     MG_CHECK(coarse_schur_apply(w.ctx, C, v.p, z.p, n, MGLMA_FP32, CMODE_Q, scr, scr_bytes, w.s,
-                                fused_dot ? w.sc.z : nullptr));
+                                fused_dot ? w.sc.z : nullptr, fused_dot));
   else
     MG_CHECK(coarse_apply(w.ctx, C, v.p, z.p, n, MGLMA_FP32, CMODE_Q, w.s, scr, scr_bytes));
-  if (!fused_dot) MG_CHECK(cdot(w.ctx, v, z, w.sc.z, w.s));
+  if (fused_dot) {
+    MG_CHECK(lanczos_norm(w.ctx, w.sc.z, w.st(MR_BETA), w.sc.active, v, vo, z, w.st(MR_BN2), w.s, w.sc.d, tol,
+                          w.cap));
+    return minres_update_image(w.ctx, C, w.st(MR_CF), w.cap, v, w1, w2, wn, x, z, scr, w.s);
+  }
+  MG_CHECK(cdot(w.ctx, v, z, w.sc.z, w.s));
   MG_CHECK(lanczos_norm(w.ctx, w.sc.z, w.st(MR_BETA), w.sc.active, v, vo, z, w.st(MR_BN2), w.s));
   {
     ProfScope ps(w.ctx, K_SCALAR, w.s);
@@ -690,7 +659,12 @@ struct CoarseSolver {
       Vec bn = be, xn = xe;
       bn.nrhs = xn.nrhs = b.nrhs;
       MG_CHECK(coarse_eo_prepare(ctx, C, b.p, bn.p, b.nrhs, MGLMA_FP32, scr, scr_bytes, s));
-      return minres_init(mw, C, bn, xn);
+      MG_CHECK(minres_init(mw, C, bn, xn));
+      // the first Lanczos vector's operator image (the iterations' updates
+      // write the later ones)
+      if (coarse_schur_dot_ok(ctx, C, b.nrhs, MGLMA_FP32))
+        MG_CHECK(coarse_x_image_half(ctx, C, mw.view(mw.Vp, 0, b.nrhs).p, b.nrhs, scr, s));
+      return MGLMA_OK;
     }
     return minres() ? minres_init(mw, C, b, x) : gcr_init(w, b, x);
   }
@@ -951,10 +925,12 @@ struct TwoLevel {
 
 // Inner-tolerance factor for a RHS at FP64 relative residual `rel`: when
 // this cycle can reach the target (inner_tol * rel < 10 tol), the inner solve
-// aims at 0.3 tol / rel instead of inner_tol.
+// aims at 0.3 tol / rel instead of inner_tol -- tighter when two cycles of
+// inner_tol would land just above tol, looser when the RHS needs less than
+// inner_tol to finish (no FGCR iterations spent below 0.3 tol).
 static double final_cycle_scale(const MgParams& p, double rel) {
   if (!(rel > 0) || p.inner_tol * rel >= 10.0 * p.tol) return 1.0;
-  return std::min(1.0, 0.3 * p.tol / (rel * p.inner_tol));
+  return 0.3 * p.tol / (rel * p.inner_tol);
 }
 
 // x (FP64, zero on entry) = D^-1 b to p.tol in the FP64 residual.
@@ -1042,8 +1018,8 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
     sqrt_kernel<<<nb, tb, 0, s>>>(rr, rn, n, 0);
     MG_CHECK(convert_spinor(ctx, r, r32, s, rinv, false));
     Vec v32 = as_vec(r32), e = as_vec(e32);
-    // a cycle that can finish a RHS aims a little below what it needs, so two
-    // cycles of inner_tol do not land just above the target
+    // a cycle that can finish a RHS aims at 0.3 tol: a little below what it
+    // needs, and no further
     std::vector<double> scale(n, 1.0);
     for (int i = 0; i < n; ++i) scale[i] = final_cycle_scale(p, out[i].residual);
     GcrResult gr;

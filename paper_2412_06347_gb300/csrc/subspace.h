@@ -105,9 +105,11 @@ mglma_status coarse_eo_setup(mglma_ctx ctx, mglma_coarse_s* C, cudaStream_t s);
 // whether coarse_schur_apply can return <X_r, Y_r> per RHS (dot_out) from
 // its last launch: FP32 on the tensor cores, one RHS tile
 bool coarse_schur_dot_ok(mglma_ctx ctx, const mglma_coarse_s* C, int nrhs, int prec);
+// x_imaged (with dot_out only): the scratch's first half already holds the
+// image of X_e (coarse_x_image_half / minres_update_image)
 mglma_status coarse_schur_apply(mglma_ctx ctx, const mglma_coarse_s* C, const void* Xe, void* Ye, int nrhs, int prec,
                                 int mode, void* scratch, size_t scratch_bytes, cudaStream_t s,
-                                double2* dot_out = nullptr);
+                                double2* dot_out = nullptr, bool x_imaged = false);
 // b_e' = b_e - D_eo D_oo^-1 b_o from a full field b; x (full) from x_e and b:
 // x_o = D_oo^-1 (b_o - D_oe x_e)
 mglma_status coarse_eo_prepare(mglma_ctx ctx, const mglma_coarse_s* C, const void* b, void* be, int nrhs, int prec,
@@ -141,12 +143,25 @@ size_t coarse_eo_scratch_bytes(const mglma_coarse_s* C, int nrhs);
 // launch with the same RHS count and mode bit 0 left, used instead of writing
 // one; Ahop (nullable) replaces the hop slots with an eight-slot image
 // indexed by the half-lattice index of the output site; dot_out (nullable,
-// one RHS tile only) receives <dotX_r, Y_r> per RHS, taken in the epilogue
+// one RHS tile only) receives <dotX_r, Y_r> per RHS, taken in the epilogue;
+// hop_imaged: the scratch's first half already holds the image of Xhop (mode
+// bit 0 clear), so no image pass runs for it
 mglma_status coarse_tc_eo_launch(mglma_ctx ctx, const mglma_coarse_s* C, const float2* Xhop, const float2* Xself,
                                  float2* Y, int nrhs, int mode, int par, int d_lo, int d_hi, const uint16_t* Aself,
                                  float sign, void* scratch, cudaStream_t s, const void* self_image = nullptr,
                                  const uint16_t* Ahop = nullptr, const float2* dotX = nullptr,
-                                 double2* dot_out = nullptr);
+                                 double2* dot_out = nullptr, bool hop_imaged = false);
+// RHS tile width of the tensor-core coarse launches for nrhs RHS
+int coarse_tc_nt(mglma_ctx ctx, const mglma_coarse_s* C, int nrhs);
+// the B-operand image (no gamma5hat) of a FP32 half-lattice field X into
+// image (the first half of the even-odd scratch), as the Schur apply's first
+// launch would write it
+mglma_status coarse_x_image_half(mglma_ctx ctx, const mglma_coarse_s* C, const void* X, int nrhs, void* image,
+                                 cudaStream_t s);
+// minres_update on FP32 half-lattice fields that also writes the image of
+// the scaled z (the next Lanczos vector) into image, as coarse_x_image_half
+mglma_status minres_update_image(mglma_ctx ctx, const mglma_coarse_s* C, const double* cf, int stride, const Vec& v,
+                                 const Vec& w1, const Vec& w2, Vec& wn, Vec& x, Vec& z, void* image, cudaStream_t s);
 size_t coarse_tc_half_image_bytes(const mglma_coarse_s* C, int nrhs);
 mglma_status coarse_tc_image_blocks(mglma_ctx ctx, const double2* A64, int64_t V1, int n2, int nslots,
                                     uint16_t** img, cudaStream_t s);
