@@ -386,6 +386,8 @@ void mglma_gauge_free(mglma_gauge G) {
   cudaFree(G->C64);
   cudaFree(G->C32);
   cudaFree(G->Cinv64);
+  cudaFree(G->Udf);
+  cudaFree(G->Cdf);
   delete G;
 }
 

@@ -222,22 +222,34 @@ __global__ void __launch_bounds__(128, dslash_min_ctas<R, NR, RW>()) dslash_kern
 #pragma unroll
     for (int r = 0; r < NR; ++r)
       if (r0 + r < a.nrhs && valid) {
-        if (a.g5out) {
+        if constexpr (std::is_same<SO, ResidF64>::value) {
+          const double sc = a.scale[r0 + r];
+          double2* p = reinterpret_cast<double2*>(out) + (size_t)(r0 + r) * 12 * V + site;
 #pragma unroll
-          for (int k = 6; k < 12; ++k) acc[r][k] = -acc[r][k];
-        }
-        if (a.bsub) {
-          Cx<R> bv[12];
-          IO<R>::load(a.bsub, V, r0 + r, site, bv);
+          for (int k = 0; k < 12; ++k) {
+            double2 v = p[k * V];
+            v.x -= sc * dfl::to_double(acc[r][k].re);
+            v.y -= sc * dfl::to_double(acc[r][k].im);
+            p[k * V] = v;
+          }
+        } else {
+          if (a.g5out) {
 #pragma unroll
-          for (int k = 0; k < 12; ++k) acc[r][k] = bv[k] - acc[r][k];
-        }
-        if constexpr (BF) {
-          // the dots below see the values as stored
+            for (int k = 6; k < 12; ++k) acc[r][k] = -acc[r][k];
+          }
+          if (a.bsub) {
+            Cx<R> bv[12];
+            IO<R>::load(a.bsub, V, r0 + r, site, bv);
 #pragma unroll
-          for (int k = 0; k < 12; ++k) acc[r][k] = bf16_unpack(bf16_pack(acc[r][k]));
+            for (int k = 0; k < 12; ++k) acc[r][k] = bv[k] - acc[r][k];
+          }
+          if constexpr (BF) {
+            // the dots below see the values as stored
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[r][k] = bf16_unpack(bf16_pack(acc[r][k]));
+          }
+          SIO<SO>::store(out, V, r0 + r, site, acc[r]);
         }
-        SIO<SO>::store(out, V, r0 + r, site, acc[r]);
       }
     if constexpr (RED) {
       if (valid) {
@@ -975,6 +987,52 @@ mglma_status dslash(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& in, Spi
     launch_dslash32(tuned(ctx, TUNE_DSLASH32_NR, in.nrhs, G->g.V, dslash32_default_tile(in.nrhs)), in, out, G->U32, G->C32,
                     a, dagger, s);
   }
+  MG_LAUNCH_CHECK();
+  return MGLMA_OK;
+}
+
+// FP64 values split into double-float pairs, elementwise (two per float4)
+__global__ void split_df_kernel(const double2* __restrict__ in, float4* __restrict__ out, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = in[i];
+  const DF a(v.x), b(v.y);
+  out[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
+static mglma_status gauge_df_ready(mglma_gauge_s* G, cudaStream_t s) {
+  if (G->Udf && G->Cdf) return MGLMA_OK;
+  const size_t V = (size_t)G->g.V, nu = 36 * V, nc = 36 * V;
+  if (!G->Udf) {
+    MG_CUDA(cudaMalloc(&G->Udf, nu * sizeof(float4)));
+    split_df_kernel<<<(unsigned)((nu + 255) / 256), 256, 0, s>>>(G->U64, G->Udf, nu);
+    MG_LAUNCH_CHECK();
+  }
+  if (!G->Cdf) {
+    MG_CUDA(cudaMalloc(&G->Cdf, nc * sizeof(float4)));
+    split_df_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(G->C64, G->Cdf, nc);
+    MG_LAUNCH_CHECK();
+  }
+  return MGLMA_OK;
+}
+
+mglma_status dslash_resid_df(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& e, Spinor& r, const double* scale,
+                             cudaStream_t s) {
+  if (e.prec != MGLMA_FP32 || r.prec != MGLMA_FP64 || e.V != G->g.V || r.V != G->g.V || e.nrhs != r.nrhs || !scale)
+    return fail(MGLMA_ERR_INVALID, "dslash_resid_df: FP32 e, FP64 r of the gauge field's volume and a scale needed");
+  if (e.nrhs == 0) return MGLMA_OK;
+  MG_CHECK(gauge_df_ready(const_cast<mglma_gauge_s*>(G), s));
+  DslashArgs a;
+  a.q = make_latidx(G->g.L);
+  a.bc = (double)G->g.t_bc;
+  a.nrhs = e.nrhs;
+  a.g5out = 0;
+  a.scale = scale;
+  // links and clover as FP64-sized double-float words, e in FP32, r read and written in FP64
+  ProfScope ps(ctx, K_DSLASH64, s, (double)e.V * (1152.0 + 480.0 * e.nrhs), dslash_flops(e.V, e.nrhs));
+  const size_t ctas = (size_t)((e.V + 127) / 128) * e.nrhs;
+  dslash_kernel<DF, 1, false, 1, false, false, SpinF32Df, ResidF64>
+      <<<(unsigned)ctas, 128, 0, s>>>(e.p, r.p, G->Udf, G->Cdf, a);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }

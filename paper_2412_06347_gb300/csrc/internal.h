@@ -136,6 +136,8 @@ struct mglma_gauge_s {
   double2* C64 = nullptr;  // [2][18][V]
   float4* C32 = nullptr;   // [2][9][V]
   double2* Cinv64 = nullptr;  // [2][18][V] inverse clover blocks (even-odd, formed on first use)
+  float4* Udf = nullptr;      // [4][9][V] U64 split into double-float (re.hi, re.lo, im.hi, im.lo), first use
+  float4* Cdf = nullptr;      // [2][18][V] C64 split likewise (two reals per float4), first use
   int slabs_loaded = 0;   // time slices received
   std::vector<char> slab_seen;
   bool ready = false;
@@ -290,6 +292,11 @@ mglma_status dslash_mr_step(mglma_ctx, const mglma_gauge_s* G, const Spinor& t, 
                             const double2* alpha, double* part, double* nrm, double2* dot, cudaStream_t s);
 // out = b - D in (FP32; the residual of the preconditioner's coarse correction
 // formed in the stencil's epilogue); out must not alias in or b
+// r -= scale[rhs] D e per RHS: e FP32, r FP64, D applied in double-float
+// arithmetic (about 2^-47 relative to the terms) on the FP64 links and clover
+// split once into double-float words (kept on the gauge handle)
+mglma_status dslash_resid_df(mglma_ctx ctx, const mglma_gauge_s* G, const Spinor& e, Spinor& r, const double* scale,
+                             cudaStream_t s);
 mglma_status dslash_resid(mglma_ctx, const mglma_gauge_s* G, const Spinor& in, const Spinor& b, Spinor& out,
                           cudaStream_t s);
 // FP32 t = D in with, per RHS, nrm = |t|^2 and dot = <t, in> = sum conj(t) in

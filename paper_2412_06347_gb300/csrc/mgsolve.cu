@@ -940,11 +940,9 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
   const int64_t V = b.V;
   out.assign(n, RhsStat());
   FreeList fl(ctx, s);
-  Spinor r, w, r32, e32;
+  Spinor r, r32, e32;
   MG_CHECK(alloc_spinor(ctx, r, MGLMA_FP64, n, V, s));
   fl.add(r.p);
-  MG_CHECK(alloc_spinor(ctx, w, MGLMA_FP64, n, V, s));
-  fl.add(w.p);
   MG_CHECK(alloc_spinor(ctx, r32, MGLMA_FP32, n, V, s));
   fl.add(r32.p);
   MG_CHECK(alloc_spinor(ctx, e32, MGLMA_FP32, n, V, s));
@@ -955,7 +953,7 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
   double* rr = sc.d + n;
   double* rn = sc.d + 2 * n;
   double* rinv = sc.d + 3 * n;
-  Vec vb = as_vec(b), vx = as_vec(x), vr = as_vec(r), vw = as_vec(w);
+  Vec vb = as_vec(b), vx = as_vec(x), vr = as_vec(r);
   MG_CHECK(norm2(ctx, vb, bb, s));
   std::vector<double> hbb, hrr;
   MG_CHECK(read_doubles(bb, hbb, n, s));
@@ -1030,11 +1028,11 @@ mglma_status mg_solve(mglma_ctx ctx, const mglma_gauge_s* G, const mglma_coarse_
       out[i].iterations += gr.per_rhs[i];
       if (!out[i].converged) out[i].outer++;
     }
-    // x += |r| e ; r = b - D x (FP64)
+    // x += |r| e ; r -= |r| D e with D e taken in double-float on the exact
+    // FP32 values of e, so r tracks b - D x to about 1e-14 |b| (the FP64
+    // products |r| e that enter x are rounded once, below that)
     MG_CHECK(convert_spinor(ctx, e32, x, s, rn, true));
-    MG_CHECK(dslash(ctx, G, x, w, false, false, s));
-    MG_CHECK(copy_vec(ctx, vb, vr, s));
-    MG_CHECK(axpby(ctx, nullptr, CM1, vw, nullptr, C1, vr, s));
+    MG_CHECK(dslash_resid_df(ctx, G, e32, r, rn, s));
   }
   MG_CHECK(K.cs.take_captured_iters(&K.coarse_iters));
   for (int i = 0; i < n; ++i) out[i].coarse_iterations = K.coarse_iters;

@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 
 #include "cplx.cuh"
+#include "df.cuh"
 #include "internal.h"
 #include "lattice.cuh"
 
@@ -114,6 +115,22 @@ struct SIO<SpinBf16> {
   }
 };
 
+// FP32 spinor storage computed on in double-float (each value exact)
+struct SpinF32Df {};
+template <>
+struct SIO<SpinF32Df> {
+  using R = DF;
+  __device__ __forceinline__ static void load(const void* b, int64_t V, int rhs, int64_t site, Cx<DF> s[12]) {
+    Cx<float> f[12];
+    IO<float>::load(b, V, rhs, site, f);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s[k] = cx(DF(f[k].re, 0.f), DF(f[k].im, 0.f));
+  }
+};
+// output of the double-float residual update: out (FP64 spinors) -=
+// scale[rhs] op(in), op(in) rounded once to FP64 per component
+struct ResidF64 {};
+
 // ------------------------------------------------------------ links
 template <typename R>
 struct Link;
@@ -144,6 +161,20 @@ struct Link<double> {  // full 18 reals
     for (int k = 0; k < 9; ++k) {
       double2 v = __ldg(p + k * V);
       m.e[k / 3][k % 3] = cx(v.x, v.y);
+    }
+  }
+};
+
+// double-float links: the FP64 links split once ([mu][9][V] float4 =
+// (re.hi, re.lo, im.hi, im.lo))
+template <>
+struct Link<DF> {
+  __device__ __forceinline__ static void load(const void* U, int64_t V, int mu, int64_t site, M3<DF>& m) {
+    const float4* p = reinterpret_cast<const float4*>(U) + (size_t)mu * 9 * V + site;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float4 v = __ldg(p + k * V);
+      m.e[k / 3][k % 3] = cx(DF(v.x, v.y), DF(v.z, v.w));
     }
   }
 };
@@ -181,6 +212,21 @@ struct Clover<double> {
       double2 v = __ldg(p + j * V);
       c[2 * j] = v.x;
       c[2 * j + 1] = v.y;
+    }
+  }
+};
+
+// double-float clover: the FP64 packed blocks split once ([chi][18][V]
+// float4 = two reals as (hi, lo) pairs)
+template <>
+struct Clover<DF> {
+  __device__ __forceinline__ static void load(const void* C, int64_t V, int chi, int64_t site, DF c[36]) {
+    const float4* p = reinterpret_cast<const float4*>(C) + (size_t)chi * 18 * V + site;
+#pragma unroll
+    for (int j = 0; j < 18; ++j) {
+      const float4 v = __ldg(p + j * V);
+      c[2 * j] = DF(v.x, v.y);
+      c[2 * j + 1] = DF(v.z, v.w);
     }
   }
 };
@@ -317,6 +363,7 @@ struct DslashArgs {
   int nrhs;
   int g5out;
   const void* bsub = nullptr;  // dslash_kernel: when set, out = bsub - op(in) (same layout as out)
+  const double* scale = nullptr;  // ResidF64 output: per-RHS factor of op(in)
 };
 
 }  // namespace mglma
