@@ -302,7 +302,10 @@ mglma_status mglma_solve_batch(mglma_ctx ctx, mglma_gauge G, mglma_coarse C, con
   // (a batch must not shrink because the library's cache grew).
   int cap = prm->max_batch > 0 ? prm->max_batch : 64;
   if (prm->max_batch <= 0) {
-    const size_t room = device_room(ctx, s);
+    size_t room = device_room(ctx, s);
+    // the multigrid solve's double-float links and clover (2 x 36 float4 per
+    // site), made on its first use, come out of the same room
+    if (prm->method == MGLMA_SOLVER_MG && !(G->Udf && G->Cdf)) room -= std::min(room, (size_t)V * 1152);
     const size_t per_site = prm->method != MGLMA_SOLVER_MG ? 6 * 192 : 4 * 192 + (size_t)(7 + 2 * prm->gcr_m) * 96;
     const size_t per_rhs = per_site * (size_t)V;
     cap = (int)std::max<size_t>(1, std::min<size_t>(64, (size_t)(0.7 * (double)room) / per_rhs));
