@@ -708,7 +708,7 @@ mglma_status axpy2_norm(mglma_ctx ctx, const double2* a, const Vec& p, Vec& x, c
   return MGLMA_OK;
 }
 
-mglma_status lanczos_norm(mglma_ctx ctx, const double2* dot, const double* beta, const int* active, const Vec& v,
+mglma_status lanczos_norm(mglma_ctx ctx, const double2* dot, const double* beta, int* active, const Vec& v,
                           const Vec& u, Vec& z, double* zz, cudaStream_t s, double* st, double tol, int cap) {
   if (v.prec != z.prec || u.prec != z.prec || v.n != z.n || u.n != z.n)
     return fail(MGLMA_ERR_INVALID, "lanczos_norm: mismatch");
@@ -722,11 +722,10 @@ mglma_status lanczos_norm(mglma_ctx ctx, const double2* dot, const double* beta,
   dim3 g(nb, z.nrhs, 1);
   if (z.prec == MGLMA_FP64)
     lanczos_norm_kernel<double><<<g, RT, 0, s>>>((const double2*)v.p, (const double2*)u.p, (double2*)z.p, dot, beta,
-                                                 active, m, part, count, zz, st, tol, cap,
-                                                 const_cast<int*>(active));
+                                                 active, m, part, count, zz, st, tol, cap, active);
   else
     lanczos_norm_kernel<float><<<g, RT, 0, s>>>((const float4*)v.p, (const float4*)u.p, (float4*)z.p, dot, beta,
-                                                active, m, part, count, zz, st, tol, cap, const_cast<int*>(active));
+                                                active, m, part, count, zz, st, tol, cap, active);
   MG_LAUNCH_CHECK();
   return MGLMA_OK;
 }

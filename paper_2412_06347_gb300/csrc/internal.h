@@ -371,7 +371,7 @@ mglma_status axpy2_norm(mglma_ctx, const double2* a, const Vec& p, Vec& x, const
 // are left alone, zz = 0)
 // st (nullable): also runs the MINRES scalar step of each RHS (minres.cuh)
 // in the kernel's last block; zz must then be st's MR_BN2 slot
-mglma_status lanczos_norm(mglma_ctx, const double2* dot, const double* beta, const int* active, const Vec& v,
+mglma_status lanczos_norm(mglma_ctx, const double2* dot, const double* beta, int* active, const Vec& v,
                           const Vec& u, Vec& z, double* zz, cudaStream_t s, double* st = nullptr, double tol = 0,
                           int cap = 0);
 // MINRES: wn = c0 v + c1 w1 + c2 w2 ; x += c3 wn ; z *= c4 for RHS with c5 != 0,
