@@ -1,7 +1,7 @@
 // Block restriction R0 (Eq. res_mg) and prolongation T0 (Eq. pro_mg) on the
 // 5th-generation tensor cores (tcgen05, sm_103a) for FP32 fields at many RHS:
-// BF16 operands, FP32 accumulation in TMEM.  R0 first, T0 at the end of the
-// file.
+// BF16 operands, FP32 accumulation in TMEM.  R0 first, T0 after it, the host
+// side at the end of the file.
 //
 // Per block y and chirality alpha the restriction is one complex product
 //     c[j][r] = sum_{k in B_y, q < 6} conj(phi_{y j}(k)_q) psi_r(k)_{6 alpha + q}
@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(RT_THREADS, 2) restrict_tc_kernel(RtRun run, B
 // half) 2 + h for q = 2 cq + h and sites 128 half .. 128 half + 127, so the
 // two components of one FP32 float4 chunk come out in consecutive tiles.  The
 // basis is imaged per tile ([chunk of 8 (p, j)][row group][8 rows][8
-// values]); the coefficients of a work unit are imaged by the producer warp.
+// values]); the coefficients of a work unit are imaged in shared memory by a
+// warp of their own.
 constexpr int PT_THREADS = 224;  // warps 0-3 epilogue (TMEM lanes 0-127), 4 basis copies, 5 MMA, 6 coefficients
 constexpr int PT_MAX_STAGES = 8;
 constexpr int PT_PAIRS = 2;      // accumulator pairs (tiles h = 0, 1 of one float4 chunk), 64 columns each
