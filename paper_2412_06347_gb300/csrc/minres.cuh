@@ -5,6 +5,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 namespace mglma {
 
 enum {
@@ -24,8 +26,8 @@ enum {
 // alpha = Re dot[r] = <v_k, Qhat v_k>, |z|^2 in slot MR_BN2: the rotation of
 // iteration k, the update coefficients (MR_CF .. MR_CF + 5; MR_CF + 5 = 1
 // when the update applies) and the new activity of RHS r
-__device__ __forceinline__ void minres_scalar_step(double* st, const double2* dot, int* active, double tol, int cap,
-                                                   int r) {
+__host__ __device__ __forceinline__ void minres_scalar_step(double* st, const double2* dot, int* active, double tol,
+                                                            int cap, int r) {
   auto S = [&](int j) -> double& { return st[(size_t)j * cap + r]; };
   S(MR_CF + 5) = 0;
   if (!active[r]) return;
